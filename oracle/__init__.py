@@ -1,0 +1,180 @@
+"""Plain FP64 CPU oracle for the cuSten hot path (arXiv:1902.09931).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this package.  It wraps ``cs_oracle.c`` (plain C loops over the
+paper's definitions, binary64) through ctypes and builds it with gcc on first use.  It shares
+no code with the GPU library in ``paper_1902_09931_gb300``.
+
+What each routine computes, with the passage it follows:
+
+* ``stencil2d``        -- weighted stencil, x / y / xy, periodic or non-periodic (Sec. 2, 3, 5.2)
+* ``stencil2d_fn``     -- user-function stencils of Sec. 4.2 and Sec. 5.2
+* ``stencil1d_batch``  -- the x stencil on each line of a ragged batch (Abstract, Sec. 5.4)
+* ``cyclic_penta_solve`` -- (I + a circ(1,-4,6,-4,1)) x = b by banded LU + Woodbury (Sec. 5.1)
+* ``ch_rhs``, ``ch_step``, ``ch_run`` -- the Cahn-Hilliard ADI scheme, Eq. (ch_adi) (Sec. 5.1)
+* ``ch_mass``, ``ch_energy`` -- the integral of C and the free energy F[C] of Eq. (1)
+
+Fields are 2D numpy arrays of shape (ny, nx), row-major, x fastest.  FP32 inputs are widened to
+FP64 before the oracle sees them, so the oracle works on exactly the values the GPU read.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cs_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+
+DIR_X, DIR_Y, DIR_XY = 0, 1, 2
+BC_NONPERIODIC, BC_PERIODIC = 0, 1
+FN_CENTRAL_D2X, FN_CH_NONLIN_LAP, FN_CUBIC_MINUS_LAP = 1, 2, 3
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compiles cs_oracle.c into a shared library (plain -O2, no fast-math) and returns its path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
+                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i64, i32, dbl, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+            lib.orc_stencil2d.argtypes = [i64, i64, i32, i32, i32, i32, i32, i32, vp, vp, vp]
+            lib.orc_stencil2d_fn.argtypes = [i64, i64, i32, i32, vp, i32, vp, vp]
+            lib.orc_stencil1d_batch.argtypes = [i64, vp, i32, i32, i32, vp, vp, vp]
+            lib.orc_cyclic_penta_solve.argtypes = [i64, dbl, i64, vp, vp]
+            lib.orc_ch_rhs.argtypes = [i64, dbl, dbl, dbl, vp, vp, vp]
+            lib.orc_ch_step.argtypes = [i64, dbl, dbl, dbl, vp, vp, vp]
+            lib.orc_ch_run.argtypes = [i64, dbl, dbl, dbl, i64, vp, vp, vp, vp]
+            lib.orc_ch_mass.argtypes = [i64, vp]
+            lib.orc_ch_mass.restype = dbl
+            lib.orc_ch_energy.argtypes = [i64, dbl, vp]
+            lib.orc_ch_energy.restype = dbl
+            _lib = lib
+    return _lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a), dtype=np.float64)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise ValueError(f"oracle {what} rejected its arguments (code {rc})")
+
+
+def stencil2d(field, weights, direction: int, bc: int, left: int = 0, right: int = 0,
+              top: int = 0, bottom: int = 0, out=None) -> np.ndarray:
+    """Weighted stencil of Sec. 3.  ``out`` (if given) supplies the untouched cells for np."""
+    f = _f64(field)
+    ny, nx = f.shape
+    w = _f64(weights).ravel()
+    if w.size != (left + right + 1) * (top + bottom + 1):
+        raise ValueError("weight count must be (left+right+1)*(top+bottom+1)")
+    o = np.zeros_like(f) if out is None else _f64(out).copy()
+    _check(_load().orc_stencil2d(nx, ny, direction, bc, left, right, top, bottom,
+                                 _ptr(w), _ptr(f), _ptr(o)), "stencil2d")
+    return o
+
+
+def stencil2d_fn(field, fn: int, coe, bc: int, out=None) -> np.ndarray:
+    """User-function stencil of Sec. 4.2 / Sec. 5.2 (``fn`` is one of the FN_* codes)."""
+    f = _f64(field)
+    ny, nx = f.shape
+    c = _f64(coe).ravel()
+    o = np.zeros_like(f) if out is None else _f64(out).copy()
+    _check(_load().orc_stencil2d_fn(nx, ny, bc, fn, _ptr(c), c.size, _ptr(f), _ptr(o)),
+           "stencil2d_fn")
+    return o
+
+
+def stencil1d_batch(packed, offsets, weights, bc: int, left: int, right: int,
+                    out=None) -> np.ndarray:
+    """The x stencil on every line [offsets[m], offsets[m+1]) of a packed ragged buffer."""
+    f = _f64(packed).ravel()
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    w = _f64(weights).ravel()
+    if w.size != left + right + 1:
+        raise ValueError("weight count must be left+right+1")
+    o = np.zeros_like(f) if out is None else _f64(out).ravel().copy()
+    _check(_load().orc_stencil1d_batch(off.size - 1, _ptr(off), bc, left, right, _ptr(w),
+                                       _ptr(f), _ptr(o)), "stencil1d_batch")
+    return o
+
+
+def cyclic_penta_solve(b, a: float) -> np.ndarray:
+    """Solves (I + a circ(1,-4,6,-4,1)) x = b for each row of ``b`` (shape (n,) or (m, n))."""
+    bb = _f64(b)
+    n = bb.shape[-1]
+    m = bb.size // n
+    x = np.empty_like(bb)
+    _check(_load().orc_cyclic_penta_solve(n, float(a), m, _ptr(bb), _ptr(x)), "cyclic_penta_solve")
+    return x
+
+
+def ch_coefficient_a(n: int, D: float, gamma: float, dt: float) -> float:
+    """a = (2/3) D gamma dt / h^4 of L = I + a d^4 (Sec. 5.1), h = 2 pi / n."""
+    h = 2.0 * np.pi / n
+    return (2.0 / 3.0) * D * gamma * dt / h ** 4
+
+
+def ch_rhs(c_prev, c_cur, D: float, gamma: float, dt: float) -> np.ndarray:
+    p, c = _f64(c_prev), _f64(c_cur)
+    n = c.shape[0]
+    r = np.empty_like(c)
+    _check(_load().orc_ch_rhs(n, D, gamma, dt, _ptr(p), _ptr(c), _ptr(r)), "ch_rhs")
+    return r
+
+
+def ch_step(c_prev, c_cur, D: float, gamma: float, dt: float) -> np.ndarray:
+    """One ADI step, Eq. (ch_adi): returns C^{n+1} from C^{n-1}, C^n."""
+    p, c = _f64(c_prev), _f64(c_cur)
+    n = c.shape[0]
+    if c.shape != (n, n) or p.shape != (n, n):
+        raise ValueError("Cahn-Hilliard fields must be square n x n")
+    o = np.empty_like(c)
+    _check(_load().orc_ch_step(n, D, gamma, dt, _ptr(p), _ptr(c), _ptr(o)), "ch_step")
+    return o
+
+
+def ch_run(c0, D: float, gamma: float, dt: float, nsteps: int):
+    """The time loop of Sec. 5.1 (C^{-1} := C^0).  Returns (C_final, mass[nsteps], energy[nsteps])."""
+    c = _f64(c0)
+    n = c.shape[0]
+    out = np.empty_like(c)
+    mass = np.empty(nsteps)
+    energy = np.empty(nsteps)
+    _check(_load().orc_ch_run(n, D, gamma, dt, nsteps, _ptr(c), _ptr(out), _ptr(mass),
+                              _ptr(energy)), "ch_run")
+    return out, mass, energy
+
+
+def ch_mass(c) -> float:
+    c = _f64(c)
+    return _load().orc_ch_mass(c.shape[0], _ptr(c))
+
+
+def ch_energy(c, gamma: float) -> float:
+    c = _f64(c)
+    return _load().orc_ch_energy(c.shape[0], gamma, _ptr(c))
