@@ -1,0 +1,207 @@
+/*
+ * custen_gb.h -- C ABI of the GB300-native cuSten hot path (arXiv:1902.09931).
+ *
+ * The library applies finite-difference stencils to 2D grids and ragged batches of 1D lines
+ * (Sec. 2-4) and advances the periodic Cahn-Hilliard ADI scheme of Sec. 5.1.  Its verbs follow
+ * the paper's Create / Compute / Swap / Destroy API (Sec. 3), with the x / y / xy direction,
+ * the periodic / non-periodic boundary and the weights-or-function choice passed as values
+ * instead of being spelled into sixteen function names.
+ *
+ * Memory and streams.  Every field buffer is allocated and owned by the caller in device
+ * memory (PyTorch tensors, cudaMalloc, ...), must be contiguous, 16-byte aligned for the fast
+ * path (any alignment of the element type is accepted), and must stay alive until the plan
+ * that references it is destroyed.  Layout of a 2D field: row-major, x fastest, element (j, i)
+ * at index j * nx + i (the contiguous y-tiles of Sec. 2).  All compute calls are asynchronous
+ * with respect to the host and ordered on the CUDA stream passed in (NULL = legacy default
+ * stream), except where a call says it synchronises.  A plan may be used from one host thread
+ * at a time; different plans are independent.  Unlike the paper there is no HOST/DEVICE flag
+ * and no y-tile count: fields stay resident in device memory (Sec. 2's Unified-Memory
+ * streaming is not needed when the whole grid fits in HBM).  cs_compute_host() is the
+ * host-buffer form of Compute for callers whose data lives in host memory.
+ *
+ * Errors.  Every call returns CS_OK (0) or a negative cs_status.  Nothing aborts or exits.
+ * cs_last_error() returns a description of the last failure on the calling host thread.
+ * Invalid arguments leave every buffer untouched.  CS_ECUDA reports a CUDA runtime error
+ * (launch failure, invalid device pointer); the plan stays valid unless the error is sticky.
+ */
+#ifndef CUSTEN_GB_H
+#define CUSTEN_GB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cs_plan* cs_plan_t; /* opaque; created and freed by the library */
+
+typedef enum {
+  CS_OK = 0,
+  CS_EINVAL = -1,       /* invalid argument (sizes, extents, enum values, null pointers) */
+  CS_EALIAS = -2,       /* input and output overlap: Sec. 2 requires distinct buffers */
+  CS_ENOMEM = -3,       /* library-owned workspace could not be allocated */
+  CS_ECUDA = -4,        /* a CUDA runtime call failed */
+  CS_EUNSUPPORTED = -5, /* valid request that this build does not implement */
+  CS_ETIMEOUT = -6      /* a bounded device-side wait ran out (reserved) */
+} cs_status;
+
+/* Direction of a 2D stencil (Sec. 3: X, Y, XY).  XY stencils read corner halos. */
+typedef enum { CS_DIR_X = 0, CS_DIR_Y = 1, CS_DIR_XY = 2 } cs_dir;
+
+/* Boundary treatment (Sec. 3: p / np).  Periodic wraps indices modulo the grid size.
+ * Non-periodic leaves every output cell whose stencil would leave the grid untouched
+ * (cells with i < left, i >= nx - right, j < top, j >= ny - bottom; Sec. 3 and Sec. 4.1). */
+typedef enum { CS_BC_NONPERIODIC = 0, CS_BC_PERIODIC = 1 } cs_bc;
+
+/* Storage (and stencil arithmetic) type of the fields.  CS_F32 stencils compute in FP32;
+ * Cahn-Hilliard line solves and reductions always run in FP64. */
+typedef enum { CS_F64 = 0, CS_F32 = 1 } cs_dtype;
+
+/* The "Fun" variant (Sec. 4.2, Sec. 5.2).  The paper takes a user device-function pointer
+ * double f(double* data, double* coe, int loc); this library compiles a fixed set of
+ * functions into its kernels instead (so they inline into the tiled sweep) and takes their
+ * coefficients `coe` at create time.  Each function fixes its own footprint.
+ *   CS_FN_CENTRAL_D2X      Sec. 4.2 example: (u[i-1] - 2u[i] + u[i+1]) * coe[0], X, 1 left/right
+ *   CS_FN_CH_NONLIN_LAP    Sec. 5.2: 5-point Laplacian of N = u^3 - u, coe[0] = 1/h^2, XY, r = 1
+ *   CS_FN_CUBIC_MINUS_LAP  u^3 - u - (5-point Laplacian of u), coe[0] = 1/h^2, XY, r = 1 */
+typedef enum {
+  CS_FN_NONE = 0,
+  CS_FN_CENTRAL_D2X = 1,
+  CS_FN_CH_NONLIN_LAP = 2,
+  CS_FN_CUBIC_MINUS_LAP = 3
+} cs_fn;
+
+/* Stencil description (Sec. 3, Sec. 4.1).  Enumerations are carried as int32_t.
+ *   nx, ny     grid size (ny = 1 allowed); ignored (nx) by cs_plan_create_1d_batch
+ *   dir        cs_dir; X requires top = bottom = 0, Y requires left = right = 0
+ *   bc         cs_bc
+ *   dtype      cs_dtype of the in / out buffers
+ *   left, right, top, bottom
+ *              stencil points on each side of (i, j) (numStenLeft / numStenRight and the y
+ *              analogues of Sec. 4.1); any non-negative values up to CS_MAX_EXTENT, asymmetric
+ *              allowed; periodic grids smaller than the stencil wrap more than once.
+ *   weights    host array of (left+right+1)*(top+bottom+1) values for fn == CS_FN_NONE,
+ *              numbered from the top-left of the stencil box, left to right in i, then row by
+ *              row in j (Sec. 5.2); the first row is j - top.  Copied at create time.
+ *   fn, coe, num_coe
+ *              user-function variant; coe (host, num_coe values) is copied at create time.
+ *              When fn != CS_FN_NONE, weights must be NULL and the extents must equal the
+ *              function's footprint. */
+#define CS_MAX_EXTENT 16
+typedef struct {
+  int64_t nx, ny;
+  int32_t dir, bc, dtype;
+  int32_t left, right, top, bottom;
+  const double* weights;
+  int32_t fn;
+  int32_t num_coe;
+  const double* coe;
+} cs_stencil_desc;
+
+/* Create (Sec. 3): validates the description, copies weights / coefficients, picks the kernel
+ * variant and tile shape, and binds the caller's device buffers d_in (read) and d_out
+ * (written).  d_in and d_out must not overlap (CS_EALIAS): blocks read overlapping halos, so
+ * outputs cannot be written in place (Sec. 2). */
+int cs_plan_create_2d(cs_plan_t* plan, const cs_stencil_desc* desc, const void* d_in, void* d_out);
+
+/* Create for a ragged batch of 1D lines (Abstract; Sec. 5.4's batched 1D problems): line m
+ * occupies elements [offsets[m], offsets[m+1]) of the packed buffers.  desc->dir must be
+ * CS_DIR_X (top = bottom = 0); a periodic stencil wraps at each line's own length.
+ *   d_offsets  device array of num_lines + 1 int64 values, non-decreasing, offsets[0] = 0,
+ *              offsets[num_lines] = total_len.  Read at create time (the library builds its
+ *              load-balancing table from it) and by every compute; must stay alive.
+ *   total_len  number of packed elements. */
+int cs_plan_create_1d_batch(cs_plan_t* plan, const cs_stencil_desc* desc, int64_t num_lines,
+                            const int64_t* d_offsets, int64_t total_len, const void* d_in,
+                            void* d_out);
+
+/* Compute (Sec. 3): applies the stencil, d_in -> d_out, stream-ordered and asynchronous. */
+int cs_compute(cs_plan_t plan, void* cuda_stream);
+
+/* Compute with host buffers (Sec. 3's HOST flag): copies h_in (host, the full input field)
+ * into the plan's device input, computes, and copies the device output back into h_out.
+ * Either pointer may be NULL to skip that copy.  Pinned host memory gives overlap-free full
+ * bandwidth; pageable memory works but is slower.  Synchronises the stream before returning
+ * when h_out is non-NULL. */
+int cs_compute_host(cs_plan_t plan, const void* h_in, void* h_out, void* cuda_stream);
+
+/* Swap (Sec. 3): exchanges the bound input and output buffers so the next Compute reads what
+ * the last one wrote. */
+int cs_swap(cs_plan_t plan);
+
+/* Rebinds the device buffers of a stencil plan without re-planning (same sizes and dtype). */
+int cs_set_buffers(cs_plan_t plan, const void* d_in, void* d_out);
+
+/* Captures the plan's compute into a CUDA graph on first use and replays it afterwards
+ * (enable = 1), or launches kernels directly (enable = 0, the default).  The graph is rebuilt
+ * automatically after cs_swap / cs_set_buffers. */
+int cs_plan_use_graph(cs_plan_t plan, int enable);
+
+/* Times the candidate tile / launch shapes of the plan's kernel on its own buffers (it
+ * overwrites d_out), keeps the fastest, and records it in the process-wide tuning table.  The
+ * table is keyed by (kernel, dtype, shape class, SM count) and can be saved to / loaded from a
+ * JSON file with cs_tune_save / cs_tune_load.  Synchronises the stream. */
+int cs_autotune(cs_plan_t plan, void* cuda_stream);
+int cs_tune_save(const char* path);
+int cs_tune_load(const char* path);
+
+/* Destroy (Sec. 3): frees the plan and the workspace the library allocated.  Never frees the
+ * caller's buffers.  Destroying NULL is a no-op. */
+int cs_destroy(cs_plan_t plan);
+
+/* ---- Cahn-Hilliard ADI (Sec. 5.1), periodic on (0, 2 pi)^2 ---------------------------------
+ * One step:  Cbar = 2 C^n - C^{n-1};
+ *            RHS = -(2/3)(C^n - C^{n-1}) - (2/3) D gamma dt lap4(Cbar) + (2/3) D dt lap2(C^3 - C)^n;
+ *            L_x w = RHS;  L_y v = w;  C^{n+1} = Cbar + v;  L = I + (2/3) D gamma dt d^4
+ * with second-order central differences (Eq. 5), h = 2 pi / n, and cyclic pentadiagonal line
+ * solves (Sec. 5.1).  The printed right-hand side omits D gamma on the lap4 term; the library
+ * uses the coefficient of L_x, the reading under which steady states of the scheme are steady
+ * states of the equation.
+ *   n        grid points per side (n x n), a multiple of 64 in [64, 65536]
+ *   storage  CS_F64, or CS_F32 (fields stored in FP32, stencils in FP32, solves in FP64)
+ *   D, gamma mobility and interface parameter (Sec. 5.3: 1.0 and 0.01)
+ *   dt       time step (Sec. 5.3: 0.1 h) */
+typedef struct {
+  int64_t n;
+  int32_t storage;
+  int32_t reserved;
+  double D, gamma, dt;
+} cs_ch_desc;
+
+/* Binds three caller-owned n x n device fields.  On entry d_c_prev holds C^{n-1} and d_c_cur
+ * holds C^n; for the first step of a run pass the initial condition in both (Sec. 5.1 sets
+ * C^{-1} = C^0).  d_c_next is workspace that receives C^{n+1}.  The plan rotates the three
+ * buffers after every step; cs_ch_fields reports where C^{n-1} and C^n currently live. */
+int cs_ch_create(cs_plan_t* plan, const cs_ch_desc* desc, void* d_c_prev, void* d_c_cur,
+                 void* d_c_next);
+
+/* Advances nsteps ADI steps on the stream.  When h_mass / h_energy are non-NULL they receive,
+ * for each step s, the mass h^2 sum C and the free energy of Eq. (1) (forward differences,
+ * rectangle rule) of the field after step s, computed in FP64 on the device; the call then
+ * synchronises the stream.  With both NULL the call is asynchronous. */
+int cs_ch_step(cs_plan_t plan, int64_t nsteps, double* h_mass, double* h_energy, void* cuda_stream);
+
+/* Mass and free energy of the current field C^n (synchronises the stream). */
+int cs_ch_invariants(cs_plan_t plan, double* mass, double* energy, void* cuda_stream);
+
+/* Current device pointers of C^{n-1} and C^n (either output may be NULL), and the number of
+ * steps taken since create. */
+int cs_ch_fields(cs_plan_t plan, void** d_c_prev, void** d_c_cur, int64_t* steps_taken);
+
+/* ---- diagnostics --------------------------------------------------------------------------- */
+
+/* Description of the last error on the calling host thread ("" if none). */
+const char* cs_last_error(void);
+
+/* Number of kernels this library has launched in the process (graph replays count each
+ * kernel node).  Used to report launch counts in benchmarks. */
+int64_t cs_launch_count(void);
+
+/* Library version, e.g. "custen_gb 0.1.0 sm_103a". */
+const char* cs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CUSTEN_GB_H */

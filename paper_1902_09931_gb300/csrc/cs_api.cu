@@ -1,0 +1,374 @@
+// C ABI of libcusten_gb: plan life cycle (Create / Compute / Swap / Destroy, Sec. 3),
+// validation, error reporting, CUDA-graph replay and the autotuner driver.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "cs_internal.h"
+
+namespace cs {
+
+namespace {
+thread_local std::string t_last_error;
+std::atomic<int64_t> g_launches{0};
+}  // namespace
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_last_error = buf;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* what) {
+  return set_error(CS_ECUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int num_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (cached[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
+}  // namespace cs
+
+enum PlanKind { kStencil2D = 1, kBatch1D = 2, kCahnHilliard = 3 };
+
+struct cs_plan {
+  int kind;
+  const void* d_in;
+  void* d_out;
+  size_t elem_bytes;
+  int64_t elems;  // elements in one field / packed buffer
+  cs::Stencil2DConfig s2;
+  cs::Batch1DConfig b1;
+  cs::CHPlan* ch;
+  // graph replay
+  int use_graph;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  int graph_kernels;
+};
+
+namespace {
+
+using namespace cs;
+
+bool overlaps(const void* a, const void* b, size_t bytes) {
+  const char* pa = static_cast<const char*>(a);
+  const char* pb = static_cast<const char*>(b);
+  return pa < pb + bytes && pb < pa + bytes;
+}
+
+void drop_graph(cs_plan* p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->exec = nullptr;
+  p->graph = nullptr;
+}
+
+int launch_direct(cs_plan* p, cudaStream_t s) {
+  switch (p->kind) {
+    case kStencil2D: return stencil2d_launch(&p->s2, p->d_in, p->d_out, s);
+    case kBatch1D: return batch1d_launch(&p->b1, p->d_in, p->d_out, s);
+    default: return set_error(CS_EINVAL, "cs_compute: not a stencil plan");
+  }
+}
+
+int validate_desc_common(const cs_stencil_desc* d) {
+  if (!d) return set_error(CS_EINVAL, "null stencil description");
+  if (d->dtype != CS_F64 && d->dtype != CS_F32) return set_error(CS_EINVAL, "dtype must be CS_F64 or CS_F32");
+  if (d->bc != CS_BC_PERIODIC && d->bc != CS_BC_NONPERIODIC) return set_error(CS_EINVAL, "bc must be periodic or non-periodic");
+  if (d->dir != CS_DIR_X && d->dir != CS_DIR_Y && d->dir != CS_DIR_XY) return set_error(CS_EINVAL, "dir must be X, Y or XY");
+  if (d->left < 0 || d->right < 0 || d->top < 0 || d->bottom < 0 || d->left > CS_MAX_EXTENT ||
+      d->right > CS_MAX_EXTENT || d->top > CS_MAX_EXTENT || d->bottom > CS_MAX_EXTENT)
+    return set_error(CS_EINVAL, "stencil extents must be in [0, %d]", CS_MAX_EXTENT);
+  if (d->dir == CS_DIR_X && (d->top != 0 || d->bottom != 0))
+    return set_error(CS_EINVAL, "an X stencil has top = bottom = 0");
+  if (d->dir == CS_DIR_Y && (d->left != 0 || d->right != 0))
+    return set_error(CS_EINVAL, "a Y stencil has left = right = 0");
+  if (d->fn == CS_FN_NONE) {
+    if (!d->weights) return set_error(CS_EINVAL, "weights are required when fn = CS_FN_NONE");
+  } else {
+    int L, R, T, B, dir;
+    switch (d->fn) {
+      case CS_FN_CENTRAL_D2X: L = R = 1; T = B = 0; dir = CS_DIR_X; break;
+      case CS_FN_CH_NONLIN_LAP:
+      case CS_FN_CUBIC_MINUS_LAP: L = R = T = B = 1; dir = CS_DIR_XY; break;
+      default: return set_error(CS_EINVAL, "unknown user function %d", d->fn);
+    }
+    if (d->weights) return set_error(CS_EINVAL, "weights must be NULL for a user function");
+    if (d->left != L || d->right != R || d->top != T || d->bottom != B || d->dir != dir)
+      return set_error(CS_EINVAL, "extents / direction must match the function's footprint (%d,%d,%d,%d)", L, R, T, B);
+    if (!d->coe || d->num_coe < 1 || d->num_coe > 8)
+      return set_error(CS_EINVAL, "user function needs 1..8 coefficients");
+  }
+  return CS_OK;
+}
+
+cs_plan* new_plan(int kind) {
+  cs_plan* p = new (std::nothrow) cs_plan;
+  if (!p) return nullptr;
+  memset(p, 0, sizeof *p);
+  p->kind = kind;
+  return p;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cs_last_error(void) { return cs::t_last_error.c_str(); }
+int64_t cs_launch_count(void) { return cs::g_launches.load(); }
+const char* cs_version(void) { return "custen_gb 0.1.0 sm_103a"; }
+
+int cs_plan_create_2d(cs_plan_t* plan, const cs_stencil_desc* d, const void* d_in, void* d_out) {
+  if (!plan) return set_error(CS_EINVAL, "null plan pointer");
+  *plan = nullptr;
+  int rc = validate_desc_common(d);
+  if (rc != CS_OK) return rc;
+  if (d->nx < 0 || d->ny < 0) return set_error(CS_EINVAL, "nx, ny must be >= 0");
+  if (d->nx > (int64_t(1) << 40) / (d->ny > 0 ? d->ny : 1)) return set_error(CS_EINVAL, "grid too large");
+  const size_t eb = d->dtype == CS_F32 ? 4 : 8;
+  const int64_t elems = d->nx * d->ny;
+  if (elems > 0 && (!d_in || !d_out)) return set_error(CS_EINVAL, "null device buffer");
+  if (elems > 0 && (reinterpret_cast<uintptr_t>(d_in) % eb || reinterpret_cast<uintptr_t>(d_out) % eb))
+    return set_error(CS_EINVAL, "buffers must be aligned to the element size");
+  if (elems > 0 && overlaps(d_in, d_out, static_cast<size_t>(elems) * eb))
+    return set_error(CS_EALIAS, "input and output buffers overlap (Sec. 2: outputs go to a separate buffer)");
+  cs_plan* p = new_plan(kStencil2D);
+  if (!p) return set_error(CS_ENOMEM, "out of host memory");
+  Stencil2DConfig& c = p->s2;
+  c.nx = d->nx; c.ny = d->ny; c.dir = d->dir; c.bc = d->bc; c.dtype = d->dtype;
+  c.left = d->left; c.right = d->right; c.top = d->top; c.bottom = d->bottom;
+  c.fn = d->fn;
+  c.tile_rows = 64;
+  const int nw = (d->left + d->right + 1) * (d->top + d->bottom + 1);
+  if (d->fn == CS_FN_NONE) {
+    memcpy(c.weights, d->weights, sizeof(double) * nw);
+  } else {
+    c.num_coe = d->num_coe;
+    memcpy(c.coe, d->coe, sizeof(double) * d->num_coe);
+  }
+  rc = stencil2d_prepare(&c);
+  if (rc != CS_OK) { delete p; return rc; }
+  p->d_in = d_in; p->d_out = d_out; p->elem_bytes = eb; p->elems = elems;
+  *plan = p;
+  return CS_OK;
+}
+
+int cs_plan_create_1d_batch(cs_plan_t* plan, const cs_stencil_desc* d, int64_t num_lines,
+                            const int64_t* d_offsets, int64_t total_len, const void* d_in, void* d_out) {
+  if (!plan) return set_error(CS_EINVAL, "null plan pointer");
+  *plan = nullptr;
+  int rc = validate_desc_common(d);
+  if (rc != CS_OK) return rc;
+  if (d->dir != CS_DIR_X || d->fn != CS_FN_NONE)
+    return set_error(CS_EINVAL, "batched 1D lines take a weighted X stencil");
+  if (num_lines < 0 || total_len < 0 || total_len > (int64_t(1) << 40))
+    return set_error(CS_EINVAL, "num_lines, total_len out of range");
+  if (num_lines > 0x7fffffff) return set_error(CS_EINVAL, "at most 2^31-1 lines");
+  if (total_len > 0 && num_lines == 0) return set_error(CS_EINVAL, "elements without lines");
+  if (!d_offsets) return set_error(CS_EINVAL, "null offsets");
+  const size_t eb = d->dtype == CS_F32 ? 4 : 8;
+  if (total_len > 0 && (!d_in || !d_out)) return set_error(CS_EINVAL, "null device buffer");
+  if (total_len > 0 && (reinterpret_cast<uintptr_t>(d_in) % eb || reinterpret_cast<uintptr_t>(d_out) % eb))
+    return set_error(CS_EINVAL, "buffers must be aligned to the element size");
+  if (total_len > 0 && overlaps(d_in, d_out, static_cast<size_t>(total_len) * eb))
+    return set_error(CS_EALIAS, "input and output buffers overlap");
+  // offsets must be consistent: offsets[0] == 0, offsets[num_lines] == total_len, non-decreasing
+  {
+    std::vector<int64_t> h(static_cast<size_t>(num_lines) + 1);
+    CS_CUDA_TRY(cudaMemcpy(h.data(), d_offsets, h.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    if (h[0] != 0 || h[num_lines] != total_len)
+      return set_error(CS_EINVAL, "offsets must start at 0 and end at total_len");
+    for (int64_t m = 0; m < num_lines; ++m)
+      if (h[m + 1] < h[m]) return set_error(CS_EINVAL, "offsets must be non-decreasing (line %lld)", (long long)m);
+  }
+  cs_plan* p = new_plan(kBatch1D);
+  if (!p) return set_error(CS_ENOMEM, "out of host memory");
+  Batch1DConfig& c = p->b1;
+  c.num_lines = num_lines; c.total_len = total_len; c.bc = d->bc; c.dtype = d->dtype;
+  c.left = d->left; c.right = d->right;
+  memcpy(c.weights, d->weights, sizeof(double) * (d->left + d->right + 1));
+  c.d_offsets = d_offsets;
+  rc = batch1d_prepare(&c, nullptr);
+  if (rc == CS_OK) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) rc = cuda_error(e, "building the line table");
+  }
+  if (rc != CS_OK) { batch1d_release(&c); delete p; return rc; }
+  p->d_in = d_in; p->d_out = d_out; p->elem_bytes = eb; p->elems = total_len;
+  *plan = p;
+  return CS_OK;
+}
+
+int cs_compute(cs_plan_t p, void* stream) {
+  if (!p) return set_error(CS_EINVAL, "null plan");
+  if (p->kind == kCahnHilliard) return set_error(CS_EINVAL, "use cs_ch_step for a Cahn-Hilliard plan");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!p->use_graph) return launch_direct(p, s);
+  if (!p->exec) {
+    // capture on a private stream (the caller's may be the legacy stream, which cannot capture)
+    cudaStream_t cap;
+    CS_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    int64_t before = cs_launch_count();
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    int rc = e == cudaSuccess ? launch_direct(p, cap) : cuda_error(e, "cudaStreamBeginCapture");
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    if (rc != CS_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e2 != cudaSuccess) return cuda_error(e2, "cudaStreamEndCapture");
+    // capture does not launch: undo the count and remember how many kernels one replay runs
+    p->graph_kernels = static_cast<int>(cs_launch_count() - before);
+    count_launches(-p->graph_kernels);
+    cudaError_t e3 = cudaGraphInstantiate(&p->exec, g, 0);
+    if (e3 != cudaSuccess) { cudaGraphDestroy(g); p->exec = nullptr; return cuda_error(e3, "cudaGraphInstantiate"); }
+    p->graph = g;
+  }
+  CS_CUDA_TRY(cudaGraphLaunch(p->exec, s));
+  count_launches(p->graph_kernels);
+  return CS_OK;
+}
+
+int cs_compute_host(cs_plan_t p, const void* h_in, void* h_out, void* stream) {
+  if (!p) return set_error(CS_EINVAL, "null plan");
+  if (p->kind == kCahnHilliard) return set_error(CS_EINVAL, "use cs_ch_step for a Cahn-Hilliard plan");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = static_cast<size_t>(p->elems) * p->elem_bytes;
+  if (h_in && bytes) CS_CUDA_TRY(cudaMemcpyAsync(const_cast<void*>(p->d_in), h_in, bytes, cudaMemcpyHostToDevice, s));
+  int rc = cs_compute(p, stream);
+  if (rc != CS_OK) return rc;
+  if (h_out && bytes) {
+    CS_CUDA_TRY(cudaMemcpyAsync(h_out, p->d_out, bytes, cudaMemcpyDeviceToHost, s));
+    CS_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return CS_OK;
+}
+
+int cs_swap(cs_plan_t p) {
+  if (!p) return set_error(CS_EINVAL, "null plan");
+  if (p->kind == kCahnHilliard) return set_error(CS_EINVAL, "Cahn-Hilliard plans rotate their fields themselves");
+  const void* in = p->d_in;
+  p->d_in = p->d_out;
+  p->d_out = const_cast<void*>(in);
+  drop_graph(p);
+  return CS_OK;
+}
+
+int cs_set_buffers(cs_plan_t p, const void* d_in, void* d_out) {
+  if (!p) return set_error(CS_EINVAL, "null plan");
+  if (p->kind == kCahnHilliard) return set_error(CS_EINVAL, "not a stencil plan");
+  const size_t bytes = static_cast<size_t>(p->elems) * p->elem_bytes;
+  if (bytes && (!d_in || !d_out)) return set_error(CS_EINVAL, "null device buffer");
+  if (bytes && (reinterpret_cast<uintptr_t>(d_in) % p->elem_bytes || reinterpret_cast<uintptr_t>(d_out) % p->elem_bytes))
+    return set_error(CS_EINVAL, "buffers must be aligned to the element size");
+  if (bytes && overlaps(d_in, d_out, bytes)) return set_error(CS_EALIAS, "input and output buffers overlap");
+  p->d_in = d_in;
+  p->d_out = d_out;
+  drop_graph(p);
+  return CS_OK;
+}
+
+int cs_plan_use_graph(cs_plan_t p, int enable) {
+  if (!p) return set_error(CS_EINVAL, "null plan");
+  if (p->kind == kCahnHilliard) return set_error(CS_EUNSUPPORTED, "graph replay is for stencil plans");
+  p->use_graph = enable != 0;
+  if (!p->use_graph) drop_graph(p);
+  return CS_OK;
+}
+
+int cs_autotune(cs_plan_t p, void* stream) {
+  if (!p) return set_error(CS_EINVAL, "null plan");
+  if (p->kind == kCahnHilliard) return set_error(CS_EUNSUPPORTED, "autotune applies to stencil plans");
+  if (p->elems == 0) return CS_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nchoices = p->kind == kStencil2D ? stencil2d_num_tile_choices() : batch1d_num_choices();
+  cudaEvent_t e0, e1;
+  CS_CUDA_TRY(cudaEventCreate(&e0));
+  CS_CUDA_TRY(cudaEventCreate(&e1));
+  int best = -1;
+  float best_ms = 1e30f;
+  int rc = CS_OK;
+  const int reps = 5;
+  for (int c = 0; c < nchoices && rc == CS_OK; ++c) {
+    if (p->kind == kStencil2D) stencil2d_set_tile_choice(&p->s2, c);
+    else p->b1.choice = c;
+    rc = launch_direct(p, s);  // warm-up
+    if (rc != CS_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && rc == CS_OK; ++r) rc = launch_direct(p, s);
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) { rc = cuda_error(e, "autotune timing"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) { best_ms = ms; best = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != CS_OK) return rc;
+  if (p->kind == kStencil2D) {
+    stencil2d_set_tile_choice(&p->s2, best);
+    tune_store(stencil2d_shape_key(&p->s2), best);
+  } else {
+    p->b1.choice = best;
+    tune_store(batch1d_shape_key(&p->b1), best);
+  }
+  drop_graph(p);
+  return CS_OK;
+}
+
+int cs_destroy(cs_plan_t p) {
+  if (!p) return CS_OK;
+  drop_graph(p);
+  if (p->kind == kStencil2D) stencil2d_release(&p->s2);
+  if (p->kind == kBatch1D) batch1d_release(&p->b1);
+  if (p->kind == kCahnHilliard) ch_destroy(p->ch);
+  delete p;
+  return CS_OK;
+}
+
+int cs_ch_create(cs_plan_t* plan, const cs_ch_desc* d, void* prev, void* cur, void* next) {
+  if (!plan) return set_error(CS_EINVAL, "null plan pointer");
+  *plan = nullptr;
+  cs_plan* p = new_plan(kCahnHilliard);
+  if (!p) return set_error(CS_ENOMEM, "out of host memory");
+  int rc = ch_create(&p->ch, d, prev, cur, next);
+  if (rc != CS_OK) { delete p; return rc; }
+  *plan = p;
+  return CS_OK;
+}
+
+int cs_ch_step(cs_plan_t p, int64_t nsteps, double* h_mass, double* h_energy, void* stream) {
+  if (!p || p->kind != kCahnHilliard) return set_error(CS_EINVAL, "not a Cahn-Hilliard plan");
+  return ch_step(p->ch, nsteps, h_mass, h_energy, static_cast<cudaStream_t>(stream));
+}
+
+int cs_ch_invariants(cs_plan_t p, double* mass, double* energy, void* stream) {
+  if (!p || p->kind != kCahnHilliard) return set_error(CS_EINVAL, "not a Cahn-Hilliard plan");
+  return ch_invariants(p->ch, mass, energy, static_cast<cudaStream_t>(stream));
+}
+
+int cs_ch_fields(cs_plan_t p, void** prev, void** cur, int64_t* steps) {
+  if (!p || p->kind != kCahnHilliard) return set_error(CS_EINVAL, "not a Cahn-Hilliard plan");
+  return ch_fields(p->ch, prev, cur, steps);
+}
+
+}  // extern "C"

@@ -1,0 +1,603 @@
+// Cahn-Hilliard ADI time step with periodic boundaries (Sec. 5.1 of arXiv:1902.09931).
+//
+//   Cbar = 2 C^n - C^{n-1}
+//   RHS  = -(2/3)(C^n - C^{n-1}) - (2/3) D gamma dt lap4(Cbar) + (2/3) D dt lap2(C^3 - C)^n
+//   L_x w = RHS,   L_y v = w,   C^{n+1} = Cbar + v,   L = I + a P,  a = (2/3) D gamma dt / h^4
+//
+// lap2 is the 5-point Laplacian of Eq. 5a and lap4 = dxxxx + 2 dxxyy + dyyyy (Eq. 5b, Fig. 1),
+// which on the periodic grid is exactly lap2 applied twice.  The right-hand side is therefore
+// evaluated in the factored form
+//   Z   = (2/3) D dt / h^2 * N - a * (sum of 4 neighbours of Cbar - 4 Cbar)
+//   RHS = -(2/3)(C^n - C^{n-1}) + (sum of 4 neighbours of Z - 4 Z)
+// which needs 16 instead of 24 FP64 operations per point (FP64 is the bound on GB300).
+//
+// Line solves (the paper uses cuPentBatch with the periodic corners treated as in Navon's
+// PENT).  Here each periodic line of length n is cut into P chunks of m = n / P points; since
+// every chunk block A (m x m pentadiagonal Toeplitz) and every coupling are identical for all
+// lines, chunks and steps, the library precomputes once:
+//   - the LU factors of A,
+//   - the spikes S_L = A^{-1} E_L, S_R = A^{-1} E_R (responses to the two values on each side),
+//   - the inverse of the block-circulant 4P x 4P system for the chunk-end values.
+// Per sweep, phase 1 solves A g = b on every (line, chunk) independently and records g at the
+// chunk ends; phase 2 forms the two end values of each neighbouring chunk from the recorded
+// ends (16 P FMAs) and corrects x = g - S_L t_{p-1} - S_R h_{p+1}.  This is exact (up to
+// rounding) and gives n * P independent threads instead of n sequential lines.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cs_internal.h"
+
+namespace cs {
+
+struct CHPlan {
+  int64_t n;
+  int storage;
+  double D, gamma, dt, h, a, alpha;
+  int P, m;
+  void* field[3];
+  int iprev, icur, inext;
+  int64_t steps;
+  double* A;         // n*n scratch (RHS, then w)
+  double* B;         // n*n scratch (local solutions g)
+  double* bnd;       // 4 * P * n chunk-end values
+  double* coef;      // 9 * m line-solve coefficients
+  double* K;         // P * 16 block-circulant inverse
+  double* partials;  // 2 per RHS block
+  double* inv;       // 2 per step (device)
+  int64_t inv_cap;
+  int rhs_blocks;
+};
+
+namespace {
+
+constexpr int kTX = 64, kTY = 32, kThreads = 256, kSolveThreads = 128;
+
+// ---- exact conversions on the integer pipe (f32 <-> f64 conversion runs on the FP64 pipe) ----
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) {
+    if ((b & 0x7fffffffu) == 0u) return __longlong_as_double(static_cast<long long>(b & 0x80000000u) << 32);
+    return static_cast<double>(f);  // subnormal, inf, nan: rare
+  }
+  const uint64_t d = (static_cast<uint64_t>(b & 0x80000000u) << 32) |
+                     (static_cast<uint64_t>(e + 896u) << 52) |
+                     (static_cast<uint64_t>(b & 0x7fffffu) << 29);
+  return __longlong_as_double(static_cast<long long>(d));
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
+__device__ __forceinline__ float narrow_rn(double x) {
+  const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x));
+  const int e = static_cast<int>((b >> 52) & 0x7ffu) - 1023 + 127;
+  if (e <= 0 || e >= 255) {
+    if ((b << 1) == 0) return __uint_as_float(static_cast<uint32_t>(b >> 32));  // +-0
+    return __double2float_rn(x);  // subnormal result, overflow, inf, nan: rare
+  }
+  const uint32_t sign = static_cast<uint32_t>(b >> 32) & 0x80000000u;
+  const uint64_t mant = b & 0xFFFFFFFFFFFFFull;
+  const uint32_t m23 = static_cast<uint32_t>(mant >> 29);
+  const uint32_t rem = static_cast<uint32_t>(mant & 0x1FFFFFFFu);
+  uint32_t r = sign | (static_cast<uint32_t>(e) << 23) | m23;
+  if (rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) r += 1u;  // ties to even
+  return __uint_as_float(r);
+}
+
+template <typename T> __device__ __forceinline__ void store_as(T* p, double v);
+template <> __device__ __forceinline__ void store_as<double>(double* p, double v) { *p = v; }
+template <> __device__ __forceinline__ void store_as<float>(float* p, double v) { *p = narrow_rn(v); }
+
+__device__ __forceinline__ int wrapn(int64_t k, int64_t n) {
+  return static_cast<int>(k < 0 ? k + n : (k >= n ? k - n : k));
+}
+
+template <typename T>
+__device__ __forceinline__ void block_reduce2(double m, double e, double* out2) {
+  __shared__ double red[2][kThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) {
+    m += __shfl_down_sync(0xffffffffu, m, off);
+    e += __shfl_down_sync(0xffffffffu, e, off);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { red[0][warp] = m; red[1][warp] = e; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sm = 0.0, se = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) { sm += red[0][w]; se += red[1][w]; }
+    out2[0] = sm;
+    out2[1] = se;
+  }
+}
+
+// RHS of the x-sweep (storage T, stencil arithmetic T) and, when partials != nullptr, the
+// per-block FP64 sums of C and of the free-energy density of C^n.  rhs == nullptr computes the
+// sums only.
+template <typename T, typename RT>
+__global__ void __launch_bounds__(kThreads)
+    k_ch_rhs(const T* __restrict__ cur, const T* __restrict__ prev, RT* __restrict__ rhs, int64_t n,
+             T alpha, T a, double half_gamma_over_h2, double* __restrict__ partials) {
+  constexpr int HR = kTY + 4, HC = kTX + 4;  // halo-2 tiles
+  constexpr int ZR = kTY + 2, ZC = kTX + 2;  // halo-1 tile
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sc = reinterpret_cast<T*>(smem_raw);  // C^n
+  T* sb = sc + HR * HC;                    // Cbar
+  T* sz = sb + HR * HC;                    // Z
+  const int64_t x0 = static_cast<int64_t>(blockIdx.x) * kTX;
+  const int64_t y0 = static_cast<int64_t>(blockIdx.y) * kTY;
+  for (int idx = threadIdx.x; idx < HR * HC; idx += kThreads) {
+    const int r = idx / HC, c = idx - r * HC;
+    const int64_t off = static_cast<int64_t>(wrapn(y0 - 2 + r, n)) * n + wrapn(x0 - 2 + c, n);
+    const T cv = cur[off];
+    sc[idx] = cv;
+    sb[idx] = T(2) * cv - prev[off];
+  }
+  __syncthreads();
+  if (rhs) {
+    for (int idx = threadIdx.x; idx < ZR * ZC; idx += kThreads) {
+      const int r = idx / ZC, c = idx - r * ZC;
+      const int hidx = (r + 1) * HC + (c + 1);
+      const T cb = sb[hidx];
+      const T lap_cb = (sb[hidx - HC] + sb[hidx + HC]) + (sb[hidx - 1] + sb[hidx + 1]) - T(4) * cb;
+      const T u = sc[hidx];
+      const T nl = u * u * u - u;
+      sz[idx] = alpha * nl - a * lap_cb;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kTY * kTX; idx += kThreads) {
+      const int r = idx / kTX, c = idx - r * kTX;
+      const int zidx = (r + 1) * ZC + (c + 1);
+      const int hidx = (r + 2) * HC + (c + 2);
+      const T lap_z = (sz[zidx - ZC] + sz[zidx + ZC]) + (sz[zidx - 1] + sz[zidx + 1]) - T(4) * sz[zidx];
+      const T diff = sb[hidx] - sc[hidx];  // Cbar - C^n = C^n - C^{n-1}
+      rhs[(y0 + r) * n + x0 + c] = static_cast<RT>(T(-2.0 / 3.0) * diff + lap_z);
+    }
+  }
+  if (partials) {
+    double m = 0.0, e = 0.0;
+    for (int idx = threadIdx.x; idx < kTY * kTX; idx += kThreads) {
+      const int r = idx / kTX, c = idx - r * kTX;
+      const int hidx = (r + 2) * HC + (c + 2);
+      const double u = widen(sc[hidx]);
+      const double gx = widen(sc[hidx + 1]) - u;
+      const double gy = widen(sc[hidx + HC]) - u;
+      const double w = u * u - 1.0;
+      m += u;
+      e += 0.25 * w * w + half_gamma_over_h2 * (gx * gx + gy * gy);
+    }
+    block_reduce2<T>(m, e, partials + 2 * (static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x));
+  }
+}
+
+// Fixed-order sum of the per-block partials -> out2 = (h^2 sum C, h^2 sum energy density).
+__global__ void k_reduce_final(const double* __restrict__ partials, int nblocks, double h2,
+                               double* __restrict__ out2) {
+  __shared__ double sm[256], se[256];
+  double m = 0.0, e = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += 256) {
+    m += partials[2 * b];
+    e += partials[2 * b + 1];
+  }
+  sm[threadIdx.x] = m;
+  se[threadIdx.x] = e;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sm[threadIdx.x] += sm[threadIdx.x + s];
+      se[threadIdx.x] += se[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out2[0] = h2 * sm[0];
+    out2[1] = h2 * se[0];
+  }
+}
+
+// Phase 1: A g = b on chunk p of a line (LU forward then backward), g over the scratch.
+// Coefficients (negated / pre-scaled): nl1, nl2, dinv, nu1, nu2 at coef[0..5m).
+template <typename IT>
+__global__ void __launch_bounds__(kSolveThreads)
+    k_solve_local(const IT* __restrict__ in, double* __restrict__ G, double* __restrict__ bnd,
+                  const double* __restrict__ coef, int64_t n, int P, int m, int64_t line_stride,
+                  int64_t elem_stride) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n * P) return;
+  const int64_t line = t % n;
+  const int p = static_cast<int>(t / n);
+  const double* nl1 = coef;
+  const double* nl2 = coef + m;
+  const double* dinv = coef + 2 * m;
+  const double* nu1 = coef + 3 * m;
+  const double* nu2 = coef + 4 * m;
+  const int64_t base = line * line_stride + static_cast<int64_t>(p) * m * elem_stride;
+  double y1 = 0.0, y2 = 0.0;
+  for (int k = 0; k < m; ++k) {
+    const int64_t at = base + k * elem_stride;
+    const double y = fma(__ldg(nl1 + k), y1, fma(__ldg(nl2 + k), y2, widen(in[at])));
+    G[at] = y;
+    y2 = y1;
+    y1 = y;
+  }
+  double g1 = 0.0, g2 = 0.0;
+  for (int k = m - 1; k >= 0; --k) {
+    const int64_t at = base + k * elem_stride;
+    const double g = fma(__ldg(nu1 + k), g1, fma(__ldg(nu2 + k), g2, G[at] * __ldg(dinv + k)));
+    G[at] = g;
+    g2 = g1;
+    g1 = g;
+  }
+  // chunk-end values: k = 0, 1 are g1, g2 after the loop; k = m-2, m-1 re-read
+  double* b = bnd + static_cast<int64_t>(p) * 4 * n + line;
+  b[0] = g1;
+  b[n] = g2;
+  b[2 * n] = G[base + (m - 2) * elem_stride];
+  b[3 * n] = G[base + (m - 1) * elem_stride];
+}
+
+// Phase 2: end values of the neighbouring chunks from the block-circulant inverse, then the
+// spike correction.  MODE 0 writes w (FP64); MODE 1 writes C^{n+1} = 2 C^n - C^{n-1} + x.
+template <int MODE, typename T>
+__global__ void __launch_bounds__(kSolveThreads)
+    k_solve_correct(const double* __restrict__ G, const double* __restrict__ bnd,
+                    const double* __restrict__ coef, const double* __restrict__ K, int64_t n, int P,
+                    int m, int64_t line_stride, int64_t elem_stride, double* __restrict__ w_out,
+                    const T* __restrict__ cur, const T* __restrict__ prev, T* __restrict__ next) {
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n * P) return;
+  const int64_t line = t % n;
+  const int p = static_cast<int>(t / n);
+  const int pm = (p + P - 1) % P, pp = (p + 1) % P;
+  double t0 = 0.0, t1 = 0.0, h0 = 0.0, h1 = 0.0;
+  for (int q = 0; q < P; ++q) {
+    const double* b = bnd + static_cast<int64_t>(q) * 4 * n + line;
+    const double g0 = b[0], g1 = b[n], g2 = b[2 * n], g3 = b[3 * n];
+    const double* Kt = K + ((pm - q + P) % P) * 16;  // K_{(p-1)-q}: rows 2, 3 give t_{p-1}
+    const double* Kh = K + ((pp - q + P) % P) * 16;  // K_{(p+1)-q}: rows 0, 1 give h_{p+1}
+    t0 = fma(__ldg(Kt + 8), g0, fma(__ldg(Kt + 9), g1, fma(__ldg(Kt + 10), g2, fma(__ldg(Kt + 11), g3, t0))));
+    t1 = fma(__ldg(Kt + 12), g0, fma(__ldg(Kt + 13), g1, fma(__ldg(Kt + 14), g2, fma(__ldg(Kt + 15), g3, t1))));
+    h0 = fma(__ldg(Kh + 0), g0, fma(__ldg(Kh + 1), g1, fma(__ldg(Kh + 2), g2, fma(__ldg(Kh + 3), g3, h0))));
+    h1 = fma(__ldg(Kh + 4), g0, fma(__ldg(Kh + 5), g1, fma(__ldg(Kh + 6), g2, fma(__ldg(Kh + 7), g3, h1))));
+  }
+  const double* sl0 = coef + 5 * m;
+  const double* sl1 = coef + 6 * m;
+  const double* sr0 = coef + 7 * m;
+  const double* sr1 = coef + 8 * m;
+  const int64_t base = line * line_stride + static_cast<int64_t>(p) * m * elem_stride;
+  for (int k = 0; k < m; ++k) {
+    const int64_t at = base + k * elem_stride;
+    const double x = fma(-__ldg(sl0 + k), t0, fma(-__ldg(sl1 + k), t1,
+                     fma(-__ldg(sr0 + k), h0, fma(-__ldg(sr1 + k), h1, G[at]))));
+    if constexpr (MODE == 0) {
+      w_out[at] = x;
+    } else {
+      const double cb = fma(2.0, widen(cur[at]), -widen(prev[at]));
+      store_as<T>(next + at, cb + x);
+    }
+  }
+}
+
+// ---- host-side precomputation ---------------------------------------------------------------
+
+// LU of the m x m pentadiagonal Toeplitz block, rows (a, -4a, 1+6a, -4a, a), no pivoting
+// (the block is symmetric positive definite).  L unit lower with bands l1, l2; U with d, u1, u2.
+void block_lu(int m, double a, std::vector<double>& l1, std::vector<double>& l2,
+              std::vector<double>& d, std::vector<double>& u1, std::vector<double>& u2) {
+  l1.assign(m, 0.0); l2.assign(m, 0.0); d.assign(m, 0.0); u1.assign(m, 0.0); u2.assign(m, 0.0);
+  for (int k = 0; k < m; ++k) {
+    const double sub2 = k >= 2 ? a : 0.0;
+    const double sub1 = k >= 1 ? -4.0 * a : 0.0;
+    l2[k] = k >= 2 ? sub2 / d[k - 2] : 0.0;
+    l1[k] = k >= 1 ? (sub1 - (k >= 2 ? l2[k] * u1[k - 2] : 0.0)) / d[k - 1] : 0.0;
+    d[k] = 1.0 + 6.0 * a - (k >= 2 ? l2[k] * u2[k - 2] : 0.0) - (k >= 1 ? l1[k] * u1[k - 1] : 0.0);
+    u1[k] = k + 1 < m ? -4.0 * a - (k >= 1 ? l1[k] * u2[k - 1] : 0.0) : 0.0;
+    u2[k] = k + 2 < m ? a : 0.0;
+  }
+}
+
+void block_solve(int m, const std::vector<double>& l1, const std::vector<double>& l2,
+                 const std::vector<double>& d, const std::vector<double>& u1,
+                 const std::vector<double>& u2, std::vector<double>& x) {
+  for (int k = 0; k < m; ++k) {
+    if (k >= 1) x[k] -= l1[k] * x[k - 1];
+    if (k >= 2) x[k] -= l2[k] * x[k - 2];
+  }
+  for (int k = m - 1; k >= 0; --k) {
+    if (k + 1 < m) x[k] -= u1[k] * x[k + 1];
+    if (k + 2 < m) x[k] -= u2[k] * x[k + 2];
+    x[k] /= d[k];
+  }
+}
+
+// Gauss-Jordan inverse with partial pivoting (dense, small).
+bool invert(int N, std::vector<double>& M, std::vector<double>& inv) {
+  inv.assign(static_cast<size_t>(N) * N, 0.0);
+  for (int i = 0; i < N; ++i) inv[static_cast<size_t>(i) * N + i] = 1.0;
+  for (int c = 0; c < N; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < N; ++r)
+      if (std::fabs(M[static_cast<size_t>(r) * N + c]) > std::fabs(M[static_cast<size_t>(piv) * N + c])) piv = r;
+    if (M[static_cast<size_t>(piv) * N + c] == 0.0) return false;
+    if (piv != c)
+      for (int k = 0; k < N; ++k) {
+        std::swap(M[static_cast<size_t>(c) * N + k], M[static_cast<size_t>(piv) * N + k]);
+        std::swap(inv[static_cast<size_t>(c) * N + k], inv[static_cast<size_t>(piv) * N + k]);
+      }
+    const double s = 1.0 / M[static_cast<size_t>(c) * N + c];
+    for (int k = 0; k < N; ++k) {
+      M[static_cast<size_t>(c) * N + k] *= s;
+      inv[static_cast<size_t>(c) * N + k] *= s;
+    }
+    for (int r = 0; r < N; ++r) {
+      if (r == c) continue;
+      const double f = M[static_cast<size_t>(r) * N + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < N; ++k) {
+        M[static_cast<size_t>(r) * N + k] -= f * M[static_cast<size_t>(c) * N + k];
+        inv[static_cast<size_t>(r) * N + k] -= f * inv[static_cast<size_t>(c) * N + k];
+      }
+    }
+  }
+  return true;
+}
+
+int build_tables(int64_t n, int P, double a, std::vector<double>& coef, std::vector<double>& K) {
+  const int m = static_cast<int>(n / P);
+  std::vector<double> l1, l2, d, u1, u2;
+  block_lu(m, a, l1, l2, d, u1, u2);
+  coef.assign(static_cast<size_t>(9) * m, 0.0);
+  for (int k = 0; k < m; ++k) {
+    coef[k] = -l1[k];
+    coef[m + k] = -l2[k];
+    coef[2 * m + k] = 1.0 / d[k];
+    coef[3 * m + k] = -u1[k] / d[k];
+    coef[4 * m + k] = -u2[k] / d[k];
+  }
+  // spikes: responses to the two values before (t) and after (h) the chunk
+  std::vector<double> s[4];
+  for (int c = 0; c < 4; ++c) s[c].assign(m, 0.0);
+  s[0][0] = a;                          // S_L column for x_{p-1}[m-2]
+  s[1][0] = -4.0 * a; s[1][1] = a;      // S_L column for x_{p-1}[m-1]
+  s[2][m - 2] = a; s[2][m - 1] = -4.0 * a;  // S_R column for x_{p+1}[0]
+  s[3][m - 1] = a;                      // S_R column for x_{p+1}[1]
+  for (int c = 0; c < 4; ++c) block_solve(m, l1, l2, d, u1, u2, s[c]);
+  for (int c = 0; c < 4; ++c)
+    for (int k = 0; k < m; ++k) coef[static_cast<size_t>(5 + c) * m + k] = s[c][k];
+  // block-circulant system for u_p = (x_p[0], x_p[1], x_p[m-2], x_p[m-1])
+  const int rows[4] = {0, 1, m - 2, m - 1};
+  const int N4 = 4 * P;
+  std::vector<double> R(static_cast<size_t>(N4) * N4, 0.0), Ri;
+  for (int i = 0; i < N4; ++i) R[static_cast<size_t>(i) * N4 + i] = 1.0;
+  for (int p = 0; p < P; ++p) {
+    const int pm = (p + P - 1) % P, pp = (p + 1) % P;
+    for (int r = 0; r < 4; ++r) {
+      const size_t row = static_cast<size_t>(4 * p + r) * N4;
+      R[row + 4 * pm + 2] += s[0][rows[r]];
+      R[row + 4 * pm + 3] += s[1][rows[r]];
+      R[row + 4 * pp + 0] += s[2][rows[r]];
+      R[row + 4 * pp + 1] += s[3][rows[r]];
+    }
+  }
+  if (!invert(N4, R, Ri)) return set_error(CS_EINVAL, "Cahn-Hilliard chunk system is singular");
+  K.assign(static_cast<size_t>(16) * P, 0.0);
+  for (int dd = 0; dd < P; ++dd)  // K_d = block (d, 0) of the inverse
+    for (int r = 0; r < 4; ++r)
+      for (int c = 0; c < 4; ++c) K[static_cast<size_t>(dd) * 16 + r * 4 + c] = Ri[static_cast<size_t>(4 * dd + r) * N4 + c];
+  return CS_OK;
+}
+
+int default_chunks(int64_t n) {
+  // enough independent (line, chunk) threads to cover the GPU, chunks of at least 64 points
+  int P = 1;
+  while (n * P < 16384 && n / (2 * P) >= 64 && 2 * P <= 64) P *= 2;
+  return P;
+}
+
+size_t rhs_smem_bytes(int storage) {
+  const size_t e = storage == CS_F32 ? 4 : 8;
+  return e * (2 * (kTY + 4) * (kTX + 4) + (kTY + 2) * (kTX + 2));
+}
+
+template <typename T> int set_rhs_attr() {
+  static bool done = false;
+  if (!done) {
+    const int bytes = static_cast<int>(rhs_smem_bytes(sizeof(T) == 4 ? CS_F32 : CS_F64));
+    CS_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    done = true;
+  }
+  return CS_OK;
+}
+
+template <typename T>
+int launch_rhs(CHPlan* p, bool with_rhs, double* partials, cudaStream_t s) {
+  int rc = set_rhs_attr<T>();
+  if (rc != CS_OK) return rc;
+  dim3 grid(static_cast<unsigned>(p->n / kTX), static_cast<unsigned>(p->n / kTY));
+  const T* cur = static_cast<const T*>(p->field[p->icur]);
+  const T* prev = static_cast<const T*>(p->field[p->iprev]);
+  T* rhs = with_rhs ? reinterpret_cast<T*>(p->A) : nullptr;
+  k_ch_rhs<T, T><<<grid, kThreads, rhs_smem_bytes(p->storage), s>>>(
+      cur, prev, rhs, p->n, static_cast<T>(p->alpha), static_cast<T>(p->a),
+      0.5 * p->gamma / (p->h * p->h), partials);
+  CS_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return CS_OK;
+}
+
+template <typename T>
+int launch_step(CHPlan* p, double* partials, cudaStream_t s) {
+  int rc = launch_rhs<T>(p, true, partials, s);
+  if (rc != CS_OK) return rc;
+  const int64_t n = p->n;
+  const unsigned sgrid = static_cast<unsigned>((n * p->P + kSolveThreads - 1) / kSolveThreads);
+  // x-sweep: lines are rows (line stride n, element stride 1)
+  k_solve_local<T><<<sgrid, kSolveThreads, 0, s>>>(reinterpret_cast<const T*>(p->A), p->B, p->bnd,
+                                                   p->coef, n, p->P, p->m, n, 1);
+  k_solve_correct<0, T><<<sgrid, kSolveThreads, 0, s>>>(p->B, p->bnd, p->coef, p->K, n, p->P, p->m,
+                                                        n, 1, p->A, nullptr, nullptr, nullptr);
+  // y-sweep: lines are columns (line stride 1, element stride n), update fused
+  k_solve_local<double><<<sgrid, kSolveThreads, 0, s>>>(p->A, p->B, p->bnd, p->coef, n, p->P,
+                                                        p->m, 1, n);
+  k_solve_correct<1, T><<<sgrid, kSolveThreads, 0, s>>>(
+      p->B, p->bnd, p->coef, p->K, n, p->P, p->m, 1, n, nullptr,
+      static_cast<const T*>(p->field[p->icur]), static_cast<const T*>(p->field[p->iprev]),
+      static_cast<T*>(p->field[p->inext]));
+  CS_CUDA_TRY(cudaGetLastError());
+  count_launches(4);
+  return CS_OK;
+}
+
+void rotate(CHPlan* p) {
+  const int old_prev = p->iprev;
+  p->iprev = p->icur;
+  p->icur = p->inext;
+  p->inext = old_prev;
+  ++p->steps;
+}
+
+int reduce_current(CHPlan* p, double* out2, cudaStream_t s) {
+  int rc = p->storage == CS_F32 ? launch_rhs<float>(p, false, p->partials, s)
+                                : launch_rhs<double>(p, false, p->partials, s);
+  if (rc != CS_OK) return rc;
+  k_reduce_final<<<1, 256, 0, s>>>(p->partials, p->rhs_blocks, p->h * p->h, out2);
+  CS_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return CS_OK;
+}
+
+void free_plan(CHPlan* p) {
+  if (!p) return;
+  cudaFree(p->A); cudaFree(p->B); cudaFree(p->bnd); cudaFree(p->coef); cudaFree(p->K);
+  cudaFree(p->partials); cudaFree(p->inv);
+  delete p;
+}
+
+}  // namespace
+
+int ch_create(CHPlan** out, const cs_ch_desc* d, void* prev, void* cur, void* next) {
+  *out = nullptr;
+  if (!d) return set_error(CS_EINVAL, "null Cahn-Hilliard description");
+  if (d->n < 64 || d->n % 64 != 0 || d->n > 65536)
+    return set_error(CS_EINVAL, "n must be a multiple of 64 in [64, 65536]");
+  if (d->storage != CS_F64 && d->storage != CS_F32) return set_error(CS_EINVAL, "storage must be CS_F64 or CS_F32");
+  if (!(d->D > 0) || !(d->gamma >= 0) || !(d->dt > 0) || !std::isfinite(d->D) || !std::isfinite(d->gamma) || !std::isfinite(d->dt))
+    return set_error(CS_EINVAL, "D > 0, gamma >= 0, dt > 0 and finite are required");
+  if (!prev || !cur || !next) return set_error(CS_EINVAL, "null field buffer");
+  const size_t eb = d->storage == CS_F32 ? 4 : 8;
+  const size_t bytes = static_cast<size_t>(d->n) * d->n * eb;
+  void* f[3] = {prev, cur, next};
+  for (int i = 0; i < 3; ++i) {
+    if (reinterpret_cast<uintptr_t>(f[i]) % eb) return set_error(CS_EINVAL, "fields must be aligned to the element size");
+    for (int j = i + 1; j < 3; ++j) {
+      const char* a = static_cast<const char*>(f[i]);
+      const char* b = static_cast<const char*>(f[j]);
+      if (a < b + bytes && b < a + bytes) return set_error(CS_EALIAS, "the three fields must not overlap");
+    }
+  }
+  CHPlan* p = new (std::nothrow) CHPlan;
+  if (!p) return set_error(CS_ENOMEM, "out of host memory");
+  memset(p, 0, sizeof *p);
+  p->n = d->n;
+  p->storage = d->storage;
+  p->D = d->D; p->gamma = d->gamma; p->dt = d->dt;
+  p->h = 2.0 * M_PI / static_cast<double>(d->n);
+  const double h2 = p->h * p->h;
+  p->a = (2.0 / 3.0) * d->D * d->gamma * d->dt / (h2 * h2);
+  p->alpha = (2.0 / 3.0) * d->D * d->dt / h2;
+  int P = default_chunks(d->n);
+  int choice;
+  char key[96];
+  snprintf(key, sizeof key, "ch|%s|n%lld|sm%d", d->storage == CS_F32 ? "f32" : "f64", (long long)d->n, num_sms());
+  if (tune_lookup(key, &choice) && choice >= 1 && choice <= 64 && d->n % choice == 0 && d->n / choice >= 16) P = choice;
+  p->P = P;
+  p->m = static_cast<int>(d->n / P);
+  p->field[0] = prev; p->field[1] = cur; p->field[2] = next;
+  p->iprev = 0; p->icur = 1; p->inext = 2;
+  p->rhs_blocks = static_cast<int>((d->n / kTX) * (d->n / kTY));
+  std::vector<double> coef, K;
+  int rc = build_tables(d->n, P, p->a, coef, K);
+  if (rc != CS_OK) { free_plan(p); return rc; }
+  const size_t nn = static_cast<size_t>(d->n) * d->n;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&p->A, nn * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&p->B, nn * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&p->bnd, static_cast<size_t>(4) * P * d->n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&p->coef, coef.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&p->K, K.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&p->partials, static_cast<size_t>(2) * p->rhs_blocks * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(p->coef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->K, K.data(), K.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    free_plan(p);
+    return e == cudaErrorMemoryAllocation ? set_error(CS_ENOMEM, "Cahn-Hilliard workspace: %s", cudaGetErrorString(e))
+                                          : cuda_error(e, "Cahn-Hilliard workspace");
+  }
+  *out = p;
+  return CS_OK;
+}
+
+int ch_step(CHPlan* p, int64_t nsteps, double* h_mass, double* h_energy, cudaStream_t s) {
+  if (nsteps < 0) return set_error(CS_EINVAL, "nsteps must be >= 0");
+  if (nsteps == 0) return CS_OK;
+  const bool want = h_mass || h_energy;
+  if (want && p->inv_cap < nsteps) {
+    if (p->inv) cudaFree(p->inv);
+    p->inv = nullptr;
+    p->inv_cap = 0;
+    cudaError_t e = cudaMalloc(&p->inv, static_cast<size_t>(2) * nsteps * sizeof(double));
+    if (e != cudaSuccess) return cuda_error(e, "invariant buffer");
+    p->inv_cap = nsteps;
+  }
+  for (int64_t st = 0; st < nsteps; ++st) {
+    // the RHS kernel of step st reads C^n = the field after step st-1: reduce it on the way
+    double* part = (want && st > 0) ? p->partials : nullptr;
+    int rc = p->storage == CS_F32 ? launch_step<float>(p, part, s) : launch_step<double>(p, part, s);
+    if (rc != CS_OK) return rc;
+    if (part) {
+      // partials were consumed into a fixed-order sum before the next RHS overwrites them
+      k_reduce_final<<<1, 256, 0, s>>>(p->partials, p->rhs_blocks, p->h * p->h, p->inv + 2 * (st - 1));
+      CS_CUDA_TRY(cudaGetLastError());
+      count_launches(1);
+    }
+    rotate(p);
+  }
+  if (!want) return CS_OK;
+  int rc = reduce_current(p, p->inv + 2 * (nsteps - 1), s);
+  if (rc != CS_OK) return rc;
+  std::vector<double> h(static_cast<size_t>(2) * nsteps);
+  CS_CUDA_TRY(cudaMemcpyAsync(h.data(), p->inv, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CS_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int64_t st = 0; st < nsteps; ++st) {
+    if (h_mass) h_mass[st] = h[2 * st];
+    if (h_energy) h_energy[st] = h[2 * st + 1];
+  }
+  return CS_OK;
+}
+
+int ch_invariants(CHPlan* p, double* mass, double* energy, cudaStream_t s) {
+  if (p->inv_cap < 1) {
+    cudaError_t e = cudaMalloc(&p->inv, 2 * sizeof(double));
+    if (e != cudaSuccess) return cuda_error(e, "invariant buffer");
+    p->inv_cap = 1;
+  }
+  int rc = reduce_current(p, p->inv, s);
+  if (rc != CS_OK) return rc;
+  double h[2];
+  CS_CUDA_TRY(cudaMemcpyAsync(h, p->inv, sizeof h, cudaMemcpyDeviceToHost, s));
+  CS_CUDA_TRY(cudaStreamSynchronize(s));
+  if (mass) *mass = h[0];
+  if (energy) *energy = h[1];
+  return CS_OK;
+}
+
+int ch_fields(CHPlan* p, void** prev, void** cur, int64_t* steps) {
+  if (prev) *prev = p->field[p->iprev];
+  if (cur) *cur = p->field[p->icur];
+  if (steps) *steps = p->steps;
+  return CS_OK;
+}
+
+void ch_destroy(CHPlan* p) { free_plan(p); }
+
+}  // namespace cs

@@ -1,0 +1,76 @@
+// Internal declarations shared by the translation units of libcusten_gb (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "custen_gb.h"
+
+namespace cs {
+
+// ---- errors ---------------------------------------------------------------------------------
+int set_error(int code, const char* fmt, ...);  // records a thread-local message, returns code
+int cuda_error(cudaError_t e, const char* what);  // CS_ECUDA with the CUDA message
+#define CS_CUDA_TRY(expr)                                   \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) return ::cs::cuda_error(_e, #expr); \
+  } while (0)
+
+void count_launches(int64_t n);  // adds to cs_launch_count()
+int num_sms();                   // SM count of the current device (cached per device)
+
+// ---- tuning table (cs_tune.cpp) ----------------------------------------------------------------
+// Key: "<kernel>|<dtype>|<shape class>|sm<count>"  ->  small integer choice.
+bool tune_lookup(const std::string& key, int* choice);
+void tune_store(const std::string& key, int choice);
+
+// ---- 2D stencil (cs_stencil2d.cu) --------------------------------------------------------------
+struct Stencil2DConfig {
+  int64_t nx, ny;
+  int dir, bc, dtype;
+  int left, right, top, bottom;
+  int fn;
+  double weights[(2 * CS_MAX_EXTENT + 1) * (2 * CS_MAX_EXTENT + 1)];
+  double coe[8];
+  int num_coe;
+  // chosen at create time
+  int variant;     // index into the specialisation table, or -1 for the generic kernel
+  int tile_rows;   // TY
+  double* d_weights;  // device copy for the generic kernel (library-owned), FP64
+  float* d_weights_f; // FP32 copy
+};
+int stencil2d_prepare(Stencil2DConfig* cfg);  // picks variant, allocates generic weights
+void stencil2d_release(Stencil2DConfig* cfg);
+int stencil2d_launch(const Stencil2DConfig* cfg, const void* in, void* out, cudaStream_t s);
+int stencil2d_num_tile_choices();
+int stencil2d_set_tile_choice(Stencil2DConfig* cfg, int choice);
+std::string stencil2d_shape_key(const Stencil2DConfig* cfg);
+
+// ---- batched 1D (cs_batch1d.cu) -------------------------------------------------------------
+struct Batch1DConfig {
+  int64_t num_lines, total_len;
+  int bc, dtype, left, right;
+  double weights[2 * CS_MAX_EXTENT + 1];
+  const int64_t* d_offsets;  // caller-owned
+  int32_t* d_seg_line;       // library-owned: line containing element s * kSegTable
+  int64_t num_table;
+  int choice;                // launch shape index
+};
+int batch1d_prepare(Batch1DConfig* cfg, cudaStream_t s);
+void batch1d_release(Batch1DConfig* cfg);
+int batch1d_launch(const Batch1DConfig* cfg, const void* in, void* out, cudaStream_t s);
+int batch1d_num_choices();
+std::string batch1d_shape_key(const Batch1DConfig* cfg);
+
+// ---- Cahn-Hilliard ADI (cs_ch.cu) -------------------------------------------------------------
+struct CHPlan;
+int ch_create(CHPlan** out, const cs_ch_desc* d, void* prev, void* cur, void* next);
+int ch_step(CHPlan* p, int64_t nsteps, double* h_mass, double* h_energy, cudaStream_t s);
+int ch_invariants(CHPlan* p, double* mass, double* energy, cudaStream_t s);
+int ch_fields(CHPlan* p, void** prev, void** cur, int64_t* steps);
+void ch_destroy(CHPlan* p);
+
+}  // namespace cs

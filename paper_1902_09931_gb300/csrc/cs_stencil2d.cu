@@ -1,0 +1,120 @@
+// Host side of the 2D stencil: validation helpers, functor mapping (Sec. 4.2, Sec. 5.2),
+// choice of the specialised kernel and tile shape, and dispatch by storage type.
+#include <cstdio>
+#include <cstring>
+
+#include "cs_stencil2d_kernels.cuh"
+
+namespace cs {
+
+int stencil2d_launch_f32(const Stencil2DConfig* cfg, const void* in, void* out, cudaStream_t s);
+int stencil2d_launch_f64(const Stencil2DConfig* cfg, const void* in, void* out, cudaStream_t s);
+
+namespace {
+
+// Effective weights of the compiled-in user functions, in the Sec. 5.2 ordering.
+int map_function(Stencil2DConfig* cfg) {
+  const double c = cfg->coe[0];
+  switch (cfg->fn) {
+    case CS_FN_CENTRAL_D2X: {  // Sec. 4.2: second-order central difference in x
+      const double w[3] = {c, -2.0 * c, c};
+      memcpy(cfg->weights, w, sizeof w);
+      cfg->variant = 4;
+      return CS_OK;
+    }
+    case CS_FN_CH_NONLIN_LAP: {  // Laplacian of u^3 - u (staged transform)
+      const double w[9] = {0, c, 0, c, -4.0 * c, c, 0, c, 0};
+      memcpy(cfg->weights, w, sizeof w);
+      cfg->variant = 12;
+      return CS_OK;
+    }
+    case CS_FN_CUBIC_MINUS_LAP: {  // u^3 - u - Laplacian(u)
+      const double w[9] = {0, -c, 0, -c, 4.0 * c, -c, 0, -c, 0};
+      memcpy(cfg->weights, w, sizeof w);
+      cfg->variant = 13;
+      return CS_OK;
+    }
+    default:
+      return set_error(CS_EINVAL, "unknown user function %d", cfg->fn);
+  }
+}
+
+}  // namespace
+
+int stencil2d_prepare(Stencil2DConfig* cfg) {
+  cfg->d_weights = nullptr;
+  cfg->d_weights_f = nullptr;
+  cfg->variant = -1;
+  if (cfg->tile_rows != 32 && cfg->tile_rows != 64) cfg->tile_rows = 64;
+  const int W = cfg->left + cfg->right + 1, H = cfg->top + cfg->bottom + 1;
+  if (cfg->fn != CS_FN_NONE) {
+    int rc = map_function(cfg);
+    if (rc != CS_OK) return rc;
+  } else {
+    // smallest specialisation with the same extents whose mask covers every non-zero weight
+    uint32_t mask = 0;
+    bool fits = W * H <= 32;
+    if (fits)
+      for (int i = 0; i < W * H; ++i)
+        if (cfg->weights[i] != 0.0) mask |= 1u << i;
+    int best = -1, best_taps = 1 << 30;
+    for (int v = 0; fits && v < s2d::kNumSpecs; ++v) {
+      const s2d::SpecDesc& sd = s2d::kSpecs[v];
+      if (sd.xform || sd.epi) continue;
+      if (sd.L != cfg->left || sd.R != cfg->right || sd.T != cfg->top || sd.B != cfg->bottom) continue;
+      if ((mask & ~sd.mask) != 0) continue;
+      const int taps = __builtin_popcount(sd.mask);
+      if (taps < best_taps) { best = v; best_taps = taps; }
+    }
+    cfg->variant = best;
+  }
+  if (cfg->variant < 0) {  // generic kernel: weights in device memory
+    const size_t n = static_cast<size_t>(W) * H;
+    CS_CUDA_TRY(cudaMalloc(&cfg->d_weights, n * sizeof(double)));
+    cudaError_t e = cudaMalloc(&cfg->d_weights_f, n * sizeof(float));
+    if (e != cudaSuccess) {
+      cudaFree(cfg->d_weights);
+      cfg->d_weights = nullptr;
+      return cuda_error(e, "cudaMalloc(weights)");
+    }
+    float wf[(2 * CS_MAX_EXTENT + 1) * (2 * CS_MAX_EXTENT + 1)];
+    for (size_t i = 0; i < n; ++i) wf[i] = static_cast<float>(cfg->weights[i]);
+    CS_CUDA_TRY(cudaMemcpy(cfg->d_weights, cfg->weights, n * sizeof(double), cudaMemcpyHostToDevice));
+    CS_CUDA_TRY(cudaMemcpy(cfg->d_weights_f, wf, n * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  int choice;
+  if (tune_lookup(stencil2d_shape_key(cfg), &choice)) stencil2d_set_tile_choice(cfg, choice);
+  return CS_OK;
+}
+
+void stencil2d_release(Stencil2DConfig* cfg) {
+  if (cfg->d_weights) cudaFree(cfg->d_weights);
+  if (cfg->d_weights_f) cudaFree(cfg->d_weights_f);
+  cfg->d_weights = nullptr;
+  cfg->d_weights_f = nullptr;
+}
+
+int stencil2d_num_tile_choices() { return 2; }
+
+int stencil2d_set_tile_choice(Stencil2DConfig* cfg, int choice) {
+  cfg->tile_rows = choice == 0 ? 32 : 64;
+  return CS_OK;
+}
+
+std::string stencil2d_shape_key(const Stencil2DConfig* cfg) {
+  char buf[160];
+  const int64_t cells = cfg->nx * cfg->ny;
+  const int size_class = cells <= (1 << 16) ? 0 : cells <= (1 << 22) ? 1 : 2;
+  snprintf(buf, sizeof buf, "stencil2d|%s|v%d_e%d.%d.%d.%d_bc%d_s%d|sm%d",
+           cfg->dtype == CS_F32 ? "f32" : "f64", cfg->variant, cfg->left, cfg->right, cfg->top,
+           cfg->bottom, cfg->bc, size_class, num_sms());
+  return buf;
+}
+
+int stencil2d_launch(const Stencil2DConfig* cfg, const void* in, void* out, cudaStream_t s) {
+  if (cfg->nx == 0 || cfg->ny == 0) return CS_OK;
+  return cfg->dtype == CS_F32 ? stencil2d_launch_f32(cfg, in, out, s)
+                              : stencil2d_launch_f64(cfg, in, out, s);
+}
+
+}  // namespace cs

@@ -1,0 +1,107 @@
+"""The C ABI library builds, loads without a GPU and exports every entry point that
+include/custen_gb.h declares; argument validation runs on the host (no kernel is launched)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "custen_gb.h")
+
+
+@pytest.fixture(scope="module")
+def cs():
+    import paper_1902_09931_gb300 as cs
+    cs.load()
+    return cs
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(cs_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ["cs_plan_create_2d", "cs_plan_create_1d_batch", "cs_compute", "cs_swap",
+                 "cs_destroy", "cs_ch_create", "cs_ch_step", "cs_last_error"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(cs):
+    lib = ctypes.CDLL(cs.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert set(declared_functions()) == set(cs.exported_symbols())
+
+
+def test_version_and_counters(cs):
+    assert "sm_103a" in cs.cs_version()
+    assert cs.cs_launch_count() >= 0
+    assert isinstance(cs.cs_last_error(), str)
+
+
+def test_destroy_null_is_noop(cs):
+    assert cs.load().cs_destroy(None) == 0
+
+
+def rc_of(fn, *args):
+    try:
+        fn(*args)
+        return 0
+    except Exception as e:  # CSError
+        return getattr(e, "code", None)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nx=-1),
+    dict(left=-1),
+    dict(left=17),
+    dict(dir=0, top=1),            # X stencil with a y extent
+    dict(dir=1, left=1),           # Y stencil with an x extent
+    dict(bc=7),
+    dict(dtype=3),
+    dict(dir=9),
+])
+def test_invalid_descriptions_rejected_on_host(cs, bad):
+    base = dict(nx=16, ny=16, dir=cs.CS_DIR_XY, bc=cs.CS_BC_PERIODIC, dtype=cs.CS_F64,
+                left=1, right=1, top=1, bottom=1)
+    base.update(bad)
+    nw = max(1, (base["left"] + base["right"] + 1) * (base["top"] + base["bottom"] + 1))
+    d = cs.StencilDesc(**base, weights=[1.0] * nw)
+    assert rc_of(cs.cs_plan_create_2d, d, 4096, 1 << 40) == cs.CS_EINVAL
+
+
+def test_aliasing_rejected_on_host(cs):
+    """Sec. 2: outputs go to a separate buffer; overlapping in/out is refused before any launch."""
+    d = cs.StencilDesc(nx=64, ny=64, dir=cs.CS_DIR_X, bc=cs.CS_BC_PERIODIC, dtype=cs.CS_F64,
+                       left=1, right=1, weights=[1.0, -2.0, 1.0])
+    assert rc_of(cs.cs_plan_create_2d, d, 1 << 30, 1 << 30) == cs.CS_EALIAS
+    assert rc_of(cs.cs_plan_create_2d, d, 1 << 30, (1 << 30) + 8 * 64 * 64 - 8) == cs.CS_EALIAS
+    assert "overlap" in cs.cs_last_error()
+
+
+def test_function_footprint_validated(cs):
+    d = cs.StencilDesc(nx=64, ny=64, dir=cs.CS_DIR_XY, bc=cs.CS_BC_PERIODIC, dtype=cs.CS_F64,
+                       left=2, right=2, top=2, bottom=2, fn=cs.CS_FN_CH_NONLIN_LAP, coe=[1.0])
+    assert rc_of(cs.cs_plan_create_2d, d, 1 << 30, 1 << 32) == cs.CS_EINVAL
+    d = cs.StencilDesc(nx=64, ny=64, dir=cs.CS_DIR_XY, bc=cs.CS_BC_PERIODIC, dtype=cs.CS_F64,
+                       left=1, right=1, top=1, bottom=1, fn=cs.CS_FN_CH_NONLIN_LAP, coe=None)
+    assert rc_of(cs.cs_plan_create_2d, d, 1 << 30, 1 << 32) == cs.CS_EINVAL
+
+
+@pytest.mark.parametrize("n,storage", [(32, 0), (100, 0), (128, 5)])
+def test_ch_description_rejected_on_host(cs, n, storage):
+    d = cs.CHDesc(n=n, storage=storage, D=1.0, gamma=0.01, dt=0.01)
+    assert rc_of(cs.cs_ch_create, d, 1 << 30, 1 << 34, 1 << 36) == cs.CS_EINVAL
+
+
+def test_ch_fields_must_not_overlap(cs):
+    d = cs.CHDesc(n=64, storage=cs.CS_F64, D=1.0, gamma=0.01, dt=0.01)
+    assert rc_of(cs.cs_ch_create, d, 1 << 30, (1 << 30) + 64, 1 << 36) == cs.CS_EALIAS
+
+
+def test_wrong_plan_kind_rejected(cs):
+    assert rc_of(cs.cs_ch_step, None, 1, False, 0) == cs.CS_EINVAL
