@@ -1,0 +1,500 @@
+#!/usr/bin/env python3
+"""Benchmark of the cuSten hot path on GB300 (one JSON line on stdout, rank 0).
+
+Headline workload: the 2D stencil suite on 4096^2 and 8192^2 grids, FP64 and FP32 storage --
+xy 9-point Laplacian, 13-point biharmonic, 4th-order d/dx and d/dy, each periodic and
+non-periodic, plus the user function c^3 - c - Laplacian(c) -- on sums of 8 random-phase sines
+(wavenumbers 1..32) plus 1e-3 uniform noise.  One step = one sweep of every stencil of the
+suite (40 sweeps).  `value` = grid points updated per second over the suite (whole job,
+all ranks).  The L2 (129 MB) is flushed before every sweep, outside the timed kernel intervals.
+
+Other parts of the metric are measured after the timed steps and reported beside it:
+Cahn-Hilliard ADI steps/s (N = 1024, 4096; FP64 and FP32 storage) and the ragged batched-1D
+sweep (65536 lines, log-uniform 64..4096, FP32, persistent launch replayed from a CUDA graph).
+
+--impl reference runs the CPU oracle (the reference arm of this build: a plain FP64 C program)
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "stencil Gpts/s and HBM GB/s vs ~8 TB/s; CH-ADI steps/s; served p50/p99 vs plain"
+WORKLOAD = ("2D stencil suite: nx=ny in {4096, 8192}, FP64 and FP32 storage; xy 9-point "
+            "Laplacian, 13-point biharmonic, 4th-order d/dx and d/dy, periodic and non-periodic, "
+            "plus user function c^3-c-Lap(c) (periodic and non-periodic); A9 sine fields")
+SIZES = (4096, 8192)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s; probe: 1.9 DFMA/clk)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def stencil_suite(h):
+    lap9 = np.array([1, 4, 1, 4, -20, 4, 1, 4, 1.0]) / (6 * h * h)
+    b = np.zeros((5, 5))
+    b[2, 2] = 20
+    b[1, 2] = b[3, 2] = b[2, 1] = b[2, 3] = -8
+    b[1, 1] = b[1, 3] = b[3, 1] = b[3, 3] = 2
+    b[0, 2] = b[4, 2] = b[2, 0] = b[2, 4] = 1
+    d1 = np.array([1, -8, 0, 8, -1.0]) / (12 * h)
+    return [
+        # name, dir, L, R, T, B, weights, fn, coe, nonzero taps
+        ("lap9", 2, 1, 1, 1, 1, lap9, 0, None, 9),
+        ("biharm13", 2, 2, 2, 2, 2, b.ravel() / h ** 4, 0, None, 13),
+        ("ddx4", 0, 2, 2, 0, 0, d1, 0, None, 4),
+        ("ddy4", 1, 0, 0, 2, 2, d1, 0, None, 4),
+        ("cubic_minus_lap", 2, 1, 1, 1, 1, None, 3, [1.0 / (h * h)], 5),
+    ]
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region (clocks and throttle reasons)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_id(torch, local):
+    """nvidia-smi identifier of the GPU this process uses (UUID when torch exposes it)."""
+    try:
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v for v in vis.split(",") if v.strip()]
+        return ids[local] if local < len(ids) else str(local)
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------------------------
+def build_suite(cs, torch, rank, only=None):
+    """Resident fields and one plan per (size, dtype, stencil, bc).  `only` = (name, n, dtype,
+    bc) restricts the suite to one sweep (used to profile one kernel on its own)."""
+    sweeps = []
+    keep = []
+    sizes = SIZES if only is None else (int(only[1]),)
+    for n in sizes:
+        h = 2 * np.pi / n
+        base = W.sines_field(n, seed=1902 + n + 7 * rank)
+        for dtype in (cs.CS_F64, cs.CS_F32):
+            if only is not None and only[2] != ("f64" if dtype == cs.CS_F64 else "f32"):
+                continue
+            tdt = torch.float64 if dtype == cs.CS_F64 else torch.float32
+            d_in = torch.from_numpy(base).to("cuda", tdt)
+            d_out = torch.zeros_like(d_in)
+            keep += [d_in, d_out]
+            eb = 8 if dtype == cs.CS_F64 else 4
+            for name, d, L, R, T, B, w, fn, coe, taps in stencil_suite(h):
+                for bc in (cs.CS_BC_PERIODIC, cs.CS_BC_NONPERIODIC):
+                    if only is not None and (only[0] != name or only[3] != ("p" if bc else "np")):
+                        continue
+                    desc = cs.StencilDesc(nx=n, ny=n, dir=d, bc=bc, dtype=dtype, left=L, right=R, top=T,
+                                          bottom=B, weights=w, fn=fn, coe=coe)
+                    plan = cs.cs_plan_create_2d(desc, d_in, d_out)
+                    sweeps.append(dict(name=name, n=n, dtype="f64" if eb == 8 else "f32", bc="p" if bc else "np",
+                                       plan=plan, points=n * n, bytes=2 * eb * n * n, taps=taps,
+                                       d_in=d_in, d_out=d_out, eb=eb))
+        del base
+    return sweeps, keep
+
+
+def timed_sweeps(cs, torch, sweeps, flush, stream, record):
+    """One step: flush L2, then time each sweep with events on the launch stream."""
+    evs = []
+    for sw in sweeps:
+        flush.add_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cs.cs_compute(sw["plan"], stream)
+        e1.record(stream)
+        evs.append((sw, e0, e1))
+    if record is not None:
+        record.append(evs)
+
+
+def run_ours(args):
+    import torch
+    import paper_1902_09931_gb300 as cs
+    world, rank, local = dist_setup(args)
+    cs.load()
+    hbm_peak, peak_kind = peaks()
+    stream = torch.cuda.current_stream()
+    only = tuple(args.only.split(",")) if args.only else None
+    sweeps, keep = build_suite(cs, torch, rank, only)
+    if not args.no_autotune:
+        for sw in sweeps:  # pick tile shapes with the project's autotuner
+            cs.cs_autotune(sw["plan"], stream)
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    for _ in range(args.warmup):
+        timed_sweeps(cs, torch, sweeps, flush, stream, None)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = Clocks(gpu_id(torch, local))
+    clocks.start()
+    launches0 = cs.cs_launch_count()
+    record = []
+    for _ in range(args.steps):
+        timed_sweeps(cs, torch, sweeps, flush, stream, record)
+    torch.cuda.synchronize()
+    launches = cs.cs_launch_count() - launches0
+    clk = clocks.stop()
+    barrier(world)
+    torch.cuda.synchronize()
+    # per-sweep device times
+    per = {}
+    total_ms = 0.0
+    for evs in record:
+        for sw, e0, e1 in evs:
+            ms = e0.elapsed_time(e1)
+            key = f'{sw["name"]}|{sw["n"]}|{sw["dtype"]}|{sw["bc"]}'
+            per.setdefault(key, []).append(ms)
+            total_ms += ms
+    ms_per_step = max_over_ranks(world, total_ms / args.steps)
+    pts_per_step = sum(sw["points"] for sw in sweeps)
+    bytes_per_step = sum(sw["bytes"] for sw in sweeps)
+    value = world * pts_per_step / (ms_per_step * 1e-3) / 1e9
+    hbm_gbs = world * bytes_per_step / (ms_per_step * 1e-3) / 1e9
+
+    # dominant kernel: largest share of the step
+    shares = {k: statistics.mean(v) for k, v in per.items()}
+    dom_key = max(shares, key=shares.get)
+    dom = [sw for sw in sweeps if f'{sw["name"]}|{sw["n"]}|{sw["dtype"]}|{sw["bc"]}' == dom_key][0]
+    dom_ms = shares[dom_key]
+    if dom["eb"] == 8:  # FP64 arithmetic: bound by the FP64 pipe
+        flops = 2 * dom["taps"] * dom["points"]
+        achieved = flops / (dom_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                "peak_kind": "derived: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz", "kernel": dom_key,
+                "traffic": traffic_for(dom_key)}
+    else:
+        achieved = dom["bytes"] / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "peak_kind": peak_kind, "kernel": dom_key,
+                "traffic": traffic_for(dom_key)}
+
+    # every sweep against the HBM roofline
+    f32 = {}
+    for k, v in shares.items():
+        name, n, dt, bc = k.split("|")
+        sw = [s for s in sweeps if s["name"] == name and s["n"] == int(n) and s["dtype"] == dt and s["bc"] == bc][0]
+        gbs = sw["bytes"] / (v * 1e-3) / 1e9
+        f32[k] = {"ms": round(v, 4), "gpts": round(sw["points"] / (v * 1e-3) / 1e9, 2),
+                  "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 3)}
+
+    e2e = e2e_host(cs, torch, sweeps, stream, max(1, min(args.steps, 2)), world)
+    parts = {}
+    if not args.skip_parts:
+        parts["ch_adi"] = bench_ch(cs, torch, stream)
+        parts["batch1d"] = bench_batch1d(cs, torch, stream, hbm_peak)
+        parts["launches_in_parts"] = True
+    for sw in sweeps:
+        cs.cs_destroy(sw["plan"])
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Gpts/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sweeps_per_step": len(sweeps), "points_per_step": pts_per_step,
+                   "l2": "flushed (256 MB write) before every sweep, outside the timed intervals",
+                   "parallelism": f"replicas x{world} (independent grids per GPU)"},
+        "hbm_gbs": round(hbm_gbs, 1), "hbm_frac_of_measured": round(hbm_gbs / hbm_peak, 4),
+        "hbm_frac_of_8tbs": round(hbm_gbs / 8000.0, 4),
+        "roofline": roof, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
+        "per_sweep": f32, "parts": parts,
+    }
+    if rank == 0 and not args.skip_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def traffic_for(key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        for line in open(path):
+            if line.startswith("#") or not line.strip():
+                continue
+            k, b = line.split()[:2]
+            if k == key:
+                return int(float(b))
+    except OSError:
+        pass
+    return None
+
+
+def e2e_host(cs, torch, sweeps, stream, steps, world):
+    """The suite through cs_compute_host: pinned host input copied in and output copied back
+    every sweep, timed end to end."""
+    host = {}
+    for sw in sweeps:
+        key = (sw["n"], sw["dtype"])
+        if key not in host:
+            host[key] = (sw["d_in"].cpu().pin_memory(), torch.empty(sw["d_out"].shape, dtype=sw["d_out"].dtype).pin_memory())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for sw in sweeps:
+            h_in, h_out = host[(sw["n"], sw["dtype"])]
+            cs.cs_compute_host(sw["plan"], h_in, h_out, stream)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    dt = max_over_ranks(world, dt)
+    pts = sum(sw["points"] for sw in sweeps)
+    nbytes = sum(sw["points"] * sw["eb"] for sw in sweeps)
+    return {"value": round(world * pts * steps / dt / 1e9, 3), "unit": "Gpts/s",
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": steps}
+
+
+def bench_ch(cs, torch, stream):
+    out = {}
+    for n, storage, steps in [(1024, cs.CS_F64, 200), (4096, cs.CS_F64, 30), (1024, cs.CS_F32, 200), (4096, cs.CS_F32, 30)]:
+        h = 2 * np.pi / n
+        tdt = torch.float64 if storage == cs.CS_F64 else torch.float32
+        c0 = torch.from_numpy(W.ch_initial(n, seed=5)).to("cuda", tdt)
+        f = [c0.clone(), c0.clone(), torch.zeros_like(c0)]
+        plan = cs.cs_ch_create(cs.CHDesc(n=n, storage=storage, D=1.0, gamma=0.01, dt=0.1 * h), *f)
+        cs.cs_ch_step(plan, 5, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cs.cs_ch_step(plan, steps, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        chunks, m = cs.cs_ch_config(plan)
+        cs.cs_destroy(plan)
+        key = f"n{n}_{'f64' if storage == cs.CS_F64 else 'f32'}"
+        fp64_ops = ch_fp64_ops_per_point(storage == cs.CS_F64, chunks, m) * n * n
+        out[key] = {"ms_per_step": round(ms, 4), "steps_per_s": round(1e3 / ms, 1),
+                    "fp64_tflops": round(fp64_ops / (ms * 1e-3) / 1e12, 3)}
+    return out
+
+
+def ch_fp64_ops_per_point(rhs_in_fp64: bool, chunks: int, m: int) -> float:
+    """FP64 operations per grid point of one ADI step as the kernels perform them: RHS 16.5
+    (Cbar on the halo-2 tile, Z on the halo-1 tile, the outer Laplacian and combination; done in
+    FP32 for FP32 storage), two sweeps of local LU (5) + spike correction (4) + chunk-end system
+    (16 chunks / m), and the update (2)."""
+    per_sweep = 5 + 4 + 16.0 * chunks / m
+    return (16.5 if rhs_in_fp64 else 0.0) + 2 * per_sweep + 2
+
+
+def bench_batch1d(cs, torch, stream, hbm_peak):
+    off = W.ragged_offsets(65536, seed=2019)
+    x = W.sines_lines(off, seed=2020).astype(np.float32)
+    d_off = torch.from_numpy(off).cuda()
+    d_in = torch.from_numpy(x).cuda()
+    d_out = torch.zeros_like(d_in)
+    w = np.array([-1, 16, -30, 16, -1.0]) / 12.0
+    desc = cs.StencilDesc(dir=cs.CS_DIR_X, bc=cs.CS_BC_PERIODIC, dtype=cs.CS_F32, left=2, right=2, weights=w)
+    plan = cs.cs_plan_create_1d_batch(desc, off.size - 1, d_off, int(off[-1]), d_in, d_out)
+    cs.cs_autotune(plan, stream)
+    cs.cs_plan_use_graph(plan, True)
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    times = []
+    for r in range(12):
+        flush.add_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cs.cs_compute(plan, stream)
+        e1.record(stream)
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = statistics.median([a.elapsed_time(b) for a, b in times[2:]])
+    cs.cs_destroy(plan)
+    total = int(off[-1])
+    nbytes = 8 * total + 8 * off.size
+    return {"lines": off.size - 1, "points": total, "ms": round(ms, 4),
+            "gpts_per_s": round(total / (ms * 1e-3) / 1e9, 2),
+            "hbm_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1), "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / hbm_peak, 3)}
+
+
+# --------------------------------------------------------------------------------------------
+def cpu_sample(seconds: float):
+    """The oracle (single-threaded C) on row bands of the suite's grids: the same stencils,
+    periodic and non-periodic, FP64 arithmetic.  Returns (points, seconds, description)."""
+    import oracle
+    oracle.build()
+    rows = 16
+    pts = 0
+    t_total = 0.0
+    done = 0
+    deadline = time.perf_counter() + seconds
+    while time.perf_counter() < deadline:
+        for n in SIZES:
+            h = 2 * np.pi / n
+            band = W.sines_field(n, seed=1902 + n, ny=rows)
+            for name, d, L, R, T, B, w, fn, coe, taps in stencil_suite(h):
+                for bc in (1, 0):
+                    t0 = time.perf_counter()
+                    if fn:
+                        oracle.stencil2d_fn(band, fn, coe, bc)
+                    else:
+                        oracle.stencil2d(band, w, d, bc, L, R, T, B)
+                    t_total += time.perf_counter() - t0
+                    pts += band.size
+            done += 1
+    desc = (f"oracle (C, 1 thread) on {rows}-row bands of the 4096^2 and 8192^2 grids, all 10 "
+            f"stencil/bc combinations, {done} passes")
+    return pts, t_total, desc
+
+
+def cpu_baseline(seconds: float):
+    pts, t, desc = cpu_sample(seconds)
+    return {"value": round(pts / t / 1e9, 6), "unit": "Gpts/s", "cores": 1, "kind": "oracle",
+            "sample": desc, "seconds": round(t, 2), "host_cores_available": os.cpu_count()}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = max(1.0, args.cpu_seconds / max(1, args.steps))
+    for _ in range(args.warmup):
+        cpu_sample(min(1.0, per_step / 4))
+    tot_pts, tot_t, desc = 0, 0.0, ""
+    for _ in range(args.steps):
+        p, t, desc = cpu_sample(per_step)
+        tot_pts += p
+        tot_t += t
+    value = tot_pts / tot_t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Gpts/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * tot_t / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": desc},
+            "cpu_baseline": {"value": round(value, 6), "unit": "Gpts/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": round(value, 6), "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-parts", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--only", default="", help="profile one sweep: name,n,f64|f32,p|np")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

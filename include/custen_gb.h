@@ -188,6 +188,10 @@ int cs_ch_invariants(cs_plan_t plan, double* mass, double* energy, void* cuda_st
  * steps taken since create. */
 int cs_ch_fields(cs_plan_t plan, void** d_c_prev, void** d_c_cur, int64_t* steps_taken);
 
+/* Line-solve partition of a Cahn-Hilliard plan: every periodic line of n points is split into
+ * *chunks pieces of *chunk_len points (see cs_ch_create); either output may be NULL. */
+int cs_ch_config(cs_plan_t plan, int32_t* chunks, int32_t* chunk_len);
+
 /* ---- diagnostics --------------------------------------------------------------------------- */
 
 /* Description of the last error on the calling host thread ("" if none). */

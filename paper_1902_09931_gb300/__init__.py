@@ -21,7 +21,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 from typing import Optional, Sequence
 
 from . import _build
@@ -100,6 +100,7 @@ _SYMBOLS = {
     "cs_ch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_ch_invariants": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "cs_ch_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)]),
+    "cs_ch_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "cs_last_error": (ctypes.c_char_p, []),
     "cs_launch_count": (ctypes.c_int64, []),
     "cs_version": (ctypes.c_char_p, []),
@@ -256,6 +257,13 @@ def cs_ch_fields(plan):
     p, c, s = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64()
     _check(load().cs_ch_fields(plan, ctypes.byref(p), ctypes.byref(c), ctypes.byref(s)))
     return p.value, c.value, s.value
+
+
+def cs_ch_config(plan):
+    """(chunks per line, chunk length) of the plan's partitioned line solve."""
+    c, m = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().cs_ch_config(plan, ctypes.byref(c), ctypes.byref(m)))
+    return c.value, m.value
 
 
 def cs_last_error() -> str:

@@ -371,4 +371,9 @@ int cs_ch_fields(cs_plan_t p, void** prev, void** cur, int64_t* steps) {
   return ch_fields(p->ch, prev, cur, steps);
 }
 
+int cs_ch_config(cs_plan_t p, int32_t* chunks, int32_t* chunk_len) {
+  if (!p || p->kind != kCahnHilliard) return set_error(CS_EINVAL, "not a Cahn-Hilliard plan");
+  return ch_config(p->ch, chunks, chunk_len);
+}
+
 }  // extern "C"

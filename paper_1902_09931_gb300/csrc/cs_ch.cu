@@ -598,6 +598,12 @@ int ch_fields(CHPlan* p, void** prev, void** cur, int64_t* steps) {
   return CS_OK;
 }
 
+int ch_config(CHPlan* p, int32_t* chunks, int32_t* chunk_len) {
+  if (chunks) *chunks = p->P;
+  if (chunk_len) *chunk_len = p->m;
+  return CS_OK;
+}
+
 void ch_destroy(CHPlan* p) { free_plan(p); }
 
 }  // namespace cs

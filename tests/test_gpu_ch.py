@@ -1,7 +1,7 @@
 """GPU parity of the Cahn-Hilliard ADI step (Sec. 5.1) against the CPU oracle, through the C ABI.
 
 Per-step tolerance.  From an identical state (C^{n-1}, C^n), every stage of the step is held to
-the benchmark spec's 1e-12 relative to the magnitude it works at:
+the 1e-12 relative FP64 bound, taken relative to the magnitude it works at:
     |C_gpu - C_oracle| <= 1e-12 * (max|C^n| + max|RHS| + kappa * max|v|),
 with RHS the x-sweep right-hand side, v = C^{n+1} - Cbar the solve result, and
 kappa = 1 + 16 a the condition number of L = I + a P (its forward error bound); for small grids

@@ -1,6 +1,6 @@
 """GPU parity of the 2D stencil sweep against the CPU oracle, through the C ABI.
 
-Tolerances (the benchmark spec / reading A14): max |gpu - oracle| / (sum |w| * max |in|) <= 1e-12 for
+Tolerances: max |gpu - oracle| / (sum |w| * max |in|) <= 1e-12 for
 FP64 storage and <= 1e-5 for FP32 storage (the oracle reads the same FP32 inputs widened to
 FP64).  Integer-valued data with small-integer weights makes every sum exact in both precisions,
 so the index and halo maps must then match bit for bit.  Non-periodic runs pre-fill the output
@@ -37,7 +37,7 @@ def test_all_stencil_variants_match_oracle(env, dtype, bc, shape):
     field = W.sines_field(nx, seed=nx + ny, ny=ny)
     if dtype == 1:
         field = field.astype(np.float32).astype(np.float64)
-    sentinel = np.full(shape, -3.0e38 if dtype == 1 else -7.5e300)
+    sentinel = np.full(shape, -2.0 ** 120)  # exactly representable in FP32 and FP64
     for name, L, R, T, B, d, w in stencil_cases(h):
         if d == 0 and (T or B):
             continue
@@ -76,7 +76,7 @@ def test_integer_data_bit_exact(env, dtype, bc, n, ext):
 def test_impulse_gives_flipped_stencil(env, dtype):
     cs, torch, orc = env
     L, R, T, B = 2, 1, 0, 3
-    w = np.arange(1, 13, dtype=float)
+    w = np.arange(1, (L + R + 1) * (T + B + 1) + 1, dtype=float)
     u = np.zeros((20, 30))
     u[9, 12] = 1.0
     got = run2d(cs, torch, u, dict(dir=2, bc=1, left=L, right=R, top=T, bottom=B, weights=w), dtype)
@@ -111,7 +111,9 @@ def test_user_functions_match_oracle(env, dtype, fn, bc):
     scale = scale_w * max(1.0, np.abs(field).max() ** 3)
     assert np.abs(got - ref).max() / scale <= TOL[dtype]
     if bc == 0:
-        assert np.all(got[0] == 9.0) and np.all(got[:, -1] == 9.0)
+        assert np.all(got[:, 0] == 9.0) and np.all(got[:, -1] == 9.0)
+        if fn != 1:  # the x-only function writes every row
+            assert np.all(got[0] == 9.0) and np.all(got[-1] == 9.0)
 
 
 def test_paper_example_sec41_on_gpu(env):
