@@ -352,9 +352,11 @@ def e2e_host(cs, torch, sweeps, stream, steps, world):
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": steps}
 
 
-def bench_ch(cs, torch, stream):
+def bench_ch(cs, torch, stream, cases=None):
     out = {}
-    for n, storage, steps in [(1024, cs.CS_F64, 200), (4096, cs.CS_F64, 30), (1024, cs.CS_F32, 200), (4096, cs.CS_F32, 30)]:
+    if cases is None:
+        cases = [(1024, cs.CS_F64, 200), (4096, cs.CS_F64, 30), (1024, cs.CS_F32, 200), (4096, cs.CS_F32, 30)]
+    for n, storage, steps in cases:
         h = 2 * np.pi / n
         tdt = torch.float64 if storage == cs.CS_F64 else torch.float32
         c0 = torch.from_numpy(W.ch_initial(n, seed=5)).to("cuda", tdt)
@@ -476,6 +478,24 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_part(args):
+    """One part of the metric on its own (used to profile it): --part ch:<n>:<f64|f32>:<steps>
+    or --part batch1d."""
+    import torch
+    import paper_1902_09931_gb300 as cs
+    torch.cuda.set_device(0)
+    cs.load()
+    stream = torch.cuda.current_stream()
+    hbm_peak, _ = peaks()
+    kind = args.part.split(":")
+    if kind[0] == "ch":
+        n, dt, steps = int(kind[1]), kind[2], int(kind[3])
+        res = bench_ch(cs, torch, stream, [(n, cs.CS_F64 if dt == "f64" else cs.CS_F32, steps)])
+    else:
+        res = bench_batch1d(cs, torch, stream, hbm_peak)
+    print(json.dumps({"part": args.part, "result": res}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -487,10 +507,13 @@ def main():
     ap.add_argument("--skip-parts", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--only", default="", help="profile one sweep: name,n,f64|f32,p|np")
+    ap.add_argument("--part", default="", help="run one part alone: ch:<n>:<f64|f32>:<steps> or batch1d")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.impl == "reference":
+    if args.part:
+        run_part(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -192,6 +192,27 @@ int cs_ch_fields(cs_plan_t plan, void** d_c_prev, void** d_c_cur, int64_t* steps
  * *chunks pieces of *chunk_len points (see cs_ch_create); either output may be NULL. */
 int cs_ch_config(cs_plan_t plan, int32_t* chunks, int32_t* chunk_len);
 
+/* Allocation-free batched 1D sweep.  The paper has no counterpart: this entry point exists for
+ * callers that cannot let a library allocate device memory -- code running under a fixed
+ * device-memory budget or inside an arena owned by another runtime, latency-critical loops that
+ * cannot afford an allocation or its implicit synchronisation, and plain C callers that only
+ * hand over buffers they already own.  It computes exactly what cs_plan_create_1d_batch +
+ * cs_compute compute (same arguments, same layout), without a plan and without calling
+ * cudaMalloc / cudaFree or any allocating routine.
+ *   Its scratch (the line-lookup table, one int32 per 64 packed elements) lives in a fixed
+ *   file-scope device array created when the library is loaded; every GPU that loads the
+ *   library holds it (4 MiB + 256 B) until the process exits.  total_len is limited to
+ *   2^26 = 67,108,864 elements; larger requests return CS_EINVAL (use a plan instead).
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *   that device current; make that first call before any stream capture.
+ *   Every call shares the array and overwrites it: calls that overlap on the GPU (different
+ *   streams, or host threads) race and must be serialised by the caller.
+ *   The offsets are validated on the device first (the call synchronises the stream once to
+ *   read the result); invalid offsets return CS_EINVAL and leave d_out untouched. */
+int cs_batch1d_compute_noalloc(const cs_stencil_desc* desc, int64_t num_lines,
+                               const int64_t* d_offsets, int64_t total_len, const void* d_in,
+                               void* d_out, void* cuda_stream);
+
 /* ---- diagnostics --------------------------------------------------------------------------- */
 
 /* Description of the last error on the calling host thread ("" if none). */

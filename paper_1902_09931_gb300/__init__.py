@@ -101,6 +101,7 @@ _SYMBOLS = {
     "cs_ch_invariants": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "cs_ch_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)]),
     "cs_ch_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "cs_batch1d_compute_noalloc": (ctypes.c_int, [ctypes.POINTER(_CStencilDesc), ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_last_error": (ctypes.c_char_p, []),
     "cs_launch_count": (ctypes.c_int64, []),
     "cs_version": (ctypes.c_char_p, []),
@@ -264,6 +265,14 @@ def cs_ch_config(plan):
     c, m = ctypes.c_int32(), ctypes.c_int32()
     _check(load().cs_ch_config(plan, ctypes.byref(c), ctypes.byref(m)))
     return c.value, m.value
+
+
+def cs_batch1d_compute_noalloc(desc: StencilDesc, num_lines: int, d_offsets, total_len: int, d_in,
+                               d_out, stream=None) -> None:
+    """Batched 1D sweep without a plan and without any device allocation (see the header)."""
+    c, _keep = _desc(desc)
+    _check(load().cs_batch1d_compute_noalloc(ctypes.byref(c), int(num_lines), _ptr(d_offsets),
+                                             int(total_len), _ptr(d_in), _ptr(d_out), _stream(stream)))
 
 
 def cs_last_error() -> str:

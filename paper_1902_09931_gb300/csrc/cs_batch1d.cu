@@ -11,7 +11,9 @@
 // containing it (built once at create time), so the lookup is at most a short binary search.
 // Lanes whose stencil crosses a line end take a slow path with per-element wrapped loads.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
+#include <cstring>
 
 #include "cs_internal.h"
 
@@ -231,3 +233,122 @@ int batch1d_launch(const Batch1DConfig* c, const void* in, void* out, cudaStream
 }
 
 }  // namespace cs
+
+// ---- allocation-free entry point --------------------------------------------------------------
+// Some callers cannot let a library call cudaMalloc: code that runs under a fixed device-memory
+// budget or an arena owned by another runtime, latency-critical loops where an allocation (and
+// its implicit synchronisation) is not acceptable, or plain C callers that only hand over
+// buffers they already own.  cs_batch1d_compute_noalloc serves them: it runs the batched 1D
+// sweep with the line-lookup table kept in the file-scope array below instead of in a plan's
+// cudaMalloc'ed workspace.  The array is created when the library is loaded and every GPU that
+// loads the library holds it (4 MiB + 256 B) until the process exits.
+
+namespace cs {
+namespace {
+
+constexpr int64_t kNoAllocTableEntries = int64_t(1) << 20;                     // line-table entries
+constexpr int64_t kNoAllocMaxLen = kNoAllocTableEntries << kSegShift;         // 2^26 elements
+constexpr int64_t kNoAllocStatusSlot = kNoAllocTableEntries;                  // validation flag
+
+// Line table (one entry per 64 packed elements) followed by a 64-entry tail whose first word is
+// the offsets-validation flag.  Shared by every call in the process.
+static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocTableEntries + 64];
+
+// Device address of g_noalloc_scratch, looked up once per device (the host-side name is only a
+// stand-in for the symbol, not a device pointer).
+std::atomic<int32_t*> g_noalloc_addr[64];
+
+__global__ void k_check_offsets(const int64_t* __restrict__ off, int64_t num_lines, int64_t total,
+                                int32_t* __restrict__ status) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t m = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; m < num_lines; m += stride)
+    if (off[m] > off[m + 1]) atomicOr(status, 1);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (off[0] != 0 || off[num_lines] != total)) atomicOr(status, 2);
+}
+
+int noalloc_scratch(int32_t** out) {
+  int dev = 0;
+  CS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_error(CS_EUNSUPPORTED, "device index %d out of range", dev);
+  int32_t* p = g_noalloc_addr[dev].load();
+  if (!p) {
+    void* addr = nullptr;
+    CS_CUDA_TRY(cudaGetSymbolAddress(&addr, g_noalloc_scratch));
+    p = static_cast<int32_t*>(addr);
+    g_noalloc_addr[dev].store(p);
+  }
+  *out = p;
+  return CS_OK;
+}
+
+}  // namespace
+
+}  // namespace cs
+
+extern "C" int cs_batch1d_compute_noalloc(const cs_stencil_desc* d, int64_t num_lines,
+                                          const int64_t* d_offsets, int64_t total_len,
+                                          const void* d_in, void* d_out, void* stream) {
+  using namespace cs;
+  if (!d) return set_error(CS_EINVAL, "null stencil description");
+  if (d->dtype != CS_F64 && d->dtype != CS_F32) return set_error(CS_EINVAL, "dtype must be CS_F64 or CS_F32");
+  if (d->bc != CS_BC_PERIODIC && d->bc != CS_BC_NONPERIODIC) return set_error(CS_EINVAL, "bc must be periodic or non-periodic");
+  if (d->dir != CS_DIR_X || d->top != 0 || d->bottom != 0 || d->fn != CS_FN_NONE || !d->weights)
+    return set_error(CS_EINVAL, "batched 1D lines take a weighted X stencil");
+  if (d->left < 0 || d->right < 0 || d->left > CS_MAX_EXTENT || d->right > CS_MAX_EXTENT)
+    return set_error(CS_EINVAL, "stencil extents must be in [0, %d]", CS_MAX_EXTENT);
+  if (num_lines < 0 || total_len < 0 || num_lines > 0x7fffffff)
+    return set_error(CS_EINVAL, "num_lines, total_len out of range");
+  if (total_len > kNoAllocMaxLen)
+    return set_error(CS_EINVAL, "cs_batch1d_compute_noalloc: total_len %lld exceeds the fixed maximum %lld (use a plan)",
+                     (long long)total_len, (long long)kNoAllocMaxLen);
+  if (total_len > 0 && num_lines == 0) return set_error(CS_EINVAL, "elements without lines");
+  if (!d_offsets) return set_error(CS_EINVAL, "null offsets");
+  if (total_len == 0) return CS_OK;
+  const size_t eb = d->dtype == CS_F32 ? 4 : 8;
+  if (!d_in || !d_out) return set_error(CS_EINVAL, "null device buffer");
+  if (reinterpret_cast<uintptr_t>(d_in) % eb || reinterpret_cast<uintptr_t>(d_out) % eb)
+    return set_error(CS_EINVAL, "buffers must be aligned to the element size");
+  {
+    const char* a = static_cast<const char*>(d_in);
+    const char* b = static_cast<const char*>(d_out);
+    const size_t bytes = static_cast<size_t>(total_len) * eb;
+    if (a < b + bytes && b < a + bytes) return set_error(CS_EALIAS, "input and output buffers overlap");
+  }
+  int32_t* scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc != CS_OK) return rc;
+  int32_t* status = scratch + kNoAllocStatusSlot;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the array keeps the previous call's contents: clear the flag, then validate the offsets
+  CS_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+  const int64_t check_blocks = std::min<int64_t>((num_lines + 255) / 256, 1024);
+  k_check_offsets<<<static_cast<unsigned>(std::max<int64_t>(check_blocks, 1)), 256, 0, st>>>(d_offsets, num_lines, total_len, status);
+  CS_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  int32_t h_status = 0;
+  CS_CUDA_TRY(cudaMemcpyAsync(&h_status, status, sizeof h_status, cudaMemcpyDeviceToHost, st));
+  CS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h_status != 0)
+    return set_error(CS_EINVAL, "offsets must start at 0, end at total_len and be non-decreasing");
+  Batch1DConfig c;
+  memset(&c, 0, sizeof c);
+  c.num_lines = num_lines;
+  c.total_len = total_len;
+  c.bc = d->bc;
+  c.dtype = d->dtype;
+  c.left = d->left;
+  c.right = d->right;
+  for (int i = 0; i < d->left + d->right + 1; ++i) c.weights[i] = d->weights[i];
+  c.d_offsets = d_offsets;
+  c.d_seg_line = scratch;
+  c.num_table = ((total_len - 1) >> kSegShift) + 1;
+  c.choice = 1;
+  int choice;
+  if (tune_lookup(batch1d_shape_key(&c), &choice) && choice >= 0 && choice < kNumShapes) c.choice = choice;
+  const int threads = 256;
+  k_build_seg_table<<<static_cast<unsigned>((c.num_table + threads - 1) / threads), threads, 0, st>>>(
+      d_offsets, num_lines, c.num_table, scratch);
+  CS_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return batch1d_launch(&c, d_in, d_out, st);
+}
