@@ -108,7 +108,7 @@ int cs_plan_create_2d(cs_plan_t* plan, const cs_stencil_desc* desc, const void* 
  * occupies elements [offsets[m], offsets[m+1]) of the packed buffers.  desc->dir must be
  * CS_DIR_X (top = bottom = 0); a periodic stencil wraps at each line's own length.
  *   d_offsets  device array of num_lines + 1 int64 values, non-decreasing, offsets[0] = 0,
- *              offsets[num_lines] = total_len.  Read at create time (the library builds its
+ *              offsets[num_lines] = total_len, every line shorter than 2^31 elements.  Read at create time (the library builds its
  *              load-balancing table from it) and by every compute; must stay alive.
  *   total_len  number of packed elements. */
 int cs_plan_create_1d_batch(cs_plan_t* plan, const cs_stencil_desc* desc, int64_t num_lines,
@@ -128,6 +128,15 @@ int cs_compute_host(cs_plan_t plan, const void* h_in, void* h_out, void* cuda_st
 /* Swap (Sec. 3): exchanges the bound input and output buffers so the next Compute reads what
  * the last one wrote. */
 int cs_swap(cs_plan_t plan);
+
+/* Arithmetic used for CS_F64 stencils.  CS_FP64_AUTO (default) evaluates the specialised
+ * stencils in double-float arithmetic (each value an unevaluated sum of two floats, products
+ * and sums error-free on the FP32 pipes, one FP64 rounding at the end), which keeps the error
+ * below ~2^-46 of sum|w| * max|in| and falls back to native FP64 for any tile whose values lie
+ * outside [2^-70, 2^60) or whose largest value is below 2^-30, and for weights outside
+ * [2^-60, 2^50).  CS_FP64_NATIVE always uses FP64 instructions.  CS_F32 plans ignore this. */
+typedef enum { CS_FP64_AUTO = 0, CS_FP64_NATIVE = 1 } cs_fp64_mode;
+int cs_plan_set_fp64_mode(cs_plan_t plan, int32_t mode);
 
 /* Rebinds the device buffers of a stencil plan without re-planning (same sizes and dtype). */
 int cs_set_buffers(cs_plan_t plan, const void* d_in, void* d_out);

@@ -31,6 +31,7 @@ CS_DIR_X, CS_DIR_Y, CS_DIR_XY = 0, 1, 2
 CS_BC_NONPERIODIC, CS_BC_PERIODIC = 0, 1
 CS_F64, CS_F32 = 0, 1
 CS_FN_NONE, CS_FN_CENTRAL_D2X, CS_FN_CH_NONLIN_LAP, CS_FN_CUBIC_MINUS_LAP = 0, 1, 2, 3
+CS_FP64_AUTO, CS_FP64_NATIVE = 0, 1
 CS_MAX_EXTENT = 16
 
 LIB_PATH = _build.LIB
@@ -92,6 +93,7 @@ _SYMBOLS = {
     "cs_swap": (ctypes.c_int, [ctypes.c_void_p]),
     "cs_set_buffers": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_plan_use_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "cs_plan_set_fp64_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "cs_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "cs_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
     "cs_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
@@ -203,6 +205,10 @@ def cs_swap(plan) -> None:
 
 def cs_set_buffers(plan, d_in, d_out) -> None:
     _check(load().cs_set_buffers(plan, _ptr(d_in), _ptr(d_out)))
+
+
+def cs_plan_set_fp64_mode(plan, mode: int) -> None:
+    _check(load().cs_plan_set_fp64_mode(plan, int(mode)))
 
 
 def cs_plan_use_graph(plan, enable: bool = True) -> None:

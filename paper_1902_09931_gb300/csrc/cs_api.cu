@@ -199,6 +199,7 @@ int cs_plan_create_1d_batch(cs_plan_t* plan, const cs_stencil_desc* d, int64_t n
       return set_error(CS_EINVAL, "offsets must start at 0 and end at total_len");
     for (int64_t m = 0; m < num_lines; ++m)
       if (h[m + 1] < h[m]) return set_error(CS_EINVAL, "offsets must be non-decreasing (line %lld)", (long long)m);
+      else if (h[m + 1] - h[m] > 0x7fffffff) return set_error(CS_EINVAL, "line %lld is longer than 2^31-1", (long long)m);
   }
   cs_plan* p = new_plan(kBatch1D);
   if (!p) return set_error(CS_ENOMEM, "out of host memory");
@@ -286,6 +287,14 @@ int cs_set_buffers(cs_plan_t p, const void* d_in, void* d_out) {
   return CS_OK;
 }
 
+int cs_plan_set_fp64_mode(cs_plan_t p, int32_t mode) {
+  if (!p || p->kind != kStencil2D) return set_error(CS_EINVAL, "not a 2D stencil plan");
+  if (mode != CS_FP64_AUTO && mode != CS_FP64_NATIVE) return set_error(CS_EINVAL, "unknown FP64 mode %d", mode);
+  p->s2.fp64_mode = mode;
+  drop_graph(p);
+  return CS_OK;
+}
+
 int cs_plan_use_graph(cs_plan_t p, int enable) {
   if (!p) return set_error(CS_EINVAL, "null plan");
   if (p->kind == kCahnHilliard) return set_error(CS_EUNSUPPORTED, "graph replay is for stencil plans");
@@ -311,6 +320,10 @@ int cs_autotune(cs_plan_t p, void* stream) {
     if (p->kind == kStencil2D) stencil2d_set_tile_choice(&p->s2, c);
     else p->b1.choice = c;
     rc = launch_direct(p, s);  // warm-up
+    if (rc == CS_EUNSUPPORTED) {  // this candidate cannot run on this device: skip it
+      rc = CS_OK;
+      continue;
+    }
     if (rc != CS_OK) break;
     cudaEventRecord(e0, s);
     for (int r = 0; r < reps && rc == CS_OK; ++r) rc = launch_direct(p, s);
@@ -324,6 +337,7 @@ int cs_autotune(cs_plan_t p, void* stream) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != CS_OK) return rc;
+  if (best < 0) return set_error(CS_EUNSUPPORTED, "no launch shape of this plan runs on this device");
   if (p->kind == kStencil2D) {
     stencil2d_set_tile_choice(&p->s2, best);
     tune_store(stencil2d_shape_key(&p->s2), best);

@@ -29,7 +29,7 @@ template <> struct Vec1<double> { static constexpr int n = 2; using V = double2;
 template <typename T> struct BTaps { T w[2 * CS_MAX_EXTENT + 1]; };
 
 struct LaunchShape { int threads, ctas_per_sm; };
-constexpr LaunchShape kShapes[] = {{256, 4}, {256, 8}, {512, 4}, {128, 16}, {1024, 2}};
+constexpr LaunchShape kShapes[] = {{256, 4}, {256, 8}, {512, 2}, {128, 8}, {512, 1}, {256, 2}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 __global__ void k_build_seg_table(const int64_t* __restrict__ off, int64_t num_lines,
@@ -61,6 +61,97 @@ __device__ __forceinline__ int64_t find_line(int64_t k, const int64_t* __restric
   return lo;
 }
 
+// One warp segment: own values v (already loaded), neighbours by shuffle, the line lookup, and
+// the weighted sum (fast path) or per-element wrapped loads (lanes at a line end).
+template <typename T, int LL, int RR>
+__device__ __forceinline__ void segment(const T* __restrict__ in, T* __restrict__ out,
+                                        const int64_t* __restrict__ off,
+                                        const int32_t* __restrict__ seg, int64_t ntab,
+                                        int64_t total, int64_t num_lines, int periodic, int L,
+                                        int R, bool vec_ok, const BTaps<T>& taps, int64_t k0,
+                                        const T (&v)[Vec1<T>::n]) {
+  constexpr int V = Vec1<T>::n;
+  using VT = typename Vec1<T>::V;
+  const int W = L + R + 1;
+  const bool shuffle_ok = L <= V && R <= V;
+  const int lane = threadIdx.x & 31;
+  // window[0 .. 3V): values at k0 - V .. k0 + 2V - 1 (valid where inside the same line)
+  T win[3 * V];
+#pragma unroll
+  for (int e = 0; e < V; ++e) {
+    win[e] = __shfl_up_sync(0xffffffffu, v[e], 1);
+    win[V + e] = v[e];
+    win[2 * V + e] = __shfl_down_sync(0xffffffffu, v[e], 1);
+  }
+  if (k0 >= total) return;
+  if (lane == 0) {
+#pragma unroll
+    for (int e = 0; e < V; ++e) win[e] = (k0 - V + e >= 0) ? in[k0 - V + e] : T(0);
+  }
+  if (lane == 31) {
+#pragma unroll
+    for (int e = 0; e < V; ++e) win[2 * V + e] = (k0 + V + e < total) ? in[k0 + V + e] : T(0);
+  }
+  int64_t m = find_line(k0, off, seg, ntab, num_lines);
+  int64_t ls = __ldg(off + m), le = __ldg(off + m + 1);
+  const bool fast = shuffle_ok && k0 + V <= total && k0 - L >= ls && k0 + V - 1 + R < le;
+  if (fast) {
+    T res[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      T acc = T(0);
+      if constexpr (LL >= 0 && RR >= 0) {
+#pragma unroll
+        for (int p = 0; p < LL + RR + 1; ++p) acc = fma(taps.w[p], win[V + e - LL + p], acc);
+      } else {
+        for (int p = 0; p < W; ++p) acc = fma(taps.w[p], win[V + e - L + p], acc);
+      }
+      res[e] = acc;
+    }
+    if (vec_ok) {
+      VT y;
+      if constexpr (V == 4) { y.x = res[0]; y.y = res[1]; y.z = res[2]; y.w = res[3]; }
+      else { y.x = res[0]; y.y = res[1]; }
+      *reinterpret_cast<VT*>(out + k0) = y;
+    } else {
+#pragma unroll
+      for (int e = 0; e < V; ++e) out[k0 + e] = res[e];
+    }
+  } else {
+    for (int e = 0; e < V; ++e) {
+      const int64_t k = k0 + e;
+      if (k >= total) break;
+      while (k >= le) {  // advance to the line holding k (skips empty lines)
+        ++m;
+        ls = le;
+        le = __ldg(off + m + 1);
+      }
+      const int64_t len = le - ls;
+      if (!periodic && (k - ls < L || le - 1 - k < R)) continue;  // boundary cell untouched
+      const int rel0 = static_cast<int>(k - ls) - L;  // lines hold < 2^31 elements
+      const int ilen = static_cast<int>(len);
+      T acc = T(0);
+      if (ilen >= L && ilen >= R) {  // at most one wrap: a compare instead of a division
+        for (int p = 0; p < W; ++p) {
+          int rel = rel0 + p;
+          rel = rel < 0 ? rel + ilen : (rel >= ilen ? rel - ilen : rel);
+          acc = fma(taps.w[p], __ldg(in + ls + rel), acc);
+        }
+      } else {
+        for (int p = 0; p < W; ++p) {
+          int rel = (rel0 + p) % ilen;
+          if (rel < 0) rel += ilen;
+          acc = fma(taps.w[p], __ldg(in + ls + rel), acc);
+        }
+      }
+      out[k] = acc;
+    }
+  }
+}
+
+// Each warp takes kG consecutive segments per iteration and issues all their loads first.
+constexpr int kG = 4;
+
 template <typename T, int LL, int RR>
 __global__ void k_batch1d(const T* __restrict__ in, T* __restrict__ out,
                           const int64_t* __restrict__ off, const int32_t* __restrict__ seg,
@@ -70,89 +161,31 @@ __global__ void k_batch1d(const T* __restrict__ in, T* __restrict__ out,
   using VT = typename Vec1<T>::V;
   const int L = LL >= 0 ? LL : Lr;
   const int R = RR >= 0 ? RR : Rr;
-  const int W = L + R + 1;
-  const bool shuffle_ok = L <= V && R <= V;
   const int lane = threadIdx.x & 31;
   const int64_t warp_id = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
   constexpr int64_t kSeg = 32 * V;
   const int64_t nseg = (total + kSeg - 1) / kSeg;
 
-  for (int64_t s = warp_id; s < nseg; s += nwarps) {  // warp-uniform loop
-    const int64_t k0 = s * kSeg + lane * V;
-    T v[V];
-    if (vec_ok && k0 + V <= total) {
-      const VT x = *reinterpret_cast<const VT*>(in + k0);
-      if constexpr (V == 4) { v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w; }
-      else { v[0] = x.x; v[1] = x.y; }
-    } else {
+  for (int64_t s0 = warp_id * kG; s0 < nseg; s0 += nwarps * kG) {  // warp-uniform loop
+    T v[kG][V];
 #pragma unroll
-      for (int e = 0; e < V; ++e) v[e] = (k0 + e < total) ? in[k0 + e] : T(0);
-    }
-    // window[0 .. 3V): values at k0 - V .. k0 + 2V - 1 (valid where inside the same line)
-    T win[3 * V];
-#pragma unroll
-    for (int e = 0; e < V; ++e) {
-      win[e] = __shfl_up_sync(0xffffffffu, v[e], 1);
-      win[V + e] = v[e];
-      win[2 * V + e] = __shfl_down_sync(0xffffffffu, v[e], 1);
-    }
-    if (k0 >= total) continue;
-    if (lane == 0) {
-#pragma unroll
-      for (int e = 0; e < V; ++e) win[e] = (k0 - V + e >= 0) ? in[k0 - V + e] : T(0);
-    }
-    if (lane == 31) {
-#pragma unroll
-      for (int e = 0; e < V; ++e) win[2 * V + e] = (k0 + V + e < total) ? in[k0 + V + e] : T(0);
-    }
-    int64_t m = find_line(k0, off, seg, ntab, num_lines);
-    int64_t ls = __ldg(off + m), le = __ldg(off + m + 1);
-    const bool fast = shuffle_ok && k0 + V <= total && k0 - L >= ls && k0 + V - 1 + R < le;
-    if (fast) {
-      T res[V];
-#pragma unroll
-      for (int e = 0; e < V; ++e) {
-        T acc = T(0);
-        if constexpr (LL >= 0 && RR >= 0) {
-#pragma unroll
-          for (int p = 0; p < LL + RR + 1; ++p) acc = fma(taps.w[p], win[V + e - LL + p], acc);
-        } else {
-          for (int p = 0; p < W; ++p) acc = fma(taps.w[p], win[V + e - L + p], acc);
-        }
-        res[e] = acc;
-      }
-      if (vec_ok) {
-        VT y;
-        if constexpr (V == 4) { y.x = res[0]; y.y = res[1]; y.z = res[2]; y.w = res[3]; }
-        else { y.x = res[0]; y.y = res[1]; }
-        *reinterpret_cast<VT*>(out + k0) = y;
+    for (int g = 0; g < kG; ++g) {
+      const int64_t k0 = (s0 + g) * kSeg + lane * V;
+      if (vec_ok && k0 + V <= total) {
+        const VT x = *reinterpret_cast<const VT*>(in + k0);
+        if constexpr (V == 4) { v[g][0] = x.x; v[g][1] = x.y; v[g][2] = x.z; v[g][3] = x.w; }
+        else { v[g][0] = x.x; v[g][1] = x.y; }
       } else {
 #pragma unroll
-        for (int e = 0; e < V; ++e) out[k0 + e] = res[e];
+        for (int e = 0; e < V; ++e) v[g][e] = (k0 + e < total) ? in[k0 + e] : T(0);
       }
-    } else {
-      for (int e = 0; e < V; ++e) {
-        const int64_t k = k0 + e;
-        if (k >= total) break;
-        while (k >= le) {  // advance to the line holding k (skips empty lines)
-          ++m;
-          ls = le;
-          le = __ldg(off + m + 1);
-        }
-        const int64_t len = le - ls;
-        if (!periodic && (k - ls < L || le - 1 - k < R)) continue;  // boundary cell untouched
-        T acc = T(0);
-        for (int p = 0; p < W; ++p) {
-          int64_t rel = k - ls - L + p;
-          if (periodic) {
-            rel %= len;
-            if (rel < 0) rel += len;
-          }
-          acc = fma(taps.w[p], __ldg(in + ls + rel), acc);
-        }
-        out[k] = acc;
-      }
+    }
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+      if (s0 + g >= nseg) break;  // warp-uniform
+      segment<T, LL, RR>(in, out, off, seg, ntab, total, num_lines, periodic, L, R, vec_ok != 0,
+                         taps, (s0 + g) * kSeg + lane * V, v[g]);
     }
   }
 }
@@ -171,8 +204,13 @@ int launch_t(const Batch1DConfig* c, const void* vin, void* vout, cudaStream_t s
   const int64_t seg_elems = 32 * Vec1<T>::n;
   const int64_t nseg = (c->total_len + seg_elems - 1) / seg_elems;
   const int64_t warps_per_cta = sh.threads / 32;
-  int64_t grid = std::min<int64_t>((nseg + warps_per_cta - 1) / warps_per_cta,
-                                   static_cast<int64_t>(num_sms()) * sh.ctas_per_sm);
+  int resident = 0;  // persistent grid: never more CTAs than can be resident at once
+  CS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_batch1d<T, LL, RR>, sh.threads, 0));
+  if (resident < 1)
+    return set_error(CS_EUNSUPPORTED, "batched 1D launch shape %d x %d does not fit on an SM", sh.threads, sh.ctas_per_sm);
+  const int per_sm = std::min(sh.ctas_per_sm, resident);
+  int64_t grid = std::min<int64_t>((nseg + warps_per_cta * kG - 1) / (warps_per_cta * kG),
+                                   static_cast<int64_t>(num_sms()) * per_sm);
   grid = std::max<int64_t>(grid, 1);
   k_batch1d<T, LL, RR><<<static_cast<unsigned>(grid), sh.threads, 0, st>>>(
       in, out, c->d_offsets, c->d_seg_line, c->num_table, c->total_len, c->num_lines,

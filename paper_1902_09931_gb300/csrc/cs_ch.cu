@@ -196,8 +196,11 @@ __global__ void k_reduce_final(const double* __restrict__ partials, int nblocks,
 }
 
 // Phase 1: A g = b on chunk p of a line (LU forward then backward), g over the scratch.
-// Coefficients (negated / pre-scaled): nl1, nl2, dinv, nu1, nu2 at coef[0..5m).
-template <typename IT>
+// Coefficients (negated / pre-scaled): nl1, nl2, dinv, nu1, nu2 at coef[0..5m).  Elements are
+// processed in register batches of kU so that a batch's loads are in flight together.
+constexpr int kU = 8;
+
+template <typename IT, bool CONTIG>
 __global__ void __launch_bounds__(kSolveThreads)
     k_solve_local(const IT* __restrict__ in, double* __restrict__ G, double* __restrict__ bnd,
                   const double* __restrict__ coef, int64_t n, int P, int m, int64_t line_stride,
@@ -206,74 +209,112 @@ __global__ void __launch_bounds__(kSolveThreads)
   if (t >= n * P) return;
   const int64_t line = t % n;
   const int p = static_cast<int>(t / n);
+  const int64_t es = CONTIG ? 1 : elem_stride;
   const double* nl1 = coef;
   const double* nl2 = coef + m;
   const double* dinv = coef + 2 * m;
   const double* nu1 = coef + 3 * m;
   const double* nu2 = coef + 4 * m;
-  const int64_t base = line * line_stride + static_cast<int64_t>(p) * m * elem_stride;
+  const int64_t base = line * line_stride + static_cast<int64_t>(p) * m * es;
   double y1 = 0.0, y2 = 0.0;
-  for (int k = 0; k < m; ++k) {
-    const int64_t at = base + k * elem_stride;
-    const double y = fma(__ldg(nl1 + k), y1, fma(__ldg(nl2 + k), y2, widen(in[at])));
-    G[at] = y;
-    y2 = y1;
-    y1 = y;
+  for (int k0 = 0; k0 < m; k0 += kU) {
+    double v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) v[u] = widen(in[base + (k0 + u) * es]);
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const double y = fma(__ldg(nl1 + k0 + u), y1, fma(__ldg(nl2 + k0 + u), y2, v[u]));
+      v[u] = y;
+      y2 = y1;
+      y1 = y;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) G[base + (k0 + u) * es] = v[u];
   }
-  double g1 = 0.0, g2 = 0.0;
-  for (int k = m - 1; k >= 0; --k) {
-    const int64_t at = base + k * elem_stride;
-    const double g = fma(__ldg(nu1 + k), g1, fma(__ldg(nu2 + k), g2, G[at] * __ldg(dinv + k)));
-    G[at] = g;
-    g2 = g1;
-    g1 = g;
+  double g1 = 0.0, g2 = 0.0, g_last = 0.0, g_last2 = 0.0;
+  for (int k0 = m - kU; k0 >= 0; k0 -= kU) {
+    double v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) v[u] = G[base + (k0 + u) * es];
+#pragma unroll
+    for (int u = kU - 1; u >= 0; --u) {
+      const int k = k0 + u;
+      const double g = fma(__ldg(nu1 + k), g1, fma(__ldg(nu2 + k), g2, v[u] * __ldg(dinv + k)));
+      v[u] = g;
+      g2 = g1;
+      g1 = g;
+    }
+    if (k0 == m - kU) {
+      g_last2 = v[kU - 2];
+      g_last = v[kU - 1];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) G[base + (k0 + u) * es] = v[u];
   }
-  // chunk-end values: k = 0, 1 are g1, g2 after the loop; k = m-2, m-1 re-read
+  // chunk-end values: k = 0, 1 are g1, g2 after the loop; k = m-2, m-1 kept from the first batch
   double* b = bnd + static_cast<int64_t>(p) * 4 * n + line;
   b[0] = g1;
   b[n] = g2;
-  b[2 * n] = G[base + (m - 2) * elem_stride];
-  b[3 * n] = G[base + (m - 1) * elem_stride];
+  b[2 * n] = g_last2;
+  b[3 * n] = g_last;
 }
 
-// Phase 2: end values of the neighbouring chunks from the block-circulant inverse, then the
-// spike correction.  MODE 0 writes w (FP64); MODE 1 writes C^{n+1} = 2 C^n - C^{n-1} + x.
-template <int MODE, typename T>
+// Phase 2: end values of the neighbouring chunks from the block-circulant inverse (staged in
+// shared memory), then the spike correction.  MODE 0 writes w (FP64); MODE 1 writes
+// C^{n+1} = 2 C^n - C^{n-1} + x.
+template <int MODE, typename T, bool CONTIG>
 __global__ void __launch_bounds__(kSolveThreads)
     k_solve_correct(const double* __restrict__ G, const double* __restrict__ bnd,
                     const double* __restrict__ coef, const double* __restrict__ K, int64_t n, int P,
                     int m, int64_t line_stride, int64_t elem_stride, double* __restrict__ w_out,
                     const T* __restrict__ cur, const T* __restrict__ prev, T* __restrict__ next) {
+  extern __shared__ double sK[];
+  for (int i = threadIdx.x; i < 16 * P; i += blockDim.x) sK[i] = K[i];
+  __syncthreads();
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= n * P) return;
   const int64_t line = t % n;
   const int p = static_cast<int>(t / n);
+  const int64_t es = CONTIG ? 1 : elem_stride;
   const int pm = (p + P - 1) % P, pp = (p + 1) % P;
   double t0 = 0.0, t1 = 0.0, h0 = 0.0, h1 = 0.0;
   for (int q = 0; q < P; ++q) {
     const double* b = bnd + static_cast<int64_t>(q) * 4 * n + line;
     const double g0 = b[0], g1 = b[n], g2 = b[2 * n], g3 = b[3 * n];
-    const double* Kt = K + ((pm - q + P) % P) * 16;  // K_{(p-1)-q}: rows 2, 3 give t_{p-1}
-    const double* Kh = K + ((pp - q + P) % P) * 16;  // K_{(p+1)-q}: rows 0, 1 give h_{p+1}
-    t0 = fma(__ldg(Kt + 8), g0, fma(__ldg(Kt + 9), g1, fma(__ldg(Kt + 10), g2, fma(__ldg(Kt + 11), g3, t0))));
-    t1 = fma(__ldg(Kt + 12), g0, fma(__ldg(Kt + 13), g1, fma(__ldg(Kt + 14), g2, fma(__ldg(Kt + 15), g3, t1))));
-    h0 = fma(__ldg(Kh + 0), g0, fma(__ldg(Kh + 1), g1, fma(__ldg(Kh + 2), g2, fma(__ldg(Kh + 3), g3, h0))));
-    h1 = fma(__ldg(Kh + 4), g0, fma(__ldg(Kh + 5), g1, fma(__ldg(Kh + 6), g2, fma(__ldg(Kh + 7), g3, h1))));
+    const double* Kt = sK + ((pm - q + P) % P) * 16;  // K_{(p-1)-q}: rows 2, 3 give t_{p-1}
+    const double* Kh = sK + ((pp - q + P) % P) * 16;  // K_{(p+1)-q}: rows 0, 1 give h_{p+1}
+    t0 = fma(Kt[8], g0, fma(Kt[9], g1, fma(Kt[10], g2, fma(Kt[11], g3, t0))));
+    t1 = fma(Kt[12], g0, fma(Kt[13], g1, fma(Kt[14], g2, fma(Kt[15], g3, t1))));
+    h0 = fma(Kh[0], g0, fma(Kh[1], g1, fma(Kh[2], g2, fma(Kh[3], g3, h0))));
+    h1 = fma(Kh[4], g0, fma(Kh[5], g1, fma(Kh[6], g2, fma(Kh[7], g3, h1))));
   }
   const double* sl0 = coef + 5 * m;
   const double* sl1 = coef + 6 * m;
   const double* sr0 = coef + 7 * m;
   const double* sr1 = coef + 8 * m;
-  const int64_t base = line * line_stride + static_cast<int64_t>(p) * m * elem_stride;
-  for (int k = 0; k < m; ++k) {
-    const int64_t at = base + k * elem_stride;
-    const double x = fma(-__ldg(sl0 + k), t0, fma(-__ldg(sl1 + k), t1,
-                     fma(-__ldg(sr0 + k), h0, fma(-__ldg(sr1 + k), h1, G[at]))));
+  const int64_t base = line * line_stride + static_cast<int64_t>(p) * m * es;
+  for (int k0 = 0; k0 < m; k0 += kU) {
+    double x[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) x[u] = G[base + (k0 + u) * es];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int k = k0 + u;
+      x[u] = fma(-__ldg(sl0 + k), t0, fma(-__ldg(sl1 + k), t1,
+             fma(-__ldg(sr0 + k), h0, fma(-__ldg(sr1 + k), h1, x[u]))));
+    }
     if constexpr (MODE == 0) {
-      w_out[at] = x;
+#pragma unroll
+      for (int u = 0; u < kU; ++u) w_out[base + (k0 + u) * es] = x[u];
     } else {
-      const double cb = fma(2.0, widen(cur[at]), -widen(prev[at]));
-      store_as<T>(next + at, cb + x);
+      double c[kU], pv[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        c[u] = widen(cur[base + (k0 + u) * es]);
+        pv[u] = widen(prev[base + (k0 + u) * es]);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) store_as<T>(next + base + (k0 + u) * es, fma(2.0, c[u], -pv[u]) + x[u]);
     }
   }
 }
@@ -387,10 +428,16 @@ int build_tables(int64_t n, int P, double a, std::vector<double>& coef, std::vec
   return CS_OK;
 }
 
+// Valid partition: P divides n, chunks of at least 16 points in whole register batches.
+bool valid_chunks(int64_t n, int P) {
+  return P >= 1 && P <= 64 && n % P == 0 && (n / P) >= 16 && (n / P) % kU == 0;
+}
+
 int default_chunks(int64_t n) {
-  // enough independent (line, chunk) threads to cover the GPU, chunks of at least 64 points
+  // enough independent (line, chunk) threads to fill the GPU, while the chunk-end system
+  // (16 P^2 / n FP64 operations per point) stays at most 4 per point
   int P = 1;
-  while (n * P < 16384 && n / (2 * P) >= 64 && 2 * P <= 64) P *= 2;
+  while (n * P < 65536 && valid_chunks(n, 2 * P) && 16.0 * (2 * P) * (2 * P) / n <= 4.0) P *= 2;
   return P;
 }
 
@@ -431,15 +478,16 @@ int launch_step(CHPlan* p, double* partials, cudaStream_t s) {
   if (rc != CS_OK) return rc;
   const int64_t n = p->n;
   const unsigned sgrid = static_cast<unsigned>((n * p->P + kSolveThreads - 1) / kSolveThreads);
+  const size_t ksmem = static_cast<size_t>(16) * p->P * sizeof(double);
   // x-sweep: lines are rows (line stride n, element stride 1)
-  k_solve_local<T><<<sgrid, kSolveThreads, 0, s>>>(reinterpret_cast<const T*>(p->A), p->B, p->bnd,
-                                                   p->coef, n, p->P, p->m, n, 1);
-  k_solve_correct<0, T><<<sgrid, kSolveThreads, 0, s>>>(p->B, p->bnd, p->coef, p->K, n, p->P, p->m,
-                                                        n, 1, p->A, nullptr, nullptr, nullptr);
+  k_solve_local<T, true><<<sgrid, kSolveThreads, 0, s>>>(reinterpret_cast<const T*>(p->A), p->B, p->bnd,
+                                                         p->coef, n, p->P, p->m, n, 1);
+  k_solve_correct<0, T, true><<<sgrid, kSolveThreads, ksmem, s>>>(p->B, p->bnd, p->coef, p->K, n, p->P,
+                                                                  p->m, n, 1, p->A, nullptr, nullptr, nullptr);
   // y-sweep: lines are columns (line stride 1, element stride n), update fused
-  k_solve_local<double><<<sgrid, kSolveThreads, 0, s>>>(p->A, p->B, p->bnd, p->coef, n, p->P,
-                                                        p->m, 1, n);
-  k_solve_correct<1, T><<<sgrid, kSolveThreads, 0, s>>>(
+  k_solve_local<double, false><<<sgrid, kSolveThreads, 0, s>>>(p->A, p->B, p->bnd, p->coef, n, p->P,
+                                                               p->m, 1, n);
+  k_solve_correct<1, T, false><<<sgrid, kSolveThreads, ksmem, s>>>(
       p->B, p->bnd, p->coef, p->K, n, p->P, p->m, 1, n, nullptr,
       static_cast<const T*>(p->field[p->icur]), static_cast<const T*>(p->field[p->iprev]),
       static_cast<T*>(p->field[p->inext]));
@@ -509,7 +557,7 @@ int ch_create(CHPlan** out, const cs_ch_desc* d, void* prev, void* cur, void* ne
   int choice;
   char key[96];
   snprintf(key, sizeof key, "ch|%s|n%lld|sm%d", d->storage == CS_F32 ? "f32" : "f64", (long long)d->n, num_sms());
-  if (tune_lookup(key, &choice) && choice >= 1 && choice <= 64 && d->n % choice == 0 && d->n / choice >= 16) P = choice;
+  if (tune_lookup(key, &choice) && valid_chunks(d->n, choice)) P = choice;
   p->P = P;
   p->m = static_cast<int>(d->n / P);
   p->field[0] = prev; p->field[1] = cur; p->field[2] = next;

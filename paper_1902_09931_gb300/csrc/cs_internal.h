@@ -41,6 +41,8 @@ struct Stencil2DConfig {
   int tile_rows;   // TY
   double* d_weights;  // device copy for the generic kernel (library-owned), FP64
   float* d_weights_f; // FP32 copy
+  int dd_ok;          // weights fit the double-float path (FP64 storage)
+  int fp64_mode;      // CS_FP64_AUTO or CS_FP64_NATIVE
 };
 int stencil2d_prepare(Stencil2DConfig* cfg);  // picks variant, allocates generic weights
 void stencil2d_release(Stencil2DConfig* cfg);

@@ -1,5 +1,6 @@
 // Host side of the 2D stencil: validation helpers, functor mapping (Sec. 4.2, Sec. 5.2),
 // choice of the specialised kernel and tile shape, and dispatch by storage type.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 
@@ -81,6 +82,18 @@ int stencil2d_prepare(Stencil2DConfig* cfg) {
     for (size_t i = 0; i < n; ++i) wf[i] = static_cast<float>(cfg->weights[i]);
     CS_CUDA_TRY(cudaMemcpy(cfg->d_weights, cfg->weights, n * sizeof(double), cudaMemcpyHostToDevice));
     CS_CUDA_TRY(cudaMemcpy(cfg->d_weights_f, wf, n * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  // double-float eligibility: every non-zero weight in [2^-60, 2^50), at least one non-zero
+  {
+    const int nw = (cfg->fn != CS_FN_NONE) ? 9 : W * H;
+    bool any = false, fits = true;
+    for (int i = 0; i < nw; ++i) {
+      const double a = fabs(cfg->weights[i]);
+      if (a == 0.0) continue;
+      any = true;
+      if (!(a >= 0x1p-60 && a < 0x1p50)) fits = false;
+    }
+    cfg->dd_ok = any && fits;
   }
   int choice;
   if (tune_lookup(stencil2d_shape_key(cfg), &choice)) stencil2d_set_tile_choice(cfg, choice);

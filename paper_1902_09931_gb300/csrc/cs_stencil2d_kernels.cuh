@@ -136,27 +136,20 @@ __device__ __forceinline__ void xform_tile(T* s, int n) {
   __syncthreads();
 }
 
+// Compute phase of the specialised kernels in the storage type: each thread owns one column
+// of the tile and walks down its rows with a register window; `s` is the staged tile.
 template <typename T, int TY, int SPEC>
-__global__ void __launch_bounds__(kThreads)
-    k_stencil2d_spec(const T* __restrict__ in, T* __restrict__ out, int64_t nx, int64_t ny,
-                     int periodic, int vec_ok, Taps<T> taps) {
+__device__ __forceinline__ void spec_compute(const T* s, T* __restrict__ out, int64_t nx,
+                                             int64_t ny, int periodic, int64_t x0, int64_t y0,
+                                             const Taps<T>& taps) {
   constexpr SpecDesc sd = kSpecs[SPEC];
   constexpr int L = sd.L, R = sd.R, TT = sd.T, BB = sd.B;
   constexpr int V = Vec<T>::n;
   constexpr int TX = tile_x<T>();
   constexpr int LA = (L + V - 1) / V * V, RA = (R + V - 1) / V * V;
-  constexpr int COLS = LA + TX + RA, ROWS = TY + TT + BB;
+  constexpr int COLS = LA + TX + RA;
   constexpr int W = L + R + 1, H = TT + BB + 1;
   constexpr int WX = TX / 32, WY = 8 / WX, RW = TY / WY;
-  static_assert(W * H <= 32, "tap table too small");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* s = reinterpret_cast<T*>(smem_raw);
-
-  const int64_t x0 = static_cast<int64_t>(blockIdx.x) * TX;
-  const int64_t y0 = static_cast<int64_t>(blockIdx.y) * TY;
-  load_tile<T>(s, in, nx, ny, periodic != 0, vec_ok != 0, x0, y0, TT, LA, COLS, ROWS);
-  if constexpr (sd.xform) xform_tile<T>(s, ROWS * COLS);
-
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = (warp % WX) * 32 + lane;
   const int r0 = (warp / WX) * RW;
@@ -187,6 +180,215 @@ __global__ void __launch_bounds__(kThreads)
     if constexpr (sd.epi) acc = cubic_minus(win[TT][L]) + acc;
     const int64_t gy = y0 + r0 + k;
     if (col_ok && gy < ny && (periodic || (gy >= TT && gy < ny - BB))) out[gy * nx + gx] = acc;
+  }
+}
+
+template <typename T, int TY, int SPEC>
+__global__ void __launch_bounds__(kThreads)
+    k_stencil2d_spec(const T* __restrict__ in, T* __restrict__ out, int64_t nx, int64_t ny,
+                     int periodic, int vec_ok, Taps<T> taps) {
+  constexpr SpecDesc sd = kSpecs[SPEC];
+  constexpr int V = Vec<T>::n;
+  constexpr int TX = tile_x<T>();
+  constexpr int LA = (sd.L + V - 1) / V * V, RA = (sd.R + V - 1) / V * V;
+  constexpr int COLS = LA + TX + RA, ROWS = TY + sd.T + sd.B;
+  static_assert((sd.L + sd.R + 1) * (sd.T + sd.B + 1) <= 32, "tap table too small");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  const int64_t x0 = static_cast<int64_t>(blockIdx.x) * TX;
+  const int64_t y0 = static_cast<int64_t>(blockIdx.y) * TY;
+  load_tile<T>(s, in, nx, ny, periodic != 0, vec_ok != 0, x0, y0, sd.T, LA, COLS, ROWS);
+  if constexpr (sd.xform) xform_tile<T>(s, ROWS * COLS);
+  spec_compute<T, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
+}
+
+template <typename T>
+inline size_t tile_smem_bytes(int L, int R, int TT, int BB, int TY, bool generic) {
+  constexpr int V = Vec<T>::n;
+  const int LA = (L + V - 1) / V * V, RA = (R + V - 1) / V * V;
+  size_t b = sizeof(T) * static_cast<size_t>(TY + TT + BB) * (LA + tile_x<T>() + RA);
+  if (generic) b += sizeof(T) * static_cast<size_t>((L + R + 1) * (TT + BB + 1));
+  return b;
+}
+
+// ---- double-float evaluation of FP64-storage stencils ---------------------------------------
+// GB300 issues FP64 at 2 DFMA/clk/SM against ~128 FP32 ops/clk/SM, so FP64-storage sweeps are
+// evaluated in double-float arithmetic (Dekker 1971: a value is an unevaluated sum hi + lo of
+// two floats) on the FP32 pipes.  Every element is split with integer operations (the
+// f64 -> f32 conversion instruction itself runs on the FP64 pipe); each tap adds the exact
+// product of the split weight and value (FMA error term) into an error-free TwoSum
+// accumulator; the result is hi + lo rounded once to FP64.  The error is below ~2^-46 of
+// sum|w| * max|in|.  A tile whose values leave the safe exponent range (or whose largest value
+// is tiny) is evaluated in native FP64 instead, so results stay correct for every input.
+
+struct DDTaps { float hi[32], lo[32]; };
+
+constexpr int kDDMinExp = 1023 - 70;   // smallest biased exponent split on the fast path
+constexpr int kDDMaxExp = 1023 + 60;   // first biased exponent that is not
+constexpr int kDDTileExp = 1023 - 30;  // a tile's largest value must reach 2^-30 (or be 0)
+
+// x = hi + lo: hi is x truncated to 24 significant bits, lo the remainder rounded to 24 bits.
+// Returns false outside the fast exponent range; ebias = biased exponent (0 for +-0).
+__device__ __forceinline__ bool dd_split(double x, float& hi, float& lo, int& ebias) {
+  const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x));
+  const uint32_t top = static_cast<uint32_t>(b >> 32);
+  const uint32_t sign = top & 0x80000000u;
+  const int e = static_cast<int>((top >> 20) & 0x7ffu);
+  if ((b << 1) == 0) {
+    hi = __uint_as_float(sign);
+    lo = 0.0f;
+    ebias = 0;
+    return true;
+  }
+  ebias = e;
+  if (e < kDDMinExp || e >= kDDMaxExp) return false;
+  const uint64_t mant = b & 0xFFFFFFFFFFFFFull;
+  hi = __uint_as_float(sign | (static_cast<uint32_t>(e - 1023 + 127) << 23) | static_cast<uint32_t>(mant >> 29));
+  const uint32_t rem = static_cast<uint32_t>(mant & 0x1FFFFFFFu);            // 29 low bits
+  const float scale = __uint_as_float(static_cast<uint32_t>(e - 1075 + 127) << 23);  // 2^(e-1075)
+  lo = __fmul_rn(__uint2float_rn(rem), scale);
+  lo = __uint_as_float(__float_as_uint(lo) | sign);
+  return true;
+}
+
+// Exact float -> double on the integer pipe.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) {
+    if ((b & 0x7fffffffu) == 0u) return __longlong_as_double(static_cast<long long>(b & 0x80000000u) << 32);
+    return static_cast<double>(f);  // subnormal / inf / nan: rare
+  }
+  const uint64_t d = (static_cast<uint64_t>(b & 0x80000000u) << 32) | (static_cast<uint64_t>(e + 896u) << 52) |
+                     (static_cast<uint64_t>(b & 0x7fffffu) << 29);
+  return __longlong_as_double(static_cast<long long>(d));
+}
+
+// (sh, sl) += (wh + wl) * (xh + xl); the wl * xl term (~2^-48 relative) is dropped.
+__device__ __forceinline__ void dd_mac(float& sh, float& sl, float wh, float wl, float xh, float xl) {
+  const float p = __fmul_rn(wh, xh);
+  float e = __fmaf_rn(wh, xh, -p);  // exact: wh * xh = p + e
+  e = __fmaf_rn(wh, xl, e);
+  e = __fmaf_rn(wl, xh, e);
+  const float s = __fadd_rn(sh, p);  // TwoSum(sh, p) = s + err exactly
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+  sh = s;
+}
+
+template <int TY, int SPEC>
+__device__ __forceinline__ void dd_compute(const float2* sf, const double* s, double* __restrict__ out,
+                                           int64_t nx, int64_t ny, int periodic, int64_t x0,
+                                           int64_t y0, const DDTaps& taps) {
+  constexpr SpecDesc sd = kSpecs[SPEC];
+  constexpr int L = sd.L, R = sd.R, TT = sd.T, BB = sd.B;
+  constexpr int V = Vec<double>::n;
+  constexpr int TX = tile_x<double>();
+  constexpr int LA = (L + V - 1) / V * V, RA = (R + V - 1) / V * V;
+  constexpr int COLS = LA + TX + RA;
+  constexpr int W = L + R + 1, H = TT + BB + 1;
+  constexpr int WX = TX / 32, WY = 8 / WX, RW = TY / WY;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = (warp % WX) * 32 + lane;
+  const int r0 = (warp / WX) * RW;
+  const int64_t gx = x0 + c;
+  const bool col_ok = gx < nx && (periodic || (gx >= L && gx < nx - R));
+  const float2* sc = sf + LA + c - L;
+  const double* dc = s + LA + c - L;
+  float2 win[H][W];
+#pragma unroll
+  for (int q = 0; q < H - 1; ++q)
+#pragma unroll
+    for (int p = 0; p < W; ++p) win[q + 1][p] = sc[(r0 + q) * COLS + p];
+#pragma unroll
+  for (int k = 0; k < RW; ++k) {
+#pragma unroll
+    for (int q = 0; q < H - 1; ++q)
+#pragma unroll
+      for (int p = 0; p < W; ++p) win[q][p] = win[q + 1][p];
+#pragma unroll
+    for (int p = 0; p < W; ++p) win[H - 1][p] = sc[(r0 + k + H - 1) * COLS + p];
+    float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+    for (int q = 0; q < H; ++q)
+#pragma unroll
+      for (int p = 0; p < W; ++p)
+        if ((sd.mask >> (q * W + p)) & 1u)
+          dd_mac(sh, sl, taps.hi[q * W + p], taps.lo[q * W + p], win[q][p].x, win[q][p].y);
+    double acc = f2d_exact(sh) + f2d_exact(sl);
+    if constexpr (sd.epi) acc = cubic_minus(dc[(r0 + k + TT) * COLS + L]) + acc;
+    const int64_t gy = y0 + r0 + k;
+    if (col_ok && gy < ny && (periodic || (gy >= TT && gy < ny - BB))) out[gy * nx + gx] = acc;
+  }
+}
+
+template <int TY, int SPEC>
+__global__ void __launch_bounds__(kThreads)
+    k_stencil2d_dd(const double* __restrict__ in, double* __restrict__ out, int64_t nx, int64_t ny,
+                   int periodic, int vec_ok, Taps<double> taps, DDTaps dtaps) {
+  constexpr SpecDesc sd = kSpecs[SPEC];
+  constexpr int V = Vec<double>::n;
+  constexpr int TX = tile_x<double>();
+  constexpr int LA = (sd.L + V - 1) / V * V, RA = (sd.R + V - 1) / V * V;
+  constexpr int COLS = LA + TX + RA, ROWS = TY + sd.T + sd.B;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* s = reinterpret_cast<double*>(smem_raw);
+  float2* sf = reinterpret_cast<float2*>(s + ROWS * COLS);
+  __shared__ int s_maxe;
+  if (threadIdx.x == 0) s_maxe = 0;
+  const int64_t x0 = static_cast<int64_t>(blockIdx.x) * TX;
+  const int64_t y0 = static_cast<int64_t>(blockIdx.y) * TY;
+  load_tile<double>(s, in, nx, ny, periodic != 0, vec_ok != 0, x0, y0, sd.T, LA, COLS, ROWS);
+  if constexpr (sd.xform) xform_tile<double>(s, ROWS * COLS);
+  bool ok = true;
+  int maxe = 0;
+  for (int i = threadIdx.x; i < ROWS * COLS; i += kThreads) {
+    float h, l;
+    int e;
+    ok = dd_split(s[i], h, l, e) && ok;
+    maxe = max(maxe, e);
+    sf[i] = make_float2(h, l);
+  }
+  for (int off = 16; off > 0; off >>= 1) maxe = max(maxe, __shfl_xor_sync(0xffffffffu, maxe, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(&s_maxe, maxe);
+  const bool all_ok = __syncthreads_and(ok);
+  if (all_ok && (s_maxe == 0 || s_maxe >= kDDTileExp))
+    dd_compute<TY, SPEC>(sf, s, out, nx, ny, periodic, x0, y0, dtaps);
+  else
+    spec_compute<double, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
+}
+
+template <int TY, int SPEC>
+int launch_dd(const double* in, double* out, int64_t nx, int64_t ny, int periodic, int vec_ok,
+              const Taps<double>& taps, const DDTaps& dtaps, cudaStream_t st) {
+  constexpr SpecDesc sd = kSpecs[SPEC];
+  const size_t smem = 2 * tile_smem_bytes<double>(sd.L, sd.R, sd.T, sd.B, TY, false);
+  auto kern = k_stencil2d_dd<TY, SPEC>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    CS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    attr_set = true;
+  }
+  dim3 grid(static_cast<unsigned>((nx + tile_x<double>() - 1) / tile_x<double>()),
+            static_cast<unsigned>((ny + TY - 1) / TY));
+  kern<<<grid, kThreads, smem, st>>>(in, out, nx, ny, periodic, vec_ok, taps, dtaps);
+  CS_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return CS_OK;
+}
+
+template <int TY>
+int dispatch_dd(int variant, const double* in, double* out, int64_t nx, int64_t ny, int periodic,
+                int vec_ok, const Taps<double>& taps, const DDTaps& dtaps, cudaStream_t st) {
+  switch (variant) {
+#define CS_DD_CASE(I) \
+  case I: return launch_dd<TY, I>(in, out, nx, ny, periodic, vec_ok, taps, dtaps, st);
+    CS_DD_CASE(0) CS_DD_CASE(1) CS_DD_CASE(2) CS_DD_CASE(3) CS_DD_CASE(4)
+    CS_DD_CASE(5) CS_DD_CASE(6) CS_DD_CASE(7) CS_DD_CASE(8) CS_DD_CASE(9)
+    CS_DD_CASE(10) CS_DD_CASE(11) CS_DD_CASE(12) CS_DD_CASE(13)
+#undef CS_DD_CASE
+    default: return set_error(CS_EINVAL, "internal: unknown stencil variant %d", variant);
   }
 }
 
@@ -231,14 +433,6 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-template <typename T>
-inline size_t tile_smem_bytes(int L, int R, int TT, int BB, int TY, bool generic) {
-  constexpr int V = Vec<T>::n;
-  const int LA = (L + V - 1) / V * V, RA = (R + V - 1) / V * V;
-  size_t b = sizeof(T) * static_cast<size_t>(TY + TT + BB) * (LA + tile_x<T>() + RA);
-  if (generic) b += sizeof(T) * static_cast<size_t>((L + R + 1) * (TT + BB + 1));
-  return b;
-}
 
 template <typename T, int TY, int SPEC>
 int launch_spec(const T* in, T* out, int64_t nx, int64_t ny, int periodic, int vec_ok,
@@ -309,6 +503,19 @@ int launch_stencil2d_t(const Stencil2DConfig* cfg, const void* vin, void* vout, 
     const SpecDesc& sd = kSpecs[cfg->variant];
     const int nt = (sd.L + sd.R + 1) * (sd.T + sd.B + 1);
     for (int i = 0; i < 32; ++i) taps.w[i] = i < nt ? static_cast<T>(cfg->weights[i]) : T(0);
+    if constexpr (sizeof(T) == 8) {
+      if (cfg->dd_ok && cfg->fp64_mode == CS_FP64_AUTO) {
+        DDTaps dt;
+        for (int i = 0; i < 32; ++i) {
+          const double w = i < nt ? cfg->weights[i] : 0.0;
+          dt.hi[i] = static_cast<float>(w);
+          dt.lo[i] = static_cast<float>(w - static_cast<double>(dt.hi[i]));
+        }
+        if (cfg->tile_rows == 32)
+          return dispatch_dd<32>(cfg->variant, in, out, cfg->nx, cfg->ny, periodic, vec_ok, taps, dt, st);
+        return dispatch_dd<64>(cfg->variant, in, out, cfg->nx, cfg->ny, periodic, vec_ok, taps, dt, st);
+      }
+    }
     if (cfg->tile_rows == 32)
       return dispatch_spec<T, 32>(cfg->variant, in, out, cfg->nx, cfg->ny, periodic, vec_ok, taps, st);
     return dispatch_spec<T, 64>(cfg->variant, in, out, cfg->nx, cfg->ny, periodic, vec_ok, taps, st);

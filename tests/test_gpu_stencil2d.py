@@ -54,6 +54,54 @@ def test_all_stencil_variants_match_oracle(env, dtype, bc, shape):
             assert err <= TOL[dtype], (name, err)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_fp64_double_float_and_native_match_oracle(env, mode, bc):
+    """FP64 storage in both arithmetic modes (double-float on the FP32 pipes, native FP64) on
+    every specialised stencil, against the oracle at the FP64 tolerance."""
+    cs, torch, orc = env
+    ny, nx = 150, 260
+    h = 2 * np.pi / nx
+    field = W.sines_field(nx, seed=17, ny=ny)
+    for name, L, R, T, B, d, w in stencil_cases(h):
+        kw = dict(dir=d, bc=bc, left=L, right=R, top=T, bottom=B, weights=w)
+        got = run2d(cs, torch, field, kw, 0, fp64_mode=mode)
+        ref = orc.stencil2d(field, w, d, bc, L, R, T, B)
+        written = np.zeros(field.shape, bool)
+        written[T:ny - B, L:nx - R] = True
+        if bc == 1:
+            written[:] = True
+        assert scaled_err(got[written], ref[written], w, field) <= 1e-12, (name, mode)
+
+
+@pytest.mark.parametrize("case", ["huge", "tiny", "subnormal", "tiny_tile", "weights"])
+def test_double_float_falls_back_outside_its_range(env, case):
+    """Tiles holding values outside the double-float range, tiles whose values are all tiny,
+    and weights outside the range are computed exactly as in native FP64."""
+    cs, torch, orc = env
+    ny, nx = 140, 200
+    h = 2 * np.pi / nx
+    field = W.sines_field(nx, seed=23, ny=ny)
+    w = biharm13(h)
+    if case == "huge":
+        field[70, 100] = 3.0e25
+    elif case == "tiny":
+        field[10:20, 10:20] *= 1e-30
+    elif case == "subnormal":
+        field[5, 5] = 4.9e-320
+    elif case == "tiny_tile":
+        field[:64, :64] = W.uniform_field(64, 64, seed=2) * 1e-12
+    else:
+        w = w * 1e-25
+    kw = dict(dir=2, bc=1, left=2, right=2, top=2, bottom=2, weights=w)
+    got = run2d(cs, torch, field, kw, 0)
+    ref = orc.stencil2d(field, w, 2, 1, 2, 2, 2, 2)
+    if case == "tiny_tile":  # judge the tiny tile on its own scale
+        blk = (slice(2, 62), slice(2, 62))
+        assert scaled_err(got[blk], ref[blk], w, field[:64, :64]) <= 1e-12
+    assert scaled_err(got, ref, w, field) <= 1e-12
+
+
 @pytest.mark.parametrize("dtype", [0, 1])
 @pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 16, 17, 64, 255])
