@@ -307,7 +307,7 @@ def run_ours(args):
     if not args.skip_parts:
         parts["ch_adi"] = bench_ch(cs, torch, stream)
         parts["batch1d"] = bench_batch1d(cs, torch, stream, hbm_peak)
-        parts["launches_in_parts"] = True
+        parts["serve"] = bench_serve(cs, torch)
     for sw in sweeps:
         cs.cs_destroy(sw["plan"])
     line = {
@@ -394,6 +394,31 @@ def bench_ch(cs, torch, stream, cases=None):
         fp64_ops = ch_fp64_ops_per_point(storage == cs.CS_F64, chunks, m) * n * n
         out[key] = {"ms_per_step": round(ms, 4), "steps_per_s": round(1e3 / ms, 1),
                     "fp64_tflops": round(fp64_ops / (ms * 1e-3) / 1e12, 3)}
+    return out
+
+
+def bench_serve(cs, torch, factors=(0.5, 0.9, 1.5), count=120, seed=2026):
+    """Poisson stream of mixed jobs (2D sweeps and 10-step FP32 Cahn-Hilliard advances, grids
+    128^2..4096^2), continuous batching vs sequential plain calls at arrival rates that are
+    fractions of the sequential capacity (1 / mean service time, measured back to back)."""
+    from paper_1902_09931_gb300 import serving as S
+    be = S.GpuBackend(cs, torch, streams=8, keep_outputs=False)
+    be.warmup(S.SIZES, copies=3)
+    calib = S.poisson_jobs(count, rate=0.0, seed=seed)  # all at t = 0: back to back
+    S.run_sequential(be, calib[:20])  # warm-up
+    seq0 = S.run_sequential(be, calib)
+    capacity = seq0["jobs"] / seq0["span_s"]
+    out = {"capacity_jobs_per_s": round(capacity, 1), "jobs_per_run": count,
+           "mix": "50% sweeps (lap9/biharm13/ddx4/ddy4), 50% 10-step CH advances, FP32, n in 128..4096"}
+    for f in factors:
+        rate = f * capacity
+        a = S.poisson_jobs(count, rate=rate, seed=seed + 1)
+        b = S.poisson_jobs(count, rate=rate, seed=seed + 1)
+        srv = S.Server(be, max_inflight=12).run(a)
+        seq = S.run_sequential(be, b)
+        keep = ("p50_ms", "p99_ms", "jobs_per_s", "gpts_per_s")
+        out[f"load_{f}"] = {"server": {k: round(srv[k], 3) for k in keep} | {"launches": srv["launches"]},
+                            "sequential": {k: round(seq[k], 3) for k in keep}}
     return out
 
 
@@ -509,6 +534,8 @@ def run_part(args):
     if kind[0] == "ch":
         n, dt, steps = int(kind[1]), kind[2], int(kind[3])
         res = bench_ch(cs, torch, stream, [(n, cs.CS_F64 if dt == "f64" else cs.CS_F32, steps)])
+    elif kind[0] == "serve":
+        res = bench_serve(cs, torch)
     else:
         res = bench_batch1d(cs, torch, stream, hbm_peak)
     print(json.dumps({"part": args.part, "result": res}), flush=True)

@@ -118,6 +118,14 @@ int cs_plan_create_1d_batch(cs_plan_t* plan, const cs_stencil_desc* desc, int64_
 /* Compute (Sec. 3): applies the stencil, d_in -> d_out, stream-ordered and asynchronous. */
 int cs_compute(cs_plan_t plan, void* cuda_stream);
 
+/* Grouped Compute: applies `count` 2D stencil plans -- independent grids of any sizes -- in as
+ * few kernel launches as possible (one launch per 16 plans).  The plans must share dtype,
+ * stencil shape (left/right/top/bottom and the non-zero tap pattern, i.e. the same specialised
+ * kernel) and tile shape; CS_EINVAL otherwise, CS_EUNSUPPORTED for plans on the generic
+ * kernel.  Storage-type arithmetic (FP64 plans use native FP64 here).  Used by the serving
+ * loop to batch small sweeps.  Stream-ordered and asynchronous. */
+int cs_compute_group(const cs_plan_t* plans, int32_t count, void* cuda_stream);
+
 /* Compute with host buffers (Sec. 3's HOST flag): copies h_in (host, the full input field)
  * into the plan's device input, computes, and copies the device output back into h_out.
  * Either pointer may be NULL to skip that copy.  Pinned host memory gives overlap-free full
@@ -196,6 +204,11 @@ int cs_ch_invariants(cs_plan_t plan, double* mass, double* energy, void* cuda_st
 /* Current device pointers of C^{n-1} and C^n (either output may be NULL), and the number of
  * steps taken since create. */
 int cs_ch_fields(cs_plan_t plan, void** d_c_prev, void** d_c_cur, int64_t* steps_taken);
+
+/* Rebinds a Cahn-Hilliard plan to three other caller-owned n x n fields (same meaning as in
+ * cs_ch_create; the step count restarts at 0).  Lets a caller keep a plan -- and its device
+ * workspace -- for many runs of the same grid size without allocating again. */
+int cs_ch_set_fields(cs_plan_t plan, void* d_c_prev, void* d_c_cur, void* d_c_next);
 
 /* Line-solve partition of a Cahn-Hilliard plan: every periodic line of n points is split into
  * *chunks pieces of *chunk_len points (see cs_ch_create); either output may be NULL. */

@@ -90,6 +90,7 @@ _SYMBOLS = {
     "cs_plan_create_1d_batch": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_CStencilDesc), ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_compute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "cs_compute_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "cs_compute_group": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.c_void_p]),
     "cs_swap": (ctypes.c_int, [ctypes.c_void_p]),
     "cs_set_buffers": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_plan_use_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
@@ -102,6 +103,7 @@ _SYMBOLS = {
     "cs_ch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_ch_invariants": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "cs_ch_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)]),
+    "cs_ch_set_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_ch_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "cs_batch1d_compute_noalloc": (ctypes.c_int, [ctypes.POINTER(_CStencilDesc), ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_last_error": (ctypes.c_char_p, []),
@@ -195,6 +197,12 @@ def cs_compute(plan, stream=None) -> None:
     _check(load().cs_compute(plan, _stream(stream)))
 
 
+def cs_compute_group(plans, stream=None) -> None:
+    """One grouped launch (per 16 plans) over several 2D stencil plans of the same shape."""
+    arr = (ctypes.c_void_p * len(plans))(*[p.value if hasattr(p, "value") else p for p in plans])
+    _check(load().cs_compute_group(arr, len(plans), _stream(stream)))
+
+
 def cs_compute_host(plan, h_in, h_out, stream=None) -> None:
     _check(load().cs_compute_host(plan, _ptr(h_in), _ptr(h_out), _stream(stream)))
 
@@ -264,6 +272,10 @@ def cs_ch_fields(plan):
     p, c, s = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64()
     _check(load().cs_ch_fields(plan, ctypes.byref(p), ctypes.byref(c), ctypes.byref(s)))
     return p.value, c.value, s.value
+
+
+def cs_ch_set_fields(plan, d_c_prev, d_c_cur, d_c_next) -> None:
+    _check(load().cs_ch_set_fields(plan, _ptr(d_c_prev), _ptr(d_c_cur), _ptr(d_c_next)))
 
 
 def cs_ch_config(plan):

@@ -248,6 +248,34 @@ int cs_compute(cs_plan_t p, void* stream) {
   return CS_OK;
 }
 
+int cs_compute_group(const cs_plan_t* plans, int32_t count, void* stream) {
+  if (count < 0 || (count > 0 && !plans)) return set_error(CS_EINVAL, "cs_compute_group: bad plan array");
+  if (count == 0) return CS_OK;
+  const cs_plan* first = plans[0];
+  for (int32_t i = 0; i < count; ++i) {
+    const cs_plan* p = plans[i];
+    if (!p || p->kind != kStencil2D) return set_error(CS_EINVAL, "cs_compute_group: plan %d is not a 2D stencil plan", i);
+    if (p->s2.variant < 0) return set_error(CS_EUNSUPPORTED, "cs_compute_group: plan %d uses the generic kernel", i);
+    if (p->s2.dtype != first->s2.dtype || p->s2.variant != first->s2.variant || p->s2.tile_rows != first->s2.tile_rows)
+      return set_error(CS_EINVAL, "cs_compute_group: plans must share dtype, stencil shape and tile shape");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int32_t b = 0; b < count; b += kMaxGroupJobs) {
+    const int n = count - b < kMaxGroupJobs ? count - b : kMaxGroupJobs;
+    const Stencil2DConfig* cfgs[kMaxGroupJobs];
+    const void* ins[kMaxGroupJobs];
+    void* outs[kMaxGroupJobs];
+    for (int j = 0; j < n; ++j) {
+      cfgs[j] = &plans[b + j]->s2;
+      ins[j] = plans[b + j]->d_in;
+      outs[j] = plans[b + j]->d_out;
+    }
+    int rc = stencil2d_group(cfgs, ins, outs, n, s);
+    if (rc != CS_OK) return rc;
+  }
+  return CS_OK;
+}
+
 int cs_compute_host(cs_plan_t p, const void* h_in, void* h_out, void* stream) {
   if (!p) return set_error(CS_EINVAL, "null plan");
   if (p->kind == kCahnHilliard) return set_error(CS_EINVAL, "use cs_ch_step for a Cahn-Hilliard plan");
@@ -383,6 +411,11 @@ int cs_ch_invariants(cs_plan_t p, double* mass, double* energy, void* stream) {
 int cs_ch_fields(cs_plan_t p, void** prev, void** cur, int64_t* steps) {
   if (!p || p->kind != kCahnHilliard) return set_error(CS_EINVAL, "not a Cahn-Hilliard plan");
   return ch_fields(p->ch, prev, cur, steps);
+}
+
+int cs_ch_set_fields(cs_plan_t p, void* prev, void* cur, void* next) {
+  if (!p || p->kind != kCahnHilliard) return set_error(CS_EINVAL, "not a Cahn-Hilliard plan");
+  return ch_set_fields(p->ch, prev, cur, next);
 }
 
 int cs_ch_config(cs_plan_t p, int32_t* chunks, int32_t* chunk_len) {

@@ -646,6 +646,25 @@ int ch_fields(CHPlan* p, void** prev, void** cur, int64_t* steps) {
   return CS_OK;
 }
 
+int ch_set_fields(CHPlan* p, void* prev, void* cur, void* next) {
+  if (!prev || !cur || !next) return set_error(CS_EINVAL, "null field buffer");
+  const size_t eb = p->storage == CS_F32 ? 4 : 8;
+  const size_t bytes = static_cast<size_t>(p->n) * p->n * eb;
+  void* f[3] = {prev, cur, next};
+  for (int i = 0; i < 3; ++i) {
+    if (reinterpret_cast<uintptr_t>(f[i]) % eb) return set_error(CS_EINVAL, "fields must be aligned to the element size");
+    for (int j = i + 1; j < 3; ++j) {
+      const char* a = static_cast<const char*>(f[i]);
+      const char* b = static_cast<const char*>(f[j]);
+      if (a < b + bytes && b < a + bytes) return set_error(CS_EALIAS, "the three fields must not overlap");
+    }
+  }
+  p->field[0] = prev; p->field[1] = cur; p->field[2] = next;
+  p->iprev = 0; p->icur = 1; p->inext = 2;
+  p->steps = 0;
+  return CS_OK;
+}
+
 int ch_config(CHPlan* p, int32_t* chunks, int32_t* chunk_len) {
   if (chunks) *chunks = p->P;
   if (chunk_len) *chunk_len = p->m;

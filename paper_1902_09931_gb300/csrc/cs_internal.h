@@ -50,6 +50,9 @@ int stencil2d_launch(const Stencil2DConfig* cfg, const void* in, void* out, cuda
 int stencil2d_num_tile_choices();
 int stencil2d_set_tile_choice(Stencil2DConfig* cfg, int choice);
 std::string stencil2d_shape_key(const Stencil2DConfig* cfg);
+int stencil2d_group(const Stencil2DConfig* const* cfgs, const void* const* ins, void* const* outs,
+                    int count, cudaStream_t s);  // same dtype / variant / tile rows, count <= 16
+constexpr int kMaxGroupJobs = 16;
 
 // ---- batched 1D (cs_batch1d.cu) -------------------------------------------------------------
 struct Batch1DConfig {
@@ -74,6 +77,7 @@ int ch_step(CHPlan* p, int64_t nsteps, double* h_mass, double* h_energy, cudaStr
 int ch_invariants(CHPlan* p, double* mass, double* energy, cudaStream_t s);
 int ch_fields(CHPlan* p, void** prev, void** cur, int64_t* steps);
 int ch_config(CHPlan* p, int32_t* chunks, int32_t* chunk_len);
+int ch_set_fields(CHPlan* p, void* prev, void* cur, void* next);
 void ch_destroy(CHPlan* p);
 
 }  // namespace cs

@@ -10,6 +10,10 @@ namespace cs {
 
 int stencil2d_launch_f32(const Stencil2DConfig* cfg, const void* in, void* out, cudaStream_t s);
 int stencil2d_launch_f64(const Stencil2DConfig* cfg, const void* in, void* out, cudaStream_t s);
+int stencil2d_group_f32(const Stencil2DConfig* const* cfgs, const void* const* ins, void* const* outs,
+                        int count, cudaStream_t s);
+int stencil2d_group_f64(const Stencil2DConfig* const* cfgs, const void* const* ins, void* const* outs,
+                        int count, cudaStream_t s);
 
 namespace {
 
@@ -122,6 +126,12 @@ std::string stencil2d_shape_key(const Stencil2DConfig* cfg) {
            cfg->dtype == CS_F32 ? "f32" : "f64", cfg->variant, cfg->left, cfg->right, cfg->top,
            cfg->bottom, cfg->bc, size_class, num_sms());
   return buf;
+}
+
+int stencil2d_group(const Stencil2DConfig* const* cfgs, const void* const* ins, void* const* outs,
+                    int count, cudaStream_t s) {
+  return cfgs[0]->dtype == CS_F32 ? stencil2d_group_f32(cfgs, ins, outs, count, s)
+                                  : stencil2d_group_f64(cfgs, ins, outs, count, s);
 }
 
 int stencil2d_launch(const Stencil2DConfig* cfg, const void* in, void* out, cudaStream_t s) {

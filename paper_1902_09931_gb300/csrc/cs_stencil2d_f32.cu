@@ -5,4 +5,8 @@ namespace cs {
 int stencil2d_launch_f32(const Stencil2DConfig* cfg, const void* in, void* out, cudaStream_t s) {
   return s2d::launch_stencil2d_t<float>(cfg, in, out, s);
 }
+int stencil2d_group_f32(const Stencil2DConfig* const* cfgs, const void* const* ins, void* const* outs,
+                        int count, cudaStream_t s) {
+  return s2d::launch_group_t<float>(cfgs, ins, outs, count, s);
+}
 }  // namespace cs

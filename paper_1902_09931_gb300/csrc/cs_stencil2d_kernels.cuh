@@ -17,6 +17,7 @@
 #pragma once
 
 #include <stdint.h>
+#include <string.h>
 
 #include "cs_internal.h"
 
@@ -209,6 +210,107 @@ inline size_t tile_smem_bytes(int L, int R, int TT, int BB, int TY, bool generic
   size_t b = sizeof(T) * static_cast<size_t>(TY + TT + BB) * (LA + tile_x<T>() + RA);
   if (generic) b += sizeof(T) * static_cast<size_t>((L + R + 1) * (TT + BB + 1));
   return b;
+}
+
+// ---- grouped launch: several independent grids, one kernel ---------------------------------
+// The job table travels as a __grid_constant__ kernel parameter (kept in the constant bank,
+// indexable without a local copy).  CTA b belongs to the job whose tile range holds b; inside
+// the job it is an ordinary tile of the specialised kernel (storage-type arithmetic).
+constexpr int kMaxGroup = 16;
+
+template <typename T> struct GroupJob {
+  const T* in;
+  T* out;
+  int64_t nx, ny;
+  int tiles_x, tile_begin, periodic, vec_ok;
+  Taps<T> taps;
+};
+template <typename T> struct GroupTable {
+  int count, total_tiles;
+  GroupJob<T> job[kMaxGroup];
+};
+
+template <typename T, int TY, int SPEC>
+__global__ void __launch_bounds__(kThreads) k_stencil2d_group(const __grid_constant__ GroupTable<T> tab) {
+  constexpr SpecDesc sd = kSpecs[SPEC];
+  constexpr int V = Vec<T>::n;
+  constexpr int TX = tile_x<T>();
+  constexpr int LA = (sd.L + V - 1) / V * V, RA = (sd.R + V - 1) / V * V;
+  constexpr int COLS = LA + TX + RA, ROWS = TY + sd.T + sd.B;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  int j = 0;
+  while (j + 1 < tab.count && static_cast<int>(blockIdx.x) >= tab.job[j + 1].tile_begin) ++j;
+  const GroupJob<T>& g = tab.job[j];
+  const int t = static_cast<int>(blockIdx.x) - g.tile_begin;
+  const int64_t x0 = static_cast<int64_t>(t % g.tiles_x) * TX;
+  const int64_t y0 = static_cast<int64_t>(t / g.tiles_x) * TY;
+  load_tile<T>(s, g.in, g.nx, g.ny, g.periodic != 0, g.vec_ok != 0, x0, y0, sd.T, LA, COLS, ROWS);
+  if constexpr (sd.xform) xform_tile<T>(s, ROWS * COLS);
+  spec_compute<T, TY, SPEC>(s, g.out, g.nx, g.ny, g.periodic, x0, y0, g.taps);
+}
+
+template <typename T, int TY, int SPEC>
+int launch_group(const GroupTable<T>& tab, cudaStream_t st) {
+  constexpr SpecDesc sd = kSpecs[SPEC];
+  const size_t smem = tile_smem_bytes<T>(sd.L, sd.R, sd.T, sd.B, TY, false);
+  auto kern = k_stencil2d_group<T, TY, SPEC>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    CS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    attr_set = true;
+  }
+  kern<<<static_cast<unsigned>(tab.total_tiles), kThreads, smem, st>>>(tab);
+  CS_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return CS_OK;
+}
+
+template <typename T, int TY>
+int dispatch_group(int variant, const GroupTable<T>& tab, cudaStream_t st) {
+  switch (variant) {
+#define CS_GR_CASE(I) \
+  case I: return launch_group<T, TY, I>(tab, st);
+    CS_GR_CASE(0) CS_GR_CASE(1) CS_GR_CASE(2) CS_GR_CASE(3) CS_GR_CASE(4)
+    CS_GR_CASE(5) CS_GR_CASE(6) CS_GR_CASE(7) CS_GR_CASE(8) CS_GR_CASE(9)
+    CS_GR_CASE(10) CS_GR_CASE(11) CS_GR_CASE(12) CS_GR_CASE(13)
+#undef CS_GR_CASE
+    default: return set_error(CS_EINVAL, "internal: unknown stencil variant %d", variant);
+  }
+}
+
+// Launches up to kMaxGroup plans (same dtype, specialised variant and tile rows) as one grid.
+template <typename T>
+int launch_group_t(const Stencil2DConfig* const* cfgs, const void* const* ins, void* const* outs,
+                   int count, cudaStream_t st) {
+  GroupTable<T> tab;
+  memset(&tab, 0, sizeof tab);
+  const int variant = cfgs[0]->variant, TY = cfgs[0]->tile_rows;
+  int tiles = 0;
+  for (int j = 0; j < count; ++j) {
+    const Stencil2DConfig* c = cfgs[j];
+    GroupJob<T>& g = tab.job[tab.count];
+    if (c->nx == 0 || c->ny == 0) continue;
+    g.in = static_cast<const T*>(ins[j]);
+    g.out = static_cast<T*>(outs[j]);
+    g.nx = c->nx;
+    g.ny = c->ny;
+    g.tiles_x = static_cast<int>((c->nx + tile_x<T>() - 1) / tile_x<T>());
+    const int64_t ty = (c->ny + TY - 1) / TY;
+    if (static_cast<int64_t>(tiles) + g.tiles_x * ty > 0x7fffffff)
+      return set_error(CS_EINVAL, "grouped launch too large");
+    g.tile_begin = tiles;
+    tiles += static_cast<int>(g.tiles_x * ty);
+    g.periodic = c->bc == CS_BC_PERIODIC;
+    g.vec_ok = (c->nx % Vec<T>::n == 0) && (reinterpret_cast<uintptr_t>(ins[j]) % 16 == 0);
+    const SpecDesc& sd = kSpecs[variant];
+    const int nt = (sd.L + sd.R + 1) * (sd.T + sd.B + 1);
+    for (int i = 0; i < 32; ++i) g.taps.w[i] = i < nt ? static_cast<T>(c->weights[i]) : T(0);
+    ++tab.count;
+  }
+  tab.total_tiles = tiles;
+  if (tab.count == 0) return CS_OK;
+  return TY == 32 ? dispatch_group<T, 32>(variant, tab, st) : dispatch_group<T, 64>(variant, tab, st);
 }
 
 // ---- double-float evaluation of FP64-storage stencils ---------------------------------------

@@ -277,3 +277,32 @@ def test_full_size_configs(env, n, dtype):
     got = run2d(cs, torch, field, dict(dir=2, bc=1, left=1, right=1, top=1, bottom=1, fn=3, coe=[1 / h ** 2]), dtype)
     ref = orc.stencil2d_fn(field, 3, [1 / h ** 2], 1)
     assert np.abs(got - ref).max() / (8 / h ** 2 + 2) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_grouped_launch_equals_individual_plans(env, dtype):
+    """cs_compute_group over grids of different sizes (one launch) gives bit-for-bit the results
+    of computing each plan alone with the same arithmetic."""
+    cs, torch, orc = env
+    tdt = torch.float64 if dtype == 0 else torch.float32
+    sizes = [(64, 64), (100, 260), (257, 129), (31, 517), (128, 128)]
+    ins, outs, refs, plans = [], [], [], []
+    for k, (ny, nx) in enumerate(sizes):
+        h = 2 * np.pi / nx
+        x = torch.from_numpy(W.sines_field(nx, seed=k, ny=ny)).to("cuda", tdt)
+        y = torch.zeros_like(x)
+        r = torch.zeros_like(x)
+        w = biharm13(h)
+        desc = cs.StencilDesc(nx=nx, ny=ny, dir=2, bc=k % 2, dtype=dtype, left=2, right=2, top=2, bottom=2, weights=w)
+        p_alone = cs.cs_plan_create_2d(desc, x, r)
+        cs.cs_plan_set_fp64_mode(p_alone, cs.CS_FP64_NATIVE)
+        cs.cs_compute(p_alone)
+        cs.cs_destroy(p_alone)
+        plans.append(cs.cs_plan_create_2d(desc, x, y))
+        ins.append(x); outs.append(y); refs.append(r)
+    cs.cs_compute_group(plans)
+    torch.cuda.synchronize()
+    for p in plans:
+        cs.cs_destroy(p)
+    for y, r in zip(outs, refs):
+        assert torch.equal(y, r)

@@ -111,3 +111,12 @@ def single_mode(n: int, k: int, l: int, amplitude: float, phase: float = 0.3) ->
     """amplitude * sin(k x + l y + phase) on the n x n periodic grid."""
     x = np.arange(n) * (TWO_PI / n)
     return amplitude * np.sin(k * x[None, :] + l * x[:, None] + phase)
+
+
+def device_uniform(shape, seed: int, lo: float, hi: float, device, dtype):
+    """U[lo, hi) values drawn directly on the device (torch Philox generator, seeded); used for
+    the serving workload, whose many resident fields are too large to stage through the host."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    return torch.empty(shape, dtype=dtype, device=device).uniform_(lo, hi, generator=g)
