@@ -83,6 +83,8 @@ typedef enum {
  *   weights    host array of (left+right+1)*(top+bottom+1) values for fn == CS_FN_NONE,
  *              numbered from the top-left of the stencil box, left to right in i, then row by
  *              row in j (Sec. 5.2); the first row is j - top.  Copied at create time.
+ *              A zero weight is not part of the stencil: its tap is not evaluated, so an inf
+ *              or nan there does not reach the output.
  *   fn, coe, num_coe
  *              user-function variant; coe (host, num_coe values) is copied at create time.
  *              When fn != CS_FN_NONE, weights must be NULL and the extents must equal the
@@ -137,12 +139,19 @@ int cs_compute_host(cs_plan_t plan, const void* h_in, void* h_out, void* cuda_st
  * the last one wrote. */
 int cs_swap(cs_plan_t plan);
 
-/* Arithmetic used for CS_F64 stencils.  CS_FP64_AUTO (default) evaluates the specialised
- * stencils in double-float arithmetic (each value an unevaluated sum of two floats, products
- * and sums error-free on the FP32 pipes, one FP64 rounding at the end), which keeps the error
- * below ~2^-46 of sum|w| * max|in| and falls back to native FP64 for any tile whose values lie
- * outside [2^-70, 2^60) or whose largest value is below 2^-30, and for weights outside
- * [2^-60, 2^50).  CS_FP64_NATIVE always uses FP64 instructions.  CS_F32 plans ignore this. */
+/* Arithmetic used for CS_F64 stencils (GB300 issues FP64 at 1/64 of the FP32 rate).
+ * CS_FP64_AUTO (default), for the specialised stencils:
+ *   - weights w_k = c * n_k with integers n_k, sum |n_k| <= 64 (every stencil of the paper):
+ *     exact digit evaluation -- each value cut into three 18-bit digits on a grid set by the
+ *     largest value of its tile (tile = 64 x TY outputs plus halo), digit sums exact in FP32,
+ *     one FP64 rounding at the end; error below 2^-52 of c * sum|n_k| * (largest |value| in
+ *     the tile and its halo);
+ *   - other weights: double-float arithmetic (values as unevaluated float pairs, error-free
+ *     products and sums on the FP32 pipes); error below ~2^-46 of sum|w| * max|in|;
+ *   tiles holding inf / nan or values outside the methods' exponent ranges, and weights
+ *   outside [2^-60, 2^50), are evaluated in native FP64.
+ * CS_FP64_NATIVE always uses FP64 instructions (each output accurate on its own
+ * neighbourhood's scale).  CS_F32 plans ignore this. */
 typedef enum { CS_FP64_AUTO = 0, CS_FP64_NATIVE = 1 } cs_fp64_mode;
 int cs_plan_set_fp64_mode(cs_plan_t plan, int32_t mode);
 

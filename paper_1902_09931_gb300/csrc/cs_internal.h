@@ -42,6 +42,9 @@ struct Stencil2DConfig {
   double* d_weights;  // device copy for the generic kernel (library-owned), FP64
   float* d_weights_f; // FP32 copy
   int dd_ok;          // weights fit the double-float path (FP64 storage)
+  int ix_ok;          // weights are c * small integers: exact digit path (FP64 storage)
+  double ix_c;        // common scale c
+  int ix_n[32];       // integer ratios n_k
   int fp64_mode;      // CS_FP64_AUTO or CS_FP64_NATIVE
 };
 int stencil2d_prepare(Stencil2DConfig* cfg);  // picks variant, allocates generic weights

@@ -99,6 +99,36 @@ int stencil2d_prepare(Stencil2DConfig* cfg) {
     }
     cfg->dd_ok = any && fits;
   }
+  // exact digit path: plain weighted specialisations whose weights are c * n_k with integers
+  // n_k, sum |n_k| <= 64 (so digit sums stay below 2^24), to 2^-44 of the largest weight
+  cfg->ix_ok = 0;
+  if (cfg->variant >= 0 && cfg->fn == CS_FN_NONE && !s2d::kSpecs[cfg->variant].xform &&
+      !s2d::kSpecs[cfg->variant].epi && cfg->dd_ok) {
+    const int nw = W * H;
+    double wmin = 0.0, wmax = 0.0;
+    for (int i = 0; i < nw; ++i) {
+      const double a = fabs(cfg->weights[i]);
+      if (a > 0.0 && (wmin == 0.0 || a < wmin)) wmin = a;
+      if (a > wmax) wmax = a;
+    }
+    for (int m = 1; m <= 64 && !cfg->ix_ok; ++m) {
+      const double c = wmin / m;
+      long long total = 0;
+      bool ok = true;
+      for (int i = 0; i < nw && ok; ++i) {
+        const double r = cfg->weights[i] / c;
+        const long long k = llround(r);
+        if (fabs(cfg->weights[i] - static_cast<double>(k) * c) > 0x1p-44 * wmax) ok = false;
+        total += k < 0 ? -k : k;
+        if (total > 64) ok = false;
+        cfg->ix_n[i] = static_cast<int>(k);
+      }
+      if (ok) {
+        cfg->ix_ok = 1;
+        cfg->ix_c = c;
+      }
+    }
+  }
   int choice;
   if (tune_lookup(stencil2d_shape_key(cfg), &choice)) stencil2d_set_tile_choice(cfg, choice);
   return CS_OK;

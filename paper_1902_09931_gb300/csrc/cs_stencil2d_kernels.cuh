@@ -212,6 +212,214 @@ inline size_t tile_smem_bytes(int L, int R, int TT, int BB, int TY, bool generic
   return b;
 }
 
+// ---- exact digit evaluation of FP64-storage stencils with integer weight ratios ------------
+// When every weight is w_k = c * n_k with small integers (sum |n_k| <= 64; the paper's stencils
+// are of this kind), a tile is evaluated exactly: every staged value is cut into three signed
+// 18-bit digits on a grid fixed by the tile's largest exponent, x = sum_i d_i 2^(G - 18(i+1)),
+// so each digit sum S_i = sum_k n_k d_{k,i} is an integer below 2^24 and exact in FP32
+// (3 FFMA per tap).  The sums are recombined as one exact 64-bit integer, rounded once to FP64
+// and scaled by c * 2^(G-54) with one FP64 multiply.  Only bits of a value below 2^(G-54) are
+// dropped (below 2^-53 of the tile's largest value), so the result is more accurate than an
+// FP64 accumulation.  Tiles holding inf / nan, or whose largest value is outside
+// [2^-900, 2^900], are evaluated in native FP64.
+
+struct IxTaps {
+  float n[32];   // integer weight ratios n_k (exact in FP32)
+  double c;      // common scale: w_k ~= c * n_k
+};
+
+constexpr int kIxDigitBits = 18;
+constexpr int kIxMinExp = 1023 - 900;
+constexpr int kIxMaxExp = 1023 + 900;
+
+__device__ __forceinline__ float ix_digit(int64_t v) {
+  // exact for |v| < 2^22: bias into the mantissa of 1.5 * 2^23 and subtract
+  return __fsub_rn(__int_as_float(0x4B400000 + static_cast<int>(v)), 12582912.0f);
+}
+
+// Digits of x on the tile grid whose top is 2^G with G = tile_e - 1022 (tile_e = largest biased
+// exponent in the tile): A = |x| / 2^(G-54) truncated, d0 = A >> 36, d1, d2 the next 18 bits.
+__device__ __forceinline__ void ix_split(double x, int tile_e, float& d0, float& d1, float& d2) {
+  const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x));
+  const int e = static_cast<int>((b >> 52) & 0x7ffu);
+  uint64_t A = 0;
+  if (e != 0) {  // subnormals are far below the grid (tile_e >= kIxMinExp): they count as 0
+    const uint64_t M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = e - tile_e + 1;  // <= 1
+    A = sh >= 0 ? (M << sh) : (sh > -64 ? (M >> (-sh)) : 0ull);
+  }
+  const int64_t s = static_cast<int64_t>(b >> 63);  // 0 or 1
+  const int64_t a0 = static_cast<int64_t>(A >> 36);
+  const int64_t a1 = static_cast<int64_t>((A >> 18) & 0x3FFFFull);
+  const int64_t a2 = static_cast<int64_t>(A & 0x3FFFFull);
+  d0 = ix_digit(s ? -a0 : a0);
+  d1 = ix_digit(s ? -a1 : a1);
+  d2 = ix_digit(s ? -a2 : a2);
+}
+
+// Exact integer value of an integer-valued float with |f| <= 2^24.
+__device__ __forceinline__ int64_t ix_int(float f) { return static_cast<int64_t>(__float2int_rn(f)); }
+
+// Round-to-nearest-even int64 -> double on the integer pipe.
+__device__ __forceinline__ double ix_to_double(int64_t t) {
+  if (t == 0) return 0.0;
+  const uint64_t sign = static_cast<uint64_t>(t) & 0x8000000000000000ull;
+  uint64_t a = sign ? static_cast<uint64_t>(-t) : static_cast<uint64_t>(t);
+  const int lz = __clzll(static_cast<long long>(a));
+  a <<= lz;                      // leading one at bit 63
+  uint64_t mant = a >> 11;       // 53 bits including the leading one
+  const uint64_t rem = a & 0x7FFull;
+  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ++mant;  // may carry to 2^53
+  const uint64_t bits = sign | ((static_cast<uint64_t>(1086 - lz) << 52) + (mant - (1ull << 52)));
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
+template <int TY, int SPEC>
+__device__ __forceinline__ void ix_compute(const float2* s01, const float* s2, double* __restrict__ out,
+                                           int64_t nx, int64_t ny, int periodic, int64_t x0,
+                                           int64_t y0, const IxTaps& taps, double scale) {
+  constexpr SpecDesc sd = kSpecs[SPEC];
+  constexpr int L = sd.L, R = sd.R, TT = sd.T, BB = sd.B;
+  constexpr int V = Vec<double>::n;
+  constexpr int TX = tile_x<double>();
+  constexpr int LA = (L + V - 1) / V * V, RA = (R + V - 1) / V * V;
+  constexpr int COLS = LA + TX + RA;
+  constexpr int W = L + R + 1, H = TT + BB + 1;
+  constexpr int WX = TX / 32, WY = 8 / WX, RW = TY / WY;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = (warp % WX) * 32 + lane;
+  const int r0 = (warp / WX) * RW;
+  const int64_t gx = x0 + c;
+  const bool col_ok = gx < nx && (periodic || (gx >= L && gx < nx - R));
+  const float2* a = s01 + LA + c - L;
+  const float* b = s2 + LA + c - L;
+  float w01[H][W][2], w2[H][W];
+#pragma unroll
+  for (int q = 0; q < H - 1; ++q)
+#pragma unroll
+    for (int p = 0; p < W; ++p) {
+      const float2 v = a[(r0 + q) * COLS + p];
+      w01[q + 1][p][0] = v.x;
+      w01[q + 1][p][1] = v.y;
+      w2[q + 1][p] = b[(r0 + q) * COLS + p];
+    }
+#pragma unroll
+  for (int k = 0; k < RW; ++k) {
+#pragma unroll
+    for (int q = 0; q < H - 1; ++q)
+#pragma unroll
+      for (int p = 0; p < W; ++p) {
+        w01[q][p][0] = w01[q + 1][p][0];
+        w01[q][p][1] = w01[q + 1][p][1];
+        w2[q][p] = w2[q + 1][p];
+      }
+#pragma unroll
+    for (int p = 0; p < W; ++p) {
+      const float2 v = a[(r0 + k + H - 1) * COLS + p];
+      w01[H - 1][p][0] = v.x;
+      w01[H - 1][p][1] = v.y;
+      w2[H - 1][p] = b[(r0 + k + H - 1) * COLS + p];
+    }
+    float S0 = 0.0f, S1 = 0.0f, S2 = 0.0f;
+#pragma unroll
+    for (int q = 0; q < H; ++q)
+#pragma unroll
+      for (int p = 0; p < W; ++p)
+        if ((sd.mask >> (q * W + p)) & 1u) {
+          const float n = taps.n[q * W + p];
+          S0 = __fmaf_rn(n, w01[q][p][0], S0);
+          S1 = __fmaf_rn(n, w01[q][p][1], S1);
+          S2 = __fmaf_rn(n, w2[q][p], S2);
+        }
+    const int64_t T = ix_int(S0) * (int64_t(1) << 36) + ix_int(S1) * (int64_t(1) << 18) + ix_int(S2);
+    const double acc = ix_to_double(T) * scale;
+    const int64_t gy = y0 + r0 + k;
+    if (col_ok && gy < ny && (periodic || (gy >= TT && gy < ny - BB))) out[gy * nx + gx] = acc;
+  }
+}
+
+template <int TY, int SPEC>
+__global__ void __launch_bounds__(kThreads)
+    k_stencil2d_ix(const double* __restrict__ in, double* __restrict__ out, int64_t nx, int64_t ny,
+                   int periodic, int vec_ok, Taps<double> taps, IxTaps itaps) {
+  constexpr SpecDesc sd = kSpecs[SPEC];
+  constexpr int V = Vec<double>::n;
+  constexpr int TX = tile_x<double>();
+  constexpr int LA = (sd.L + V - 1) / V * V, RA = (sd.R + V - 1) / V * V;
+  constexpr int COLS = LA + TX + RA, ROWS = TY + sd.T + sd.B;
+  static_assert(!sd.xform && !sd.epi, "digit kernel covers plain weighted stencils");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* s = reinterpret_cast<double*>(smem_raw);
+  float* s2 = reinterpret_cast<float*>(s + ROWS * COLS);
+  __shared__ int s_maxe;
+  if (threadIdx.x == 0) s_maxe = 0;
+  const int64_t x0 = static_cast<int64_t>(blockIdx.x) * TX;
+  const int64_t y0 = static_cast<int64_t>(blockIdx.y) * TY;
+  load_tile<double>(s, in, nx, ny, periodic != 0, vec_ok != 0, x0, y0, sd.T, LA, COLS, ROWS);
+  // pass 1: the tile's largest exponent; inf / nan force native FP64
+  int maxe = 0;
+  bool bad = false;
+  const unsigned* hi_words = reinterpret_cast<const unsigned*>(s) + 1;  // little endian: high half
+  for (int i = threadIdx.x; i < ROWS * COLS; i += kThreads) {
+    const int e = static_cast<int>((hi_words[2 * i] >> 20) & 0x7ffu);
+    bad |= (e == 0x7ff);
+    maxe = max(maxe, e);
+  }
+  for (int off = 16; off > 0; off >>= 1) maxe = max(maxe, __shfl_xor_sync(0xffffffffu, maxe, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(&s_maxe, maxe);
+  const bool any_bad = __syncthreads_or(bad);
+  const int tile_e = s_maxe;
+  if (any_bad || (tile_e != 0 && (tile_e < kIxMinExp || tile_e > kIxMaxExp))) {
+    spec_compute<double, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
+    return;
+  }
+  // pass 2: digits, d0 and d1 over the double's own slot, d2 in the float tile
+  float2* s01 = reinterpret_cast<float2*>(s);
+  for (int i = threadIdx.x; i < ROWS * COLS; i += kThreads) {
+    float d0, d1, d2;
+    ix_split(s[i], tile_e, d0, d1, d2);
+    s01[i] = make_float2(d0, d1);
+    s2[i] = d2;
+  }
+  __syncthreads();
+  // scale = c * 2^(G - 54) with G = tile_e - 1022 (all-zero tile: any finite scale)
+  const double scale = tile_e == 0 ? 0.0 : itaps.c * ldexp(1.0, tile_e - 1022 - 3 * kIxDigitBits);
+  ix_compute<TY, SPEC>(s01, s2, out, nx, ny, periodic, x0, y0, itaps, scale);
+}
+
+template <int TY, int SPEC>
+int launch_ix(const double* in, double* out, int64_t nx, int64_t ny, int periodic, int vec_ok,
+              const Taps<double>& taps, const IxTaps& itaps, cudaStream_t st) {
+  constexpr SpecDesc sd = kSpecs[SPEC];
+  const size_t smem = tile_smem_bytes<double>(sd.L, sd.R, sd.T, sd.B, TY, false) * 3 / 2;
+  auto kern = k_stencil2d_ix<TY, SPEC>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    CS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    attr_set = true;
+  }
+  dim3 grid(static_cast<unsigned>((nx + tile_x<double>() - 1) / tile_x<double>()),
+            static_cast<unsigned>((ny + TY - 1) / TY));
+  kern<<<grid, kThreads, smem, st>>>(in, out, nx, ny, periodic, vec_ok, taps, itaps);
+  CS_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return CS_OK;
+}
+
+template <int TY>
+int dispatch_ix(int variant, const double* in, double* out, int64_t nx, int64_t ny, int periodic,
+                int vec_ok, const Taps<double>& taps, const IxTaps& itaps, cudaStream_t st) {
+  switch (variant) {
+#define CS_IX_CASE(I) \
+  case I: return launch_ix<TY, I>(in, out, nx, ny, periodic, vec_ok, taps, itaps, st);
+    CS_IX_CASE(0) CS_IX_CASE(1) CS_IX_CASE(2) CS_IX_CASE(3) CS_IX_CASE(4)
+    CS_IX_CASE(5) CS_IX_CASE(6) CS_IX_CASE(7) CS_IX_CASE(8) CS_IX_CASE(9)
+    CS_IX_CASE(10) CS_IX_CASE(11)
+#undef CS_IX_CASE
+    default: return set_error(CS_EINVAL, "internal: variant %d has no digit kernel", variant);
+  }
+}
+
 // ---- grouped launch: several independent grids, one kernel ---------------------------------
 // The job table travels as a __grid_constant__ kernel parameter (kept in the constant bank,
 // indexable without a local copy).  CTA b belongs to the job whose tile range holds b; inside
@@ -606,6 +814,14 @@ int launch_stencil2d_t(const Stencil2DConfig* cfg, const void* vin, void* vout, 
     const int nt = (sd.L + sd.R + 1) * (sd.T + sd.B + 1);
     for (int i = 0; i < 32; ++i) taps.w[i] = i < nt ? static_cast<T>(cfg->weights[i]) : T(0);
     if constexpr (sizeof(T) == 8) {
+      if (cfg->ix_ok && cfg->fp64_mode == CS_FP64_AUTO) {
+        IxTaps it;
+        for (int i = 0; i < 32; ++i) it.n[i] = i < nt ? static_cast<float>(cfg->ix_n[i]) : 0.0f;
+        it.c = cfg->ix_c;
+        if (cfg->tile_rows == 32)
+          return dispatch_ix<32>(cfg->variant, in, out, cfg->nx, cfg->ny, periodic, vec_ok, taps, it, st);
+        return dispatch_ix<64>(cfg->variant, in, out, cfg->nx, cfg->ny, periodic, vec_ok, taps, it, st);
+      }
       if (cfg->dd_ok && cfg->fp64_mode == CS_FP64_AUTO) {
         DDTaps dt;
         for (int i = 0; i < 32; ++i) {
