@@ -167,13 +167,21 @@ def barrier(world):
 
 
 def max_over_ranks(world, value: float) -> float:
+    """Largest value over all ranks (the slowest rank's time); NCCL on CUDA, gloo on CPU."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_gpts(world: int, points_per_rank_step: int, ms_per_step: float) -> float:
+    """Whole-job throughput: every rank updates its own grids (weak scaling), and the step
+    lasts as long as the slowest rank."""
+    return world * points_per_rank_step / (ms_per_step * 1e-3) / 1e9
 
 
 # --------------------------------------------------------------------------------------------
@@ -270,7 +278,7 @@ def run_ours(args):
     ms_per_step = max_over_ranks(world, total_ms / args.steps)
     pts_per_step = sum(sw["points"] for sw in sweeps)
     bytes_per_step = sum(sw["bytes"] for sw in sweeps)
-    value = world * pts_per_step / (ms_per_step * 1e-3) / 1e9
+    value = whole_job_gpts(world, pts_per_step, ms_per_step)
     hbm_gbs = world * bytes_per_step / (ms_per_step * 1e-3) / 1e9
 
     # dominant kernel: largest share of the step
