@@ -56,11 +56,16 @@ FP32_LANE_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 
 
 def dd_ops_per_point(taps: int, name: str) -> int:
-    """FP32/INT lane operations per output point of the double-float formulation: 12 per tap
-    (product, its FMA error, two cross terms, TwoSum, error accumulation), 12 to split the one new
-    input value per point into a float pair, 8 to widen hi and lo to FP64 (integer ops); the
-    final FP64 add and, for the cubic function, its FP64 epilogue run on the FP64 pipe."""
-    return 12 * taps + 12 + 8
+    """FP32/INT lane operations per output point of the FP64-storage formulations.  Exact digit
+    path (weights c * small integers: the 9-point, 13-point and first-derivative stencils): 3
+    FFMA per tap, 24 to cut the one new input value per point into three digits, 20 to
+    recombine the digit sums into an int64 and round it to FP64.  Double-float path (the cubic
+    user function): 12 per tap (product, its FMA error, two cross terms, TwoSum, error
+    accumulation), 20 for u^3 - u, 12 to split the new value into a float pair, 8 to widen the
+    result.  The single FP64 multiply or add per point runs on the FP64 pipe."""
+    if name == "cubic_minus_lap":
+        return 12 * taps + 20 + 12 + 8
+    return 3 * taps + 24 + 20
 
 
 def stencil_suite(h):
@@ -213,7 +218,18 @@ def build_suite(cs, torch, rank, only=None):
                                        plan=plan, points=n * n, bytes=2 * eb * n * n, taps=taps,
                                        d_in=d_in, d_out=d_out, eb=eb))
         del base
-    return sweeps, keep
+    # consecutive sweeps never share an input: round-robin over the (size, dtype) grids, so a
+    # sweep's input was last touched several hundred MB of traffic ago (plus the flush)
+    groups = {}
+    for sw in sweeps:
+        groups.setdefault((sw["n"], sw["dtype"]), []).append(sw)
+    order = []
+    lists = list(groups.values())
+    for i in range(max(len(g) for g in lists)):
+        for g in lists:
+            if i < len(g):
+                order.append(g[i])
+    return order, keep
 
 
 def flush_l2(buf):
@@ -246,7 +262,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     only = tuple(args.only.split(",")) if args.only else None
     sweeps, keep = build_suite(cs, torch, rank, only)
-    if not args.no_autotune:
+    if args.tile_choice >= 0:
+        for sw in sweeps:
+            cs.cs_plan_set_tile_choice(sw["plan"], args.tile_choice)
+    elif not args.no_autotune:
         for sw in sweeps:  # pick tile shapes with the project's autotuner
             cs.cs_autotune(sw["plan"], stream)
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
@@ -308,7 +327,8 @@ def run_ours(args):
         sw = [s for s in sweeps if s["name"] == name and s["n"] == int(n) and s["dtype"] == dt and s["bc"] == bc][0]
         gbs = sw["bytes"] / (v * 1e-3) / 1e9
         f32[k] = {"ms": round(v, 4), "gpts": round(sw["points"] / (v * 1e-3) / 1e9, 2),
-                  "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 3)}
+                  "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 3),
+                  "tile_choice": cs.cs_plan_get_tile_choice(sw["plan"])}
 
     e2e = e2e_host(cs, torch, sweeps, stream, max(1, min(args.steps, 2)), world)
     parts = {}
@@ -559,6 +579,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-parts", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tile-choice", type=int, default=-1, help="force a tile choice (0, 1, 2) instead of autotuning")
     ap.add_argument("--only", default="", help="profile one sweep: name,n,f64|f32,p|np")
     ap.add_argument("--part", default="", help="run one part alone: ch:<n>:<f64|f32>:<steps> or batch1d")
     args = ap.parse_args()

@@ -155,6 +155,15 @@ int cs_swap(cs_plan_t plan);
 typedef enum { CS_FP64_AUTO = 0, CS_FP64_NATIVE = 1 } cs_fp64_mode;
 int cs_plan_set_fp64_mode(cs_plan_t plan, int32_t mode);
 
+/* Tile / pipeline shape of a 2D stencil plan (normally picked by cs_autotune):
+ *   0  tiles of 32 rows staged with cp.async, one tile per CTA
+ *   1  tiles of 64 rows staged with cp.async, one tile per CTA
+ *   2  TMA-pipelined persistent sweep: tiles of 64 rows, each CTA walks its tiles through a
+ *      two-stage shared-memory ring filled by tensor-memory-access copies (default; used when
+ *      nx is a multiple of 16 bytes / element size and d_in is 16-byte aligned, else 1). */
+int cs_plan_set_tile_choice(cs_plan_t plan, int32_t choice);
+int cs_plan_get_tile_choice(cs_plan_t plan, int32_t* choice);
+
 /* Rebinds the device buffers of a stencil plan without re-planning (same sizes and dtype). */
 int cs_set_buffers(cs_plan_t plan, const void* d_in, void* d_out);
 
@@ -164,7 +173,9 @@ int cs_set_buffers(cs_plan_t plan, const void* d_in, void* d_out);
 int cs_plan_use_graph(cs_plan_t plan, int enable);
 
 /* Times the candidate tile / launch shapes of the plan's kernel on its own buffers (it
- * overwrites d_out), keeps the fastest, and records it in the process-wide tuning table.  The
+ * overwrites d_out), each launch from a cold L2 (the first call allocates a 256 MB buffer that
+ * the library reads to evict the cache, kept until exit), keeps the fastest, and records it in
+ * the process-wide tuning table.  The
  * table is keyed by (kernel, dtype, shape class, SM count) and can be saved to / loaded from a
  * JSON file with cs_tune_save / cs_tune_load.  Synchronises the stream. */
 int cs_autotune(cs_plan_t plan, void* cuda_stream);

@@ -95,6 +95,8 @@ _SYMBOLS = {
     "cs_set_buffers": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_plan_use_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "cs_plan_set_fp64_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "cs_plan_set_tile_choice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "cs_plan_get_tile_choice": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
     "cs_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "cs_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
     "cs_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
@@ -217,6 +219,16 @@ def cs_set_buffers(plan, d_in, d_out) -> None:
 
 def cs_plan_set_fp64_mode(plan, mode: int) -> None:
     _check(load().cs_plan_set_fp64_mode(plan, int(mode)))
+
+
+def cs_plan_set_tile_choice(plan, choice: int) -> None:
+    _check(load().cs_plan_set_tile_choice(plan, int(choice)))
+
+
+def cs_plan_get_tile_choice(plan) -> int:
+    c = ctypes.c_int32()
+    _check(load().cs_plan_get_tile_choice(plan, ctypes.byref(c)))
+    return c.value
 
 
 def cs_plan_use_graph(plan, enable: bool = True) -> None:

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libcusten_gb (not installed).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -42,6 +43,9 @@ struct Stencil2DConfig {
   double* d_weights;  // device copy for the generic kernel (library-owned), FP64
   float* d_weights_f; // FP32 copy
   int dd_ok;          // weights fit the double-float path (FP64 storage)
+  int use_tma;        // tile choice 2: TMA-pipelined persistent sweep (aligned buffers)
+  mutable CUtensorMap tmap;      // tensor map of the last input pointer (rebuilt on change)
+  mutable const void* tmap_in;
   int ix_ok;          // weights are c * small integers: exact digit path (FP64 storage)
   double ix_c;        // common scale c
   int ix_n[32];       // integer ratios n_k
@@ -51,6 +55,7 @@ int stencil2d_prepare(Stencil2DConfig* cfg);  // picks variant, allocates generi
 void stencil2d_release(Stencil2DConfig* cfg);
 int stencil2d_launch(const Stencil2DConfig* cfg, const void* in, void* out, cudaStream_t s);
 int stencil2d_num_tile_choices();
+int stencil2d_status_ptr(int** out);  // device word a timed-out bounded wait sets to 1
 int stencil2d_set_tile_choice(Stencil2DConfig* cfg, int choice);
 std::string stencil2d_shape_key(const Stencil2DConfig* cfg);
 int stencil2d_group(const Stencil2DConfig* const* cfgs, const void* const* ins, void* const* outs,

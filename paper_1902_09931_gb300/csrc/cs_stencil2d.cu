@@ -4,6 +4,9 @@
 #include <cstdio>
 #include <cstring>
 
+#include <atomic>
+#include <cudaTypedefs.h>
+
 #include "cs_stencil2d_kernels.cuh"
 
 namespace cs {
@@ -50,7 +53,9 @@ int stencil2d_prepare(Stencil2DConfig* cfg) {
   cfg->d_weights = nullptr;
   cfg->d_weights_f = nullptr;
   cfg->variant = -1;
+  cfg->tmap_in = nullptr;
   if (cfg->tile_rows != 32 && cfg->tile_rows != 64) cfg->tile_rows = 64;
+  cfg->use_tma = 1;
   const int W = cfg->left + cfg->right + 1, H = cfg->top + cfg->bottom + 1;
   if (cfg->fn != CS_FN_NONE) {
     int rc = map_function(cfg);
@@ -141,10 +146,63 @@ void stencil2d_release(Stencil2DConfig* cfg) {
   cfg->d_weights_f = nullptr;
 }
 
-int stencil2d_num_tile_choices() { return 2; }
+// Tile / pipeline choices the autotuner times: 0 = cp.async tiles of 32 rows, 1 = cp.async
+// tiles of 64 rows, 2 = TMA-pipelined persistent sweep (64-row tiles; aligned buffers only).
+int stencil2d_num_tile_choices() { return 3; }
 
 int stencil2d_set_tile_choice(Stencil2DConfig* cfg, int choice) {
+  cfg->use_tma = choice == 2;
   cfg->tile_rows = choice == 0 ? 32 : 64;
+  return CS_OK;
+}
+
+namespace {
+// Status word shared by every TMA sweep in the process (per device): a bounded mbarrier wait
+// that runs out writes 1 here instead of hanging.
+__device__ int g_stencil_status;
+std::atomic<int*> g_status_addr[64];
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::atomic<int> g_encode_state{0};
+}  // namespace
+
+int stencil2d_status_ptr(int** out) {
+  int dev = 0;
+  CS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_error(CS_EUNSUPPORTED, "device index %d out of range", dev);
+  int* p = g_status_addr[dev].load();
+  if (!p) {
+    void* a = nullptr;
+    CS_CUDA_TRY(cudaGetSymbolAddress(&a, g_stencil_status));
+    p = static_cast<int*>(a);
+    g_status_addr[dev].store(p);
+  }
+  *out = p;
+  return CS_OK;
+}
+
+int s2d::make_tensor_map(const Stencil2DConfig* cfg, const void* in, int elem_bytes, int cols, int rows) {
+  if (g_encode_state.load() == 0) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+      g_encode_state.store(-1);
+    } else {
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+      g_encode_state.store(1);
+    }
+  }
+  if (g_encode_state.load() < 0) return set_error(CS_EUNSUPPORTED, "cuTensorMapEncodeTiled is not available");
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(cfg->nx), static_cast<cuuint64_t>(cfg->ny)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(cfg->nx) * elem_bytes};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(cols), static_cast<cuuint32_t>(rows)};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(&cfg->tmap, elem_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                        2, const_cast<void*>(in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(CS_ECUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+  cfg->tmap_in = in;
   return CS_OK;
 }
 

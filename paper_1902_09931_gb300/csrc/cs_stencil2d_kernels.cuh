@@ -16,8 +16,11 @@
 // kernel takes any extents up to CS_MAX_EXTENT at run time.
 #pragma once
 
+#include <cuda.h>
 #include <stdint.h>
 #include <string.h>
+
+#include <algorithm>
 
 #include "cs_internal.h"
 
@@ -95,6 +98,7 @@ __device__ __forceinline__ void load_tile(T* s, const T* __restrict__ in, int64_
   constexpr int V = Vec<T>::n;
   const int nch = cols / V;
   const int total = rows * nch;
+  const bool one_wrap = nx >= cols && ny >= rows;  // tile halo reaches at most one period out
   for (int idx = threadIdx.x; idx < total; idx += kThreads) {
     const int r = idx / nch;
     const int ch = idx - r * nch;
@@ -106,7 +110,7 @@ __device__ __forceinline__ void load_tile(T* s, const T* __restrict__ in, int64_
         for (int e = 0; e < V; ++e) dst[e] = T(0);
         continue;
       }
-      gy = wrap_idx(gy, ny);
+      gy = one_wrap ? (gy < 0 ? gy + ny : gy - ny) : wrap_idx(gy, ny);
     }
     const T* row = in + gy * nx;
     const int64_t gx0 = x0 - LA + static_cast<int64_t>(ch) * V;
@@ -121,7 +125,7 @@ __device__ __forceinline__ void load_tile(T* s, const T* __restrict__ in, int64_
             dst[e] = T(0);
             continue;
           }
-          gx = wrap_idx(gx, nx);
+          gx = one_wrap ? (gx < 0 ? gx + nx : gx - nx) : wrap_idx(gx, nx);
         }
         cp_async_elem(dst + e, row + gx);
       }
@@ -587,6 +591,27 @@ __device__ __forceinline__ void dd_mac(float& sh, float& sl, float wh, float wl,
   sh = s;
 }
 
+// (sh, sl) += u^3 - u for u = uh + ul, with error-free products and sums (terms below ~2^-46
+// of |u| dropped), so the cubic of the user function stays on the FP32 pipes.
+__device__ __forceinline__ void dd_add_exact(float& sh, float& sl, float p, float e) {
+  const float s = __fadd_rn(sh, p);
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+  sh = s;
+}
+__device__ __forceinline__ void dd_add_cubic_minus(float& sh, float& sl, float uh, float ul) {
+  const float p2 = __fmul_rn(uh, uh);  // u^2 = p2 + e2
+  float e2 = __fmaf_rn(uh, uh, -p2);
+  e2 = __fmaf_rn(__fmul_rn(2.0f, uh), ul, e2);
+  const float p3 = __fmul_rn(p2, uh);  // u^3 = p3 + e3
+  float e3 = __fmaf_rn(p2, uh, -p3);
+  e3 = __fmaf_rn(p2, ul, e3);
+  e3 = __fmaf_rn(e2, uh, e3);
+  dd_add_exact(sh, sl, p3, e3);
+  dd_add_exact(sh, sl, -uh, -ul);
+}
+
 template <int TY, int SPEC>
 __device__ __forceinline__ void dd_compute(const float2* sf, const double* s, double* __restrict__ out,
                                            int64_t nx, int64_t ny, int periodic, int64_t x0,
@@ -605,7 +630,7 @@ __device__ __forceinline__ void dd_compute(const float2* sf, const double* s, do
   const int64_t gx = x0 + c;
   const bool col_ok = gx < nx && (periodic || (gx >= L && gx < nx - R));
   const float2* sc = sf + LA + c - L;
-  const double* dc = s + LA + c - L;
+  (void)s;
   float2 win[H][W];
 #pragma unroll
   for (int q = 0; q < H - 1; ++q)
@@ -626,8 +651,8 @@ __device__ __forceinline__ void dd_compute(const float2* sf, const double* s, do
       for (int p = 0; p < W; ++p)
         if ((sd.mask >> (q * W + p)) & 1u)
           dd_mac(sh, sl, taps.hi[q * W + p], taps.lo[q * W + p], win[q][p].x, win[q][p].y);
-    double acc = f2d_exact(sh) + f2d_exact(sl);
-    if constexpr (sd.epi) acc = cubic_minus(dc[(r0 + k + TT) * COLS + L]) + acc;
+    if constexpr (sd.epi) dd_add_cubic_minus(sh, sl, win[TT][L].x, win[TT][L].y);
+    const double acc = f2d_exact(sh) + f2d_exact(sl);
     const int64_t gy = y0 + r0 + k;
     if (col_ok && gy < ny && (periodic || (gy >= TT && gy < ny - BB))) out[gy * nx + gx] = acc;
   }
@@ -698,6 +723,250 @@ int dispatch_dd(int variant, const double* in, double* out, int64_t nx, int64_t 
     CS_DD_CASE(5) CS_DD_CASE(6) CS_DD_CASE(7) CS_DD_CASE(8) CS_DD_CASE(9)
     CS_DD_CASE(10) CS_DD_CASE(11) CS_DD_CASE(12) CS_DD_CASE(13)
 #undef CS_DD_CASE
+    default: return set_error(CS_EINVAL, "internal: unknown stencil variant %d", variant);
+  }
+}
+
+// ---- TMA-pipelined persistent sweep ------------------------------------------------------------
+// Persistent CTAs walk their tiles (t = blockIdx.x, blockIdx.x + gridDim.x, ...) through a
+// two-stage shared-memory ring.  One thread fills a stage with a single 2D tensor-memory-access
+// copy (cp.async.bulk.tensor) of the tile plus halo, completed on the stage's mbarrier, so the
+// next tile's load overlaps the current tile's compute.  The copy zero-fills cells outside the
+// grid; for periodic boundaries the threads of an edge tile then overwrite those cells with the
+// wrapped values.  MODE 0 computes in the storage type, MODE 1 is the exact digit path and
+// MODE 2 the double-float path of FP64 storage (each with its native-FP64 tile fallback).
+// Every mbarrier wait is bounded: when it runs out the kernel records 1 in *status and returns.
+
+constexpr int kStages = 2;
+constexpr long long kWaitLimit = 1ll << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (long long it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Periodic halo of an edge tile: cells outside the grid get their wrapped values.  Only the
+// out-of-range strips are visited (whole rows above / below the grid, then the columns left /
+// right of it); a grid at least as large as the tile wraps with one compare-and-add.
+template <typename T, int COLS, int ROWS>
+__device__ __forceinline__ void fixup_periodic(T* s, const T* __restrict__ in, int64_t nx, int64_t ny,
+                                               int64_t gx0, int64_t gy0) {
+  const bool one_wrap = nx >= COLS && ny >= ROWS;
+  auto wx = [&](int64_t g) { return one_wrap ? (g < 0 ? g + nx : (g >= nx ? g - nx : g)) : wrap_idx(g, nx); };
+  auto wy = [&](int64_t g) { return one_wrap ? (g < 0 ? g + ny : (g >= ny ? g - ny : g)) : wrap_idx(g, ny); };
+  auto clamp = [](int64_t v, int64_t lo, int64_t hi) { return static_cast<int>(v < lo ? lo : (v > hi ? hi : v)); };
+  const int r_lo = clamp(-gy0, 0, ROWS);            // rows [0, r_lo) lie above the grid
+  const int r_hi = clamp(ny - gy0, r_lo, ROWS);     // rows [r_hi, ROWS) lie below it
+  const int c_lo = clamp(-gx0, 0, COLS);
+  const int c_hi = clamp(nx - gx0, c_lo, COLS);
+  const int out_rows = r_lo + (ROWS - r_hi);
+  for (int idx = threadIdx.x; idx < out_rows * COLS; idx += kThreads) {  // whole rows
+    const int rr = idx / COLS, c = idx - rr * COLS;
+    const int r = rr < r_lo ? rr : r_hi + (rr - r_lo);
+    s[r * COLS + c] = in[wy(gy0 + r) * nx + wx(gx0 + c)];
+  }
+  const int side = c_lo + (COLS - c_hi);
+  const int mid_rows = r_hi - r_lo;
+  for (int idx = threadIdx.x; idx < mid_rows * side; idx += kThreads) {  // side columns
+    const int rr = idx / side, cc = idx - rr * side;
+    const int r = r_lo + rr;
+    const int c = cc < c_lo ? cc : c_hi + (cc - c_lo);
+    s[r * COLS + c] = in[(gy0 + r) * nx + wx(gx0 + c)];
+  }
+}
+
+template <int MODE, typename T, int SPEC>
+struct TmaGeom {
+  static constexpr SpecDesc sd = kSpecs[SPEC];
+  static constexpr int TY = 64;
+  static constexpr int V = Vec<T>::n;
+  static constexpr int TX = tile_x<T>();
+  static constexpr int LA = (sd.L + V - 1) / V * V, RA = (sd.R + V - 1) / V * V;
+  static constexpr int COLS = LA + TX + RA, ROWS = TY + sd.T + sd.B;
+  static constexpr int SE = ROWS * COLS;
+  static constexpr size_t STAGE_BYTES = (SE * sizeof(T) + 127) / 128 * 128;
+  static constexpr size_t EXTRA_BYTES = MODE == 1 ? SE * sizeof(float) : (MODE == 2 ? SE * sizeof(float2) : 0);
+  static constexpr size_t SMEM = kStages * STAGE_BYTES + EXTRA_BYTES;
+};
+
+template <int MODE, typename T, int SPEC>
+__global__ void __launch_bounds__(kThreads)
+    k_stencil2d_tma(const __grid_constant__ CUtensorMap tmap, const T* __restrict__ in,
+                    T* __restrict__ out, int64_t nx, int64_t ny, int periodic, int tiles_x,
+                    int tiles, Taps<T> taps, IxTaps itaps, DDTaps dtaps, int* status) {
+  using G = TmaGeom<MODE, T, SPEC>;
+  constexpr SpecDesc sd = kSpecs[SPEC];
+  constexpr int TY = G::TY, TX = G::TX, COLS = G::COLS, ROWS = G::ROWS, SE = G::SE;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t mbar[kStages];
+  __shared__ int s_wmax[kThreads / 32];
+  unsigned char* extra = smem_raw + kStages * G::STAGE_BYTES;
+  const int tid = threadIdx.x;
+  if (blockIdx.x >= tiles) return;
+  const int my_tiles = (tiles - 1 - static_cast<int>(blockIdx.x)) / static_cast<int>(gridDim.x) + 1;
+  if (tid == 0) {
+    for (int st = 0; st < kStages; ++st) mbar_init(&mbar[st], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int i, int st) {
+    const int t = static_cast<int>(blockIdx.x) + i * static_cast<int>(gridDim.x);
+    const int bx = t % tiles_x, by = t / tiles_x;
+    fence_proxy_async();  // order this stage's generic-proxy writes before the async copy
+    mbar_expect_tx(&mbar[st], static_cast<uint32_t>(SE * sizeof(T)));
+    tma_load_2d(smem_raw + st * G::STAGE_BYTES, &tmap, bx * TX - G::LA, by * TY - sd.T, &mbar[st]);
+  };
+  if (tid == 0)
+    for (int st = 0; st < kStages && st < my_tiles; ++st) issue(st, st);
+
+  for (int i = 0; i < my_tiles; ++i) {
+    const int st = i % kStages;
+    if (!mbar_wait_bounded(&mbar[st], static_cast<uint32_t>((i / kStages) & 1))) {
+      if (tid == 0) atomicExch(status, 1);
+      // let the copies already issued into this CTA's stages land before leaving
+      for (int j = i + 1; j < i + kStages && j < my_tiles; ++j)
+        mbar_wait_bounded(&mbar[j % kStages], static_cast<uint32_t>((j / kStages) & 1));
+      return;
+    }
+    T* s = reinterpret_cast<T*>(smem_raw + st * G::STAGE_BYTES);
+    const int t = static_cast<int>(blockIdx.x) + i * static_cast<int>(gridDim.x);
+    const int64_t x0 = static_cast<int64_t>(t % tiles_x) * TX;
+    const int64_t y0 = static_cast<int64_t>(t / tiles_x) * TY;
+    const int64_t gx0 = x0 - G::LA, gy0 = y0 - sd.T;
+    if (periodic && (gx0 < 0 || gx0 + COLS > nx || gy0 < 0 || gy0 + ROWS > ny)) {
+      fixup_periodic<T, COLS, ROWS>(s, in, nx, ny, gx0, gy0);
+      __syncthreads();
+    }
+    if constexpr (MODE == 0) {
+      if constexpr (sd.xform) xform_tile<T>(s, SE);
+      spec_compute<T, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
+    } else if constexpr (MODE == 1) {
+      const unsigned* hi_words = reinterpret_cast<const unsigned*>(s) + 1;
+      int maxe = 0;
+      bool bad = false;
+      for (int k = tid; k < SE; k += kThreads) {
+        const int e = static_cast<int>((hi_words[2 * k] >> 20) & 0x7ffu);
+        bad |= (e == 0x7ff);
+        maxe = max(maxe, e);
+      }
+      for (int off = 16; off > 0; off >>= 1) maxe = max(maxe, __shfl_xor_sync(0xffffffffu, maxe, off));
+      if ((tid & 31) == 0) s_wmax[tid >> 5] = maxe;
+      const bool any_bad = __syncthreads_or(bad);
+      int tile_e = 0;
+#pragma unroll
+      for (int w = 0; w < kThreads / 32; ++w) tile_e = max(tile_e, s_wmax[w]);
+      if (any_bad || (tile_e != 0 && (tile_e < kIxMinExp || tile_e > kIxMaxExp))) {
+        spec_compute<double, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
+      } else {
+        float2* s01 = reinterpret_cast<float2*>(s);
+        float* s2 = reinterpret_cast<float*>(extra);
+        for (int k = tid; k < SE; k += kThreads) {
+          float d0, d1, d2;
+          ix_split(s[k], tile_e, d0, d1, d2);
+          s01[k] = make_float2(d0, d1);
+          s2[k] = d2;
+        }
+        __syncthreads();
+        const double scale = tile_e == 0 ? 0.0 : itaps.c * ldexp(1.0, tile_e - 1022 - 3 * kIxDigitBits);
+        ix_compute<TY, SPEC>(s01, s2, out, nx, ny, periodic, x0, y0, itaps, scale);
+      }
+    } else {
+      float2* sf = reinterpret_cast<float2*>(extra);
+      if constexpr (sd.xform) xform_tile<double>(s, SE);
+      bool ok = true;
+      int maxe = 0;
+      for (int k = tid; k < SE; k += kThreads) {
+        float h, l;
+        int e;
+        ok = dd_split(s[k], h, l, e) && ok;
+        maxe = max(maxe, e);
+        sf[k] = make_float2(h, l);
+      }
+      for (int off = 16; off > 0; off >>= 1) maxe = max(maxe, __shfl_xor_sync(0xffffffffu, maxe, off));
+      if ((tid & 31) == 0) s_wmax[tid >> 5] = maxe;
+      const bool all_ok = __syncthreads_and(ok);
+      int tile_e = 0;
+#pragma unroll
+      for (int w = 0; w < kThreads / 32; ++w) tile_e = max(tile_e, s_wmax[w]);
+      if (all_ok && (tile_e == 0 || tile_e >= kDDTileExp))
+        dd_compute<TY, SPEC>(sf, s, out, nx, ny, periodic, x0, y0, dtaps);
+      else
+        spec_compute<double, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
+    }
+    __syncthreads();  // every thread is done with stage st (and the extra buffer)
+    if (tid == 0 && i + kStages < my_tiles) issue(i + kStages, st);
+  }
+}
+
+template <int MODE, typename T, int SPEC>
+int launch_tma(const CUtensorMap& map, const T* in, T* out, int64_t nx, int64_t ny, int periodic,
+               const Taps<T>& taps, const IxTaps& it, const DDTaps& dt, int* status, cudaStream_t st) {
+  using G = TmaGeom<MODE, T, SPEC>;
+  auto kern = k_stencil2d_tma<MODE, T, SPEC>;
+  static int per_sm = 0;  // resident CTAs per SM for this instantiation (set on first use)
+  if (per_sm == 0) {
+    CS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(G::SMEM)));
+    int occ = 0;
+    CS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, G::SMEM));
+    per_sm = occ > 0 ? occ : -1;
+  }
+  if (per_sm < 0) return set_error(CS_EUNSUPPORTED, "TMA stencil kernel does not fit on an SM");
+  const int64_t tiles_x = (nx + G::TX - 1) / G::TX, tiles_y = (ny + G::TY - 1) / G::TY;
+  const int64_t tiles = tiles_x * tiles_y;
+  if (tiles > 0x7fffffff) return set_error(CS_EINVAL, "grid too large for the TMA sweep");
+  const int64_t grid = std::min<int64_t>(tiles, static_cast<int64_t>(num_sms()) * per_sm);
+  kern<<<static_cast<unsigned>(grid), kThreads, G::SMEM, st>>>(map, in, out, nx, ny, periodic,
+                                                               static_cast<int>(tiles_x), static_cast<int>(tiles),
+                                                               taps, it, dt, status);
+  CS_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return CS_OK;
+}
+
+template <int MODE, typename T>
+int dispatch_tma(int variant, const CUtensorMap& map, const T* in, T* out, int64_t nx, int64_t ny,
+                 int periodic, const Taps<T>& taps, const IxTaps& it, const DDTaps& dt, int* status,
+                 cudaStream_t st) {
+  switch (variant) {
+#define CS_TMA_CASE(I)                                                                          \
+  case I:                                                                                       \
+    if constexpr (MODE == 1 && (kSpecs[I].xform || kSpecs[I].epi))                              \
+      return set_error(CS_EINVAL, "internal: no digit kernel for variant %d", I);               \
+    else                                                                                        \
+      return launch_tma<MODE, T, I>(map, in, out, nx, ny, periodic, taps, it, dt, status, st);
+    CS_TMA_CASE(0) CS_TMA_CASE(1) CS_TMA_CASE(2) CS_TMA_CASE(3) CS_TMA_CASE(4)
+    CS_TMA_CASE(5) CS_TMA_CASE(6) CS_TMA_CASE(7) CS_TMA_CASE(8) CS_TMA_CASE(9)
+    CS_TMA_CASE(10) CS_TMA_CASE(11) CS_TMA_CASE(12) CS_TMA_CASE(13)
+#undef CS_TMA_CASE
     default: return set_error(CS_EINVAL, "internal: unknown stencil variant %d", variant);
   }
 }
@@ -802,6 +1071,8 @@ int dispatch_spec(int variant, const T* in, T* out, int64_t nx, int64_t ny, int 
 }
 static_assert(kNumSpecs == 14, "update dispatch_spec");
 
+int make_tensor_map(const Stencil2DConfig* cfg, const void* in, int elem_bytes, int cols, int rows);
+
 template <typename T>
 int launch_stencil2d_t(const Stencil2DConfig* cfg, const void* vin, void* vout, cudaStream_t st) {
   const T* in = static_cast<const T*>(vin);
@@ -813,6 +1084,42 @@ int launch_stencil2d_t(const Stencil2DConfig* cfg, const void* vin, void* vout, 
     const SpecDesc& sd = kSpecs[cfg->variant];
     const int nt = (sd.L + sd.R + 1) * (sd.T + sd.B + 1);
     for (int i = 0; i < 32; ++i) taps.w[i] = i < nt ? static_cast<T>(cfg->weights[i]) : T(0);
+    if (cfg->use_tma && vec_ok && cfg->nx < (int64_t(1) << 31) && cfg->ny < (int64_t(1) << 31)) {
+      constexpr int V = Vec<T>::n;
+      const int LA = (sd.L + V - 1) / V * V, RA = (sd.R + V - 1) / V * V;
+      const int cols = LA + tile_x<T>() + RA, rows = 64 + sd.T + sd.B;
+      if (cfg->tmap_in != vin) {
+        int rc = make_tensor_map(cfg, vin, sizeof(T), cols, rows);
+        if (rc != CS_OK) return rc;
+      }
+      int* status = nullptr;
+      int rc = stencil2d_status_ptr(&status);
+      if (rc != CS_OK) return rc;
+      IxTaps it{};
+      DDTaps dt{};
+      int mode = 0;
+      if constexpr (sizeof(T) == 8) {
+        if (cfg->fp64_mode == CS_FP64_AUTO && cfg->ix_ok) {
+          mode = 1;
+          for (int i = 0; i < 32; ++i) it.n[i] = i < nt ? static_cast<float>(cfg->ix_n[i]) : 0.0f;
+          it.c = cfg->ix_c;
+        } else if (cfg->fp64_mode == CS_FP64_AUTO && cfg->dd_ok) {
+          mode = 2;
+          for (int i = 0; i < 32; ++i) {
+            const double w = i < nt ? cfg->weights[i] : 0.0;
+            dt.hi[i] = static_cast<float>(w);
+            dt.lo[i] = static_cast<float>(w - static_cast<double>(dt.hi[i]));
+          }
+        }
+      }
+      if constexpr (sizeof(T) == 8) {
+        if (mode == 1)
+          return dispatch_tma<1, T>(cfg->variant, cfg->tmap, in, out, cfg->nx, cfg->ny, periodic, taps, it, dt, status, st);
+        if (mode == 2)
+          return dispatch_tma<2, T>(cfg->variant, cfg->tmap, in, out, cfg->nx, cfg->ny, periodic, taps, it, dt, status, st);
+      }
+      return dispatch_tma<0, T>(cfg->variant, cfg->tmap, in, out, cfg->nx, cfg->ny, periodic, taps, it, dt, status, st);
+    }
     if constexpr (sizeof(T) == 8) {
       if (cfg->ix_ok && cfg->fp64_mode == CS_FP64_AUTO) {
         IxTaps it;

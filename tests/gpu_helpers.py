@@ -52,7 +52,8 @@ def stencil_cases(h):
     ]
 
 
-def run2d(cs, torch, field, desc_kw, dtype, out_init=None, graph=False, reps=1, fp64_mode=None):
+def run2d(cs, torch, field, desc_kw, dtype, out_init=None, graph=False, reps=1, fp64_mode=None,
+          tile_choice=None):
     """Applies a plan once (or `reps` times, swapping) on the GPU; returns the output as FP64."""
     tdt = torch.float64 if dtype == cs.CS_F64 else torch.float32
     ndt = np.float64 if dtype == cs.CS_F64 else np.float32
@@ -67,6 +68,8 @@ def run2d(cs, torch, field, desc_kw, dtype, out_init=None, graph=False, reps=1, 
     try:
         if fp64_mode is not None:
             cs.cs_plan_set_fp64_mode(plan, fp64_mode)
+        if tile_choice is not None:
+            cs.cs_plan_set_tile_choice(plan, tile_choice)
         if graph:
             cs.cs_plan_use_graph(plan, True)
         for r in range(reps):
