@@ -51,6 +51,8 @@ def peaks():
 
 # FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s; probe: 1.9 DFMA/clk)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 instructions (DFMA, DADD, DMUL each one): 152 SMs x 2 per clock x 2.07 GHz
+FP64_PEAK_GOPS = 152 * 2 * 2.07
 # FP32/INT lanes: 152 SMs x 128 lanes x 2.07 GHz, one operation per lane per clock
 FP32_LANE_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 
@@ -408,6 +410,7 @@ def bench_ch(cs, torch, stream, cases=None):
         c0 = torch.from_numpy(W.ch_initial(n, seed=5)).to("cuda", tdt)
         f = [c0.clone(), c0.clone(), torch.zeros_like(c0)]
         plan = cs.cs_ch_create(cs.CHDesc(n=n, storage=storage, D=1.0, gamma=0.01, dt=0.1 * h), *f)
+        cs.cs_autotune(plan, stream)  # chunks per line of the partitioned line solves
         cs.cs_ch_step(plan, 5, stream=stream)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -421,7 +424,9 @@ def bench_ch(cs, torch, stream, cases=None):
         key = f"n{n}_{'f64' if storage == cs.CS_F64 else 'f32'}"
         fp64_ops = ch_fp64_ops_per_point(storage == cs.CS_F64, chunks, m) * n * n
         out[key] = {"ms_per_step": round(ms, 4), "steps_per_s": round(1e3 / ms, 1),
-                    "fp64_tflops": round(fp64_ops / (ms * 1e-3) / 1e12, 3)}
+                    "fp64_gops": round(fp64_ops / (ms * 1e-3) / 1e9, 1),
+                    "fp64_frac": round(fp64_ops / (ms * 1e-3) / 1e9 / FP64_PEAK_GOPS, 3),
+                    "chunks_per_line": chunks}
     return out
 
 

@@ -175,7 +175,9 @@ int cs_plan_use_graph(cs_plan_t plan, int enable);
 /* Times the candidate tile / launch shapes of the plan's kernel on its own buffers (it
  * overwrites d_out), each launch from a cold L2 (the first call allocates a 256 MB buffer that
  * the library reads to evict the cache, kept until exit), keeps the fastest, and records it in
- * the process-wide tuning table.  The
+ * the process-wide tuning table.  For a Cahn-Hilliard plan it times one ADI step for every
+ * valid number of chunks per line (the line-solve partition) from the plan's current state and
+ * restores the fields afterwards.  The
  * table is keyed by (kernel, dtype, shape class, SM count) and can be saved to / loaded from a
  * JSON file with cs_tune_save / cs_tune_load.  Synchronises the stream. */
 int cs_autotune(cs_plan_t plan, void* cuda_stream);

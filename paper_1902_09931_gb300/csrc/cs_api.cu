@@ -389,7 +389,7 @@ int cs_plan_use_graph(cs_plan_t p, int enable) {
 
 int cs_autotune(cs_plan_t p, void* stream) {
   if (!p) return set_error(CS_EINVAL, "null plan");
-  if (p->kind == kCahnHilliard) return set_error(CS_EUNSUPPORTED, "autotune applies to stencil plans");
+  if (p->kind == kCahnHilliard) return ch_autotune(p->ch, static_cast<cudaStream_t>(stream));
   if (p->elems == 0) return CS_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int nchoices = p->kind == kStencil2D ? stencil2d_num_tile_choices() : batch1d_num_choices();

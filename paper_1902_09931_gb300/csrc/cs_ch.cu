@@ -23,6 +23,7 @@
 // ends (16 P FMAs) and corrects x = g - S_L t_{p-1} - S_R h_{p+1}.  This is exact (up to
 // rounding) and gives n * P independent threads instead of n sequential lines.
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -53,6 +54,7 @@ struct CHPlan {
 namespace {
 
 constexpr int kTX = 64, kTY = 32, kThreads = 256, kSolveThreads = 128;
+constexpr int kU = 8;  // line elements per register batch in the solves
 
 // ---- exact conversions on the integer pipe (f32 <-> f64 conversion runs on the FP64 pipe) ----
 __device__ __forceinline__ double widen(float f) {
@@ -195,11 +197,42 @@ __global__ void k_reduce_final(const double* __restrict__ partials, int nblocks,
   }
 }
 
+// A batch of kU line elements starting at `at` (element stride es): 16-byte vector accesses
+// when the line is contiguous (rows; `at` is then a multiple of kU), strided scalars otherwise.
+template <typename IT, bool CONTIG>
+__device__ __forceinline__ void load_batch(const IT* __restrict__ p, int64_t at, int64_t es, double (&v)[8]) {
+  if constexpr (CONTIG && sizeof(IT) == 8) {
+#pragma unroll
+    for (int u = 0; u < 8; u += 2) {
+      const double2 d = *reinterpret_cast<const double2*>(p + at + u);
+      v[u] = d.x;
+      v[u + 1] = d.y;
+    }
+  } else if constexpr (CONTIG) {
+#pragma unroll
+    for (int u = 0; u < 8; u += 4) {
+      const float4 f = *reinterpret_cast<const float4*>(p + at + u);
+      v[u] = widen(f.x); v[u + 1] = widen(f.y); v[u + 2] = widen(f.z); v[u + 3] = widen(f.w);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = widen(p[at + u * es]);
+  }
+}
+template <bool CONTIG>
+__device__ __forceinline__ void store_batch(double* __restrict__ p, int64_t at, int64_t es, const double (&v)[8]) {
+  if constexpr (CONTIG) {
+#pragma unroll
+    for (int u = 0; u < 8; u += 2) *reinterpret_cast<double2*>(p + at + u) = make_double2(v[u], v[u + 1]);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) p[at + u * es] = v[u];
+  }
+}
+
 // Phase 1: A g = b on chunk p of a line (LU forward then backward), g over the scratch.
 // Coefficients (negated / pre-scaled): nl1, nl2, dinv, nu1, nu2 at coef[0..5m).  Elements are
 // processed in register batches of kU so that a batch's loads are in flight together.
-constexpr int kU = 8;
-
 template <typename IT, bool CONTIG>
 __global__ void __launch_bounds__(kSolveThreads)
     k_solve_local(const IT* __restrict__ in, double* __restrict__ G, double* __restrict__ bnd,
@@ -219,8 +252,7 @@ __global__ void __launch_bounds__(kSolveThreads)
   double y1 = 0.0, y2 = 0.0;
   for (int k0 = 0; k0 < m; k0 += kU) {
     double v[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) v[u] = widen(in[base + (k0 + u) * es]);
+    load_batch<IT, CONTIG>(in, base + k0 * es, es, v);
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const double y = fma(__ldg(nl1 + k0 + u), y1, fma(__ldg(nl2 + k0 + u), y2, v[u]));
@@ -228,14 +260,12 @@ __global__ void __launch_bounds__(kSolveThreads)
       y2 = y1;
       y1 = y;
     }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) G[base + (k0 + u) * es] = v[u];
+    store_batch<CONTIG>(G, base + k0 * es, es, v);
   }
   double g1 = 0.0, g2 = 0.0, g_last = 0.0, g_last2 = 0.0;
   for (int k0 = m - kU; k0 >= 0; k0 -= kU) {
     double v[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) v[u] = G[base + (k0 + u) * es];
+    load_batch<double, CONTIG>(G, base + k0 * es, es, v);
 #pragma unroll
     for (int u = kU - 1; u >= 0; --u) {
       const int k = k0 + u;
@@ -248,8 +278,7 @@ __global__ void __launch_bounds__(kSolveThreads)
       g_last2 = v[kU - 2];
       g_last = v[kU - 1];
     }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) G[base + (k0 + u) * es] = v[u];
+    store_batch<CONTIG>(G, base + k0 * es, es, v);
   }
   // chunk-end values: k = 0, 1 are g1, g2 after the loop; k = m-2, m-1 kept from the first batch
   double* b = bnd + static_cast<int64_t>(p) * 4 * n + line;
@@ -295,8 +324,7 @@ __global__ void __launch_bounds__(kSolveThreads)
   const int64_t base = line * line_stride + static_cast<int64_t>(p) * m * es;
   for (int k0 = 0; k0 < m; k0 += kU) {
     double x[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) x[u] = G[base + (k0 + u) * es];
+    load_batch<double, CONTIG>(G, base + k0 * es, es, x);
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int k = k0 + u;
@@ -304,8 +332,7 @@ __global__ void __launch_bounds__(kSolveThreads)
              fma(-__ldg(sr0 + k), h0, fma(-__ldg(sr1 + k), h1, x[u]))));
     }
     if constexpr (MODE == 0) {
-#pragma unroll
-      for (int u = 0; u < kU; ++u) w_out[base + (k0 + u) * es] = x[u];
+      store_batch<CONTIG>(w_out, base + k0 * es, es, x);
     } else {
       double c[kU], pv[kU];
 #pragma unroll
@@ -643,6 +670,83 @@ int ch_fields(CHPlan* p, void** prev, void** cur, int64_t* steps) {
   if (prev) *prev = p->field[p->iprev];
   if (cur) *cur = p->field[p->icur];
   if (steps) *steps = p->steps;
+  return CS_OK;
+}
+
+namespace {
+
+// (Re)builds the partition tables and chunk-end buffer for P chunks per line.
+int set_partition(CHPlan* p, int P) {
+  std::vector<double> coef, K;
+  int rc = build_tables(p->n, P, p->a, coef, K);
+  if (rc != CS_OK) return rc;
+  double *bnd = nullptr, *dcoef = nullptr, *dK = nullptr;
+  cudaError_t e = cudaMalloc(&bnd, static_cast<size_t>(4) * P * p->n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&dcoef, coef.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&dK, K.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(dcoef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dK, K.data(), K.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(bnd); cudaFree(dcoef); cudaFree(dK);
+    return cuda_error(e, "Cahn-Hilliard partition tables");
+  }
+  cudaFree(p->bnd); cudaFree(p->coef); cudaFree(p->K);
+  p->bnd = bnd; p->coef = dcoef; p->K = dK;
+  p->P = P;
+  p->m = static_cast<int>(p->n / P);
+  return CS_OK;
+}
+
+}  // namespace
+
+// Times one step for every valid chunk count (1 .. 64 chunks per line) from the plan's current
+// state, keeps the fastest, records it in the tuning table, and restores the fields.
+int ch_autotune(CHPlan* p, cudaStream_t s) {
+  const size_t eb = p->storage == CS_F32 ? 4 : 8;
+  const size_t bytes = static_cast<size_t>(p->n) * p->n * eb;
+  void* save[2] = {nullptr, nullptr};
+  CS_CUDA_TRY(cudaMalloc(&save[0], bytes));
+  cudaError_t e = cudaMalloc(&save[1], bytes);
+  if (e != cudaSuccess) { cudaFree(save[0]); return cuda_error(e, "autotune state copy"); }
+  const int ip = p->iprev, ic = p->icur, in = p->inext;
+  const int64_t steps = p->steps;
+  e = cudaMemcpyAsync(save[0], p->field[ip], bytes, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(save[1], p->field[ic], bytes, cudaMemcpyDeviceToDevice, s);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  int rc = e == cudaSuccess ? CS_OK : cuda_error(e, "autotune setup");
+  int best = p->P;
+  float best_ms = 1e30f;
+  for (int P = 1; P <= 64 && rc == CS_OK; P *= 2) {
+    if (!valid_chunks(p->n, P)) continue;
+    rc = set_partition(p, P);
+    if (rc != CS_OK) break;
+    rc = ch_step(p, 1, nullptr, nullptr, s);  // warm-up
+    if (rc != CS_OK) break;
+    cudaEventRecord(e0, s);
+    rc = ch_step(p, 2, nullptr, nullptr, s);
+    cudaEventRecord(e1, s);
+    if (rc != CS_OK) break;
+    e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) { rc = cuda_error(e, "autotune timing"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) { best_ms = ms; best = P; }
+  }
+  if (rc == CS_OK) rc = set_partition(p, best);
+  // restore the state the caller had
+  p->iprev = ip; p->icur = ic; p->inext = in; p->steps = steps;
+  cudaMemcpyAsync(p->field[ip], save[0], bytes, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(p->field[ic], save[1], bytes, cudaMemcpyDeviceToDevice, s);
+  cudaStreamSynchronize(s);
+  cudaFree(save[0]); cudaFree(save[1]);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc != CS_OK) return rc;
+  char key[96];
+  snprintf(key, sizeof key, "ch|%s|n%lld|sm%d", p->storage == CS_F32 ? "f32" : "f64", (long long)p->n, num_sms());
+  tune_store(key, best);
   return CS_OK;
 }
 

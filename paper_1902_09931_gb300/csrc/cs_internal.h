@@ -86,6 +86,7 @@ int ch_invariants(CHPlan* p, double* mass, double* energy, cudaStream_t s);
 int ch_fields(CHPlan* p, void** prev, void** cur, int64_t* steps);
 int ch_config(CHPlan* p, int32_t* chunks, int32_t* chunk_len);
 int ch_set_fields(CHPlan* p, void* prev, void* cur, void* next);
+int ch_autotune(CHPlan* p, cudaStream_t s);
 void ch_destroy(CHPlan* p);
 
 }  // namespace cs

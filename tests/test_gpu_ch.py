@@ -182,3 +182,30 @@ def test_trajectory_matches_oracle(env):
     ref, _, _ = orc.ch_run(c0, D, GAMMA, dt, steps)
     growth = np.exp(D / (4 * GAMMA) * steps * dt)
     assert np.abs(got - ref).max() <= 1e-12 * growth * steps * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_autotune_restores_state_and_keeps_parity(env, storage):
+    """cs_autotune on a Cahn-Hilliard plan times the line-solve partitions, restores the fields
+    and the step count, and the tuned plan still matches the oracle step."""
+    cs, torch, orc = env
+    n = 256
+    h = 2 * np.pi / n
+    dt = 0.1 * h
+    prev = W.ch_initial(n, seed=5)
+    cur = prev + 0.01 * W.ch_initial(n, seed=6)
+    if storage == 1:
+        prev = prev.astype(np.float32).astype(np.float64)
+        cur = cur.astype(np.float32).astype(np.float64)
+    r = Run(cs, torch, prev, cur, storage, dt)
+    cs.cs_autotune(r.plan)
+    torch.cuda.synchronize()
+    p0, c0, steps0 = r.state()
+    assert steps0 == 0 and np.array_equal(p0, prev) and np.array_equal(c0, cur)
+    chunks, m = cs.cs_ch_config(r.plan)
+    assert chunks * m == n
+    r.step(1)
+    _, got, _ = r.state()
+    r.close()
+    ref = orc.ch_step(prev, cur, D, GAMMA, dt)
+    assert np.abs(got - ref).max() <= step_tolerance(orc, prev, cur, ref, n, dt, TOL[storage])
