@@ -346,7 +346,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sweeps_per_step": len(sweeps), "points_per_step": pts_per_step,
-                   "l2": "flushed (256 MB write) before every sweep, outside the timed intervals",
+                   "l2": "evicted before every sweep by reading a 256 MB buffer (2x L2), outside the timed intervals",
                    "parallelism": f"replicas x{world} (independent grids per GPU)"},
         "hbm_gbs": round(hbm_gbs, 1), "hbm_frac_of_measured": round(hbm_gbs / hbm_peak, 4),
         "hbm_frac_of_8tbs": round(hbm_gbs / 8000.0, 4),
