@@ -98,6 +98,21 @@ __device__ __forceinline__ void load_tile(T* s, const T* __restrict__ in, int64_
   constexpr int V = Vec<T>::n;
   const int nch = cols / V;
   const int total = rows * nch;
+  const int64_t gy0 = y0 - top, gx0 = x0 - LA;
+  if (vec_ok && gy0 >= 0 && gy0 + rows <= ny && gx0 >= 0 && gx0 + cols <= nx) {
+    // interior tile (the common case): warp w copies rows w, w + 8, ...; no bounds or wrap checks
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const T* src = in + (gy0 + warp) * nx + gx0;
+    T* dst = s + warp * cols;
+    for (int r = warp; r < rows; r += kThreads / 32) {
+      for (int ch = lane; ch < nch; ch += 32) cp_async16(dst + ch * V, src + ch * V);
+      src += (kThreads / 32) * nx;
+      dst += (kThreads / 32) * cols;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    return;
+  }
   const bool one_wrap = nx >= cols && ny >= rows;  // tile halo reaches at most one period out
   for (int idx = threadIdx.x; idx < total; idx += kThreads) {
     const int r = idx / nch;
@@ -236,48 +251,122 @@ constexpr int kIxDigitBits = 18;
 constexpr int kIxMinExp = 1023 - 900;
 constexpr int kIxMaxExp = 1023 + 900;
 
-__device__ __forceinline__ float ix_digit(int64_t v) {
-  // exact for |v| < 2^22: bias into the mantissa of 1.5 * 2^23 and subtract
-  return __fsub_rn(__int_as_float(0x4B400000 + static_cast<int>(v)), 12582912.0f);
-}
 
 // Digits of x on the tile grid whose top is 2^G with G = tile_e - 1022 (tile_e = largest biased
-// exponent in the tile): A = |x| / 2^(G-54) truncated, d0 = A >> 36, d1, d2 the next 18 bits.
+// exponent in the tile): A = |x| / 2^(G-54) truncated (54 bits), d0 = A >> 36, d1 and d2 the next
+// 18-bit groups, each carrying the sign of x.  Works on the two 32-bit words of x with funnel
+// shifts: A = (M << 1) >> (tile_e - e), M the 53-bit significand.
 __device__ __forceinline__ void ix_split(double x, int tile_e, float& d0, float& d1, float& d2) {
-  const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x));
-  const int e = static_cast<int>((b >> 52) & 0x7ffu);
-  uint64_t A = 0;
-  if (e != 0) {  // subnormals are far below the grid (tile_e >= kIxMinExp): they count as 0
-    const uint64_t M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = e - tile_e + 1;  // <= 1
-    A = sh >= 0 ? (M << sh) : (sh > -64 ? (M >> (-sh)) : 0ull);
+  const uint32_t hi = static_cast<uint32_t>(__double2hiint(x));
+  const uint32_t lo = static_cast<uint32_t>(__double2loint(x));
+  const int e = static_cast<int>((hi >> 20) & 0x7ffu);
+  // (M << 1) as two words, 22 + 32 bits.  Zeros and subnormals (e == 0) need no special case: a
+  // digit tile has tile_e >= kIxMinExp, so t >= 54 and every digit is 0, and an all-zero tile
+  // (tile_e == 0) is scaled by 0.
+  const uint32_t mh = __funnelshift_l(lo, (hi & 0xFFFFFu) | 0x100000u, 1);
+  const uint32_t ml = lo << 1;
+  const int t = tile_e - e;  // >= 0
+  uint32_t ah, al;
+  if (t < 32) {
+    al = __funnelshift_r(ml, mh, t);
+    ah = mh >> t;
+  } else {
+    al = t < 54 ? (mh >> (t - 32)) : 0u;
+    ah = 0u;
   }
-  const int64_t s = static_cast<int64_t>(b >> 63);  // 0 or 1
-  const int64_t a0 = static_cast<int64_t>(A >> 36);
-  const int64_t a1 = static_cast<int64_t>((A >> 18) & 0x3FFFFull);
-  const int64_t a2 = static_cast<int64_t>(A & 0x3FFFFull);
-  d0 = ix_digit(s ? -a0 : a0);
-  d1 = ix_digit(s ? -a1 : a1);
-  d2 = ix_digit(s ? -a2 : a2);
+  // a digit a < 2^18 becomes +-(2^23 + a) by setting the mantissa bits of +-2^23 (exact), and
+  // subtracting +-2^23 leaves +-a
+  const uint32_t K = 0x4B000000u | (hi & 0x80000000u);
+  const float k = __uint_as_float(K);
+  d0 = __fsub_rn(__uint_as_float((ah >> 4) | K), k);
+  d1 = __fsub_rn(__uint_as_float((__funnelshift_r(al, ah, 18) & 0x3FFFFu) | K), k);
+  d2 = __fsub_rn(__uint_as_float((al & 0x3FFFFu) | K), k);
 }
 
-// Exact integer value of an integer-valued float with |f| <= 2^24.
-__device__ __forceinline__ int64_t ix_int(float f) { return static_cast<int64_t>(__float2int_rn(f)); }
+// T = S0 * 2^36 + S1 * 2^18 + S2 (|T| < 2^61, exact: the digit sums are integers below 2^24 in
+// magnitude), formed on the integer pipe.
+__device__ __forceinline__ long long ix_join(float S0, float S1, float S2) {
+  return (static_cast<long long>(__float2int_rn(S0)) << 36) +
+         (static_cast<long long>(__float2int_rn(S1)) << 18) + static_cast<long long>(__float2int_rn(S2));
+}
 
-// Round-to-nearest-even int64 -> double on the integer pipe.
-__device__ __forceinline__ double ix_to_double(int64_t t) {
-  if (t == 0) return 0.0;
-  const uint64_t sign = static_cast<uint64_t>(t) & 0x8000000000000000ull;
-  uint64_t a = sign ? static_cast<uint64_t>(-t) : static_cast<uint64_t>(t);
-  const int lz = __clzll(static_cast<long long>(a));
-  a <<= lz;                      // leading one at bit 63
-  uint64_t mant = a >> 11;       // 53 bits including the leading one
-  const uint64_t rem = a & 0x7FFull;
-  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ++mant;  // may carry to 2^53
-  const uint64_t bits = sign | ((static_cast<uint64_t>(1086 - lz) << 52) + (mant - (1ull << 52)));
+// T rounded once, to nearest-even FP64, by the hardware conversion (an FP64-pipe instruction).
+__device__ __forceinline__ double ix_combine(float S0, float S1, float S2) {
+  return __ll2double_rn(ix_join(S0, S1, S2));
+}
+
+// The same rounding on the integer pipe: normalise |T|, keep 53 bits, round half to even, and
+// assemble sign, exponent and significand.  GB300's FP64 pipe issues about 2 operations per
+// clock per SM, so kernels with few taps convert some outputs this way to keep that pipe from
+// bounding them.
+__device__ __forceinline__ double ix_combine_int(float S0, float S1, float S2) {
+  const long long T = ix_join(S0, S1, S2);
+  if (T == 0) return 0.0;
+  const unsigned long long sgn = static_cast<unsigned long long>(T) & 0x8000000000000000ull;
+  const unsigned long long a = sgn ? 0ull - static_cast<unsigned long long>(T) : static_cast<unsigned long long>(T);
+  uint32_t ahi = static_cast<uint32_t>(a >> 32), alo = static_cast<uint32_t>(a);
+  const int lz = ahi ? __clz(ahi) : 32 + __clz(alo);
+  if (lz >= 32) {  // leading one to bit 63 of (ahi:alo)
+    ahi = alo << (lz - 32);
+    alo = 0u;
+  } else if (lz > 0) {
+    ahi = __funnelshift_l(alo, ahi, lz);
+    alo <<= lz;
+  }
+  uint32_t mhi = ahi >> 11;                      // significand bits 63..43 (with the leading one)
+  const uint32_t mlo = __funnelshift_r(alo, ahi, 11);  // bits 42..11
+  const uint32_t rem = alo & 0x7FFu;             // bits 10..0, dropped
+  const bool up = rem > 0x400u || (rem == 0x400u && (mlo & 1u));
+  const uint32_t mlo2 = mlo + (up ? 1u : 0u);
+  mhi += (up && mlo2 == 0u) ? 1u : 0u;           // a carry to 2^53 moves into the exponent field
+  const unsigned long long bits =
+      sgn + ((static_cast<unsigned long long>(1086 - lz) << 52) +
+             ((static_cast<unsigned long long>(mhi) << 32 | mlo2) - (1ull << 52)));
   return __longlong_as_double(static_cast<long long>(bits));
 }
 
+constexpr int popcount32(uint32_t m) { return m == 0u ? 0 : static_cast<int>(m & 1u) + popcount32(m >> 1); }
+
+// Largest high word (sign cleared) of the n staged FP64 values (n even, 16-byte aligned): its top
+// bits are the largest biased exponent, and it is >= 0x7ff00000 exactly when the tile holds an
+// inf or a nan.  Every thread of the block gets the result; s_red holds kThreads / 32 words.
+__device__ __forceinline__ uint32_t ix_tile_max_hi(const double* s, int n, unsigned* s_red) {
+  const uint4* q = reinterpret_cast<const uint4*>(s);
+  uint32_t m = 0u;
+  for (int k = threadIdx.x; k < n / 2; k += kThreads) {
+    const uint4 v = q[k];
+    m = __vimax3_u32(m, v.y & 0x7fffffffu, v.w & 0x7fffffffu);
+  }
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  uint32_t r = 0u;
+#pragma unroll
+  for (int w = 0; w < kThreads / 32; ++w) r = max(r, s_red[w]);
+  return r;
+}
+
+// Replaces the n staged FP64 values by their digits: (d0, d1) pairs over the values' own slots,
+// d2 in s2.  Each thread converts and overwrites two values at a time.
+__device__ __forceinline__ void ix_split_tile(double* s, float* s2, int n, int tile_e) {
+  const double2* q = reinterpret_cast<const double2*>(s);
+  float4* q01 = reinterpret_cast<float4*>(s);
+  float2* q2 = reinterpret_cast<float2*>(s2);
+  for (int k = threadIdx.x; k < n / 2; k += kThreads) {
+    const double2 v = q[k];
+    float a0, a1, a2, b0, b1, b2;
+    ix_split(v.x, tile_e, a0, a1, a2);
+    ix_split(v.y, tile_e, b0, b1, b2);
+    q01[k] = make_float4(a0, a1, b0, b1);
+    q2[k] = make_float2(a2, b2);
+  }
+}
+
+// Digit sums of two adjacent tile columns per thread, "push" form: every staged row adds its
+// contributions to the (up to H) output rows it feeds, held in H rolling accumulators per column
+// and digit; an output row is complete once its last input row has been added.  A row's digits
+// are read as 16-byte (d0, d1) and 8-byte d2 pairs, W + 1 columns (+1 when L is odd) serving both
+// outputs, and the two results leave as one 16-byte store where both columns are written.
 template <int TY, int SPEC>
 __device__ __forceinline__ void ix_compute(const float2* s01, const float* s2, double* __restrict__ out,
                                            int64_t nx, int64_t ny, int periodic, int64_t x0,
@@ -286,59 +375,97 @@ __device__ __forceinline__ void ix_compute(const float2* s01, const float* s2, d
   constexpr int L = sd.L, R = sd.R, TT = sd.T, BB = sd.B;
   constexpr int V = Vec<double>::n;
   constexpr int TX = tile_x<double>();
+  static_assert(TX == 64, "one warp spans the tile's 64 columns");
   constexpr int LA = (L + V - 1) / V * V, RA = (R + V - 1) / V * V;
   constexpr int COLS = LA + TX + RA;
   constexpr int W = L + R + 1, H = TT + BB + 1;
-  constexpr int WX = TX / 32, WY = 8 / WX, RW = TY / WY;
+  constexpr int WY = kThreads / 32, RW = TY / WY;
+  constexpr int S0 = LA - L, X = S0 & 1, NP = (W + 1 + X + 1) / 2;  // pairs read per row
+  // with at most 5 taps the FP64 pipe (conversion + scale per output) bounds the kernel: the
+  // second column's conversion then runs on the integer pipe (measured on GB300)
+  constexpr bool kIntJoin = popcount32(sd.mask) <= 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = (warp % WX) * 32 + lane;
-  const int r0 = (warp / WX) * RW;
+  const int c = 2 * lane;
+  const int r0 = warp * RW;
   const int64_t gx = x0 + c;
-  const bool col_ok = gx < nx && (periodic || (gx >= L && gx < nx - R));
-  const float2* a = s01 + LA + c - L;
-  const float* b = s2 + LA + c - L;
-  float w01[H][W][2], w2[H][W];
+  const bool ok0 = gx < nx && (periodic || (gx >= L && gx < nx - R));
+  const bool ok1 = gx + 1 < nx && (periodic || (gx + 1 >= L && gx + 1 < nx - R));
+  // one 16-byte store per row when both columns are written and every row start is 16-byte aligned
+  const bool both = ok0 && ok1 && (reinterpret_cast<uintptr_t>(out) & 15u) == 0 && (nx & 1) == 0;
+  // this thread writes rows gy0 + k for klo <= k < khi
+  const int64_t gy0 = y0 + r0;
+  const int64_t ylo = periodic ? 0 : TT, yhi = periodic ? ny : ny - BB;
+  auto rows_below = [](int64_t d) { return static_cast<int>(d < 0 ? 0 : (d > RW ? RW : d)); };
+  const int klo = rows_below(ylo - gy0);
+  const int khi = (ok0 || ok1) ? rows_below(yhi - gy0) : 0;
+  double* op = out + gy0 * nx + gx;
+  const float4* a = reinterpret_cast<const float4*>(s01 + (S0 - X) + c);  // (S0 - X + c) is even
+  const float2* b = reinterpret_cast<const float2*>(s2 + (S0 - X) + c);
+  float acc[H][2][3];
 #pragma unroll
-  for (int q = 0; q < H - 1; ++q)
+  for (int q = 0; q < H; ++q)
 #pragma unroll
-    for (int p = 0; p < W; ++p) {
-      const float2 v = a[(r0 + q) * COLS + p];
-      w01[q + 1][p][0] = v.x;
-      w01[q + 1][p][1] = v.y;
-      w2[q + 1][p] = b[(r0 + q) * COLS + p];
-    }
+    for (int j = 0; j < 2; ++j) acc[q][j][0] = acc[q][j][1] = acc[q][j][2] = 0.0f;
 #pragma unroll
-  for (int k = 0; k < RW; ++k) {
+  for (int i = 0; i < RW + H - 1; ++i) {  // input row r0 + i feeds output rows i - q
+    float v0[2 * NP], v1[2 * NP], v2[2 * NP];
 #pragma unroll
-    for (int q = 0; q < H - 1; ++q)
+    for (int k = 0; k < NP; ++k) {
+      bool used = false;
 #pragma unroll
-      for (int p = 0; p < W; ++p) {
-        w01[q][p][0] = w01[q + 1][p][0];
-        w01[q][p][1] = w01[q + 1][p][1];
-        w2[q][p] = w2[q + 1][p];
+      for (int q = 0; q < H; ++q)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+          for (int p = 0; p < W; ++p) {
+            const int e = X + j + p;
+            used |= (e >> 1) == k && ((sd.mask >> (q * W + p)) & 1u) && (i - q >= 0) && (i - q < RW);
+          }
+      if (used) {
+        const float4 d = a[(r0 + i) * (COLS / 2) + k];
+        const float2 f = b[(r0 + i) * (COLS / 2) + k];
+        v0[2 * k] = d.x;
+        v1[2 * k] = d.y;
+        v0[2 * k + 1] = d.z;
+        v1[2 * k + 1] = d.w;
+        v2[2 * k] = f.x;
+        v2[2 * k + 1] = f.y;
       }
-#pragma unroll
-    for (int p = 0; p < W; ++p) {
-      const float2 v = a[(r0 + k + H - 1) * COLS + p];
-      w01[H - 1][p][0] = v.x;
-      w01[H - 1][p][1] = v.y;
-      w2[H - 1][p] = b[(r0 + k + H - 1) * COLS + p];
     }
-    float S0 = 0.0f, S1 = 0.0f, S2 = 0.0f;
 #pragma unroll
-    for (int q = 0; q < H; ++q)
+    for (int q = 0; q < H; ++q) {
+      const int o = i - q;
+      if (o < 0 || o >= RW) continue;
 #pragma unroll
-      for (int p = 0; p < W; ++p)
-        if ((sd.mask >> (q * W + p)) & 1u) {
-          const float n = taps.n[q * W + p];
-          S0 = __fmaf_rn(n, w01[q][p][0], S0);
-          S1 = __fmaf_rn(n, w01[q][p][1], S1);
-          S2 = __fmaf_rn(n, w2[q][p], S2);
+      for (int j = 0; j < 2; ++j) {
+        float* A = acc[o % H][j];
+#pragma unroll
+        for (int p = 0; p < W; ++p)
+          if ((sd.mask >> (q * W + p)) & 1u) {
+            const float n = taps.n[q * W + p];
+            A[0] = __fmaf_rn(n, v0[X + j + p], A[0]);
+            A[1] = __fmaf_rn(n, v1[X + j + p], A[1]);
+            A[2] = __fmaf_rn(n, v2[X + j + p], A[2]);
+          }
+      }
+    }
+    const int done = i - (H - 1);  // output row complete after its last input row
+    if (done >= 0) {
+      float* A0 = acc[done % H][0];
+      float* A1 = acc[done % H][1];
+      const double val0 = ix_combine(A0[0], A0[1], A0[2]) * scale;
+      const double val1 = (kIntJoin ? ix_combine_int(A1[0], A1[1], A1[2]) : ix_combine(A1[0], A1[1], A1[2])) * scale;
+      A0[0] = A0[1] = A0[2] = A1[0] = A1[1] = A1[2] = 0.0f;
+      if (done >= klo && done < khi) {
+        if (both) {
+          *reinterpret_cast<double2*>(op) = make_double2(val0, val1);
+        } else {
+          if (ok0) op[0] = val0;
+          if (ok1) op[1] = val1;
         }
-    const int64_t T = ix_int(S0) * (int64_t(1) << 36) + ix_int(S1) * (int64_t(1) << 18) + ix_int(S2);
-    const double acc = ix_to_double(T) * scale;
-    const int64_t gy = y0 + r0 + k;
-    if (col_ok && gy < ny && (periodic || (gy >= TT && gy < ny - BB))) out[gy * nx + gx] = acc;
+      }
+      op += nx;
+    }
   }
 }
 
@@ -355,37 +482,23 @@ __global__ void __launch_bounds__(kThreads)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* s = reinterpret_cast<double*>(smem_raw);
   float* s2 = reinterpret_cast<float*>(s + ROWS * COLS);
-  __shared__ int s_maxe;
-  if (threadIdx.x == 0) s_maxe = 0;
+  __shared__ unsigned s_red[kThreads / 32];
+  static_assert(COLS % 2 == 0, "digit passes take values in pairs");
   const int64_t x0 = static_cast<int64_t>(blockIdx.x) * TX;
   const int64_t y0 = static_cast<int64_t>(blockIdx.y) * TY;
   load_tile<double>(s, in, nx, ny, periodic != 0, vec_ok != 0, x0, y0, sd.T, LA, COLS, ROWS);
-  // pass 1: the tile's largest exponent; inf / nan force native FP64
-  int maxe = 0;
-  bool bad = false;
-  const unsigned* hi_words = reinterpret_cast<const unsigned*>(s) + 1;  // little endian: high half
-  for (int i = threadIdx.x; i < ROWS * COLS; i += kThreads) {
-    const int e = static_cast<int>((hi_words[2 * i] >> 20) & 0x7ffu);
-    bad |= (e == 0x7ff);
-    maxe = max(maxe, e);
-  }
-  for (int off = 16; off > 0; off >>= 1) maxe = max(maxe, __shfl_xor_sync(0xffffffffu, maxe, off));
-  if ((threadIdx.x & 31) == 0) atomicMax(&s_maxe, maxe);
-  const bool any_bad = __syncthreads_or(bad);
-  const int tile_e = s_maxe;
-  if (any_bad || (tile_e != 0 && (tile_e < kIxMinExp || tile_e > kIxMaxExp))) {
+  // pass 1: the tile's largest exponent; inf / nan (and tiles outside the exponent window) take
+  // native FP64
+  const uint32_t mhi = ix_tile_max_hi(s, ROWS * COLS, s_red);
+  const int tile_e = static_cast<int>(mhi >> 20);
+  if (tile_e == 0x7ff || (tile_e != 0 && (tile_e < kIxMinExp || tile_e > kIxMaxExp))) {
     spec_compute<double, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
     return;
   }
   // pass 2: digits, d0 and d1 over the double's own slot, d2 in the float tile
-  float2* s01 = reinterpret_cast<float2*>(s);
-  for (int i = threadIdx.x; i < ROWS * COLS; i += kThreads) {
-    float d0, d1, d2;
-    ix_split(s[i], tile_e, d0, d1, d2);
-    s01[i] = make_float2(d0, d1);
-    s2[i] = d2;
-  }
+  ix_split_tile(s, s2, ROWS * COLS, tile_e);
   __syncthreads();
+  const float2* s01 = reinterpret_cast<const float2*>(s);
   // scale = c * 2^(G - 54) with G = tile_e - 1022 (all-zero tile: any finite scale)
   const double scale = tile_e == 0 ? 0.0 : itaps.c * ldexp(1.0, tile_e - 1022 - 3 * kIxDigitBits);
   ix_compute<TY, SPEC>(s01, s2, out, nx, ny, periodic, x0, y0, itaps, scale);
@@ -870,32 +983,16 @@ __global__ void __launch_bounds__(kThreads)
       if constexpr (sd.xform) xform_tile<T>(s, SE);
       spec_compute<T, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
     } else if constexpr (MODE == 1) {
-      const unsigned* hi_words = reinterpret_cast<const unsigned*>(s) + 1;
-      int maxe = 0;
-      bool bad = false;
-      for (int k = tid; k < SE; k += kThreads) {
-        const int e = static_cast<int>((hi_words[2 * k] >> 20) & 0x7ffu);
-        bad |= (e == 0x7ff);
-        maxe = max(maxe, e);
-      }
-      for (int off = 16; off > 0; off >>= 1) maxe = max(maxe, __shfl_xor_sync(0xffffffffu, maxe, off));
-      if ((tid & 31) == 0) s_wmax[tid >> 5] = maxe;
-      const bool any_bad = __syncthreads_or(bad);
-      int tile_e = 0;
-#pragma unroll
-      for (int w = 0; w < kThreads / 32; ++w) tile_e = max(tile_e, s_wmax[w]);
-      if (any_bad || (tile_e != 0 && (tile_e < kIxMinExp || tile_e > kIxMaxExp))) {
+      static_assert(COLS % 2 == 0, "digit passes take values in pairs");
+      const uint32_t mhi = ix_tile_max_hi(s, SE, reinterpret_cast<unsigned*>(s_wmax));
+      const int tile_e = static_cast<int>(mhi >> 20);
+      if (tile_e == 0x7ff || (tile_e != 0 && (tile_e < kIxMinExp || tile_e > kIxMaxExp))) {
         spec_compute<double, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
       } else {
-        float2* s01 = reinterpret_cast<float2*>(s);
         float* s2 = reinterpret_cast<float*>(extra);
-        for (int k = tid; k < SE; k += kThreads) {
-          float d0, d1, d2;
-          ix_split(s[k], tile_e, d0, d1, d2);
-          s01[k] = make_float2(d0, d1);
-          s2[k] = d2;
-        }
+        ix_split_tile(s, s2, SE, tile_e);
         __syncthreads();
+        const float2* s01 = reinterpret_cast<const float2*>(s);
         const double scale = tile_e == 0 ? 0.0 : itaps.c * ldexp(1.0, tile_e - 1022 - 3 * kIxDigitBits);
         ix_compute<TY, SPEC>(s01, s2, out, nx, ny, periodic, x0, y0, itaps, scale);
       }

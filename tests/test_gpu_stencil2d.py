@@ -364,3 +364,43 @@ def test_tma_pipeline_equals_cp_async_tiles(env, dtype, bc, shape):
         a = run2d(cs, torch, field, kw, dtype, tile_choice=1, out_init=np.full(shape, 3.0))
         b = run2d(cs, torch, field, kw, dtype, tile_choice=2, out_init=np.full(shape, 3.0))
         assert np.array_equal(a, b), name
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("offsets", [(0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_unaligned_buffers_match_oracle(env, dtype, offsets, bc):
+    """Input and output buffers that start one element past a 16-byte boundary take the
+    element-wise copies and stores; results equal the oracle's, untouched cells keep the
+    sentinel."""
+    cs, torch, orc = env
+    ny, nx = 130, 300
+    h = 2 * np.pi / nx
+    field = W.sines_field(nx, seed=77, ny=ny)
+    tdt = torch.float64 if dtype == 0 else torch.float32
+    ndt = np.float64 if dtype == 0 else np.float32
+    if dtype == 1:
+        field = field.astype(np.float32).astype(np.float64)
+    sentinel = -2.0 ** 120
+    in_off, out_off = offsets
+    for name, L, R, T, B, d, w in [c for c in stencil_cases(h) if c[0] in ("lap9", "biharm13", "ddx4", "d2y8")]:
+        buf_in = torch.zeros(ny * nx + 1, dtype=tdt, device="cuda")
+        buf_out = torch.full((ny * nx + 1,), sentinel, dtype=tdt, device="cuda")
+        x = buf_in[in_off:in_off + ny * nx].view(ny, nx)
+        y = buf_out[out_off:out_off + ny * nx].view(ny, nx)
+        x.copy_(torch.from_numpy(field.astype(ndt)))
+        plan = cs.cs_plan_create_2d(cs.StencilDesc(nx=nx, ny=ny, dir=d, bc=bc, dtype=dtype, left=L, right=R,
+                                                   top=T, bottom=B, weights=w), x, y)
+        cs.cs_compute(plan)
+        torch.cuda.synchronize()
+        cs.cs_destroy(plan)
+        got = y.cpu().numpy().astype(np.float64)
+        ref = orc.stencil2d(field, w, d, bc, L, R, T, B, out=np.full((ny, nx), sentinel))
+        written = np.ones((ny, nx), bool)
+        if bc == 0:
+            written[:] = False
+            written[T:ny - B, L:nx - R] = True
+            assert np.array_equal(got[~written], ref[~written]), name
+        assert scaled_err(got[written], ref[written], w, field) <= TOL[dtype], name
+        spare = buf_out[0] if out_off == 1 else buf_out[-1]
+        assert spare.item() == sentinel, name  # nothing written outside the view
