@@ -401,14 +401,20 @@ __device__ __forceinline__ void ix_compute(const float2* s01, const float* s2, d
   double* op = out + gy0 * nx + gx;
   const float4* a = reinterpret_cast<const float4*>(s01 + (S0 - X) + c);  // (S0 - X + c) is even
   const float2* b = reinterpret_cast<const float2*>(s2 + (S0 - X) + c);
-  float acc[H][2][3];
+  // (S0, S1) of an output accumulate as a pair with the packed FP32x2 FMA, S2 alone
+  float2 acc01[H][2];
+  float acc2[H][2];
 #pragma unroll
   for (int q = 0; q < H; ++q)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) acc[q][j][0] = acc[q][j][1] = acc[q][j][2] = 0.0f;
+    for (int j = 0; j < 2; ++j) {
+      acc01[q][j] = make_float2(0.0f, 0.0f);
+      acc2[q][j] = 0.0f;
+    }
 #pragma unroll
   for (int i = 0; i < RW + H - 1; ++i) {  // input row r0 + i feeds output rows i - q
-    float v0[2 * NP], v1[2 * NP], v2[2 * NP];
+    float2 v01[2 * NP];
+    float v2[2 * NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       bool used = false;
@@ -424,10 +430,8 @@ __device__ __forceinline__ void ix_compute(const float2* s01, const float* s2, d
       if (used) {
         const float4 d = a[(r0 + i) * (COLS / 2) + k];
         const float2 f = b[(r0 + i) * (COLS / 2) + k];
-        v0[2 * k] = d.x;
-        v1[2 * k] = d.y;
-        v0[2 * k + 1] = d.z;
-        v1[2 * k + 1] = d.w;
+        v01[2 * k] = make_float2(d.x, d.y);
+        v01[2 * k + 1] = make_float2(d.z, d.w);
         v2[2 * k] = f.x;
         v2[2 * k + 1] = f.y;
       }
@@ -438,24 +442,23 @@ __device__ __forceinline__ void ix_compute(const float2* s01, const float* s2, d
       if (o < 0 || o >= RW) continue;
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        float* A = acc[o % H][j];
 #pragma unroll
         for (int p = 0; p < W; ++p)
           if ((sd.mask >> (q * W + p)) & 1u) {
             const float n = taps.n[q * W + p];
-            A[0] = __fmaf_rn(n, v0[X + j + p], A[0]);
-            A[1] = __fmaf_rn(n, v1[X + j + p], A[1]);
-            A[2] = __fmaf_rn(n, v2[X + j + p], A[2]);
+            acc01[o % H][j] = __ffma2_rn(make_float2(n, n), v01[X + j + p], acc01[o % H][j]);
+            acc2[o % H][j] = __fmaf_rn(n, v2[X + j + p], acc2[o % H][j]);
           }
       }
     }
     const int done = i - (H - 1);  // output row complete after its last input row
     if (done >= 0) {
-      float* A0 = acc[done % H][0];
-      float* A1 = acc[done % H][1];
-      const double val0 = ix_combine(A0[0], A0[1], A0[2]) * scale;
-      const double val1 = (kIntJoin ? ix_combine_int(A1[0], A1[1], A1[2]) : ix_combine(A1[0], A1[1], A1[2])) * scale;
-      A0[0] = A0[1] = A0[2] = A1[0] = A1[1] = A1[2] = 0.0f;
+      const float2 p0 = acc01[done % H][0], p1 = acc01[done % H][1];
+      const float q0 = acc2[done % H][0], q1 = acc2[done % H][1];
+      const double val0 = ix_combine(p0.x, p0.y, q0) * scale;
+      const double val1 = (kIntJoin ? ix_combine_int(p1.x, p1.y, q1) : ix_combine(p1.x, p1.y, q1)) * scale;
+      acc01[done % H][0] = acc01[done % H][1] = make_float2(0.0f, 0.0f);
+      acc2[done % H][0] = acc2[done % H][1] = 0.0f;
       if (done >= klo && done < khi) {
         if (both) {
           *reinterpret_cast<double2*>(op) = make_double2(val0, val1);
