@@ -694,83 +694,183 @@ __device__ __forceinline__ double f2d_exact(float f) {
   return __longlong_as_double(static_cast<long long>(d));
 }
 
-// (sh, sl) += (wh + wl) * (xh + xl); the wl * xl term (~2^-48 relative) is dropped.
-__device__ __forceinline__ void dd_mac(float& sh, float& sl, float wh, float wl, float xh, float xl) {
-  const float p = __fmul_rn(wh, xh);
-  float e = __fmaf_rn(wh, xh, -p);  // exact: wh * xh = p + e
-  e = __fmaf_rn(wh, xl, e);
-  e = __fmaf_rn(wl, xh, e);
-  const float s = __fadd_rn(sh, p);  // TwoSum(sh, p) = s + err exactly
-  const float bb = __fsub_rn(s, sh);
-  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  sl = __fadd_rn(sl, __fadd_rn(err, e));
+// The double-float steps run packed (FP32x2) over two adjacent output columns: lane x is the left
+// column, y the right; each lane rounds exactly as a scalar evaluation would.  a - b is formed as
+// fma(b, -1, a) (one rounding, as a subtraction).
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(a, f2(-1.0f)); }
+
+// (sh, sl) += (wh + wl) * (xh + xl): the product's rounding error comes from an FMA and the sum
+// is an error-free TwoSum; the wl * xl term (~2^-48 relative) is dropped.
+__device__ __forceinline__ void dd_mac2(float2& sh, float2& sl, float wh, float wl, float2 xh, float2 xl) {
+  const float2 q = __fmul2_rn(f2(-wh), xh);  // q = -p, p = wh * xh rounded
+  float2 e = __ffma2_rn(f2(wh), xh, q);      // exact: wh * xh - p
+  e = __ffma2_rn(f2(wh), xl, e);
+  e = __ffma2_rn(f2(wl), xh, e);
+  const float2 s = sub2(sh, q);              // TwoSum(sh, p)
+  const float2 bb = sub2(s, sh);
+  const float2 err = sub2(sub2(sh, sub2(s, bb)), __fadd2_rn(q, bb));  // (sh - (s - bb)) + (p - bb)
+  sl = __fadd2_rn(sl, __fadd2_rn(err, e));
+  sh = s;
+}
+
+// (sh, sl) += p + e with an error-free TwoSum of sh and p.
+__device__ __forceinline__ void dd_add_exact2(float2& sh, float2& sl, float2 p, float2 e) {
+  const float2 s = __fadd2_rn(sh, p);
+  const float2 bb = sub2(s, sh);
+  const float2 err = __fadd2_rn(sub2(sh, sub2(s, bb)), sub2(p, bb));
+  sl = __fadd2_rn(sl, __fadd2_rn(err, e));
   sh = s;
 }
 
 // (sh, sl) += u^3 - u for u = uh + ul, with error-free products and sums (terms below ~2^-46
 // of |u| dropped), so the cubic of the user function stays on the FP32 pipes.
-__device__ __forceinline__ void dd_add_exact(float& sh, float& sl, float p, float e) {
-  const float s = __fadd_rn(sh, p);
-  const float bb = __fsub_rn(s, sh);
-  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  sl = __fadd_rn(sl, __fadd_rn(err, e));
-  sh = s;
-}
-__device__ __forceinline__ void dd_add_cubic_minus(float& sh, float& sl, float uh, float ul) {
-  const float p2 = __fmul_rn(uh, uh);  // u^2 = p2 + e2
-  float e2 = __fmaf_rn(uh, uh, -p2);
-  e2 = __fmaf_rn(__fmul_rn(2.0f, uh), ul, e2);
-  const float p3 = __fmul_rn(p2, uh);  // u^3 = p3 + e3
-  float e3 = __fmaf_rn(p2, uh, -p3);
-  e3 = __fmaf_rn(p2, ul, e3);
-  e3 = __fmaf_rn(e2, uh, e3);
-  dd_add_exact(sh, sl, p3, e3);
-  dd_add_exact(sh, sl, -uh, -ul);
+__device__ __forceinline__ void dd_add_cubic_minus2(float2& sh, float2& sl, float2 uh, float2 ul) {
+  const float2 p2 = __fmul2_rn(uh, uh);  // u^2 = p2 + e2
+  float2 e2 = __ffma2_rn(uh, uh, neg2(p2));
+  e2 = __ffma2_rn(__fmul2_rn(f2(2.0f), uh), ul, e2);
+  const float2 p3 = __fmul2_rn(p2, uh);  // u^3 = p3 + e3
+  float2 e3 = __ffma2_rn(p2, uh, neg2(p3));
+  e3 = __ffma2_rn(p2, ul, e3);
+  e3 = __ffma2_rn(e2, uh, e3);
+  dd_add_exact2(sh, sl, p3, e3);
+  dd_add_exact2(sh, sl, neg2(uh), neg2(ul));
 }
 
+// Splits the N staged FP64 values (N even) in place: each 16-byte pair of values becomes
+// (hi0, hi1, lo0, lo1).  Returns, uniformly over the block, whether the double-float path
+// applies to the tile; when it does not, the tile still holds the FP64 values.
+template <int N>
+__device__ __forceinline__ bool dd_split_tile(double* s, int* s_red) {
+  constexpr int NPAIR = N / 2, PER = (NPAIR + kThreads - 1) / kThreads;
+  const double2* q = reinterpret_cast<const double2*>(s);
+  float4 v[PER];
+  bool ok = true;
+  int maxe = 0;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int k = static_cast<int>(threadIdx.x) + j * kThreads;
+    if (k < NPAIR) {
+      const double2 d = q[k];
+      float h0, l0, h1, l1;
+      int e0, e1;
+      ok = dd_split(d.x, h0, l0, e0) && ok;
+      ok = dd_split(d.y, h1, l1, e1) && ok;
+      maxe = max(maxe, max(e0, e1));
+      v[j] = make_float4(h0, h1, l0, l1);
+    }
+  }
+  maxe = __reduce_max_sync(0xffffffffu, maxe);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = maxe;
+  const bool all_ok = __syncthreads_and(ok);
+  int tile_e = 0;
+#pragma unroll
+  for (int w = 0; w < kThreads / 32; ++w) tile_e = max(tile_e, s_red[w]);
+  const bool use = all_ok && (tile_e == 0 || tile_e >= kDDTileExp);
+  if (use) {
+    float4* o = reinterpret_cast<float4*>(s);
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int k = static_cast<int>(threadIdx.x) + j * kThreads;
+      if (k < NPAIR) o[k] = v[j];
+    }
+    __syncthreads();
+  }
+  return use;
+}
+
+// Double-float stencil of two adjacent tile columns per thread, "push" form (each staged row
+// adds its taps to the up to H output rows it feeds, in the order (row, column) of the taps, as
+// a one-output-at-a-time evaluation would).  A row is read as 16-byte (hi, hi, lo, lo) column
+// pairs; taps at an odd column offset take their pair from two neighbouring loads.
 template <int TY, int SPEC>
-__device__ __forceinline__ void dd_compute(const float2* sf, const double* s, double* __restrict__ out,
-                                           int64_t nx, int64_t ny, int periodic, int64_t x0,
-                                           int64_t y0, const DDTaps& taps) {
+__device__ __forceinline__ void dd_compute(const float4* sp, double* __restrict__ out, int64_t nx,
+                                           int64_t ny, int periodic, int64_t x0, int64_t y0,
+                                           const DDTaps& taps) {
   constexpr SpecDesc sd = kSpecs[SPEC];
   constexpr int L = sd.L, R = sd.R, TT = sd.T, BB = sd.B;
   constexpr int V = Vec<double>::n;
   constexpr int TX = tile_x<double>();
+  static_assert(TX == 64, "one warp spans the tile's 64 columns");
   constexpr int LA = (L + V - 1) / V * V, RA = (R + V - 1) / V * V;
-  constexpr int COLS = LA + TX + RA;
+  constexpr int COLS = LA + TX + RA, CP = COLS / 2;
   constexpr int W = L + R + 1, H = TT + BB + 1;
-  constexpr int WX = TX / 32, WY = 8 / WX, RW = TY / WY;
+  constexpr int WY = kThreads / 32, RW = TY / WY;
+  constexpr int S0 = LA - L, X = S0 & 1, NP = (W + 1 + X + 1) / 2;  // pairs read per row
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = (warp % WX) * 32 + lane;
-  const int r0 = (warp / WX) * RW;
+  const int c = 2 * lane;
+  const int r0 = warp * RW;
   const int64_t gx = x0 + c;
-  const bool col_ok = gx < nx && (periodic || (gx >= L && gx < nx - R));
-  const float2* sc = sf + LA + c - L;
-  (void)s;
-  float2 win[H][W];
+  const bool ok0 = gx < nx && (periodic || (gx >= L && gx < nx - R));
+  const bool ok1 = gx + 1 < nx && (periodic || (gx + 1 >= L && gx + 1 < nx - R));
+  const bool both = ok0 && ok1 && (reinterpret_cast<uintptr_t>(out) & 15u) == 0 && (nx & 1) == 0;
+  const int64_t gy0 = y0 + r0;
+  const int64_t ylo = periodic ? 0 : TT, yhi = periodic ? ny : ny - BB;
+  auto rows_below = [](int64_t d) { return static_cast<int>(d < 0 ? 0 : (d > RW ? RW : d)); };
+  const int klo = rows_below(ylo - gy0);
+  const int khi = (ok0 || ok1) ? rows_below(yhi - gy0) : 0;
+  double* op = out + gy0 * nx + gx;
+  const float4* a = sp + (S0 - X + c) / 2;
+  float2 sh[H], sl[H];
 #pragma unroll
-  for (int q = 0; q < H - 1; ++q)
+  for (int q = 0; q < H; ++q) sh[q] = sl[q] = make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int p = 0; p < W; ++p) win[q + 1][p] = sc[(r0 + q) * COLS + p];
+  for (int i = 0; i < RW + H - 1; ++i) {
+    float4 P[NP];
 #pragma unroll
-  for (int k = 0; k < RW; ++k) {
+    for (int k = 0; k < NP; ++k) {
+      bool used = false;
 #pragma unroll
-    for (int q = 0; q < H - 1; ++q)
+      for (int q = 0; q < H; ++q)
 #pragma unroll
-      for (int p = 0; p < W; ++p) win[q][p] = win[q + 1][p];
+        for (int p = 0; p < W; ++p) {
+          const int e = X + p;
+          used |= ((e >> 1) == k || ((e + 1) >> 1) == k) && ((sd.mask >> (q * W + p)) & 1u) &&
+                  (i - q >= 0) && (i - q < RW);
+        }
+      if (used) P[k] = a[(r0 + i) * CP + k];
+    }
 #pragma unroll
-    for (int p = 0; p < W; ++p) win[H - 1][p] = sc[(r0 + k + H - 1) * COLS + p];
-    float sh = 0.0f, sl = 0.0f;
-#pragma unroll
-    for (int q = 0; q < H; ++q)
+    for (int q = 0; q < H; ++q) {
+      const int o = i - q;
+      if (o < 0 || o >= RW) continue;
 #pragma unroll
       for (int p = 0; p < W; ++p)
-        if ((sd.mask >> (q * W + p)) & 1u)
-          dd_mac(sh, sl, taps.hi[q * W + p], taps.lo[q * W + p], win[q][p].x, win[q][p].y);
-    if constexpr (sd.epi) dd_add_cubic_minus(sh, sl, win[TT][L].x, win[TT][L].y);
-    const double acc = f2d_exact(sh) + f2d_exact(sl);
-    const int64_t gy = y0 + r0 + k;
-    if (col_ok && gy < ny && (periodic || (gy >= TT && gy < ny - BB))) out[gy * nx + gx] = acc;
+        if ((sd.mask >> (q * W + p)) & 1u) {
+          const int e = X + p;
+          float2 xh, xl;
+          if ((e & 1) == 0) {
+            xh = make_float2(P[e >> 1].x, P[e >> 1].y);
+            xl = make_float2(P[e >> 1].z, P[e >> 1].w);
+          } else {
+            xh = make_float2(P[e >> 1].y, P[(e >> 1) + 1].x);
+            xl = make_float2(P[e >> 1].w, P[(e >> 1) + 1].z);
+          }
+          dd_mac2(sh[o % H], sl[o % H], taps.hi[q * W + p], taps.lo[q * W + p], xh, xl);
+        }
+    }
+    const int done = i - (H - 1);
+    if (done >= 0) {
+      float2& h = sh[done % H];
+      float2& l = sl[done % H];
+      if constexpr (sd.epi) {
+        const float4 u = sp[(r0 + done + TT) * CP + (LA + c) / 2];  // centre values
+        dd_add_cubic_minus2(h, l, make_float2(u.x, u.y), make_float2(u.z, u.w));
+      }
+      const double val0 = f2d_exact(h.x) + f2d_exact(l.x);
+      const double val1 = f2d_exact(h.y) + f2d_exact(l.y);
+      h = l = make_float2(0.0f, 0.0f);
+      if (done >= klo && done < khi) {
+        if (both) {
+          *reinterpret_cast<double2*>(op) = make_double2(val0, val1);
+        } else {
+          if (ok0) op[0] = val0;
+          if (ok1) op[1] = val1;
+        }
+      }
+      op += nx;
+    }
   }
 }
 
@@ -783,29 +883,16 @@ __global__ void __launch_bounds__(kThreads)
   constexpr int TX = tile_x<double>();
   constexpr int LA = (sd.L + V - 1) / V * V, RA = (sd.R + V - 1) / V * V;
   constexpr int COLS = LA + TX + RA, ROWS = TY + sd.T + sd.B;
+  static_assert(COLS % 2 == 0, "the split takes values in pairs");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* s = reinterpret_cast<double*>(smem_raw);
-  float2* sf = reinterpret_cast<float2*>(s + ROWS * COLS);
-  __shared__ int s_maxe;
-  if (threadIdx.x == 0) s_maxe = 0;
+  __shared__ int s_red[kThreads / 32];
   const int64_t x0 = static_cast<int64_t>(blockIdx.x) * TX;
   const int64_t y0 = static_cast<int64_t>(blockIdx.y) * TY;
   load_tile<double>(s, in, nx, ny, periodic != 0, vec_ok != 0, x0, y0, sd.T, LA, COLS, ROWS);
   if constexpr (sd.xform) xform_tile<double>(s, ROWS * COLS);
-  bool ok = true;
-  int maxe = 0;
-  for (int i = threadIdx.x; i < ROWS * COLS; i += kThreads) {
-    float h, l;
-    int e;
-    ok = dd_split(s[i], h, l, e) && ok;
-    maxe = max(maxe, e);
-    sf[i] = make_float2(h, l);
-  }
-  for (int off = 16; off > 0; off >>= 1) maxe = max(maxe, __shfl_xor_sync(0xffffffffu, maxe, off));
-  if ((threadIdx.x & 31) == 0) atomicMax(&s_maxe, maxe);
-  const bool all_ok = __syncthreads_and(ok);
-  if (all_ok && (s_maxe == 0 || s_maxe >= kDDTileExp))
-    dd_compute<TY, SPEC>(sf, s, out, nx, ny, periodic, x0, y0, dtaps);
+  if (dd_split_tile<ROWS * COLS>(s, s_red))
+    dd_compute<TY, SPEC>(reinterpret_cast<const float4*>(s), out, nx, ny, periodic, x0, y0, dtaps);
   else
     spec_compute<double, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
 }
@@ -814,7 +901,7 @@ template <int TY, int SPEC>
 int launch_dd(const double* in, double* out, int64_t nx, int64_t ny, int periodic, int vec_ok,
               const Taps<double>& taps, const DDTaps& dtaps, cudaStream_t st) {
   constexpr SpecDesc sd = kSpecs[SPEC];
-  const size_t smem = 2 * tile_smem_bytes<double>(sd.L, sd.R, sd.T, sd.B, TY, false);
+  const size_t smem = tile_smem_bytes<double>(sd.L, sd.R, sd.T, sd.B, TY, false);
   auto kern = k_stencil2d_dd<TY, SPEC>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -930,7 +1017,7 @@ struct TmaGeom {
   static constexpr int COLS = LA + TX + RA, ROWS = TY + sd.T + sd.B;
   static constexpr int SE = ROWS * COLS;
   static constexpr size_t STAGE_BYTES = (SE * sizeof(T) + 127) / 128 * 128;
-  static constexpr size_t EXTRA_BYTES = MODE == 1 ? SE * sizeof(float) : (MODE == 2 ? SE * sizeof(float2) : 0);
+  static constexpr size_t EXTRA_BYTES = MODE == 1 ? SE * sizeof(float) : 0;
   static constexpr size_t SMEM = kStages * STAGE_BYTES + EXTRA_BYTES;
 };
 
@@ -1000,25 +1087,10 @@ __global__ void __launch_bounds__(kThreads)
         ix_compute<TY, SPEC>(s01, s2, out, nx, ny, periodic, x0, y0, itaps, scale);
       }
     } else {
-      float2* sf = reinterpret_cast<float2*>(extra);
+      static_assert(COLS % 2 == 0, "the split takes values in pairs");
       if constexpr (sd.xform) xform_tile<double>(s, SE);
-      bool ok = true;
-      int maxe = 0;
-      for (int k = tid; k < SE; k += kThreads) {
-        float h, l;
-        int e;
-        ok = dd_split(s[k], h, l, e) && ok;
-        maxe = max(maxe, e);
-        sf[k] = make_float2(h, l);
-      }
-      for (int off = 16; off > 0; off >>= 1) maxe = max(maxe, __shfl_xor_sync(0xffffffffu, maxe, off));
-      if ((tid & 31) == 0) s_wmax[tid >> 5] = maxe;
-      const bool all_ok = __syncthreads_and(ok);
-      int tile_e = 0;
-#pragma unroll
-      for (int w = 0; w < kThreads / 32; ++w) tile_e = max(tile_e, s_wmax[w]);
-      if (all_ok && (tile_e == 0 || tile_e >= kDDTileExp))
-        dd_compute<TY, SPEC>(sf, s, out, nx, ny, periodic, x0, y0, dtaps);
+      if (dd_split_tile<SE>(s, s_wmax))
+        dd_compute<TY, SPEC>(reinterpret_cast<const float4*>(s), out, nx, ny, periodic, x0, y0, dtaps);
       else
         spec_compute<double, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
     }
