@@ -75,6 +75,9 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async16_s(unsigned smem_addr, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr), "l"(gmem) : "memory");
+}
 template <typename T> __device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
   unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   if constexpr (sizeof(T) == 8)
@@ -91,6 +94,33 @@ template <typename T> __device__ __forceinline__ T cubic_minus(T u) { return u *
 // Stages rows [y0 - top, y0 + TY + bottom) x columns [x0 - LA, x0 + TX + RA) into s
 // (pitch = cols).  LA, RA are left/right rounded up to the vector width so every chunk is
 // 16-byte aligned in both memories.
+// Interior tile with compile-time shape: warp w copies rows w, w + 8, ...; lane l the 16-byte
+// chunks l and l + 32 of each row (a row has 32 to 64 chunks); no loops left after unrolling,
+// no bounds or wrap checks, addresses advanced by constant steps.
+template <typename T, int ROWS, int COLS>
+__device__ __forceinline__ void load_tile_interior(T* s, const T* __restrict__ in, int64_t nx,
+                                                   int64_t gy0, int64_t gx0) {
+  constexpr int V = Vec<T>::n, NCH = COLS / V, WARPS = kThreads / 32;
+  static_assert(NCH >= 32 && NCH <= 64, "one or two chunks per lane and row");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const char* src = reinterpret_cast<const char*>(in + (gy0 + warp) * nx + gx0) + 16 * lane;
+  unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(s + warp * COLS)) + 16u * lane;
+  const int64_t src_step = static_cast<int64_t>(WARPS) * nx * static_cast<int64_t>(sizeof(T));
+  constexpr unsigned kDstStep = WARPS * COLS * sizeof(T);
+  const bool second = lane + 32 < NCH;
+#pragma unroll
+  for (int k = 0; k < (ROWS + WARPS - 1) / WARPS; ++k) {
+    if (k * WARPS + warp < ROWS) {
+      cp_async16_s(dst, src);
+      if (second) cp_async16_s(dst + 512u, src + 512);
+    }
+    src += src_step;
+    dst += kDstStep;
+  }
+  cp_async_wait_all();
+  __syncthreads();
+}
+
 template <typename T>
 __device__ __forceinline__ void load_tile(T* s, const T* __restrict__ in, int64_t nx, int64_t ny,
                                           bool periodic, bool vec_ok, int64_t x0, int64_t y0,
@@ -100,14 +130,18 @@ __device__ __forceinline__ void load_tile(T* s, const T* __restrict__ in, int64_
   const int total = rows * nch;
   const int64_t gy0 = y0 - top, gx0 = x0 - LA;
   if (vec_ok && gy0 >= 0 && gy0 + rows <= ny && gx0 >= 0 && gx0 + cols <= nx) {
-    // interior tile (the common case): warp w copies rows w, w + 8, ...; no bounds or wrap checks
+    // interior tile (the common case): warp w copies rows w, w + 8, ...; lane l the 16-byte
+    // chunks l, l + 32, ...; no bounds or wrap checks, addresses advanced by constant steps
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const T* src = in + (gy0 + warp) * nx + gx0;
-    T* dst = s + warp * cols;
+    const char* src = reinterpret_cast<const char*>(in + (gy0 + warp) * nx + gx0) + 16 * lane;
+    unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(s + warp * cols)) + 16u * lane;
+    const int64_t src_step = static_cast<int64_t>(kThreads / 32) * nx * static_cast<int64_t>(sizeof(T));
+    const unsigned dst_step = static_cast<unsigned>((kThreads / 32) * cols * sizeof(T));
+#pragma unroll 4
     for (int r = warp; r < rows; r += kThreads / 32) {
-      for (int ch = lane; ch < nch; ch += 32) cp_async16(dst + ch * V, src + ch * V);
-      src += (kThreads / 32) * nx;
-      dst += (kThreads / 32) * cols;
+      for (int ch = lane; ch < nch; ch += 32) cp_async16_s(dst + 16u * (ch - lane), src + 16 * (ch - lane));
+      src += src_step;
+      dst += dst_step;
     }
     cp_async_wait_all();
     __syncthreads();
@@ -150,10 +184,120 @@ __device__ __forceinline__ void load_tile(T* s, const T* __restrict__ in, int64_
   __syncthreads();
 }
 
+// load_tile for a compile-time tile shape: interior tiles take the unrolled copy.
+template <typename T, int ROWS, int COLS>
+__device__ __forceinline__ void load_tile_ct(T* s, const T* __restrict__ in, int64_t nx, int64_t ny,
+                                             bool periodic, bool vec_ok, int64_t x0, int64_t y0,
+                                             int top, int LA) {
+  const int64_t gy0 = y0 - top, gx0 = x0 - LA;
+  if (vec_ok && gy0 >= 0 && gy0 + ROWS <= ny && gx0 >= 0 && gx0 + COLS <= nx) {
+    load_tile_interior<T, ROWS, COLS>(s, in, nx, gy0, gx0);
+    return;
+  }
+  load_tile<T>(s, in, nx, ny, periodic, vec_ok, x0, y0, top, LA, COLS, ROWS);
+}
+
 template <typename T>
 __device__ __forceinline__ void xform_tile(T* s, int n) {
   for (int i = threadIdx.x; i < n; i += kThreads) s[i] = cubic_minus(s[i]);
   __syncthreads();
+}
+
+// FP32 compute phase of the specialised kernels: each thread owns four adjacent columns of the
+// tile (one warp spans its 128 columns) and walks down its rows in "push" form: every staged row
+// adds its taps to the (up to H) output rows it feeds, in the tap order (row, column) of a
+// one-output evaluation, so each output is the same chain of FMAs.  Rows are read as 16-byte
+// column groups and the four results leave as one 16-byte store where all four are written.
+template <int TY, int SPEC>
+__device__ __forceinline__ void spec_compute_f32(const float* s, float* __restrict__ out, int64_t nx,
+                                                 int64_t ny, int periodic, int64_t x0, int64_t y0,
+                                                 const Taps<float>& taps) {
+  constexpr SpecDesc sd = kSpecs[SPEC];
+  constexpr int L = sd.L, R = sd.R, TT = sd.T, BB = sd.B;
+  constexpr int TX = tile_x<float>();
+  static_assert(TX == 128, "one warp spans the tile's 128 columns");
+  constexpr int LA = (L + 3) / 4 * 4, RA = (R + 3) / 4 * 4;
+  constexpr int COLS = LA + TX + RA, C4 = COLS / 4;
+  constexpr int W = L + R + 1, H = TT + BB + 1;
+  constexpr int WY = kThreads / 32, RW = TY / WY;
+  constexpr int NC = LA / 4 + 1 + (3 + R) / 4;  // 16-byte groups read per row
+  constexpr int OFF = LA - L;                   // window index of tap p for column j: OFF + j + p
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = 4 * lane;
+  const int r0 = warp * RW;
+  const int64_t gx = x0 + c;
+  bool ok[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) ok[j] = gx + j < nx && (periodic || (gx + j >= L && gx + j < nx - R));
+  const bool any = ok[0] || ok[1] || ok[2] || ok[3];
+  const bool all4 = ok[0] && ok[1] && ok[2] && ok[3] && (reinterpret_cast<uintptr_t>(out) & 15u) == 0 &&
+                    (nx & 3) == 0;
+  const int64_t gy0 = y0 + r0;
+  const int64_t ylo = periodic ? 0 : TT, yhi = periodic ? ny : ny - BB;
+  auto rows_below = [](int64_t d) { return static_cast<int>(d < 0 ? 0 : (d > RW ? RW : d)); };
+  const int klo = rows_below(ylo - gy0);
+  const int khi = any ? rows_below(yhi - gy0) : 0;
+  float* op = out + gy0 * nx + gx;
+  const float4* a = reinterpret_cast<const float4*>(s) + lane;  // window starts at smem column c
+  float acc[H][4];
+#pragma unroll
+  for (int q = 0; q < H; ++q)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[q][j] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < RW + H - 1; ++i) {
+    float x[4 * NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      bool used = false;
+#pragma unroll
+      for (int q = 0; q < H; ++q)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int p = 0; p < W; ++p)
+            used |= (OFF + j + p) / 4 == k && ((sd.mask >> (q * W + p)) & 1u) && (i - q >= 0) && (i - q < RW);
+      if (used) {
+        const float4 v = a[(r0 + i) * C4 + k];
+        x[4 * k] = v.x;
+        x[4 * k + 1] = v.y;
+        x[4 * k + 2] = v.z;
+        x[4 * k + 3] = v.w;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < H; ++q) {
+      const int o = i - q;
+      if (o < 0 || o >= RW) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int p = 0; p < W; ++p)
+          if ((sd.mask >> (q * W + p)) & 1u) acc[o % H][j] = fmaf(taps.w[q * W + p], x[OFF + j + p], acc[o % H][j]);
+    }
+    const int done = i - (H - 1);
+    if (done >= 0) {
+      float* r = acc[done % H];
+      if constexpr (sd.epi) {
+        const float4 u = reinterpret_cast<const float4*>(s)[(r0 + done + TT) * C4 + lane + LA / 4];
+        r[0] = cubic_minus(u.x) + r[0];
+        r[1] = cubic_minus(u.y) + r[1];
+        r[2] = cubic_minus(u.z) + r[2];
+        r[3] = cubic_minus(u.w) + r[3];
+      }
+      if (done >= klo && done < khi) {
+        if (all4) {
+          *reinterpret_cast<float4*>(op) = make_float4(r[0], r[1], r[2], r[3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (ok[j]) op[j] = r[j];
+        }
+      }
+      r[0] = r[1] = r[2] = r[3] = 0.0f;
+      op += nx;
+    }
+  }
 }
 
 // Compute phase of the specialised kernels in the storage type: each thread owns one column
@@ -162,6 +306,10 @@ template <typename T, int TY, int SPEC>
 __device__ __forceinline__ void spec_compute(const T* s, T* __restrict__ out, int64_t nx,
                                              int64_t ny, int periodic, int64_t x0, int64_t y0,
                                              const Taps<T>& taps) {
+  if constexpr (sizeof(T) == 4) {
+    spec_compute_f32<TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
+    return;
+  }
   constexpr SpecDesc sd = kSpecs[SPEC];
   constexpr int L = sd.L, R = sd.R, TT = sd.T, BB = sd.B;
   constexpr int V = Vec<T>::n;
@@ -175,6 +323,13 @@ __device__ __forceinline__ void spec_compute(const T* s, T* __restrict__ out, in
   const int r0 = (warp / WX) * RW;
   const int64_t gx = x0 + c;
   const bool col_ok = gx < nx && (periodic || (gx >= L && gx < nx - R));
+  // this thread writes rows gy0 + k for klo <= k < khi of its column
+  const int64_t gy0 = y0 + r0;
+  const int64_t ylo = periodic ? 0 : TT, yhi = periodic ? ny : ny - BB;
+  auto rows_below = [](int64_t d) { return static_cast<int>(d < 0 ? 0 : (d > RW ? RW : d)); };
+  const int klo = rows_below(ylo - gy0);
+  const int khi = col_ok ? rows_below(yhi - gy0) : 0;
+  T* op = out + gy0 * nx + gx;
   const T* sc = s + LA + c - L;
 
   T win[H][W];
@@ -198,8 +353,8 @@ __device__ __forceinline__ void spec_compute(const T* s, T* __restrict__ out, in
       for (int p = 0; p < W; ++p)
         if ((sd.mask >> (q * W + p)) & 1u) acc = fma(taps.w[q * W + p], win[q][p], acc);
     if constexpr (sd.epi) acc = cubic_minus(win[TT][L]) + acc;
-    const int64_t gy = y0 + r0 + k;
-    if (col_ok && gy < ny && (periodic || (gy >= TT && gy < ny - BB))) out[gy * nx + gx] = acc;
+    if (k >= klo && k < khi) *op = acc;
+    op += nx;
   }
 }
 
@@ -217,7 +372,7 @@ __global__ void __launch_bounds__(kThreads)
   T* s = reinterpret_cast<T*>(smem_raw);
   const int64_t x0 = static_cast<int64_t>(blockIdx.x) * TX;
   const int64_t y0 = static_cast<int64_t>(blockIdx.y) * TY;
-  load_tile<T>(s, in, nx, ny, periodic != 0, vec_ok != 0, x0, y0, sd.T, LA, COLS, ROWS);
+  load_tile_ct<T, ROWS, COLS>(s, in, nx, ny, periodic != 0, vec_ok != 0, x0, y0, sd.T, LA);
   if constexpr (sd.xform) xform_tile<T>(s, ROWS * COLS);
   spec_compute<T, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
 }
@@ -489,7 +644,7 @@ __global__ void __launch_bounds__(kThreads)
   static_assert(COLS % 2 == 0, "digit passes take values in pairs");
   const int64_t x0 = static_cast<int64_t>(blockIdx.x) * TX;
   const int64_t y0 = static_cast<int64_t>(blockIdx.y) * TY;
-  load_tile<double>(s, in, nx, ny, periodic != 0, vec_ok != 0, x0, y0, sd.T, LA, COLS, ROWS);
+  load_tile_ct<double, ROWS, COLS>(s, in, nx, ny, periodic != 0, vec_ok != 0, x0, y0, sd.T, LA);
   // pass 1: the tile's largest exponent; inf / nan (and tiles outside the exponent window) take
   // native FP64
   const uint32_t mhi = ix_tile_max_hi(s, ROWS * COLS, s_red);
@@ -573,7 +728,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil2d_group(const __grid_const
   const int t = static_cast<int>(blockIdx.x) - g.tile_begin;
   const int64_t x0 = static_cast<int64_t>(t % g.tiles_x) * TX;
   const int64_t y0 = static_cast<int64_t>(t / g.tiles_x) * TY;
-  load_tile<T>(s, g.in, g.nx, g.ny, g.periodic != 0, g.vec_ok != 0, x0, y0, sd.T, LA, COLS, ROWS);
+  load_tile_ct<T, ROWS, COLS>(s, g.in, g.nx, g.ny, g.periodic != 0, g.vec_ok != 0, x0, y0, sd.T, LA);
   if constexpr (sd.xform) xform_tile<T>(s, ROWS * COLS);
   spec_compute<T, TY, SPEC>(s, g.out, g.nx, g.ny, g.periodic, x0, y0, g.taps);
 }
@@ -889,7 +1044,7 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ int s_red[kThreads / 32];
   const int64_t x0 = static_cast<int64_t>(blockIdx.x) * TX;
   const int64_t y0 = static_cast<int64_t>(blockIdx.y) * TY;
-  load_tile<double>(s, in, nx, ny, periodic != 0, vec_ok != 0, x0, y0, sd.T, LA, COLS, ROWS);
+  load_tile_ct<double, ROWS, COLS>(s, in, nx, ny, periodic != 0, vec_ok != 0, x0, y0, sd.T, LA);
   if constexpr (sd.xform) xform_tile<double>(s, ROWS * COLS);
   if (dd_split_tile<ROWS * COLS>(s, s_red))
     dd_compute<TY, SPEC>(reinterpret_cast<const float4*>(s), out, nx, ny, periodic, x0, y0, dtaps);
