@@ -7,9 +7,14 @@
 // lines start, so every warp does the same amount of work whatever the length mix.  A
 // persistent grid-stride launch walks the segments.  Each lane loads its 16-byte vector, takes
 // its left / right neighbours from the adjacent lanes with warp shuffles (lanes 0 and 31 load
-// the two ends), and finds its line through a table that maps every 64th element to the line
-// containing it (built once at create time), so the lookup is at most a short binary search.
-// Lanes whose stencil crosses a line end take a slow path with per-element wrapped loads.
+// the few values beyond the segment), and forms its sums uniformly.  A table that maps every
+// 64th element to the line containing it (built once at create time) gives the line of the
+// segment's first element; lanes 0..3 load that line's start and the next three line
+// boundaries, which reach every lane by shuffle, so a lane finds its line with two compares.
+// An element is written by the segment walk only when its stencil stays inside its line; the
+// first L and last R elements of every periodic line (whose stencils wrap) are then written by
+// the same launch, one thread per such element, and those of a non-periodic line are left
+// untouched.  Stencils wider than the vector width take a per-element kernel.
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
@@ -47,67 +52,91 @@ __global__ void k_build_seg_table(const int64_t* __restrict__ off, int64_t num_l
   seg[t] = static_cast<int32_t>(lo);
 }
 
-__device__ __forceinline__ int64_t find_line(int64_t k, const int64_t* __restrict__ off,
-                                             const int32_t* __restrict__ seg, int64_t ntab,
-                                             int64_t num_lines) {
-  const int64_t t = k >> kSegShift;
-  int64_t lo = seg[t];
-  int64_t hi = (t + 1 < ntab) ? seg[t + 1] : num_lines - 1;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi + 1) >> 1;
-    if (__ldg(off + mid) <= k) lo = mid;
-    else hi = mid - 1;
+// Per-element evaluation of elements k0 .. k0 + n - 1 with wrapped loads: lanes beyond a
+// segment's fourth line boundary (lines shorter than a segment) and stencils wider than the
+// vector width.  m, ls, le: a line at or before the one holding k0, and its bounds.
+template <typename T>
+__device__ __forceinline__ void elements_general(const T* __restrict__ in, T* __restrict__ out,
+                                                 const int64_t* __restrict__ off, int64_t total,
+                                                 int periodic, int L, int R, const BTaps<T>& taps,
+                                                 int64_t k0, int n, int64_t m, int64_t ls, int64_t le) {
+  const int W = L + R + 1;
+  for (int e = 0; e < n; ++e) {
+    const int64_t k = k0 + e;
+    if (k >= total) break;
+    while (k >= le) {  // advance to the line holding k (skips empty lines)
+      ++m;
+      ls = le;
+      le = __ldg(off + m + 1);
+    }
+    const int64_t len = le - ls;
+    if (!periodic && (k - ls < L || le - 1 - k < R)) continue;  // boundary cell untouched
+    const int rel0 = static_cast<int>(k - ls) - L;  // lines hold < 2^31 elements
+    const int ilen = static_cast<int>(len);
+    T acc = T(0);
+    for (int p = 0; p < W; ++p) {
+      int rel = (rel0 + p) % ilen;
+      if (rel < 0) rel += ilen;
+      acc = fma(taps.w[p], __ldg(in + ls + rel), acc);
+    }
+    out[k] = acc;
   }
-  return lo;
 }
 
-// One warp segment: own values v (already loaded), neighbours by shuffle, the line lookup, and
-// the weighted sum (fast path) or per-element wrapped loads (lanes at a line end).
+// One warp segment of 32 * V packed elements starting at s: own values v (already loaded),
+// neighbours by shuffle (lanes 0 and 31 take the nearest L / R values of the adjacent segments
+// from hl / hr, loaded with the segment), the lane's line from the segment's boundaries, and the
+// weighted sum.  r holds, on lanes 0..3, the boundary off[m0 + lane] relative to s (clamped;
+// total past the last line), m0 the line of s.  Elements whose stencil would cross the end of
+// their line are not written here.
 template <typename T, int LL, int RR>
 __device__ __forceinline__ void segment(const T* __restrict__ in, T* __restrict__ out,
-                                        const int64_t* __restrict__ off,
-                                        const int32_t* __restrict__ seg, int64_t ntab,
-                                        int64_t total, int64_t num_lines, int periodic, int L,
-                                        int R, bool vec_ok, const BTaps<T>& taps, int64_t k0,
-                                        const T (&v)[Vec1<T>::n]) {
+                                        const int64_t* __restrict__ off, int64_t total,
+                                        int Lr, int Rr, bool vec_ok,
+                                        const BTaps<T>& taps, int64_t s, int64_t m0, int r,
+                                        const T (&v)[Vec1<T>::n], const T (&hl)[LL > 0 ? LL : 1],
+                                        const T (&hr)[RR > 0 ? RR : 1]) {
   constexpr int V = Vec1<T>::n;
   using VT = typename Vec1<T>::V;
-  const int W = L + R + 1;
-  const bool shuffle_ok = L <= V && R <= V;
+  constexpr int L = LL, R = RR, W = LL + RR + 1;
+  static_assert(LL >= 0 && RR >= 0 && LL <= V && RR <= V, "compile-time extents within one vector");
+  (void)Lr;
+  (void)Rr;
   const int lane = threadIdx.x & 31;
-  // window[0 .. 3V): values at k0 - V .. k0 + 2V - 1 (valid where inside the same line)
-  T win[3 * V];
+  const int64_t k0 = s + lane * V;
+  // win[j]: value at k0 - L + j, j < V + L + R (valid where inside the element's line)
+  T win[V + L + R];
+#pragma unroll
+  for (int e = 0; e < V; ++e) win[L + e] = v[e];
+#pragma unroll
+  for (int e = 0; e < L; ++e) {
+    const T u = __shfl_up_sync(0xffffffffu, v[V - L + e], 1);
+    win[e] = lane == 0 ? hl[e] : u;
+  }
+#pragma unroll
+  for (int e = 0; e < R; ++e) {
+    const T d = __shfl_down_sync(0xffffffffu, v[e], 1);
+    win[L + V + e] = lane == 31 ? hr[e] : d;
+  }
+  const int r0 = __shfl_sync(0xffffffffu, r, 0), r1 = __shfl_sync(0xffffffffu, r, 1);
+  const int r2 = __shfl_sync(0xffffffffu, r, 2), r3 = __shfl_sync(0xffffffffu, r, 3);
+  if (k0 >= total) return;
+  // every lane forms its V sums from the window; an element is written here only when its
+  // stencil stays inside its line (the first L and last R elements of a periodic line are
+  // written by the line-ends pass, those of a non-periodic line stay untouched)
+  T res[V];
 #pragma unroll
   for (int e = 0; e < V; ++e) {
-    win[e] = __shfl_up_sync(0xffffffffu, v[e], 1);
-    win[V + e] = v[e];
-    win[2 * V + e] = __shfl_down_sync(0xffffffffu, v[e], 1);
+    T acc = T(0);
+#pragma unroll
+    for (int p = 0; p < W; ++p) acc = fma(taps.w[p], win[e + p], acc);
+    res[e] = acc;
   }
-  if (k0 >= total) return;
-  if (lane == 0) {
-#pragma unroll
-    for (int e = 0; e < V; ++e) win[e] = (k0 - V + e >= 0) ? in[k0 - V + e] : T(0);
-  }
-  if (lane == 31) {
-#pragma unroll
-    for (int e = 0; e < V; ++e) win[2 * V + e] = (k0 + V + e < total) ? in[k0 + V + e] : T(0);
-  }
-  int64_t m = find_line(k0, off, seg, ntab, num_lines);
-  int64_t ls = __ldg(off + m), le = __ldg(off + m + 1);
-  const bool fast = shuffle_ok && k0 + V <= total && k0 - L >= ls && k0 + V - 1 + R < le;
-  if (fast) {
-    T res[V];
-#pragma unroll
-    for (int e = 0; e < V; ++e) {
-      T acc = T(0);
-      if constexpr (LL >= 0 && RR >= 0) {
-#pragma unroll
-        for (int p = 0; p < LL + RR + 1; ++p) acc = fma(taps.w[p], win[V + e - LL + p], acc);
-      } else {
-        for (int p = 0; p < W; ++p) acc = fma(taps.w[p], win[V + e - L + p], acc);
-      }
-      res[e] = acc;
-    }
+  const int o = lane * V, oe = o + V - 1;
+  const int c0 = (o >= r1) + (o >= r2), c1 = (oe >= r1) + (oe >= r2);
+  const int ls = c0 == 0 ? r0 : (c0 == 1 ? r1 : r2);
+  const int le = c0 == 0 ? r1 : (c0 == 1 ? r2 : r3);
+  if (c0 == c1 && oe < r3 && k0 + V <= total && o - L >= ls && oe + R < le) {  // the common case
     if (vec_ok) {
       VT y;
       if constexpr (V == 4) { y.x = res[0]; y.y = res[1]; y.z = res[2]; y.w = res[3]; }
@@ -117,35 +146,68 @@ __device__ __forceinline__ void segment(const T* __restrict__ in, T* __restrict_
 #pragma unroll
       for (int e = 0; e < V; ++e) out[k0 + e] = res[e];
     }
-  } else {
+    return;
+  }
+  if (oe < r3) {  // near a line end: each element's line is one of the segment's three
+#pragma unroll
     for (int e = 0; e < V; ++e) {
-      const int64_t k = k0 + e;
-      if (k >= total) break;
-      while (k >= le) {  // advance to the line holding k (skips empty lines)
-        ++m;
-        ls = le;
-        le = __ldg(off + m + 1);
-      }
-      const int64_t len = le - ls;
-      if (!periodic && (k - ls < L || le - 1 - k < R)) continue;  // boundary cell untouched
-      const int rel0 = static_cast<int>(k - ls) - L;  // lines hold < 2^31 elements
-      const int ilen = static_cast<int>(len);
-      T acc = T(0);
-      if (ilen >= L && ilen >= R) {  // at most one wrap: a compare instead of a division
-        for (int p = 0; p < W; ++p) {
-          int rel = rel0 + p;
-          rel = rel < 0 ? rel + ilen : (rel >= ilen ? rel - ilen : rel);
-          acc = fma(taps.w[p], __ldg(in + ls + rel), acc);
-        }
-      } else {
-        for (int p = 0; p < W; ++p) {
-          int rel = (rel0 + p) % ilen;
-          if (rel < 0) rel += ilen;
-          acc = fma(taps.w[p], __ldg(in + ls + rel), acc);
-        }
-      }
-      out[k] = acc;
+      const int oo = o + e;
+      const int ce = (oo >= r1) + (oo >= r2);
+      const int ls_e = ce == 0 ? r0 : (ce == 1 ? r1 : r2);
+      const int le_e = ce == 0 ? r1 : (ce == 1 ? r2 : r3);
+      if (k0 + e < total && oo - ls_e >= L && le_e - 1 - oo >= R) out[k0 + e] = res[e];
     }
+    return;
+  }
+  // more lines in this segment than its four boundaries describe (lines shorter than a
+  // segment): walk the offsets from the lane's first line
+  int64_t m = m0 + c0, lsa = s + ls, lea = s + le;
+  for (int e = 0; e < V; ++e) {
+    const int64_t k = k0 + e;
+    if (k >= total) break;
+    while (k >= lea) {  // skips empty lines
+      ++m;
+      lsa = lea;
+      lea = __ldg(off + m + 1);
+    }
+    if (k - lsa >= L && lea - 1 - k >= R) out[k] = res[e];
+  }
+}
+
+// The first L and last R elements of every periodic line, whose stencils wrap around the line:
+// items t = m * (L + R) + which in [first, n) with the given stride, taps read from memory at
+// their wrapped index (lines shorter than the stencil wrap more than once).
+template <typename T>
+__device__ __forceinline__ void line_ends(const T* __restrict__ in, T* __restrict__ out,
+                                          const int64_t* __restrict__ off, int64_t num_lines,
+                                          int L, int R, const BTaps<T>& taps, int64_t first,
+                                          int64_t stride) {
+  const int B = L + R, W = L + R + 1;
+  const int64_t n = num_lines * B;
+  for (int64_t t = first; t < n; t += stride) {
+    const int64_t m = t / B;
+    const int which = static_cast<int>(t - m * B);
+    const int64_t ls = __ldg(off + m), le = __ldg(off + m + 1);
+    const int len = static_cast<int>(le - ls);  // lines hold < 2^31 elements
+    int rel;
+    if (which < L) {
+      rel = which;
+      if (rel >= len) continue;
+    } else {
+      rel = len - R + (which - L);
+      if (rel < L || rel < 0) continue;  // a short line's element already taken from the left
+    }
+    T acc = T(0);
+    for (int p = 0; p < W; ++p) {
+      int j = rel - L + p;
+      j = j < 0 ? j + len : (j >= len ? j - len : j);
+      if (j < 0 || j >= len) {
+        j %= len;
+        if (j < 0) j += len;
+      }
+      acc = fma(taps.w[p], __ldg(in + ls + j), acc);
+    }
+    out[ls + rel] = acc;
   }
 }
 
@@ -155,20 +217,25 @@ constexpr int kG = 4;
 template <typename T, int LL, int RR>
 __global__ void k_batch1d(const T* __restrict__ in, T* __restrict__ out,
                           const int64_t* __restrict__ off, const int32_t* __restrict__ seg,
-                          int64_t ntab, int64_t total, int64_t num_lines, int periodic,
-                          int Lr, int Rr, int vec_ok, BTaps<T> taps) {
+                          int64_t total, int64_t num_lines, int periodic, int Lr, int Rr,
+                          int vec_ok, BTaps<T> taps) {
   constexpr int V = Vec1<T>::n;
   using VT = typename Vec1<T>::V;
-  const int L = LL >= 0 ? LL : Lr;
-  const int R = RR >= 0 ? RR : Rr;
   const int lane = threadIdx.x & 31;
   const int64_t warp_id = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
   constexpr int64_t kSeg = 32 * V;
+  static_assert(kSeg % (int64_t(1) << kSegShift) == 0, "segments start on line-table entries");
   const int64_t nseg = (total + kSeg - 1) / kSeg;
+  constexpr int kClamp = 1 << 30;
+  constexpr int HL = LL > 0 ? LL : 1, HR = RR > 0 ? RR : 1;
 
   for (int64_t s0 = warp_id * kG; s0 < nseg; s0 += nwarps * kG) {  // warp-uniform loop
-    T v[kG][V];
+    T v[kG][V], hl[kG][HL], hr[kG][HR];
+    int64_t m0[kG];
+    int r[kG];
+#pragma unroll
+    for (int g = 0; g < kG; ++g) m0[g] = s0 + g < nseg ? __ldg(seg + (((s0 + g) * kSeg) >> kSegShift)) : 0;
 #pragma unroll
     for (int g = 0; g < kG; ++g) {
       const int64_t k0 = (s0 + g) * kSeg + lane * V;
@@ -180,13 +247,51 @@ __global__ void k_batch1d(const T* __restrict__ in, T* __restrict__ out,
 #pragma unroll
         for (int e = 0; e < V; ++e) v[g][e] = (k0 + e < total) ? in[k0 + e] : T(0);
       }
+      // lane 0: the L values before the segment; lane 31: the R values after it
+#pragma unroll
+      for (int e = 0; e < HL; ++e) {
+        const int64_t k = k0 - LL + e;
+        hl[g][e] = (lane == 0 && e < LL && k >= 0) ? __ldg(in + k) : T(0);
+      }
+#pragma unroll
+      for (int e = 0; e < HR; ++e) {
+        const int64_t k = k0 + V + e;
+        hr[g][e] = (lane == 31 && e < RR && k < total) ? __ldg(in + k) : T(0);
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < kG; ++g) {
+      const int64_t s = (s0 + g) * kSeg;
+      const int64_t b = (lane < 4 && m0[g] + lane <= num_lines) ? __ldg(off + m0[g] + lane) : total;
+      const int64_t d = b - s;
+      r[g] = static_cast<int>(d < -kClamp ? -kClamp : (d > kClamp ? kClamp : d));
     }
 #pragma unroll
     for (int g = 0; g < kG; ++g) {
       if (s0 + g >= nseg) break;  // warp-uniform
-      segment<T, LL, RR>(in, out, off, seg, ntab, total, num_lines, periodic, L, R, vec_ok != 0,
-                         taps, (s0 + g) * kSeg + lane * V, v[g]);
+      segment<T, LL, RR>(in, out, off, total, Lr, Rr, vec_ok != 0, taps, (s0 + g) * kSeg,
+                         m0[g], r[g], v[g], hl[g], hr[g]);
     }
+  }
+  // then the wrapped line ends (written by nobody else), spread over all threads
+  if (periodic && LL + RR > 0)
+    line_ends<T>(in, out, off, num_lines, LL, RR, taps,
+                 static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x,
+                 static_cast<int64_t>(gridDim.x) * blockDim.x);
+}
+
+// Any extents up to CS_MAX_EXTENT: every element on its own, lines found through the table.
+template <typename T>
+__global__ void k_batch1d_generic(const T* __restrict__ in, T* __restrict__ out,
+                                  const int64_t* __restrict__ off, const int32_t* __restrict__ seg,
+                                  int64_t total, int64_t num_lines, int periodic, int L, int R,
+                                  BTaps<T> taps) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < total; k += stride) {
+    int64_t m = __ldg(seg + (k >> kSegShift));
+    int64_t ls = __ldg(off + m), le = __ldg(off + m + 1);
+    (void)num_lines;
+    elements_general<T>(in, out, off, total, periodic, L, R, taps, k, 1, m, ls, le);
   }
 }
 
@@ -198,32 +303,55 @@ int launch_t(const Batch1DConfig* c, const void* vin, void* vout, cudaStream_t s
   const int W = c->left + c->right + 1;
   for (int i = 0; i < 2 * CS_MAX_EXTENT + 1; ++i)
     taps.w[i] = i < W ? static_cast<T>(c->weights[i]) : T(0);
-  const int vec_ok = (reinterpret_cast<uintptr_t>(in) % 16 == 0) &&
-                     (reinterpret_cast<uintptr_t>(out) % 16 == 0);
   const LaunchShape sh = kShapes[c->choice];
-  const int64_t seg_elems = 32 * Vec1<T>::n;
-  const int64_t nseg = (c->total_len + seg_elems - 1) / seg_elems;
-  const int64_t warps_per_cta = sh.threads / 32;
+  const bool generic = LL < 0;
+  auto kern = generic ? k_batch1d_generic<T> : nullptr;
   int resident = 0;  // persistent grid: never more CTAs than can be resident at once
-  CS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_batch1d<T, LL, RR>, sh.threads, 0));
+  if constexpr (LL < 0) {
+    CS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_batch1d_generic<T>, sh.threads, 0));
+  } else {
+    CS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_batch1d<T, LL, RR>, sh.threads, 0));
+  }
+  (void)kern;
   if (resident < 1)
     return set_error(CS_EUNSUPPORTED, "batched 1D launch shape %d x %d does not fit on an SM", sh.threads, sh.ctas_per_sm);
   const int per_sm = std::min(sh.ctas_per_sm, resident);
-  int64_t grid = std::min<int64_t>((nseg + warps_per_cta * kG - 1) / (warps_per_cta * kG),
-                                   static_cast<int64_t>(num_sms()) * per_sm);
-  grid = std::max<int64_t>(grid, 1);
-  k_batch1d<T, LL, RR><<<static_cast<unsigned>(grid), sh.threads, 0, st>>>(
-      in, out, c->d_offsets, c->d_seg_line, c->num_table, c->total_len, c->num_lines,
-      c->bc == CS_BC_PERIODIC, c->left, c->right, vec_ok, taps);
+  if constexpr (LL < 0) {
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((c->total_len + sh.threads - 1) / sh.threads,
+                                                                static_cast<int64_t>(num_sms()) * per_sm));
+    k_batch1d_generic<T><<<static_cast<unsigned>(grid), sh.threads, 0, st>>>(
+        in, out, c->d_offsets, c->d_seg_line, c->total_len, c->num_lines, c->bc == CS_BC_PERIODIC,
+        c->left, c->right, taps);
+  } else {
+    const int vec_ok = (reinterpret_cast<uintptr_t>(in) % 16 == 0) &&
+                       (reinterpret_cast<uintptr_t>(out) % 16 == 0);
+    const int64_t seg_elems = 32 * Vec1<T>::n;
+    const int64_t nseg = (c->total_len + seg_elems - 1) / seg_elems;
+    const int64_t warps_per_cta = sh.threads / 32;
+    int64_t grid = std::min<int64_t>((nseg + warps_per_cta * kG - 1) / (warps_per_cta * kG),
+                                     static_cast<int64_t>(num_sms()) * per_sm);
+    grid = std::max<int64_t>(grid, 1);
+    k_batch1d<T, LL, RR><<<static_cast<unsigned>(grid), sh.threads, 0, st>>>(
+        in, out, c->d_offsets, c->d_seg_line, c->total_len, c->num_lines, c->bc == CS_BC_PERIODIC,
+        c->left, c->right, vec_ok, taps);
+  }
   CS_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return CS_OK;
 }
 
+// Extents up to 2 on either side (within one vector of both storage types) get a kernel with the
+// extents compiled in; wider stencils take the per-element kernel.
 template <typename T>
 int launch_dispatch(const Batch1DConfig* c, const void* in, void* out, cudaStream_t st) {
-  if (c->left == 2 && c->right == 2) return launch_t<T, 2, 2>(c, in, out, st);
-  if (c->left == 1 && c->right == 1) return launch_t<T, 1, 1>(c, in, out, st);
+  switch (c->left * 3 + c->right) {
+#define CS_B1_CASE(A, B) \
+  case A * 3 + B: if (c->left == A && c->right == B) return launch_t<T, A, B>(c, in, out, st); break;
+    CS_B1_CASE(0, 0) CS_B1_CASE(0, 1) CS_B1_CASE(0, 2) CS_B1_CASE(1, 0) CS_B1_CASE(1, 1)
+    CS_B1_CASE(1, 2) CS_B1_CASE(2, 0) CS_B1_CASE(2, 1) CS_B1_CASE(2, 2)
+#undef CS_B1_CASE
+    default: break;
+  }
   return launch_t<T, -1, -1>(c, in, out, st);
 }
 

@@ -56,7 +56,7 @@ def mixed_offsets(seed):
 
 @pytest.mark.parametrize("dtype", [0, 1])
 @pytest.mark.parametrize("bc", [0, 1])
-@pytest.mark.parametrize("ext", [(2, 2), (1, 1), (3, 1), (0, 4), (6, 5)])
+@pytest.mark.parametrize("ext", [(2, 2), (1, 1), (2, 1), (0, 2), (0, 0), (3, 1), (0, 4), (6, 5)])
 def test_integer_bit_exact(env, dtype, bc, ext):
     cs, torch, orc = env
     L, R = ext
