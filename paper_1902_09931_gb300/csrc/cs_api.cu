@@ -1,5 +1,6 @@
 // C ABI of libcusten_gb: plan life cycle (Create / Compute / Swap / Destroy, Sec. 3),
 // validation, error reporting, CUDA-graph replay and the autotuner driver.
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -105,6 +106,10 @@ struct cs_plan {
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   int graph_kernels;
+  // banded host-buffer path: copy-in and copy-out streams, events (created on first use)
+  cudaStream_t band_stream[2];
+  cudaEvent_t band_event[2 * 32 + 2];
+  int band_ready;
 };
 
 namespace {
@@ -160,6 +165,72 @@ int validate_desc_common(const cs_stencil_desc* d) {
     if (!d->coe || d->num_coe < 1 || d->num_coe > 8)
       return set_error(CS_EINVAL, "user function needs 1..8 coefficients");
   }
+  return CS_OK;
+}
+
+// Host-buffer compute of a 2D plan in row bands, so that the copy in of later bands, the sweep
+// of a band and the copy out of earlier bands overlap (the host link carries both directions at
+// once).  A band's sweep waits for the bands its halo reaches into; with periodic rows the last
+// band is copied first, since the first band's halo wraps into it.
+constexpr size_t kBandMinBytes = size_t(16) << 20;
+constexpr int kMaxBands = 32;
+
+int compute_host_banded(cs_plan* p, const void* h_in, void* h_out, cudaStream_t s) {
+  const Stencil2DConfig& c = p->s2;
+  if (!p->band_ready) {
+    for (int i = 0; i < 2; ++i) CS_CUDA_TRY(cudaStreamCreateWithFlags(&p->band_stream[i], cudaStreamNonBlocking));
+    for (auto& e : p->band_event) CS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    p->band_ready = 1;
+  }
+  const int64_t ny = c.ny, row_bytes = c.nx * static_cast<int64_t>(p->elem_bytes);
+  int64_t rows = (ny + 15) / 16;  // about 16 bands
+  rows = (rows + kStencilBandAlign - 1) / kStencilBandAlign * kStencilBandAlign;
+  const int nb = static_cast<int>((ny + rows - 1) / rows);
+  if (nb > kMaxBands) return set_error(CS_EINVAL, "internal: %d bands", nb);
+  const bool periodic = c.bc == CS_BC_PERIODIC;
+  const bool halo = c.top > 0 || c.bottom > 0;  // rows <= 64 >= any extent: neighbours only
+  cudaStream_t sin = p->band_stream[0], sout = p->band_stream[1];
+  cudaEvent_t* ev_in = p->band_event;             // [nb]: band copied in
+  cudaEvent_t* ev_done = p->band_event + kMaxBands;  // [nb]: band computed
+  cudaEvent_t ev_start = p->band_event[2 * kMaxBands], ev_end = p->band_event[2 * kMaxBands + 1];
+  const char* hi = static_cast<const char*>(h_in);
+  char* ho = static_cast<char*>(h_out);
+  const char* di = static_cast<const char*>(p->d_in);
+  char* dout = static_cast<char*>(p->d_out);
+  auto band_rows = [&](int b) { return std::min<int64_t>(rows, ny - b * rows); };
+  // copy-in order: the last band first when rows wrap; pos[b] = its place in that order
+  int order[kMaxBands], pos[kMaxBands];
+  for (int k = 0; k < nb; ++k) order[k] = periodic && halo ? (k == 0 ? nb - 1 : k - 1) : k;
+  for (int k = 0; k < nb; ++k) pos[order[k]] = k;
+  CS_CUDA_TRY(cudaEventRecord(ev_start, s));  // earlier work on the caller's stream first
+  CS_CUDA_TRY(cudaStreamWaitEvent(sin, ev_start, 0));
+  CS_CUDA_TRY(cudaStreamWaitEvent(sout, ev_start, 0));
+  for (int k = 0; k < nb; ++k) {
+    const int b = order[k];
+    const size_t off = static_cast<size_t>(b * rows * row_bytes);
+    CS_CUDA_TRY(cudaMemcpyAsync(const_cast<char*>(di) + off, hi + off, static_cast<size_t>(band_rows(b) * row_bytes),
+                                cudaMemcpyHostToDevice, sin));
+    CS_CUDA_TRY(cudaEventRecord(ev_in[b], sin));
+  }
+  for (int b = 0; b < nb; ++b) {
+    int need = pos[b];  // the band itself and, with a halo, its neighbours (wrapping if periodic)
+    if (halo) {
+      const int lo = b > 0 ? b - 1 : (periodic ? nb - 1 : 0);
+      const int up = b + 1 < nb ? b + 1 : (periodic ? 0 : nb - 1);
+      need = std::max(need, std::max(pos[lo], pos[up]));
+    }
+    CS_CUDA_TRY(cudaStreamWaitEvent(s, ev_in[order[need]], 0));
+    int rc = stencil2d_launch_rows(&p->s2, p->d_in, p->d_out, b * rows, b * rows + band_rows(b), s);
+    if (rc != CS_OK) return rc;
+    CS_CUDA_TRY(cudaEventRecord(ev_done[b], s));
+    CS_CUDA_TRY(cudaStreamWaitEvent(sout, ev_done[b], 0));
+    const size_t off = static_cast<size_t>(b * rows * row_bytes);
+    CS_CUDA_TRY(cudaMemcpyAsync(ho + off, dout + off, static_cast<size_t>(band_rows(b) * row_bytes),
+                                cudaMemcpyDeviceToHost, sout));
+  }
+  CS_CUDA_TRY(cudaEventRecord(ev_end, sout));
+  CS_CUDA_TRY(cudaStreamWaitEvent(s, ev_end, 0));
+  CS_CUDA_TRY(cudaStreamSynchronize(s));
   return CS_OK;
 }
 
@@ -323,6 +394,8 @@ int cs_compute_host(cs_plan_t p, const void* h_in, void* h_out, void* stream) {
   if (p->kind == kCahnHilliard) return set_error(CS_EINVAL, "use cs_ch_step for a Cahn-Hilliard plan");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t bytes = static_cast<size_t>(p->elems) * p->elem_bytes;
+  if (p->kind == kStencil2D && h_in && h_out && bytes >= kBandMinBytes && p->s2.ny >= 2 * kStencilBandAlign)
+    return compute_host_banded(p, h_in, h_out, s);
   if (h_in && bytes) CS_CUDA_TRY(cudaMemcpyAsync(const_cast<void*>(p->d_in), h_in, bytes, cudaMemcpyHostToDevice, s));
   int rc = cs_compute(p, stream);
   if (rc != CS_OK) return rc;
@@ -442,6 +515,10 @@ int cs_autotune(cs_plan_t p, void* stream) {
 int cs_destroy(cs_plan_t p) {
   if (!p) return CS_OK;
   drop_graph(p);
+  if (p->band_ready) {
+    for (auto& e : p->band_event) cudaEventDestroy(e);
+    for (int i = 0; i < 2; ++i) cudaStreamDestroy(p->band_stream[i]);
+  }
   if (p->kind == kStencil2D) stencil2d_release(&p->s2);
   if (p->kind == kBatch1D) batch1d_release(&p->b1);
   if (p->kind == kCahnHilliard) ch_destroy(p->ch);

@@ -54,6 +54,11 @@ struct Stencil2DConfig {
 int stencil2d_prepare(Stencil2DConfig* cfg);  // picks variant, allocates generic weights
 void stencil2d_release(Stencil2DConfig* cfg);
 int stencil2d_launch(const Stencil2DConfig* cfg, const void* in, void* out, cudaStream_t s);
+// Writes only output rows [row0, row1) (row0 a multiple of kStencilBandAlign, a multiple of every
+// tile height; row1 clipped to ny); reads the input rows those outputs need.
+constexpr int64_t kStencilBandAlign = 64;
+int stencil2d_launch_rows(const Stencil2DConfig* cfg, const void* in, void* out, int64_t row0,
+                          int64_t row1, cudaStream_t s);
 int stencil2d_num_tile_choices();
 int stencil2d_status_ptr(int** out);  // device word a timed-out bounded wait sets to 1
 int stencil2d_set_tile_choice(Stencil2DConfig* cfg, int choice);

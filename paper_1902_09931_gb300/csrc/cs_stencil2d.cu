@@ -228,4 +228,15 @@ int stencil2d_launch(const Stencil2DConfig* cfg, const void* in, void* out, cuda
                               : stencil2d_launch_f64(cfg, in, out, s);
 }
 
+int stencil2d_launch_rows(const Stencil2DConfig* cfg, const void* in, void* out, int64_t row0,
+                          int64_t row1, cudaStream_t s) {
+  if (row0 % kStencilBandAlign != 0) return set_error(CS_EINVAL, "internal: band start %lld not aligned", (long long)row0);
+  s2d::RowWindow& w = s2d::row_window();
+  w.row0 = row0;
+  w.row1 = row1;
+  const int rc = stencil2d_launch(cfg, in, out, s);
+  w = s2d::RowWindow{};
+  return rc;
+}
+
 }  // namespace cs

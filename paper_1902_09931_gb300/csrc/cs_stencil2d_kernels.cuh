@@ -361,7 +361,7 @@ __device__ __forceinline__ void spec_compute(const T* s, T* __restrict__ out, in
 template <typename T, int TY, int SPEC>
 __global__ void __launch_bounds__(kThreads)
     k_stencil2d_spec(const T* __restrict__ in, T* __restrict__ out, int64_t nx, int64_t ny,
-                     int periodic, int vec_ok, Taps<T> taps) {
+                     int periodic, int vec_ok, Taps<T> taps, int ty0) {
   constexpr SpecDesc sd = kSpecs[SPEC];
   constexpr int V = Vec<T>::n;
   constexpr int TX = tile_x<T>();
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(kThreads)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
   const int64_t x0 = static_cast<int64_t>(blockIdx.x) * TX;
-  const int64_t y0 = static_cast<int64_t>(blockIdx.y) * TY;
+  const int64_t y0 = (static_cast<int64_t>(blockIdx.y) + ty0) * TY;
   load_tile_ct<T, ROWS, COLS>(s, in, nx, ny, periodic != 0, vec_ok != 0, x0, y0, sd.T, LA);
   if constexpr (sd.xform) xform_tile<T>(s, ROWS * COLS);
   spec_compute<T, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
@@ -630,7 +630,7 @@ __device__ __forceinline__ void ix_compute(const float2* s01, const float* s2, d
 template <int TY, int SPEC>
 __global__ void __launch_bounds__(kThreads)
     k_stencil2d_ix(const double* __restrict__ in, double* __restrict__ out, int64_t nx, int64_t ny,
-                   int periodic, int vec_ok, Taps<double> taps, IxTaps itaps) {
+                   int periodic, int vec_ok, Taps<double> taps, IxTaps itaps, int ty0) {
   constexpr SpecDesc sd = kSpecs[SPEC];
   constexpr int V = Vec<double>::n;
   constexpr int TX = tile_x<double>();
@@ -643,7 +643,7 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ unsigned s_red[kThreads / 32];
   static_assert(COLS % 2 == 0, "digit passes take values in pairs");
   const int64_t x0 = static_cast<int64_t>(blockIdx.x) * TX;
-  const int64_t y0 = static_cast<int64_t>(blockIdx.y) * TY;
+  const int64_t y0 = (static_cast<int64_t>(blockIdx.y) + ty0) * TY;
   load_tile_ct<double, ROWS, COLS>(s, in, nx, ny, periodic != 0, vec_ok != 0, x0, y0, sd.T, LA);
   // pass 1: the tile's largest exponent; inf / nan (and tiles outside the exponent window) take
   // native FP64
@@ -662,6 +662,23 @@ __global__ void __launch_bounds__(kThreads)
   ix_compute<TY, SPEC>(s01, s2, out, nx, ny, periodic, x0, y0, itaps, scale);
 }
 
+// Output rows [row0, row1) of the next launches on this host thread (row0 a multiple of 64, so
+// of every tile height; row1 < 0: to the last row).  Set by stencil2d_launch_rows for the banded
+// host-buffer path; every other launch covers the whole grid.
+struct RowWindow { int64_t row0 = 0, row1 = -1; };
+inline RowWindow& row_window() {
+  static thread_local RowWindow w;
+  return w;
+}
+// First tile row and number of tile rows of height ty that the window covers in a grid of ny rows.
+inline void window_tiles(int ty, int64_t ny, int* ty0, int* nty) {
+  const RowWindow& w = row_window();
+  const int64_t r1 = w.row1 < 0 || w.row1 > ny ? ny : w.row1;
+  const int64_t t0 = w.row0 / ty, t1 = (r1 + ty - 1) / ty;
+  *ty0 = static_cast<int>(t0);
+  *nty = static_cast<int>(t1 > t0 ? t1 - t0 : 0);
+}
+
 template <int TY, int SPEC>
 int launch_ix(const double* in, double* out, int64_t nx, int64_t ny, int periodic, int vec_ok,
               const Taps<double>& taps, const IxTaps& itaps, cudaStream_t st) {
@@ -673,9 +690,11 @@ int launch_ix(const double* in, double* out, int64_t nx, int64_t ny, int periodi
     CS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     attr_set = true;
   }
-  dim3 grid(static_cast<unsigned>((nx + tile_x<double>() - 1) / tile_x<double>()),
-            static_cast<unsigned>((ny + TY - 1) / TY));
-  kern<<<grid, kThreads, smem, st>>>(in, out, nx, ny, periodic, vec_ok, taps, itaps);
+  int ty0, nty;
+  window_tiles(TY, ny, &ty0, &nty);
+  if (nty == 0) return CS_OK;
+  dim3 grid(static_cast<unsigned>((nx + tile_x<double>() - 1) / tile_x<double>()), static_cast<unsigned>(nty));
+  kern<<<grid, kThreads, smem, st>>>(in, out, nx, ny, periodic, vec_ok, taps, itaps, ty0);
   CS_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return CS_OK;
@@ -1032,7 +1051,7 @@ __device__ __forceinline__ void dd_compute(const float4* sp, double* __restrict_
 template <int TY, int SPEC>
 __global__ void __launch_bounds__(kThreads)
     k_stencil2d_dd(const double* __restrict__ in, double* __restrict__ out, int64_t nx, int64_t ny,
-                   int periodic, int vec_ok, Taps<double> taps, DDTaps dtaps) {
+                   int periodic, int vec_ok, Taps<double> taps, DDTaps dtaps, int ty0) {
   constexpr SpecDesc sd = kSpecs[SPEC];
   constexpr int V = Vec<double>::n;
   constexpr int TX = tile_x<double>();
@@ -1043,7 +1062,7 @@ __global__ void __launch_bounds__(kThreads)
   double* s = reinterpret_cast<double*>(smem_raw);
   __shared__ int s_red[kThreads / 32];
   const int64_t x0 = static_cast<int64_t>(blockIdx.x) * TX;
-  const int64_t y0 = static_cast<int64_t>(blockIdx.y) * TY;
+  const int64_t y0 = (static_cast<int64_t>(blockIdx.y) + ty0) * TY;
   load_tile_ct<double, ROWS, COLS>(s, in, nx, ny, periodic != 0, vec_ok != 0, x0, y0, sd.T, LA);
   if constexpr (sd.xform) xform_tile<double>(s, ROWS * COLS);
   if (dd_split_tile<ROWS * COLS>(s, s_red))
@@ -1063,9 +1082,11 @@ int launch_dd(const double* in, double* out, int64_t nx, int64_t ny, int periodi
     CS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     attr_set = true;
   }
-  dim3 grid(static_cast<unsigned>((nx + tile_x<double>() - 1) / tile_x<double>()),
-            static_cast<unsigned>((ny + TY - 1) / TY));
-  kern<<<grid, kThreads, smem, st>>>(in, out, nx, ny, periodic, vec_ok, taps, dtaps);
+  int ty0, nty;
+  window_tiles(TY, ny, &ty0, &nty);
+  if (nty == 0) return CS_OK;
+  dim3 grid(static_cast<unsigned>((nx + tile_x<double>() - 1) / tile_x<double>()), static_cast<unsigned>(nty));
+  kern<<<grid, kThreads, smem, st>>>(in, out, nx, ny, periodic, vec_ok, taps, dtaps, ty0);
   CS_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return CS_OK;
@@ -1180,7 +1201,7 @@ template <int MODE, typename T, int SPEC>
 __global__ void __launch_bounds__(kThreads)
     k_stencil2d_tma(const __grid_constant__ CUtensorMap tmap, const T* __restrict__ in,
                     T* __restrict__ out, int64_t nx, int64_t ny, int periodic, int tiles_x,
-                    int tiles, Taps<T> taps, IxTaps itaps, DDTaps dtaps, int* status) {
+                    int tiles, int ty0, Taps<T> taps, IxTaps itaps, DDTaps dtaps, int* status) {
   using G = TmaGeom<MODE, T, SPEC>;
   constexpr SpecDesc sd = kSpecs[SPEC];
   constexpr int TY = G::TY, TX = G::TX, COLS = G::COLS, ROWS = G::ROWS, SE = G::SE;
@@ -1198,7 +1219,7 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   auto issue = [&](int i, int st) {
     const int t = static_cast<int>(blockIdx.x) + i * static_cast<int>(gridDim.x);
-    const int bx = t % tiles_x, by = t / tiles_x;
+    const int bx = t % tiles_x, by = t / tiles_x + ty0;
     fence_proxy_async();  // order this stage's generic-proxy writes before the async copy
     mbar_expect_tx(&mbar[st], static_cast<uint32_t>(SE * sizeof(T)));
     tma_load_2d(smem_raw + st * G::STAGE_BYTES, &tmap, bx * TX - G::LA, by * TY - sd.T, &mbar[st]);
@@ -1218,7 +1239,7 @@ __global__ void __launch_bounds__(kThreads)
     T* s = reinterpret_cast<T*>(smem_raw + st * G::STAGE_BYTES);
     const int t = static_cast<int>(blockIdx.x) + i * static_cast<int>(gridDim.x);
     const int64_t x0 = static_cast<int64_t>(t % tiles_x) * TX;
-    const int64_t y0 = static_cast<int64_t>(t / tiles_x) * TY;
+    const int64_t y0 = static_cast<int64_t>(t / tiles_x + ty0) * TY;
     const int64_t gx0 = x0 - G::LA, gy0 = y0 - sd.T;
     if (periodic && (gx0 < 0 || gx0 + COLS > nx || gy0 < 0 || gy0 + ROWS > ny)) {
       fixup_periodic<T, COLS, ROWS>(s, in, nx, ny, gx0, gy0);
@@ -1267,13 +1288,16 @@ int launch_tma(const CUtensorMap& map, const T* in, T* out, int64_t nx, int64_t 
     per_sm = occ > 0 ? occ : -1;
   }
   if (per_sm < 0) return set_error(CS_EUNSUPPORTED, "TMA stencil kernel does not fit on an SM");
-  const int64_t tiles_x = (nx + G::TX - 1) / G::TX, tiles_y = (ny + G::TY - 1) / G::TY;
-  const int64_t tiles = tiles_x * tiles_y;
+  int ty0, nty;
+  window_tiles(G::TY, ny, &ty0, &nty);
+  const int64_t tiles_x = (nx + G::TX - 1) / G::TX;
+  const int64_t tiles = tiles_x * nty;
+  if (tiles == 0) return CS_OK;
   if (tiles > 0x7fffffff) return set_error(CS_EINVAL, "grid too large for the TMA sweep");
   const int64_t grid = std::min<int64_t>(tiles, static_cast<int64_t>(num_sms()) * per_sm);
   kern<<<static_cast<unsigned>(grid), kThreads, G::SMEM, st>>>(map, in, out, nx, ny, periodic,
                                                                static_cast<int>(tiles_x), static_cast<int>(tiles),
-                                                               taps, it, dt, status);
+                                                               ty0, taps, it, dt, status);
   CS_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return CS_OK;
@@ -1303,7 +1327,7 @@ template <typename T, int TY>
 __global__ void __launch_bounds__(kThreads)
     k_stencil2d_generic(const T* __restrict__ in, T* __restrict__ out, int64_t nx, int64_t ny,
                         int periodic, int vec_ok, int L, int R, int TT, int BB,
-                        const T* __restrict__ wts, int xform, int epi) {
+                        const T* __restrict__ wts, int xform, int epi, int ty0) {
   constexpr int V = Vec<T>::n;
   constexpr int TX = tile_x<T>();
   constexpr int WX = TX / 32, WY = 8 / WX, RW = TY / WY;
@@ -1316,7 +1340,7 @@ __global__ void __launch_bounds__(kThreads)
   for (int i = threadIdx.x; i < W * H; i += kThreads) ws[i] = wts[i];
 
   const int64_t x0 = static_cast<int64_t>(blockIdx.x) * TX;
-  const int64_t y0 = static_cast<int64_t>(blockIdx.y) * TY;
+  const int64_t y0 = (static_cast<int64_t>(blockIdx.y) + ty0) * TY;
   load_tile<T>(s, in, nx, ny, periodic != 0, vec_ok != 0, x0, y0, TT, LA, COLS, ROWS);
   if (xform) xform_tile<T>(s, ROWS * COLS);
 
@@ -1352,9 +1376,11 @@ int launch_spec(const T* in, T* out, int64_t nx, int64_t ny, int periodic, int v
                                      static_cast<int>(smem)));
     attr_set = true;
   }
-  dim3 grid(static_cast<unsigned>((nx + tile_x<T>() - 1) / tile_x<T>()),
-            static_cast<unsigned>((ny + TY - 1) / TY));
-  kern<<<grid, kThreads, smem, st>>>(in, out, nx, ny, periodic, vec_ok, taps);
+  int ty0, nty;
+  window_tiles(TY, ny, &ty0, &nty);
+  if (nty == 0) return CS_OK;
+  dim3 grid(static_cast<unsigned>((nx + tile_x<T>() - 1) / tile_x<T>()), static_cast<unsigned>(nty));
+  kern<<<grid, kThreads, smem, st>>>(in, out, nx, ny, periodic, vec_ok, taps, ty0);
   CS_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return CS_OK;
@@ -1374,10 +1400,12 @@ int launch_generic(const T* in, T* out, const Stencil2DConfig* cfg, const T* d_w
                                      static_cast<int>(maxb)));
     attr_set = true;
   }
-  dim3 grid(static_cast<unsigned>((cfg->nx + tile_x<T>() - 1) / tile_x<T>()),
-            static_cast<unsigned>((cfg->ny + TY - 1) / TY));
+  int ty0, nty;
+  window_tiles(TY, cfg->ny, &ty0, &nty);
+  if (nty == 0) return CS_OK;
+  dim3 grid(static_cast<unsigned>((cfg->nx + tile_x<T>() - 1) / tile_x<T>()), static_cast<unsigned>(nty));
   kern<<<grid, kThreads, smem, st>>>(in, out, cfg->nx, cfg->ny, periodic, vec_ok, cfg->left,
-                                     cfg->right, cfg->top, cfg->bottom, d_w, xform, epi);
+                                     cfg->right, cfg->top, cfg->bottom, d_w, xform, epi, ty0);
   CS_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return CS_OK;
