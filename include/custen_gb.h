@@ -130,8 +130,11 @@ int cs_compute_group(const cs_plan_t* plans, int32_t count, void* cuda_stream);
 
 /* Compute with host buffers (Sec. 3's HOST flag): copies h_in (host, the full input field)
  * into the plan's device input, computes, and copies the device output back into h_out.
- * Either pointer may be NULL to skip that copy.  Pinned host memory gives overlap-free full
- * bandwidth; pageable memory works but is slower.  Synchronises the stream before returning
+ * Either pointer may be NULL to skip that copy.  A 2D plan of 16 MB or more with both pointers
+ * set is processed in row bands whose copy-in, sweep and copy-out overlap on streams the plan
+ * owns (the results equal a device sweep bit for bit); the device input then holds the copied
+ * field and the device output the result, as with one copy.  Pinned host memory is needed for
+ * the overlap; pageable memory works but is slower.  Synchronises the stream before returning
  * when h_out is non-NULL. */
 int cs_compute_host(cs_plan_t plan, const void* h_in, void* h_out, void* cuda_stream);
 
