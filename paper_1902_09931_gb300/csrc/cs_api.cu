@@ -183,7 +183,9 @@ int compute_host_banded(cs_plan* p, const void* h_in, void* h_out, cudaStream_t 
     p->band_ready = 1;
   }
   const int64_t ny = c.ny, row_bytes = c.nx * static_cast<int64_t>(p->elem_bytes);
-  int64_t rows = (ny + 15) / 16;  // about 16 bands
+  // bands of about 8 MB (enough to amortise a copy call), between 2 and kMaxBands of them
+  const int64_t want = std::max<int64_t>(2, std::min<int64_t>(kMaxBands, ny * row_bytes / (int64_t(8) << 20)));
+  int64_t rows = (ny + want - 1) / want;
   rows = (rows + kStencilBandAlign - 1) / kStencilBandAlign * kStencilBandAlign;
   const int nb = static_cast<int>((ny + rows - 1) / rows);
   if (nb > kMaxBands) return set_error(CS_EINVAL, "internal: %d bands", nb);
