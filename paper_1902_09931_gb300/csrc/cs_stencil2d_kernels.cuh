@@ -388,14 +388,15 @@ inline size_t tile_smem_bytes(int L, int R, int TT, int BB, int TY, bool generic
 
 // ---- exact digit evaluation of FP64-storage stencils with integer weight ratios ------------
 // When every weight is w_k = c * n_k with small integers (sum |n_k| <= 64; the paper's stencils
-// are of this kind), a tile is evaluated exactly: every staged value is cut into three signed
-// 18-bit digits on a grid fixed by the tile's largest exponent, x = sum_i d_i 2^(G - 18(i+1)),
-// so each digit sum S_i = sum_k n_k d_{k,i} is an integer below 2^24 and exact in FP32
-// (3 FFMA per tap).  The sums are recombined as one exact 64-bit integer, rounded once to FP64
-// and scaled by c * 2^(G-54) with one FP64 multiply.  Only bits of a value below 2^(G-54) are
-// dropped (below 2^-53 of the tile's largest value), so the result is more accurate than an
-// FP64 accumulation.  Tiles holding inf / nan, or whose largest value is outside
-// [2^-900, 2^900], are evaluated in native FP64.
+// are of this kind), a tile is evaluated with integer-exact sums: every staged value is cut into
+// three signed 18-bit digits on a grid fixed by the tile's largest exponent,
+// x = sum_i d_i 2^(G - 18(i+1)), so each digit sum S_i = sum_k n_k d_{k,i} is an integer below
+// 2^24 and exact in FP32 (per tap one packed FMA for S0, S1 and one FMA for S2).  The sums form
+// T = S0 2^36 + S1 2^18 + S2, which is rounded to a multiple of 2^8 and scaled by c * 2^(G-54)
+// with one FP64 FMA (ix_combine).  Bits of a value below 2^(G-54) are dropped and the final sum
+// is rounded to 2^(G-46) |c|: the error is at most 2^-45 / sum|n| of sum|w| * max|in| (native
+// FP64 accumulation: about taps * 2^-53 of sum|w| |in|).  Tiles holding inf / nan, or whose
+// largest value is outside [2^-900, 2^900], are evaluated in native FP64.
 
 struct IxTaps {
   float n[32];   // integer weight ratios n_k (exact in FP32)
@@ -438,49 +439,35 @@ __device__ __forceinline__ void ix_split(double x, int tile_e, float& d0, float&
   d2 = __fsub_rn(__uint_as_float((al & 0x3FFFFu) | K), k);
 }
 
-// T = S0 * 2^36 + S1 * 2^18 + S2 (|T| < 2^61, exact: the digit sums are integers below 2^24 in
-// magnitude), formed on the integer pipe.
-__device__ __forceinline__ long long ix_join(float S0, float S1, float S2) {
-  return (static_cast<long long>(__float2int_rn(S0)) << 36) +
-         (static_cast<long long>(__float2int_rn(S1)) << 18) + static_cast<long long>(__float2int_rn(S2));
+// T * scale for T = S0 * 2^36 + S1 * 2^18 + S2 (the digit sums are integers below 2^24 in
+// magnitude, so |T| < sum|n| * 2^54 <= 2^60) with one FP64 instruction and no int64 -> FP64
+// conversion (GB300 issues about 2 FP64 instructions per clock per SM, the digit kernel's bound):
+// T' = round(T / 2^8) = S0 * 2^28 + S1 * 2^10 + round(S2 / 2^8) is exact apart from the last
+// term, |T'| <= 2^52, so D = 2^52 + |T'| is assembled by an integer add to the bit pattern of
+// 2^52, and fma(D, +-2^8 scale, -+2^60 scale) = T' * 2^8 * scale is rounded once.  sc and cs are
+// the two words of 2^8 * scale and of -2^60 * scale (exact power-of-two multiples); the sign of
+// T flips both.  Error before the final rounding: at most 2^7 units of 2^(G-54) * |c|.
+__device__ __forceinline__ double ix_combine(float S0, float S1, float S2, uint32_t sc_hi, uint32_t sc_lo,
+                                            uint32_t cs_hi, uint32_t cs_lo) {
+  const long long Tp = (static_cast<long long>(__float2int_rn(S0)) << 28) +
+                       (static_cast<long long>(__float2int_rn(S1)) << 10) +
+                       static_cast<long long>(__float2int_rn(S2 * 0x1p-8f));
+  const uint32_t sgn = static_cast<uint32_t>(static_cast<unsigned long long>(Tp) >> 63) << 31;
+  const unsigned long long A = sgn ? 0ull - static_cast<unsigned long long>(Tp) : static_cast<unsigned long long>(Tp);
+  const double D = __longlong_as_double(static_cast<long long>(0x4330000000000000ull + A));
+  const double sc = __hiloint2double(static_cast<int>(sc_hi ^ sgn), static_cast<int>(sc_lo));
+  const double cs = __hiloint2double(static_cast<int>(cs_hi ^ sgn), static_cast<int>(cs_lo));
+  return __fma_rn(D, sc, cs);
 }
 
-// T rounded once, to nearest-even FP64, by the hardware conversion (an FP64-pipe instruction).
-__device__ __forceinline__ double ix_combine(float S0, float S1, float S2) {
-  return __ll2double_rn(ix_join(S0, S1, S2));
+// A tile takes the digit path when its largest value lies in [2^-900, 2^900] and its scale
+// c * 2^(G-54) keeps 2^8 scale normal and 2^60 scale finite; an all-zero tile (tile_e 0, scale 0)
+// gives zeros.  Every other tile (inf / nan, out-of-range values) is evaluated in native FP64.
+__device__ __forceinline__ bool ix_tile_ok(int tile_e, double scale) {
+  if (tile_e == 0) return true;
+  const double a = fabs(scale);
+  return tile_e >= kIxMinExp && tile_e <= kIxMaxExp && a >= 0x1p-1000 && a < 0x1p960;
 }
-
-// The same rounding on the integer pipe: normalise |T|, keep 53 bits, round half to even, and
-// assemble sign, exponent and significand.  GB300's FP64 pipe issues about 2 operations per
-// clock per SM, so kernels with few taps convert some outputs this way to keep that pipe from
-// bounding them.
-__device__ __forceinline__ double ix_combine_int(float S0, float S1, float S2) {
-  const long long T = ix_join(S0, S1, S2);
-  if (T == 0) return 0.0;
-  const unsigned long long sgn = static_cast<unsigned long long>(T) & 0x8000000000000000ull;
-  const unsigned long long a = sgn ? 0ull - static_cast<unsigned long long>(T) : static_cast<unsigned long long>(T);
-  uint32_t ahi = static_cast<uint32_t>(a >> 32), alo = static_cast<uint32_t>(a);
-  const int lz = ahi ? __clz(ahi) : 32 + __clz(alo);
-  if (lz >= 32) {  // leading one to bit 63 of (ahi:alo)
-    ahi = alo << (lz - 32);
-    alo = 0u;
-  } else if (lz > 0) {
-    ahi = __funnelshift_l(alo, ahi, lz);
-    alo <<= lz;
-  }
-  uint32_t mhi = ahi >> 11;                      // significand bits 63..43 (with the leading one)
-  const uint32_t mlo = __funnelshift_r(alo, ahi, 11);  // bits 42..11
-  const uint32_t rem = alo & 0x7FFu;             // bits 10..0, dropped
-  const bool up = rem > 0x400u || (rem == 0x400u && (mlo & 1u));
-  const uint32_t mlo2 = mlo + (up ? 1u : 0u);
-  mhi += (up && mlo2 == 0u) ? 1u : 0u;           // a carry to 2^53 moves into the exponent field
-  const unsigned long long bits =
-      sgn + ((static_cast<unsigned long long>(1086 - lz) << 52) +
-             ((static_cast<unsigned long long>(mhi) << 32 | mlo2) - (1ull << 52)));
-  return __longlong_as_double(static_cast<long long>(bits));
-}
-
-constexpr int popcount32(uint32_t m) { return m == 0u ? 0 : static_cast<int>(m & 1u) + popcount32(m >> 1); }
 
 // Largest high word (sign cleared) of the n staged FP64 values (n even, 16-byte aligned): its top
 // bits are the largest biased exponent, and it is >= 0x7ff00000 exactly when the tile holds an
@@ -526,6 +513,9 @@ template <int TY, int SPEC>
 __device__ __forceinline__ void ix_compute(const float2* s01, const float* s2, double* __restrict__ out,
                                            int64_t nx, int64_t ny, int periodic, int64_t x0,
                                            int64_t y0, const IxTaps& taps, double scale) {
+  const double sc = scale * 0x1p8, cs = -scale * 0x1p60;  // exact
+  const uint32_t sc_hi = static_cast<uint32_t>(__double2hiint(sc)), sc_lo = static_cast<uint32_t>(__double2loint(sc));
+  const uint32_t cs_hi = static_cast<uint32_t>(__double2hiint(cs)), cs_lo = static_cast<uint32_t>(__double2loint(cs));
   constexpr SpecDesc sd = kSpecs[SPEC];
   constexpr int L = sd.L, R = sd.R, TT = sd.T, BB = sd.B;
   constexpr int V = Vec<double>::n;
@@ -536,9 +526,6 @@ __device__ __forceinline__ void ix_compute(const float2* s01, const float* s2, d
   constexpr int W = L + R + 1, H = TT + BB + 1;
   constexpr int WY = kThreads / 32, RW = TY / WY;
   constexpr int S0 = LA - L, X = S0 & 1, NP = (W + 1 + X + 1) / 2;  // pairs read per row
-  // with at most 5 taps the FP64 pipe (conversion + scale per output) bounds the kernel: the
-  // second column's conversion then runs on the integer pipe (measured on GB300)
-  constexpr bool kIntJoin = popcount32(sd.mask) <= 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = 2 * lane;
   const int r0 = warp * RW;
@@ -610,8 +597,8 @@ __device__ __forceinline__ void ix_compute(const float2* s01, const float* s2, d
     if (done >= 0) {
       const float2 p0 = acc01[done % H][0], p1 = acc01[done % H][1];
       const float q0 = acc2[done % H][0], q1 = acc2[done % H][1];
-      const double val0 = ix_combine(p0.x, p0.y, q0) * scale;
-      const double val1 = (kIntJoin ? ix_combine_int(p1.x, p1.y, q1) : ix_combine(p1.x, p1.y, q1)) * scale;
+      const double val0 = ix_combine(p0.x, p0.y, q0, sc_hi, sc_lo, cs_hi, cs_lo);
+      const double val1 = ix_combine(p1.x, p1.y, q1, sc_hi, sc_lo, cs_hi, cs_lo);
       acc01[done % H][0] = acc01[done % H][1] = make_float2(0.0f, 0.0f);
       acc2[done % H][0] = acc2[done % H][1] = 0.0f;
       if (done >= klo && done < khi) {
@@ -649,7 +636,9 @@ __global__ void __launch_bounds__(kThreads)
   // native FP64
   const uint32_t mhi = ix_tile_max_hi(s, ROWS * COLS, s_red);
   const int tile_e = static_cast<int>(mhi >> 20);
-  if (tile_e == 0x7ff || (tile_e != 0 && (tile_e < kIxMinExp || tile_e > kIxMaxExp))) {
+  // scale = c * 2^(G - 54) with G = tile_e - 1022
+  const double scale = tile_e == 0 ? 0.0 : itaps.c * ldexp(1.0, tile_e - 1022 - 3 * kIxDigitBits);
+  if (!ix_tile_ok(tile_e, scale)) {
     spec_compute<double, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
     return;
   }
@@ -657,8 +646,6 @@ __global__ void __launch_bounds__(kThreads)
   ix_split_tile(s, s2, ROWS * COLS, tile_e);
   __syncthreads();
   const float2* s01 = reinterpret_cast<const float2*>(s);
-  // scale = c * 2^(G - 54) with G = tile_e - 1022 (all-zero tile: any finite scale)
-  const double scale = tile_e == 0 ? 0.0 : itaps.c * ldexp(1.0, tile_e - 1022 - 3 * kIxDigitBits);
   ix_compute<TY, SPEC>(s01, s2, out, nx, ny, periodic, x0, y0, itaps, scale);
 }
 
@@ -1032,8 +1019,9 @@ __device__ __forceinline__ void dd_compute(const float4* sp, double* __restrict_
         const float4 u = sp[(r0 + done + TT) * CP + (LA + c) / 2];  // centre values
         dd_add_cubic_minus2(h, l, make_float2(u.x, u.y), make_float2(u.z, u.w));
       }
-      const double val0 = f2d_exact(h.x) + f2d_exact(l.x);
-      const double val1 = f2d_exact(h.y) + f2d_exact(l.y);
+      // hi converts on the FP64 pipe (idle enough here), lo on the integer pipe
+      const double val0 = static_cast<double>(h.x) + f2d_exact(l.x);
+      const double val1 = static_cast<double>(h.y) + f2d_exact(l.y);
       h = l = make_float2(0.0f, 0.0f);
       if (done >= klo && done < khi) {
         if (both) {
@@ -1252,14 +1240,14 @@ __global__ void __launch_bounds__(kThreads)
       static_assert(COLS % 2 == 0, "digit passes take values in pairs");
       const uint32_t mhi = ix_tile_max_hi(s, SE, reinterpret_cast<unsigned*>(s_wmax));
       const int tile_e = static_cast<int>(mhi >> 20);
-      if (tile_e == 0x7ff || (tile_e != 0 && (tile_e < kIxMinExp || tile_e > kIxMaxExp))) {
+      const double scale = tile_e == 0 ? 0.0 : itaps.c * ldexp(1.0, tile_e - 1022 - 3 * kIxDigitBits);
+      if (!ix_tile_ok(tile_e, scale)) {
         spec_compute<double, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
       } else {
         float* s2 = reinterpret_cast<float*>(extra);
         ix_split_tile(s, s2, SE, tile_e);
         __syncthreads();
         const float2* s01 = reinterpret_cast<const float2*>(s);
-        const double scale = tile_e == 0 ? 0.0 : itaps.c * ldexp(1.0, tile_e - 1022 - 3 * kIxDigitBits);
         ix_compute<TY, SPEC>(s01, s2, out, nx, ny, periodic, x0, y0, itaps, scale);
       }
     } else {
