@@ -433,3 +433,20 @@ def test_unaligned_buffers_match_oracle(env, dtype, offsets, bc):
         assert scaled_err(got[written], ref[written], w, field) <= TOL[dtype], name
         spare = buf_out[0] if out_off == 1 else buf_out[-1]
         assert spare.item() == sentinel, name  # nothing written outside the view
+
+
+@pytest.mark.parametrize("wscale,uscale", [(1e200, 1e100), (1e-200, 1e-100), (1e150, 1e-150)])
+def test_exact_digit_path_extreme_scales(env, wscale, uscale):
+    """Integer-ratio weights with a very large or very small common factor: tiles whose scale
+    c * 2^(G - 54) leaves the range of the one-FMA conversion take native FP64, the others the
+    digit path; every output meets the FP64 tolerance against the oracle."""
+    cs, torch, orc = env
+    ny, nx = 130, 200
+    field = W.sines_field(nx, seed=41, ny=ny) * uscale
+    for name, L, R, T, B, d, w in [c for c in stencil_cases(1.0) if c[0] in ("lap5", "biharm13", "x1", "ddy4")]:
+        w = np.asarray(w) * wscale
+        kw = dict(dir=d, bc=1, left=L, right=R, top=T, bottom=B, weights=w)
+        got = run2d(cs, torch, field, kw, 0)
+        ref = orc.stencil2d(field, w, d, 1, L, R, T, B)
+        assert np.all(np.isfinite(got)), name
+        assert scaled_err(got, ref, w, field) <= 1e-12, name
