@@ -147,8 +147,9 @@ int cs_swap(cs_plan_t plan);
  *   - weights w_k = c * n_k with integers n_k, sum |n_k| <= 64 (every stencil of the paper):
  *     exact digit evaluation -- each value cut into three 18-bit digits on a grid set by the
  *     largest value of its tile (tile = 64 x TY outputs plus halo), digit sums exact in FP32,
- *     one FP64 rounding at the end; error below 2^-52 of c * sum|n_k| * (largest |value| in
- *     the tile and its halo);
+ *     their combination rounded to 2^-46 of the tile's largest value and scaled with one FP64
+ *     FMA; error at most 2^-45 / sum|n_k| of sum|w| * (largest |value| in the tile and its
+ *     halo);
  *   - other weights: double-float arithmetic (values as unevaluated float pairs, error-free
  *     products and sums on the FP32 pipes); error below ~2^-46 of sum|w| * max|in|;
  *   tiles holding inf / nan or values outside the methods' exponent ranges, and weights
