@@ -435,11 +435,14 @@ def test_unaligned_buffers_match_oracle(env, dtype, offsets, bc):
         assert spare.item() == sentinel, name  # nothing written outside the view
 
 
-@pytest.mark.parametrize("wscale,uscale", [(1e200, 1e100), (1e-200, 1e-100), (1e150, 1e-150)])
+@pytest.mark.parametrize("wscale,uscale", [(2.0 ** -55, 2.0 ** -895), (2.0 ** 45, 2.0 ** 885),
+                                           (2.0 ** -50, 2.0 ** 800), (1e200, 1e100)])
 def test_exact_digit_path_extreme_scales(env, wscale, uscale):
-    """Integer-ratio weights with a very large or very small common factor: tiles whose scale
-    c * 2^(G - 54) leaves the range of the one-FMA conversion take native FP64, the others the
-    digit path; every output meets the FP64 tolerance against the oracle."""
+    """Integer-ratio weights near the ends of the fast-path weight range [2^-60, 2^50) on values
+    near the ends of the digit range [2^-900, 2^900]: tiles whose scale c * 2^(G - 54) leaves the
+    range of the one-FMA conversion take native FP64, the others the digit path (with constants
+    up to 2^60 scale); weights outside the range take native FP64 throughout.  Every output meets
+    the FP64 tolerance against the oracle."""
     cs, torch, orc = env
     ny, nx = 130, 200
     field = W.sines_field(nx, seed=41, ny=ny) * uscale
