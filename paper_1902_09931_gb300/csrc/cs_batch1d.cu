@@ -3,9 +3,9 @@
 //
 // out[k] = sum_p w[p] * in[line_start + wrap(k - line_start - left + p, line_len)]   (periodic)
 //
-// The packed buffer is cut into warp segments of 32 lanes x 16 bytes, independent of where
+// The packed buffer is cut into warp segments of 32 lanes x 32 bytes, independent of where
 // lines start, so every warp does the same amount of work whatever the length mix.  A
-// persistent grid-stride launch walks the segments.  Each lane loads its 16-byte vector, takes
+// persistent grid-stride launch walks the segments.  Each lane loads two 16-byte vectors, takes
 // its left / right neighbours from the adjacent lanes with warp shuffles (lanes 0 and 31 load
 // the few values beyond the segment), and forms its sums uniformly.  A table that maps every
 // 64th element to the line containing it (built once at create time) gives the line of the
@@ -83,7 +83,12 @@ __device__ __forceinline__ void elements_general(const T* __restrict__ in, T* __
   }
 }
 
-// One warp segment of 32 * V packed elements starting at s: own values v (already loaded),
+// Elements per lane: two 16-byte vectors, so the per-segment work (line boundaries, shuffles,
+// classification) is shared by 8 FP32 or 4 FP64 elements.
+constexpr int kLaneVecs = 2;
+template <typename T> constexpr int lane_elems() { return kLaneVecs * Vec1<T>::n; }
+
+// One warp segment of 32 * E packed elements starting at s: own values v (already loaded),
 // neighbours by shuffle (lanes 0 and 31 take the nearest L / R values of the adjacent segments
 // from hl / hr, loaded with the segment), the lane's line from the segment's boundaries, and the
 // weighted sum.  r holds, on lanes 0..3, the boundary off[m0 + lane] relative to s (clamped;
@@ -94,63 +99,66 @@ __device__ __forceinline__ void segment(const T* __restrict__ in, T* __restrict_
                                         const int64_t* __restrict__ off, int64_t total,
                                         int Lr, int Rr, bool vec_ok,
                                         const BTaps<T>& taps, int64_t s, int64_t m0, int r,
-                                        const T (&v)[Vec1<T>::n], const T (&hl)[LL > 0 ? LL : 1],
+                                        const T (&v)[lane_elems<T>()], const T (&hl)[LL > 0 ? LL : 1],
                                         const T (&hr)[RR > 0 ? RR : 1]) {
-  constexpr int V = Vec1<T>::n;
+  constexpr int V = Vec1<T>::n, E = lane_elems<T>();
   using VT = typename Vec1<T>::V;
   constexpr int L = LL, R = RR, W = LL + RR + 1;
-  static_assert(LL >= 0 && RR >= 0 && LL <= V && RR <= V, "compile-time extents within one vector");
+  static_assert(LL >= 0 && RR >= 0 && LL <= E && RR <= E, "compile-time extents within a lane's elements");
   (void)Lr;
   (void)Rr;
   const int lane = threadIdx.x & 31;
-  const int64_t k0 = s + lane * V;
-  // win[j]: value at k0 - L + j, j < V + L + R (valid where inside the element's line)
-  T win[V + L + R];
+  const int64_t k0 = s + lane * E;
+  // win[j]: value at k0 - L + j, j < E + L + R (valid where inside the element's line)
+  T win[E + L + R];
 #pragma unroll
-  for (int e = 0; e < V; ++e) win[L + e] = v[e];
+  for (int e = 0; e < E; ++e) win[L + e] = v[e];
 #pragma unroll
   for (int e = 0; e < L; ++e) {
-    const T u = __shfl_up_sync(0xffffffffu, v[V - L + e], 1);
+    const T u = __shfl_up_sync(0xffffffffu, v[E - L + e], 1);
     win[e] = lane == 0 ? hl[e] : u;
   }
 #pragma unroll
   for (int e = 0; e < R; ++e) {
     const T d = __shfl_down_sync(0xffffffffu, v[e], 1);
-    win[L + V + e] = lane == 31 ? hr[e] : d;
+    win[L + E + e] = lane == 31 ? hr[e] : d;
   }
   const int r0 = __shfl_sync(0xffffffffu, r, 0), r1 = __shfl_sync(0xffffffffu, r, 1);
   const int r2 = __shfl_sync(0xffffffffu, r, 2), r3 = __shfl_sync(0xffffffffu, r, 3);
   if (k0 >= total) return;
-  // every lane forms its V sums from the window; an element is written here only when its
+  // every lane forms its E sums from the window; an element is written here only when its
   // stencil stays inside its line (the first L and last R elements of a periodic line are
   // written by the line-ends pass, those of a non-periodic line stay untouched)
-  T res[V];
+  T res[E];
 #pragma unroll
-  for (int e = 0; e < V; ++e) {
+  for (int e = 0; e < E; ++e) {
     T acc = T(0);
 #pragma unroll
     for (int p = 0; p < W; ++p) acc = fma(taps.w[p], win[e + p], acc);
     res[e] = acc;
   }
-  const int o = lane * V, oe = o + V - 1;
+  const int o = lane * E, oe = o + E - 1;
   const int c0 = (o >= r1) + (o >= r2), c1 = (oe >= r1) + (oe >= r2);
   const int ls = c0 == 0 ? r0 : (c0 == 1 ? r1 : r2);
   const int le = c0 == 0 ? r1 : (c0 == 1 ? r2 : r3);
-  if (c0 == c1 && oe < r3 && k0 + V <= total && o - L >= ls && oe + R < le) {  // the common case
+  if (c0 == c1 && oe < r3 && k0 + E <= total && o - L >= ls && oe + R < le) {  // the common case
     if (vec_ok) {
-      VT y;
-      if constexpr (V == 4) { y.x = res[0]; y.y = res[1]; y.z = res[2]; y.w = res[3]; }
-      else { y.x = res[0]; y.y = res[1]; }
-      *reinterpret_cast<VT*>(out + k0) = y;
+#pragma unroll
+      for (int q = 0; q < kLaneVecs; ++q) {
+        VT y;
+        if constexpr (V == 4) { y.x = res[4 * q]; y.y = res[4 * q + 1]; y.z = res[4 * q + 2]; y.w = res[4 * q + 3]; }
+        else { y.x = res[2 * q]; y.y = res[2 * q + 1]; }
+        *reinterpret_cast<VT*>(out + k0 + q * V) = y;
+      }
     } else {
 #pragma unroll
-      for (int e = 0; e < V; ++e) out[k0 + e] = res[e];
+      for (int e = 0; e < E; ++e) out[k0 + e] = res[e];
     }
     return;
   }
   if (oe < r3) {  // near a line end: each element's line is one of the segment's three
 #pragma unroll
-    for (int e = 0; e < V; ++e) {
+    for (int e = 0; e < E; ++e) {
       const int oo = o + e;
       const int ce = (oo >= r1) + (oo >= r2);
       const int ls_e = ce == 0 ? r0 : (ce == 1 ? r1 : r2);
@@ -162,7 +170,7 @@ __device__ __forceinline__ void segment(const T* __restrict__ in, T* __restrict_
   // more lines in this segment than its four boundaries describe (lines shorter than a
   // segment): walk the offsets from the lane's first line
   int64_t m = m0 + c0, lsa = s + ls, lea = s + le;
-  for (int e = 0; e < V; ++e) {
+  for (int e = 0; e < E; ++e) {
     const int64_t k = k0 + e;
     if (k >= total) break;
     while (k >= lea) {  // skips empty lines
@@ -212,40 +220,43 @@ __device__ __forceinline__ void line_ends(const T* __restrict__ in, T* __restric
 }
 
 // Each warp takes kG consecutive segments per iteration and issues all their loads first.
-constexpr int kG = 4;
+constexpr int kG = 2;
 
 template <typename T, int LL, int RR>
 __global__ void k_batch1d(const T* __restrict__ in, T* __restrict__ out,
                           const int64_t* __restrict__ off, const int32_t* __restrict__ seg,
                           int64_t total, int64_t num_lines, int periodic, int Lr, int Rr,
                           int vec_ok, BTaps<T> taps) {
-  constexpr int V = Vec1<T>::n;
+  constexpr int V = Vec1<T>::n, E = lane_elems<T>();
   using VT = typename Vec1<T>::V;
   const int lane = threadIdx.x & 31;
   const int64_t warp_id = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-  constexpr int64_t kSeg = 32 * V;
+  constexpr int64_t kSeg = 32 * E;
   static_assert(kSeg % (int64_t(1) << kSegShift) == 0, "segments start on line-table entries");
   const int64_t nseg = (total + kSeg - 1) / kSeg;
   constexpr int kClamp = 1 << 30;
   constexpr int HL = LL > 0 ? LL : 1, HR = RR > 0 ? RR : 1;
 
   for (int64_t s0 = warp_id * kG; s0 < nseg; s0 += nwarps * kG) {  // warp-uniform loop
-    T v[kG][V], hl[kG][HL], hr[kG][HR];
+    T v[kG][E], hl[kG][HL], hr[kG][HR];
     int64_t m0[kG];
     int r[kG];
 #pragma unroll
     for (int g = 0; g < kG; ++g) m0[g] = s0 + g < nseg ? __ldg(seg + (((s0 + g) * kSeg) >> kSegShift)) : 0;
 #pragma unroll
     for (int g = 0; g < kG; ++g) {
-      const int64_t k0 = (s0 + g) * kSeg + lane * V;
-      if (vec_ok && k0 + V <= total) {
-        const VT x = *reinterpret_cast<const VT*>(in + k0);
-        if constexpr (V == 4) { v[g][0] = x.x; v[g][1] = x.y; v[g][2] = x.z; v[g][3] = x.w; }
-        else { v[g][0] = x.x; v[g][1] = x.y; }
+      const int64_t k0 = (s0 + g) * kSeg + lane * E;
+      if (vec_ok && k0 + E <= total) {
+#pragma unroll
+        for (int q = 0; q < kLaneVecs; ++q) {
+          const VT x = *reinterpret_cast<const VT*>(in + k0 + q * V);
+          if constexpr (V == 4) { v[g][4 * q] = x.x; v[g][4 * q + 1] = x.y; v[g][4 * q + 2] = x.z; v[g][4 * q + 3] = x.w; }
+          else { v[g][2 * q] = x.x; v[g][2 * q + 1] = x.y; }
+        }
       } else {
 #pragma unroll
-        for (int e = 0; e < V; ++e) v[g][e] = (k0 + e < total) ? in[k0 + e] : T(0);
+        for (int e = 0; e < E; ++e) v[g][e] = (k0 + e < total) ? in[k0 + e] : T(0);
       }
       // lane 0: the L values before the segment; lane 31: the R values after it
 #pragma unroll
@@ -255,7 +266,7 @@ __global__ void k_batch1d(const T* __restrict__ in, T* __restrict__ out,
       }
 #pragma unroll
       for (int e = 0; e < HR; ++e) {
-        const int64_t k = k0 + V + e;
+        const int64_t k = k0 + E + e;
         hr[g][e] = (lane == 31 && e < RR && k < total) ? __ldg(in + k) : T(0);
       }
     }
@@ -325,7 +336,7 @@ int launch_t(const Batch1DConfig* c, const void* vin, void* vout, cudaStream_t s
   } else {
     const int vec_ok = (reinterpret_cast<uintptr_t>(in) % 16 == 0) &&
                        (reinterpret_cast<uintptr_t>(out) % 16 == 0);
-    const int64_t seg_elems = 32 * Vec1<T>::n;
+    const int64_t seg_elems = 32 * lane_elems<T>();
     const int64_t nseg = (c->total_len + seg_elems - 1) / seg_elems;
     const int64_t warps_per_cta = sh.threads / 32;
     int64_t grid = std::min<int64_t>((nseg + warps_per_cta * kG - 1) / (warps_per_cta * kG),
