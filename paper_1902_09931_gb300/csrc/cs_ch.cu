@@ -294,7 +294,8 @@ __global__ void __launch_bounds__(kSolveThreads)
 
 // Phase 2: end values of the neighbouring chunks from the block-circulant inverse (staged in
 // shared memory), then the spike correction.  MODE 0 writes w (FP64); MODE 1 writes
-// C^{n+1} = 2 C^n - C^{n-1} + x.
+// C^{n+1} = 2 C^n - C^{n-1} + x (for FP32 storage 2 C^n - C^{n-1} is formed in FP32, as in the
+// right-hand side).
 template <int MODE, typename T, bool CONTIG>
 __global__ void __launch_bounds__(kSolveThreads)
     k_solve_correct(const double* __restrict__ G, const double* __restrict__ bnd,
@@ -338,14 +339,25 @@ __global__ void __launch_bounds__(kSolveThreads)
     if constexpr (MODE == 0) {
       store_batch<CONTIG>(w_out, base + k0 * es, es, x);
     } else {
-      double c[kU], pv[kU];
+      if constexpr (sizeof(T) == 4) {
+        // FP32 storage: Cbar = 2 C^n - C^{n-1} in FP32 arithmetic (as the right-hand side forms
+        // it), widened exactly; the FP64 add of x and the round-to-nearest narrowing (F2F, the
+        // same rounding as an integer-pipe narrowing) keep this kernel's integer work small
+        float cb[kU];
 #pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        c[u] = widen(cur[base + (k0 + u) * es]);
-        pv[u] = widen(prev[base + (k0 + u) * es]);
+        for (int u = 0; u < kU; ++u) cb[u] = fmaf(2.0f, cur[base + (k0 + u) * es], -prev[base + (k0 + u) * es]);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) next[base + (k0 + u) * es] = __double2float_rn(widen(cb[u]) + x[u]);
+      } else {
+        double c[kU], pv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          c[u] = cur[base + (k0 + u) * es];
+          pv[u] = prev[base + (k0 + u) * es];
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) store_as<T>(next + base + (k0 + u) * es, fma(2.0, c[u], -pv[u]) + x[u]);
       }
-#pragma unroll
-      for (int u = 0; u < kU; ++u) store_as<T>(next + base + (k0 + u) * es, fma(2.0, c[u], -pv[u]) + x[u]);
     }
   }
 }
