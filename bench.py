@@ -459,13 +459,14 @@ def bench_serve(cs, torch, factors=(0.5, 0.9, 1.5), count=120, seed=2026):
 
 
 def ch_fp64_ops_per_point(rhs_in_fp64: bool, chunks: int, m: int) -> float:
-    """FP64 operations per grid point of one ADI step as the kernels perform them: RHS 16.5
-    (Cbar on the halo-2 tile, Z on the halo-1 tile, the outer Laplacian and combination; done in
+    """FP64 operations per grid point of one ADI step as the kernels perform them: RHS 9.7
+    (Cbar on the halo-2 tile: 1.2; on the halo-1 tile the digit Laplacian's scaling, N and Z:
+    5 x 1.1; the outer digit Laplacian's scaling, C^n - C^{n-1} and the combination: 3; done in
     FP32 for FP32 storage), two sweeps of local LU (5) + spike correction (4) + chunk-end system
     (16 chunks / m), and the update (2: Cbar and the add; for FP32 storage Cbar is formed in FP32
     and the add is the one FP64 operation)."""
     per_sweep = 5 + 4 + 16.0 * chunks / m
-    return (16.5 if rhs_in_fp64 else 0.0) + 2 * per_sweep + (2 if rhs_in_fp64 else 1)
+    return (9.7 if rhs_in_fp64 else 0.0) + 2 * per_sweep + (2 if rhs_in_fp64 else 1)
 
 
 def bench_batch1d(cs, torch, stream, hbm_peak):

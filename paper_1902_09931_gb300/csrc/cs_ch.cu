@@ -9,7 +9,9 @@
 // evaluated in the factored form
 //   Z   = (2/3) D dt / h^2 * N - a * (sum of 4 neighbours of Cbar - 4 Cbar)
 //   RHS = -(2/3)(C^n - C^{n-1}) + (sum of 4 neighbours of Z - 4 Z)
-// which needs 16 instead of 24 FP64 operations per point (FP64 is the bound on GB300).
+// which needs 16 instead of 24 FP64 operations per point (FP64 is the bound on GB300); with FP64
+// storage the two Laplacians are exact digit sums on the FP32 / integer pipes, each scaled by one
+// FP64 FMA, which leaves about 10.
 //
 // Line solves (the paper uses cuPentBatch with the periodic corners treated as in Navon's
 // PENT).  Here each periodic line of length n is cut into P chunks of m = n / P points; since
@@ -28,6 +30,7 @@
 #include <new>
 #include <vector>
 
+#include "cs_digits.cuh"
 #include "cs_internal.h"
 
 namespace cs {
@@ -140,7 +143,92 @@ __global__ void __launch_bounds__(kThreads)
     sb[idx] = T(2) * cv - prev[off];
   }
   __syncthreads();
-  if (rhs) {
+  if constexpr (sizeof(T) == 8) {
+    if (rhs) {
+      // FP64 storage: both 5-point Laplacians as exact digit sums (integer weights 1, 1, 1, 1, -4)
+      // scaled with one FP64 FMA each, so the FP64 pipe keeps only Cbar, N, Z, the two scalings and
+      // the final combination (10 instead of 16.5 FP64 operations per point).  A tile whose values
+      // leave the digit range takes the FP64 formula for that Laplacian.
+      float* s2 = reinterpret_cast<float*>(sz + ZR * ZC);  // third digits (Cbar, then Z)
+      __shared__ unsigned s_red[kThreads / 32];
+      auto lap5 = [&](const double* t, int i, int pitch) {
+        return (t[i - pitch] + t[i + pitch]) + (t[i - 1] + t[i + 1]) - 4.0 * t[i];
+      };
+      // digit sums of the 5-point Laplacian at i of a split tile (d0, d1 pairs over t, d2 in s2)
+      auto lap5_digits = [&](const double* t, int i, int pitch, float& q0, float& q1, float& q2) {
+        const float2* d = reinterpret_cast<const float2*>(t);
+        const float2 qa = __fadd2_rn(__fadd2_rn(d[i - pitch], d[i + pitch]), __fadd2_rn(d[i - 1], d[i + 1]));
+        const float2 qb = __ffma2_rn(make_float2(-4.0f, -4.0f), d[i], qa);
+        q0 = qb.x;
+        q1 = qb.y;
+        q2 = __fmaf_rn(-4.0f, s2[i], (s2[i - pitch] + s2[i + pitch]) + (s2[i - 1] + s2[i + 1]));
+      };
+      auto tile_scale = [](int tile_e) { return tile_e == 0 ? 0.0 : ldexp(1.0, tile_e - 1022 - 3 * ixd::kDigitBits); };
+      auto words = [](double v, uint32_t& hi, uint32_t& lo) {
+        hi = static_cast<uint32_t>(__double2hiint(v));
+        lo = static_cast<uint32_t>(__double2loint(v));
+      };
+      double* cb = reinterpret_cast<double*>(sb);
+      double* zt = reinterpret_cast<double*>(sz);
+      const double* cn = reinterpret_cast<const double*>(sc);
+      {
+        const int te = static_cast<int>(ixd::ix_tile_max_hi<kThreads>(cb, HR * HC, s_red) >> 20);
+        const double scale = tile_scale(te);
+        const bool dig = ixd::ix_tile_ok(te, scale);  // uniform over the block
+        if (dig) {
+          ixd::ix_split_tile<kThreads>(cb, s2, HR * HC, te);
+          __syncthreads();
+        }
+        uint32_t sh, sl, ch, cl;
+        words(scale * 0x1p8, sh, sl);
+        words(-scale * 0x1p60, ch, cl);
+        for (int idx = threadIdx.x; idx < ZR * ZC; idx += kThreads) {
+          const int r = idx / ZC, c = idx - r * ZC;
+          const int hidx = (r + 1) * HC + (c + 1);
+          double lap_cb;
+          if (dig) {
+            float q0, q1, q2;
+            lap5_digits(cb, hidx, HC, q0, q1, q2);
+            lap_cb = ixd::ix_combine(q0, q1, q2, sh, sl, ch, cl);
+          } else {
+            lap_cb = lap5(cb, hidx, HC);
+          }
+          const double u = cn[hidx];
+          const double nl = u * u * u - u;
+          zt[idx] = static_cast<double>(alpha) * nl - static_cast<double>(a) * lap_cb;
+        }
+        __syncthreads();
+      }
+      {
+        const int te = static_cast<int>(ixd::ix_tile_max_hi<kThreads>(zt, ZR * ZC, s_red) >> 20);
+        const double scale = tile_scale(te);
+        const bool dig = ixd::ix_tile_ok(te, scale);
+        if (dig) {
+          ixd::ix_split_tile<kThreads>(zt, s2, ZR * ZC, te);
+          __syncthreads();
+        }
+        uint32_t sh, sl, ch, cl;
+        words(scale * 0x1p8, sh, sl);
+        words(-scale * 0x1p60, ch, cl);
+        for (int idx = threadIdx.x; idx < kTY * kTX; idx += kThreads) {
+          const int r = idx / kTX, c = idx - r * kTX;
+          const int zidx = (r + 1) * ZC + (c + 1);
+          const int hidx = (r + 2) * HC + (c + 2);
+          double lap_z;
+          if (dig) {
+            float q0, q1, q2;
+            lap5_digits(zt, zidx, ZC, q0, q1, q2);
+            lap_z = ixd::ix_combine(q0, q1, q2, sh, sl, ch, cl);
+          } else {
+            lap_z = lap5(zt, zidx, ZC);
+          }
+          const int64_t o = (y0 + r) * n + x0 + c;
+          const double diff = cn[hidx] - static_cast<double>(prev[o]);  // C^n - C^{n-1}
+          rhs[o] = static_cast<RT>(-2.0 / 3.0 * diff + lap_z);
+        }
+      }
+    }
+  } else if (rhs) {
     for (int idx = threadIdx.x; idx < ZR * ZC; idx += kThreads) {
       const int r = idx / ZC, c = idx - r * ZC;
       const int hidx = (r + 1) * HC + (c + 1);
@@ -486,7 +574,8 @@ int default_chunks(int64_t n) {
 
 size_t rhs_smem_bytes(int storage) {
   const size_t e = storage == CS_F32 ? 4 : 8;
-  return e * (2 * (kTY + 4) * (kTX + 4) + (kTY + 2) * (kTX + 2));
+  const size_t digits = storage == CS_F32 ? 0 : 4 * (kTY + 4) * (kTX + 4);  // FP64: third digits
+  return e * (2 * (kTY + 4) * (kTX + 4) + (kTY + 2) * (kTX + 2)) + digits;
 }
 
 template <typename T> int set_rhs_attr() {
