@@ -13,6 +13,8 @@ What each routine computes, with the passage it follows:
 * ``cyclic_penta_solve`` -- (I + a circ(1,-4,6,-4,1)) x = b by banded LU + Woodbury (Sec. 5.1)
 * ``ch_rhs``, ``ch_step``, ``ch_run`` -- the Cahn-Hilliard ADI scheme, Eq. (ch_adi) (Sec. 5.1)
 * ``ch_mass``, ``ch_energy`` -- the integral of C and the free energy F[C] of Eq. (1)
+* ``ch_coarsening_s``, ``ch_coarsening_k1`` -- the coarsening measures s(t) and k_1(t) of
+  Sec. 5.1 "Numerical Results" (numpy; the FFT is numpy's)
 
 Fields are 2D numpy arrays of shape (ny, nx), row-major, x fastest.  FP32 inputs are widened to
 FP64 before the oracle sees them, so the oracle works on exactly the values the GPU read.
@@ -178,3 +180,44 @@ def ch_mass(c) -> float:
 def ch_energy(c, gamma: float) -> float:
     c = _f64(c)
     return _load().orc_ch_energy(c.shape[0], gamma, _ptr(c))
+
+
+def simpson_weights(n: int) -> np.ndarray:
+    """Composite Simpson weights (without the h/3 factor) for the n grid points of one periodic
+    direction: Simpson's rule over [0, 2 pi] with n intervals (n even) on x_i = i h, where the
+    end point x_n = 2 pi carries the value at x_0, so x_0 takes the weights of both ends."""
+    if n % 2:
+        raise ValueError("Simpson's rule needs an even number of intervals")
+    w = np.where(np.arange(n) % 2 == 1, 4.0, 2.0)
+    w[0] = 2.0  # 1 (x_0) + 1 (x_n, the same periodic point)
+    return w
+
+
+def simpson_mean(f) -> float:
+    """Spatial average of f over the periodic domain [0, 2 pi)^2 by Simpson's rule in x and y:
+    (1 / (2 pi)^2) * (h / 3)^2 * sum_ij w_i w_j f_ij with h = 2 pi / n."""
+    f = _f64(f)
+    ny, nx = f.shape
+    wy, wx = simpson_weights(ny), simpson_weights(nx)
+    return float(wy @ f @ wx) / (9.0 * nx * ny)
+
+
+def ch_coarsening_s(c) -> float:
+    """s(t) = 1 / (1 - <C^2>), <.> the spatial average by Simpson's rule (Sec. 5.1)."""
+    return 1.0 / (1.0 - simpson_mean(_f64(c) ** 2))
+
+
+def ch_coarsening_k1(c) -> float:
+    """k_1(t) = sum |C^(k)|^2 / sum |k|^-1 |C^(k)|^2 over the discrete wavenumbers of the periodic
+    grid (the k-space integrals of Sec. 5.1 with their common measure cancelled; numpy's FFT).
+    The k = 0 mode, where |k|^-1 is undefined, is left out of both sums."""
+    c = _f64(c)
+    ny, nx = c.shape
+    p = np.abs(np.fft.fft2(c)) ** 2
+    ky = np.fft.fftfreq(ny, d=1.0 / ny)[:, None]
+    kx = np.fft.fftfreq(nx, d=1.0 / nx)[None, :]
+    k = np.sqrt(kx ** 2 + ky ** 2)
+    p[0, 0] = 0.0
+    k[0, 0] = 1.0
+    return float(p.sum() / (p / k).sum())
+
