@@ -10,7 +10,8 @@ all ranks).  The L2 (129 MB) is flushed before every sweep, outside the timed ke
 
 Other parts of the metric are measured after the timed steps and reported beside it:
 Cahn-Hilliard ADI steps/s (N = 1024, 4096; FP64 and FP32 storage) and the ragged batched-1D
-sweep (65536 lines, log-uniform 64..4096, FP32, persistent launch replayed from a CUDA graph).
+sweep (65536 lines, log-uniform 64..4096, FP32, persistent launch replayed from a CUDA graph),
+and the coarsening run of Sec. 5.1 (512^2 to t = 100, s(t) and k_1(t) on the device).
 
 --impl reference runs the CPU oracle (the reference arm of this build: a plain FP64 C program)
 on a bounded sample of the same workload.
@@ -338,6 +339,7 @@ def run_ours(args):
         parts["ch_adi"] = bench_ch(cs, torch, stream)
         parts["batch1d"] = bench_batch1d(cs, torch, stream, hbm_peak)
         parts["serve"] = bench_serve(cs, torch)
+        parts["coarsening"] = bench_coarsening(cs, torch, stream)
     for sw in sweeps:
         cs.cs_destroy(sw["plan"])
     line = {
@@ -431,6 +433,48 @@ def bench_ch(cs, torch, stream, cases=None):
                     "fp64_frac": round(fp64_ops / (ms * 1e-3) / 1e9 / FP64_PEAK_GOPS, 3),
                     "chunks_per_line": chunks}
     return out
+
+
+def bench_coarsening(cs, torch, stream, n=512, T=100.0, samples=25, window=(2.0, 30.0)):
+    """The long run of Sec. 5.1: deep quench (U[-0.1, 0.1]) on 512^2, dt = 0.1 dx, D = 1,
+    gamma = 0.01, to t = T, FP64 storage.  s(t) and k_1(t) are measured on the device at
+    log-spaced times; the exponents of s and 1 / k_1 are least-squares slopes in log-log over
+    the window (t^(1/3) is the expected law; finite-size effects bend it late in the run)."""
+    h = 2 * np.pi / n
+    dt = 0.1 * h
+    total = int(round(T / dt))
+    c0 = torch.from_numpy(W.ch_initial(n, seed=2019)).to("cuda", torch.float64)
+    f = [c0.clone(), c0.clone(), torch.zeros_like(c0)]
+    plan = cs.cs_ch_create(cs.CHDesc(n=n, storage=cs.CS_F64, D=1.0, gamma=0.01, dt=dt), *f)
+    cs.cs_autotune(plan, stream)
+    torch.cuda.synchronize()
+    marks = sorted(set(int(round(v)) for v in np.geomspace(0.25 / dt, total, samples)))
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    step_ms = diag_ms = 0.0
+    series, done = [], 0
+    for m in marks:
+        e0, e1, e2 = ev(), ev(), ev()
+        e0.record(stream)
+        cs.cs_ch_step(plan, m - done, stream=stream)
+        e1.record(stream)
+        s, k1 = cs.cs_ch_coarsening(plan, stream)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        step_ms += e0.elapsed_time(e1)
+        diag_ms += e1.elapsed_time(e2)
+        done = m
+        series.append((m * dt, s, k1))
+    cs.cs_destroy(plan)
+    t = np.array([v[0] for v in series])
+    sel = (t >= window[0]) & (t <= window[1])
+    slope = lambda y: float(np.polyfit(np.log(t[sel]), np.log(y[sel]), 1)[0])
+    s_arr = np.array([v[1] for v in series])
+    inv_k1 = 1.0 / np.array([v[2] for v in series])
+    return {"n": n, "T": T, "dt": dt, "steps": total, "steps_per_s": round(total / (step_ms * 1e-3), 1),
+            "run_s": round(step_ms * 1e-3, 3), "diag_ms": round(diag_ms / len(series), 3),
+            "fit_window": list(window), "s_exponent": round(slope(s_arr), 3),
+            "inv_k1_exponent": round(slope(inv_k1), 3),
+            "series": [[round(a, 4), round(b, 6), round(c, 5)] for a, b, c in series]}
 
 
 def bench_serve(cs, torch, factors=(0.5, 0.9, 1.5), count=120, seed=2026):
@@ -560,8 +604,8 @@ def run_reference(args):
 
 
 def run_part(args):
-    """One part of the metric on its own (used to profile it): --part ch:<n>:<f64|f32>:<steps>
-    or --part batch1d."""
+    """One part of the metric on its own (used to profile it): --part ch:<n>:<f64|f32>:<steps>,
+    batch1d, serve or coarsening."""
     import torch
     import paper_1902_09931_gb300 as cs
     torch.cuda.set_device(0)
@@ -574,6 +618,8 @@ def run_part(args):
         res = bench_ch(cs, torch, stream, [(n, cs.CS_F64 if dt == "f64" else cs.CS_F32, steps)])
     elif kind[0] == "serve":
         res = bench_serve(cs, torch)
+    elif kind[0] == "coarsening":
+        res = bench_coarsening(cs, torch, stream)
     else:
         res = bench_batch1d(cs, torch, stream, hbm_peak)
     print(json.dumps({"part": args.part, "result": res}), flush=True)
@@ -591,7 +637,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile-choice", type=int, default=-1, help="force a tile choice (0, 1, 2) instead of autotuning")
     ap.add_argument("--only", default="", help="profile one sweep: name,n,f64|f32,p|np")
-    ap.add_argument("--part", default="", help="run one part alone: ch:<n>:<f64|f32>:<steps> or batch1d")
+    ap.add_argument("--part", default="", help="run one part alone: ch:<n>:<f64|f32>:<steps>, batch1d, serve or coarsening")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -227,6 +227,18 @@ int cs_ch_step(cs_plan_t plan, int64_t nsteps, double* h_mass, double* h_energy,
 /* Mass and free energy of the current field C^n (synchronises the stream). */
 int cs_ch_invariants(cs_plan_t plan, double* mass, double* energy, void* cuda_stream);
 
+/* Coarsening measures of the current field C^n (Sec. 5.1, "Numerical Results"), both in FP64:
+ *   *s  = 1 / (1 - <C^2>), <.> the domain average by Simpson's rule applied per direction on the
+ *         periodic grid (the point 2 pi coincides with the point 0, so every even-index point has
+ *         weight 2 and every odd-index point weight 4, total 3 n per direction);
+ *   *k1 = sum |C^(k)|^2 / sum |k|^-1 |C^(k)|^2 over the n x n discrete wavenumbers of the 2D DFT
+ *         (signed, |k| <= n / 2), with k = (0, 0) left out of both sums.
+ * Either output may be NULL.  Requires n a power of two and n <= 8192 (CS_EUNSUPPORTED
+ * otherwise); uses the plan's n x n scratch, so it may be called only between steps on the
+ * plan's stream.  The first call allocates 4 n + 4 doubles of device memory (CS_ENOMEM on
+ * failure), held until cs_destroy.  Synchronises the stream. */
+int cs_ch_coarsening(cs_plan_t plan, double* s, double* k1, void* cuda_stream);
+
 /* Current device pointers of C^{n-1} and C^n (either output may be NULL), and the number of
  * steps taken since create. */
 int cs_ch_fields(cs_plan_t plan, void** d_c_prev, void** d_c_cur, int64_t* steps_taken);

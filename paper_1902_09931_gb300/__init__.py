@@ -104,6 +104,7 @@ _SYMBOLS = {
     "cs_ch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_CCHDesc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_ch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_ch_invariants": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "cs_ch_coarsening": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "cs_ch_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)]),
     "cs_ch_set_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_ch_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
@@ -277,6 +278,13 @@ def cs_ch_invariants(plan, stream=None):
     m, e = ctypes.c_double(), ctypes.c_double()
     _check(load().cs_ch_invariants(plan, ctypes.byref(m), ctypes.byref(e), _stream(stream)))
     return m.value, e.value
+
+
+def cs_ch_coarsening(plan, stream=None):
+    """(s, k_1) of the current field: the coarsening measures of Sec. 5.1, in FP64."""
+    s, k1 = ctypes.c_double(), ctypes.c_double()
+    _check(load().cs_ch_coarsening(plan, ctypes.byref(s), ctypes.byref(k1), _stream(stream)))
+    return s.value, k1.value
 
 
 def cs_ch_fields(plan):

@@ -549,6 +549,11 @@ int cs_ch_invariants(cs_plan_t p, double* mass, double* energy, void* stream) {
   return ch_invariants(p->ch, mass, energy, static_cast<cudaStream_t>(stream));
 }
 
+int cs_ch_coarsening(cs_plan_t p, double* s, double* k1, void* stream) {
+  if (!p || p->kind != kCahnHilliard) return set_error(CS_EINVAL, "not a Cahn-Hilliard plan");
+  return ch_coarsening(p->ch, s, k1, static_cast<cudaStream_t>(stream));
+}
+
 int cs_ch_fields(cs_plan_t p, void** prev, void** cur, int64_t* steps) {
   if (!p || p->kind != kCahnHilliard) return set_error(CS_EINVAL, "not a Cahn-Hilliard plan");
   return ch_fields(p->ch, prev, cur, steps);

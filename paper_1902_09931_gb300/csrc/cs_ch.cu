@@ -54,6 +54,7 @@ struct CHPlan {
   int rhs_blocks;
   cudaGraphExec_t graph3[3];  // three steps (one buffer rotation) per starting rotation phase
   int graph_kernels;
+  double* diag;  // coarsening measures: n/2 twiddles (re, im), 2 n partial sums, 4 results
 };
 
 void drop_graphs(CHPlan* p);
@@ -650,7 +651,7 @@ void free_plan(CHPlan* p) {
   if (!p) return;
   drop_graphs(p);
   cudaFree(p->A); cudaFree(p->B); cudaFree(p->bnd); cudaFree(p->coef); cudaFree(p->K);
-  cudaFree(p->partials); cudaFree(p->inv);
+  cudaFree(p->partials); cudaFree(p->inv); cudaFree(p->diag);
   delete p;
 }
 
@@ -820,6 +821,216 @@ int ch_invariants(CHPlan* p, double* mass, double* energy, cudaStream_t s) {
   CS_CUDA_TRY(cudaStreamSynchronize(s));
   if (mass) *mass = h[0];
   if (energy) *energy = h[1];
+  return CS_OK;
+}
+
+namespace {
+
+// ---- coarsening measures (Sec. 5.1, "Numerical Results") ---------------------------------------
+//   s(t)   = 1 / (1 - <C^2>), <.> the spatial average by Simpson's rule on the periodic grid
+//            (weights 2, 4, 2, 4, ... per direction: the end point 2 pi is the start point);
+//   k_1(t) = sum_k |C^(k)|^2 / sum_k |k|^-1 |C^(k)|^2 over the discrete wavenumbers, k = 0 left out
+//            (the k-space integrals with their common measure cancelled).
+// The 2D DFT is two passes of a radix-2 FFT (one CTA per row, the row in shared memory): the
+// first transforms the rows of C and writes them transposed into the (A, B) = (re, im) scratch,
+// the second transforms those rows (the columns of C) and sums the spectrum.  All FP64.
+
+constexpr int kDiagThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kDiagThreads)
+    k_simpson_rows(const T* __restrict__ c, int64_t n, double* __restrict__ partials) {
+  const int64_t j = blockIdx.x;  // one row per block
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += kDiagThreads) {
+    const double v = widen(c[j * n + i]);
+    acc += ((i & 1) ? 4.0 : 2.0) * v * v;
+  }
+  __shared__ double red[kDiagThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < kDiagThreads / 32; ++w) r += red[w];
+    partials[j] = ((j & 1) ? 4.0 : 2.0) * r;
+  }
+}
+
+// In-place radix-2 decimation-in-time FFT of the n = 2^logn points in (xr, xi) (shared memory,
+// loaded in bit-reversed order); tw holds exp(-2 pi i t / n) for t < n / 2.
+__device__ __forceinline__ void fft_smem(double* xr, double* xi, int n, int logn, const double2* __restrict__ tw) {
+  for (int len = 2, stride = n >> 1; len <= n; len <<= 1, stride >>= 1) {
+    const int half = len >> 1;
+    for (int b = threadIdx.x; b < (n >> 1); b += kDiagThreads) {
+      const int pos = b & (half - 1);
+      const int i = (b - pos) * 2 + pos, k = i + half;
+      const double2 w = tw[pos * stride];
+      const double vr = w.x * xr[k] - w.y * xi[k];
+      const double vi = w.x * xi[k] + w.y * xr[k];
+      const double ur = xr[i], ui = xi[i];
+      xr[i] = ur + vr;
+      xi[i] = ui + vi;
+      xr[k] = ur - vr;
+      xi[k] = ui - vi;
+    }
+    __syncthreads();
+  }
+  (void)logn;
+}
+
+__device__ __forceinline__ int bit_reverse(int t, int logn) { return static_cast<int>(__brev(static_cast<unsigned>(t)) >> (32 - logn)); }
+
+// Pass 1: the FFT of row j of C, written as column j of (re, im).
+template <typename T>
+__global__ void __launch_bounds__(kDiagThreads)
+    k_fft_rows(const T* __restrict__ c, int n, int logn, const double2* __restrict__ tw,
+               double* __restrict__ re, double* __restrict__ im) {
+  extern __shared__ double xs[];
+  double* xr = xs;
+  double* xi = xs + n;
+  const int64_t j = blockIdx.x;
+  for (int t = threadIdx.x; t < n; t += kDiagThreads) {
+    const int r = bit_reverse(t, logn);
+    xr[r] = widen(c[j * n + t]);
+    xi[r] = 0.0;
+  }
+  __syncthreads();
+  fft_smem(xr, xi, n, logn, tw);
+  for (int k = threadIdx.x; k < n; k += kDiagThreads) {
+    re[static_cast<int64_t>(k) * n + j] = xr[k];
+    im[static_cast<int64_t>(k) * n + j] = xi[k];
+  }
+}
+
+// Pass 2: the FFT of row kx of (re, im) (column kx of the row transforms) gives C^(kx, ky) for
+// every ky; the block sums |C^|^2 and |k|^-1 |C^|^2 (k = 0 left out) into partials[2 kx + 0/1].
+__global__ void __launch_bounds__(kDiagThreads)
+    k_fft_cols_spectrum(const double* __restrict__ re, const double* __restrict__ im, int n, int logn,
+                        const double2* __restrict__ tw, double* __restrict__ partials) {
+  extern __shared__ double xs[];
+  double* xr = xs;
+  double* xi = xs + n;
+  const int kx = blockIdx.x;
+  for (int t = threadIdx.x; t < n; t += kDiagThreads) {
+    const int r = bit_reverse(t, logn);
+    xr[r] = re[static_cast<int64_t>(kx) * n + t];
+    xi[r] = im[static_cast<int64_t>(kx) * n + t];
+  }
+  __syncthreads();
+  fft_smem(xr, xi, n, logn, tw);
+  const double fx = kx <= n / 2 ? kx : kx - n;
+  double num = 0.0, den = 0.0;
+  for (int ky = threadIdx.x; ky < n; ky += kDiagThreads) {
+    if (kx == 0 && ky == 0) continue;
+    const double fy = ky <= n / 2 ? ky : ky - n;
+    const double pw = xr[ky] * xr[ky] + xi[ky] * xi[ky];
+    num += pw;
+    den += pw / sqrt(fx * fx + fy * fy);
+  }
+  __shared__ double red[2][kDiagThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) {
+    num += __shfl_down_sync(0xffffffffu, num, off);
+    den += __shfl_down_sync(0xffffffffu, den, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = num;
+    red[1][threadIdx.x >> 5] = den;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < kDiagThreads / 32; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    partials[2 * kx] = a;
+    partials[2 * kx + 1] = b;
+  }
+}
+
+// Fixed-order sums of the partials: out[0] = sum of n Simpson row sums, out[1], out[2] = the two
+// spectral sums.
+__global__ void k_coarsening_final(const double* __restrict__ simpson, const double* __restrict__ spec,
+                                   int n, double* __restrict__ out) {
+  __shared__ double r[3][256];
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) {
+    a += simpson[i];
+    b += spec[2 * i];
+    c += spec[2 * i + 1];
+  }
+  r[0][threadIdx.x] = a;
+  r[1][threadIdx.x] = b;
+  r[2][threadIdx.x] = c;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int q = 0; q < 3; ++q) r[q][threadIdx.x] += r[q][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) out[q] = r[q][0];
+}
+
+}  // namespace
+
+int ch_coarsening(CHPlan* p, double* s_out, double* k1_out, cudaStream_t st) {
+  const int64_t n = p->n;
+  int logn = 0;
+  while ((int64_t(1) << logn) < n) ++logn;
+  if ((int64_t(1) << logn) != n) return set_error(CS_EUNSUPPORTED, "coarsening measures need n a power of two");
+  const size_t smem = 2 * static_cast<size_t>(n) * sizeof(double);
+  if (smem > 200 * 1024) return set_error(CS_EUNSUPPORTED, "n = %lld too large for the shared-memory FFT", (long long)n);
+  // diag: [0, n) twiddles as n/2 (re, im) pairs, [n, 2n) Simpson row sums, [2n, 4n) spectrum sums, 4 results
+  if (!p->diag) {
+    std::vector<double> tw(static_cast<size_t>(n));
+    for (int64_t t = 0; t < n / 2; ++t) {
+      const double ang = -2.0 * M_PI * static_cast<double>(t) / static_cast<double>(n);
+      tw[2 * t] = std::cos(ang);
+      tw[2 * t + 1] = std::sin(ang);
+    }
+    double* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, (4 * static_cast<size_t>(n) + 4) * sizeof(double));
+    if (e != cudaSuccess)
+      return e == cudaErrorMemoryAllocation ? set_error(CS_ENOMEM, "coarsening buffers: %s", cudaGetErrorString(e))
+                                            : cuda_error(e, "coarsening buffers");
+    e = cudaMemcpyAsync(d, tw.data(), n * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      cudaFree(d);
+      return cuda_error(e, "coarsening twiddles");
+    }
+    p->diag = d;
+  }
+  // the attribute is per function and process-wide: set it for this plan's n on every call
+  CS_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  CS_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  CS_CUDA_TRY(cudaFuncSetAttribute(k_fft_cols_spectrum, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  const double2* tw = reinterpret_cast<const double2*>(p->diag);
+  double* simpson = p->diag + n;
+  double* spec = p->diag + 2 * n;
+  double* res = p->diag + 4 * n;
+  const unsigned grid = static_cast<unsigned>(n);
+  if (p->storage == CS_F32) {
+    const float* c = static_cast<const float*>(p->field[p->icur]);
+    k_simpson_rows<float><<<grid, kDiagThreads, 0, st>>>(c, n, simpson);
+    k_fft_rows<float><<<grid, kDiagThreads, smem, st>>>(c, static_cast<int>(n), logn, tw, p->A, p->B);
+  } else {
+    const double* c = static_cast<const double*>(p->field[p->icur]);
+    k_simpson_rows<double><<<grid, kDiagThreads, 0, st>>>(c, n, simpson);
+    k_fft_rows<double><<<grid, kDiagThreads, smem, st>>>(c, static_cast<int>(n), logn, tw, p->A, p->B);
+  }
+  k_fft_cols_spectrum<<<grid, kDiagThreads, smem, st>>>(p->A, p->B, static_cast<int>(n), logn, tw, spec);
+  k_coarsening_final<<<1, 256, 0, st>>>(simpson, spec, static_cast<int>(n), res);
+  CS_CUDA_TRY(cudaGetLastError());
+  count_launches(4);
+  double h[3];
+  CS_CUDA_TRY(cudaMemcpyAsync(h, res, sizeof h, cudaMemcpyDeviceToHost, st));
+  CS_CUDA_TRY(cudaStreamSynchronize(st));
+  const double mean_c2 = h[0] / (9.0 * static_cast<double>(n) * static_cast<double>(n));
+  if (s_out) *s_out = 1.0 / (1.0 - mean_c2);
+  if (k1_out) *k1_out = h[1] / h[2];
   return CS_OK;
 }
 

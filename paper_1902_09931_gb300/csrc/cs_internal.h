@@ -88,6 +88,7 @@ struct CHPlan;
 int ch_create(CHPlan** out, const cs_ch_desc* d, void* prev, void* cur, void* next);
 int ch_step(CHPlan* p, int64_t nsteps, double* h_mass, double* h_energy, cudaStream_t s);
 int ch_invariants(CHPlan* p, double* mass, double* energy, cudaStream_t s);
+int ch_coarsening(CHPlan* p, double* s_out, double* k1_out, cudaStream_t s);
 int ch_fields(CHPlan* p, void** prev, void** cur, int64_t* steps);
 int ch_config(CHPlan* p, int32_t* chunks, int32_t* chunk_len);
 int ch_set_fields(CHPlan* p, void* prev, void* cur, void* next);

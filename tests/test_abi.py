@@ -26,7 +26,7 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ["cs_plan_create_2d", "cs_plan_create_1d_batch", "cs_compute", "cs_swap",
-                 "cs_destroy", "cs_ch_create", "cs_ch_step", "cs_last_error"]:
+                 "cs_destroy", "cs_ch_create", "cs_ch_step", "cs_ch_coarsening", "cs_last_error"]:
         assert must in names
 
 
@@ -105,3 +105,4 @@ def test_ch_fields_must_not_overlap(cs):
 
 def test_wrong_plan_kind_rejected(cs):
     assert rc_of(cs.cs_ch_step, None, 1, False, 0) == cs.CS_EINVAL
+    assert rc_of(cs.cs_ch_coarsening, None, 0) == cs.CS_EINVAL
