@@ -11,7 +11,8 @@ all ranks).  The L2 (129 MB) is flushed before every sweep, outside the timed ke
 Other parts of the metric are measured after the timed steps and reported beside it:
 Cahn-Hilliard ADI steps/s (N = 1024, 4096; FP64 and FP32 storage) and the ragged batched-1D
 sweep (65536 lines, log-uniform 64..4096, FP32, persistent launch replayed from a CUDA graph),
-and the coarsening run of Sec. 5.1 (512^2 to t = 100, s(t) and k_1(t) on the device).
+the coarsening run of Sec. 5.1 (512^2 to t = 100, s(t) and k_1(t) on the device), and
+host-resident grids streamed through 256 MiB of device band slots.
 
 --impl reference runs the CPU oracle (the reference arm of this build: a plain FP64 C program)
 on a bounded sample of the same workload.
@@ -340,6 +341,7 @@ def run_ours(args):
         parts["batch1d"] = bench_batch1d(cs, torch, stream, hbm_peak)
         parts["serve"] = bench_serve(cs, torch)
         parts["coarsening"] = bench_coarsening(cs, torch, stream)
+        parts["streamed"] = bench_streamed(cs, torch, stream)
     for sw in sweeps:
         cs.cs_destroy(sw["plan"])
     line = {
@@ -432,6 +434,39 @@ def bench_ch(cs, torch, stream, cases=None):
                     "fp64_gops": round(fp64_ops / (ms * 1e-3) / 1e9, 1),
                     "fp64_frac": round(fp64_ops / (ms * 1e-3) / 1e9 / FP64_PEAK_GOPS, 3),
                     "chunks_per_line": chunks}
+    return out
+
+
+def bench_streamed(cs, torch, stream, budget_mib=256, reps=5):
+    """Host-resident (out-of-core) plans: the grid in pinned host memory streams through a
+    256 MiB ring of device band slots.  Time per sweep (wall clock around cs_compute_host,
+    which synchronises), grid points per second and host-link bytes per second (copy in plus
+    copy out) for a periodic 9-point Laplacian; 8192^2 FP64 and 16384^2 FP32 (1 GiB grids)."""
+    out = {}
+    for n, dtype in ((8192, cs.CS_F64), (16384, cs.CS_F32)):
+        h = 2 * np.pi / n
+        tdt = torch.float64 if dtype == cs.CS_F64 else torch.float32
+        eb = 8 if dtype == cs.CS_F64 else 4
+        w = np.array([1, 4, 1, 4, -20, 4, 1, 4, 1.0]) / (6 * h * h)
+        desc = cs.StencilDesc(nx=n, ny=n, dir=cs.CS_DIR_XY, bc=cs.CS_BC_PERIODIC, dtype=dtype,
+                              left=1, right=1, top=1, bottom=1, weights=w)
+        plan = cs.cs_plan_create_2d_host(desc, budget_mib << 20)
+        rows, held = cs.cs_plan_host_info(plan)
+        h_in = torch.from_numpy(W.sines_field(n, seed=61)).to(tdt).pin_memory()
+        h_out = torch.empty(n, n, dtype=tdt).pin_memory()
+        cs.cs_compute_host(plan, h_in, h_out, stream)  # warm-up: streams and events
+        times = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            cs.cs_compute_host(plan, h_in, h_out, stream)
+            times.append(time.perf_counter() - t0)
+        cs.cs_destroy(plan)
+        t = statistics.median(times)
+        key = f"n{n}_{'f64' if dtype == cs.CS_F64 else 'f32'}"
+        out[key] = {"ms": round(t * 1e3, 3), "gpts_per_s": round(n * n / t / 1e9, 2),
+                    "link_gbs": round(2 * n * n * eb / t / 1e9, 1), "band_rows": rows,
+                    "bands": -(-n // rows), "device_mib": round(held / 2 ** 20, 1)}
+        del h_in, h_out
     return out
 
 
@@ -605,7 +640,7 @@ def run_reference(args):
 
 def run_part(args):
     """One part of the metric on its own (used to profile it): --part ch:<n>:<f64|f32>:<steps>,
-    batch1d, serve or coarsening."""
+    batch1d, serve, coarsening or streamed."""
     import torch
     import paper_1902_09931_gb300 as cs
     torch.cuda.set_device(0)
@@ -620,6 +655,8 @@ def run_part(args):
         res = bench_serve(cs, torch)
     elif kind[0] == "coarsening":
         res = bench_coarsening(cs, torch, stream)
+    elif kind[0] == "streamed":
+        res = bench_streamed(cs, torch, stream)
     else:
         res = bench_batch1d(cs, torch, stream, hbm_peak)
     print(json.dumps({"part": args.part, "result": res}), flush=True)
@@ -637,7 +674,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile-choice", type=int, default=-1, help="force a tile choice (0, 1, 2) instead of autotuning")
     ap.add_argument("--only", default="", help="profile one sweep: name,n,f64|f32,p|np")
-    ap.add_argument("--part", default="", help="run one part alone: ch:<n>:<f64|f32>:<steps>, batch1d, serve or coarsening")
+    ap.add_argument("--part", default="", help="run one part alone: ch:<n>:<f64|f32>:<steps>, batch1d, serve, coarsening or streamed")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

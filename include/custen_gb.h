@@ -17,7 +17,8 @@
  * at a time; different plans are independent.  Unlike the paper there is no HOST/DEVICE flag
  * and no y-tile count: fields stay resident in device memory (Sec. 2's Unified-Memory
  * streaming is not needed when the whole grid fits in HBM).  cs_compute_host() is the
- * host-buffer form of Compute for callers whose data lives in host memory.
+ * host-buffer form of Compute for callers whose data lives in host memory, and
+ * cs_plan_create_2d_host() streams grids of any size through bounded device memory.
  *
  * Errors.  Every call returns CS_OK (0) or a negative cs_status.  Nothing aborts or exits.
  * cs_last_error() returns a description of the last failure on the calling host thread.
@@ -128,6 +129,25 @@ int cs_compute(cs_plan_t plan, void* cuda_stream);
  * loop to batch small sweeps.  Stream-ordered and asynchronous. */
 int cs_compute_group(const cs_plan_t* plans, int32_t count, void* cuda_stream);
 
+/* Create for a 2D grid that lives in host memory (Sec. 2's y-tile streaming of grids larger
+ * than device memory).  The plan owns a ring of 3 band slots in device memory, each holding
+ * input and output for a band of rows plus halo rows; cs_compute_host then streams the grid
+ * through them -- copy in, sweep, copy out on three streams, overlapped -- so device memory
+ * stays bounded by device_bytes whatever the grid's size.
+ *   desc          as for cs_plan_create_2d; ny >= 128 (CS_EINVAL otherwise).
+ *   device_bytes  device memory the slots may use (0 = 512 MiB).  Band height = the largest
+ *                 multiple of 64 rows that fits (at most the grid, rounded up to 64); CS_EINVAL
+ *                 when not even 64 rows fit, CS_ENOMEM when the allocation fails.
+ * Results equal a device-buffer plan's sweep (same description, tile choice and FP64 mode) bit
+ * for bit; for a non-periodic plan, host output cells of the boundary rows and columns are left
+ * untouched.  cs_compute, cs_swap, cs_set_buffers and graph replay do not apply (CS_EINVAL /
+ * CS_EUNSUPPORTED); cs_autotune leaves the plan unchanged; tile choice and FP64 mode may be set. */
+int cs_plan_create_2d_host(cs_plan_t* plan, const cs_stencil_desc* desc, int64_t device_bytes);
+
+/* Band height in rows and device bytes held by a host-resident plan (either output may be
+ * NULL); CS_EINVAL for any other plan. */
+int cs_plan_host_info(cs_plan_t plan, int64_t* band_rows, int64_t* device_bytes);
+
 /* Compute with host buffers (Sec. 3's HOST flag): copies h_in (host, the full input field)
  * into the plan's device input, computes, and copies the device output back into h_out.
  * Either pointer may be NULL to skip that copy.  A 2D plan of 16 MB or more with both pointers
@@ -135,7 +155,9 @@ int cs_compute_group(const cs_plan_t* plans, int32_t count, void* cuda_stream);
  * owns (the results equal a device sweep bit for bit); the device input then holds the copied
  * field and the device output the result, as with one copy.  Pinned host memory is needed for
  * the overlap; pageable memory works but is slower.  Synchronises the stream before returning
- * when h_out is non-NULL. */
+ * when h_out is non-NULL.  For a host-resident plan (cs_plan_create_2d_host) both pointers are
+ * required (full host fields, not overlapping, CS_EALIAS otherwise) and the grid streams through
+ * the plan's band slots; pinned host memory gives the overlap. */
 int cs_compute_host(cs_plan_t plan, const void* h_in, void* h_out, void* cuda_stream);
 
 /* Swap (Sec. 3): exchanges the bound input and output buffers so the next Compute reads what

@@ -87,6 +87,8 @@ _lib = None
 _SYMBOLS = {
     # name: (restype, argtypes)
     "cs_plan_create_2d": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_CStencilDesc), ctypes.c_void_p, ctypes.c_void_p]),
+    "cs_plan_create_2d_host": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_CStencilDesc), ctypes.c_int64]),
+    "cs_plan_host_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "cs_plan_create_1d_batch": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_CStencilDesc), ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_compute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "cs_compute_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -185,6 +187,22 @@ def cs_plan_create_2d(desc: StencilDesc, d_in, d_out) -> ctypes.c_void_p:
     plan = ctypes.c_void_p()
     _check(load().cs_plan_create_2d(ctypes.byref(plan), ctypes.byref(c), _ptr(d_in), _ptr(d_out)))
     return plan
+
+
+def cs_plan_create_2d_host(desc: StencilDesc, device_bytes: int = 0) -> ctypes.c_void_p:
+    """A 2D plan for a grid in host memory, streamed through device band slots of at most
+    ``device_bytes`` (0: the library default); compute with cs_compute_host."""
+    c, _keep = _desc(desc)
+    plan = ctypes.c_void_p()
+    _check(load().cs_plan_create_2d_host(ctypes.byref(plan), ctypes.byref(c), int(device_bytes)))
+    return plan
+
+
+def cs_plan_host_info(plan):
+    """(band rows, device bytes held) of a host-resident plan."""
+    r, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().cs_plan_host_info(plan, ctypes.byref(r), ctypes.byref(b)))
+    return r.value, b.value
 
 
 def cs_plan_create_1d_batch(desc: StencilDesc, num_lines: int, d_offsets, total_len: int, d_in,

@@ -90,7 +90,11 @@ int flush_l2(cudaStream_t s) {
 }  // namespace autotune_detail
 }  // namespace cs
 
-enum PlanKind { kStencil2D = 1, kBatch1D = 2, kCahnHilliard = 3 };
+enum PlanKind { kStencil2D = 1, kBatch1D = 2, kCahnHilliard = 3, kStencil2DHost = 4 };
+
+// Band slots of a host-resident (out-of-core) 2D plan: one being copied in, one swept, one
+// copied out.
+constexpr int kRingSlots = 3;
 
 struct cs_plan {
   int kind;
@@ -110,6 +114,13 @@ struct cs_plan {
   cudaStream_t band_stream[2];
   cudaEvent_t band_event[2 * 32 + 2];
   int band_ready;
+  // host-resident 2D plan: the grid lives in host memory and streams through kRingSlots device
+  // band slots of ring_ny rows each (kRingTop halo rows, ring_rows band rows, kRingBottom rows)
+  int64_t ring_rows, ring_ny;
+  void* ring_in[kRingSlots];
+  void* ring_out[kRingSlots];
+  cs::Stencil2DConfig* ring_cfg;  // kRingSlots copies of s2 with ny = ring_ny (own tensor maps)
+  int64_t ring_bytes;
 };
 
 namespace {
@@ -133,6 +144,7 @@ int launch_direct(cs_plan* p, cudaStream_t s) {
   switch (p->kind) {
     case kStencil2D: return stencil2d_launch(&p->s2, p->d_in, p->d_out, s);
     case kBatch1D: return batch1d_launch(&p->b1, p->d_in, p->d_out, s);
+    case kStencil2DHost: return set_error(CS_EINVAL, "a host-resident plan computes through cs_compute_host");
     default: return set_error(CS_EINVAL, "cs_compute: not a stencil plan");
   }
 }
@@ -236,6 +248,142 @@ int compute_host_banded(cs_plan* p, const void* h_in, void* h_out, cudaStream_t 
   return CS_OK;
 }
 
+// Fills a 2D plan's stencil configuration from a validated description and prepares it.
+int fill_2d_config(cs_plan* p, const cs_stencil_desc* d) {
+  Stencil2DConfig& c = p->s2;
+  c.nx = d->nx; c.ny = d->ny; c.dir = d->dir; c.bc = d->bc; c.dtype = d->dtype;
+  c.left = d->left; c.right = d->right; c.top = d->top; c.bottom = d->bottom;
+  c.fn = d->fn;
+  c.tile_rows = 64;
+  const int nw = (d->left + d->right + 1) * (d->top + d->bottom + 1);
+  if (d->fn == CS_FN_NONE) {
+    memcpy(c.weights, d->weights, sizeof(double) * nw);
+  } else {
+    c.num_coe = d->num_coe;
+    memcpy(c.coe, d->coe, sizeof(double) * d->num_coe);
+  }
+  return stencil2d_prepare(&c);
+}
+
+// ---- host-resident (out-of-core) 2D plans --------------------------------------------------------
+// The grid stays in host memory and passes through a ring of kRingSlots band slots in device
+// memory (Sec. 2's y-tiles, streamed: copy in, sweep, copy out on three streams).  Slot layout:
+// row kRingTop of a slot is the band's first row (a multiple of 64 in the grid, so the band's
+// tiles are the grid's tiles); the rows above and below hold the halo the band's tiles read --
+// the neighbouring grid rows, wrapped at the grid's ends for periodic plans and zero for
+// non-periodic ones, exactly what the device sweep's tile loader stages there.  Every tile of a
+// band therefore stages the same values as in a sweep of the whole grid, and the streamed result
+// equals the device sweep bit for bit.
+constexpr int64_t kRingTop = kStencilBandAlign;
+constexpr int64_t kRingBottom = kStencilBandAlign + CS_MAX_EXTENT;  // ragged last tile + halo
+constexpr int64_t kRingMinRows = 2 * kStencilBandAlign;
+
+void ring_free(cs_plan* p) {
+  for (int k = 0; k < kRingSlots; ++k) {
+    cudaFree(p->ring_in[k]);
+    cudaFree(p->ring_out[k]);
+    p->ring_in[k] = p->ring_out[k] = nullptr;
+  }
+  delete[] p->ring_cfg;
+  p->ring_cfg = nullptr;
+}
+
+int ring_streams(cs_plan* p) {
+  if (p->band_ready) return CS_OK;
+  for (int i = 0; i < 2; ++i) CS_CUDA_TRY(cudaStreamCreateWithFlags(&p->band_stream[i], cudaStreamNonBlocking));
+  for (auto& e : p->band_event) CS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  p->band_ready = 1;
+  return CS_OK;
+}
+
+// Copies grid rows [g_lo, g_hi) (any integers; ny >= kRingMinRows > the widest reach, so one wrap
+// at most) into slot rows starting at `slot_row`: rows inside the grid from h_in, rows outside
+// wrapped (periodic) or zeroed (non-periodic).
+int ring_fill(const cs_plan* p, const char* h_in, char* slot, int64_t g_lo, int64_t g_hi, int64_t slot_row,
+              cudaStream_t st) {
+  const int64_t ny = p->s2.ny, rb = p->s2.nx * static_cast<int64_t>(p->elem_bytes);
+  const bool periodic = p->s2.bc == CS_BC_PERIODIC;
+  const int64_t cuts[4] = {g_lo, std::max<int64_t>(g_lo, std::min<int64_t>(0, g_hi)),
+                           std::max<int64_t>(g_lo, std::min<int64_t>(ny, g_hi)), g_hi};
+  for (int part = 0; part < 3; ++part) {
+    const int64_t a = std::max(cuts[part], g_lo), b = cuts[part + 1];
+    if (b <= a) continue;
+    char* dst = slot + (slot_row + a - g_lo) * rb;
+    const size_t bytes = static_cast<size_t>((b - a) * rb);
+    if (part == 1) {
+      CS_CUDA_TRY(cudaMemcpyAsync(dst, h_in + a * rb, bytes, cudaMemcpyHostToDevice, st));
+    } else if (periodic) {
+      const int64_t src = part == 0 ? a + ny : a - ny;
+      CS_CUDA_TRY(cudaMemcpyAsync(dst, h_in + src * rb, bytes, cudaMemcpyHostToDevice, st));
+    } else {
+      CS_CUDA_TRY(cudaMemsetAsync(dst, 0, bytes, st));
+    }
+  }
+  return CS_OK;
+}
+
+int compute_host_streamed(cs_plan* p, const void* h_in, void* h_out, cudaStream_t s) {
+  const Stencil2DConfig& c = p->s2;
+  int rc = ring_streams(p);
+  if (rc != CS_OK) return rc;
+  for (int k = 0; k < kRingSlots; ++k) {  // fresh copies: tile choice or FP64 mode may have changed
+    p->ring_cfg[k] = c;
+    p->ring_cfg[k].ny = p->ring_ny;
+    p->ring_cfg[k].tmap_in = nullptr;
+  }
+  const int64_t ny = c.ny, nx = c.nx, eb = static_cast<int64_t>(p->elem_bytes), rb = nx * eb;
+  const int64_t rows = p->ring_rows, nb = (ny + rows - 1) / rows;
+  const bool periodic = c.bc == CS_BC_PERIODIC;
+  // the rows and columns a sweep writes: all for periodic plans, the interior for non-periodic
+  const int64_t w_lo = periodic ? 0 : c.top, w_hi = periodic ? ny : ny - c.bottom;
+  const int64_t x_lo = periodic ? 0 : c.left, x_hi = periodic ? nx : nx - c.right;
+  cudaStream_t sin = p->band_stream[0], sout = p->band_stream[1];
+  cudaEvent_t* ev_in = p->band_event;
+  cudaEvent_t* ev_comp = p->band_event + kRingSlots;
+  cudaEvent_t* ev_out = p->band_event + 2 * kRingSlots;
+  cudaEvent_t ev_start = p->band_event[3 * kRingSlots], ev_end = p->band_event[3 * kRingSlots + 1];
+  const char* hi = static_cast<const char*>(h_in);
+  char* ho = static_cast<char*>(h_out);
+  CS_CUDA_TRY(cudaEventRecord(ev_start, s));
+  CS_CUDA_TRY(cudaStreamWaitEvent(sin, ev_start, 0));
+  CS_CUDA_TRY(cudaStreamWaitEvent(sout, ev_start, 0));
+  for (int64_t b = 0; b < nb; ++b) {
+    const int k = static_cast<int>(b % kRingSlots);
+    const int64_t g0 = b * rows, g1 = std::min(ny, g0 + rows);
+    // the rows the band's tiles stage: from g0 - top to the end of the last 64-row tile + bottom
+    const int64_t r_lo = g0 - c.top, r_hi = (g1 + kStencilBandAlign - 1) / kStencilBandAlign * kStencilBandAlign + c.bottom;
+    char* slot_in = static_cast<char*>(p->ring_in[k]);
+    char* slot_out = static_cast<char*>(p->ring_out[k]);
+    if (b >= kRingSlots) CS_CUDA_TRY(cudaStreamWaitEvent(sin, ev_comp[k], 0));  // slot's last sweep done
+    rc = ring_fill(p, hi, slot_in, r_lo, r_hi, kRingTop - c.top, sin);
+    if (rc != CS_OK) return rc;
+    CS_CUDA_TRY(cudaEventRecord(ev_in[k], sin));
+    CS_CUDA_TRY(cudaStreamWaitEvent(s, ev_in[k], 0));
+    if (b >= kRingSlots) CS_CUDA_TRY(cudaStreamWaitEvent(s, ev_out[k], 0));  // slot's last copy-out done
+    rc = stencil2d_launch_rows(&p->ring_cfg[k], slot_in, slot_out, kRingTop, kRingTop + (g1 - g0), s);
+    if (rc != CS_OK) return rc;
+    CS_CUDA_TRY(cudaEventRecord(ev_comp[k], s));
+    CS_CUDA_TRY(cudaStreamWaitEvent(sout, ev_comp[k], 0));
+    const int64_t o0 = std::max(g0, w_lo), o1 = std::min(g1, w_hi);
+    if (o1 > o0 && x_hi > x_lo) {
+      const char* src = slot_out + (kRingTop + o0 - g0) * rb + x_lo * eb;
+      if (x_lo == 0 && x_hi == nx)
+        CS_CUDA_TRY(cudaMemcpyAsync(ho + o0 * rb, src, static_cast<size_t>((o1 - o0) * rb), cudaMemcpyDeviceToHost, sout));
+      else
+        CS_CUDA_TRY(cudaMemcpy2DAsync(ho + o0 * rb + x_lo * eb, static_cast<size_t>(rb), src, static_cast<size_t>(rb),
+                                      static_cast<size_t>((x_hi - x_lo) * eb), static_cast<size_t>(o1 - o0),
+                                      cudaMemcpyDeviceToHost, sout));
+    }
+    CS_CUDA_TRY(cudaEventRecord(ev_out[k], sout));
+  }
+  CS_CUDA_TRY(cudaEventRecord(ev_end, sout));
+  CS_CUDA_TRY(cudaStreamWaitEvent(s, ev_end, 0));
+  CS_CUDA_TRY(cudaStreamSynchronize(s));
+  return CS_OK;
+}
+
+bool is_2d(const cs_plan* p) { return p && (p->kind == kStencil2D || p->kind == kStencil2DHost); }
+
 cs_plan* new_plan(int kind) {
   cs_plan* p = new (std::nothrow) cs_plan;
   if (!p) return nullptr;
@@ -268,22 +416,65 @@ int cs_plan_create_2d(cs_plan_t* plan, const cs_stencil_desc* d, const void* d_i
     return set_error(CS_EALIAS, "input and output buffers overlap (Sec. 2: outputs go to a separate buffer)");
   cs_plan* p = new_plan(kStencil2D);
   if (!p) return set_error(CS_ENOMEM, "out of host memory");
-  Stencil2DConfig& c = p->s2;
-  c.nx = d->nx; c.ny = d->ny; c.dir = d->dir; c.bc = d->bc; c.dtype = d->dtype;
-  c.left = d->left; c.right = d->right; c.top = d->top; c.bottom = d->bottom;
-  c.fn = d->fn;
-  c.tile_rows = 64;
-  const int nw = (d->left + d->right + 1) * (d->top + d->bottom + 1);
-  if (d->fn == CS_FN_NONE) {
-    memcpy(c.weights, d->weights, sizeof(double) * nw);
-  } else {
-    c.num_coe = d->num_coe;
-    memcpy(c.coe, d->coe, sizeof(double) * d->num_coe);
-  }
-  rc = stencil2d_prepare(&c);
+  rc = fill_2d_config(p, d);
   if (rc != CS_OK) { delete p; return rc; }
   p->d_in = d_in; p->d_out = d_out; p->elem_bytes = eb; p->elems = elems;
   *plan = p;
+  return CS_OK;
+}
+
+int cs_plan_create_2d_host(cs_plan_t* plan, const cs_stencil_desc* d, int64_t device_bytes) {
+  if (!plan) return set_error(CS_EINVAL, "null plan pointer");
+  *plan = nullptr;
+  int rc = validate_desc_common(d);
+  if (rc != CS_OK) return rc;
+  if (d->nx < 1 || d->ny < kRingMinRows)
+    return set_error(CS_EINVAL, "a host-resident plan needs nx >= 1 and ny >= %lld", (long long)kRingMinRows);
+  if (d->nx > (int64_t(1) << 40) / d->ny) return set_error(CS_EINVAL, "grid too large");
+  if (device_bytes < 0) return set_error(CS_EINVAL, "device_bytes must be >= 0");
+  const int64_t eb = d->dtype == CS_F32 ? 4 : 8;
+  const int64_t budget = device_bytes ? device_bytes : (int64_t(512) << 20);
+  // slots x (input + output) x (top + rows + bottom) rows of nx elements within the budget
+  const int64_t row_pair = 2 * kRingSlots * d->nx * eb;
+  int64_t rows = budget / row_pair - kRingTop - kRingBottom;
+  rows = rows / kStencilBandAlign * kStencilBandAlign;
+  const int64_t grid_rows = (d->ny + kStencilBandAlign - 1) / kStencilBandAlign * kStencilBandAlign;
+  rows = std::min(rows, grid_rows);
+  if (rows < kStencilBandAlign)
+    return set_error(CS_EINVAL, "device_bytes %lld is below one %lld-row band per slot (%lld bytes)",
+                     (long long)budget, (long long)kStencilBandAlign,
+                     (long long)(row_pair * (kStencilBandAlign + kRingTop + kRingBottom)));
+  cs_plan* p = new_plan(kStencil2DHost);
+  if (!p) return set_error(CS_ENOMEM, "out of host memory");
+  rc = fill_2d_config(p, d);
+  if (rc != CS_OK) { delete p; return rc; }
+  p->elem_bytes = static_cast<size_t>(eb);
+  p->elems = d->nx * d->ny;
+  p->ring_rows = rows;
+  p->ring_ny = kRingTop + rows + kRingBottom;
+  p->ring_cfg = new (std::nothrow) Stencil2DConfig[kRingSlots];
+  const size_t slot_bytes = static_cast<size_t>(p->ring_ny * d->nx * eb);
+  cudaError_t e = p->ring_cfg ? cudaSuccess : cudaErrorMemoryAllocation;
+  for (int k = 0; k < kRingSlots && e == cudaSuccess; ++k) {
+    e = cudaMalloc(&p->ring_in[k], slot_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&p->ring_out[k], slot_bytes);
+  }
+  if (e != cudaSuccess) {
+    ring_free(p);
+    stencil2d_release(&p->s2);
+    delete p;
+    return e == cudaErrorMemoryAllocation ? set_error(CS_ENOMEM, "band slots of %zu bytes: %s", slot_bytes, cudaGetErrorString(e))
+                                          : cuda_error(e, "band slots");
+  }
+  p->ring_bytes = static_cast<int64_t>(2 * kRingSlots * slot_bytes);
+  *plan = p;
+  return CS_OK;
+}
+
+int cs_plan_host_info(cs_plan_t p, int64_t* band_rows, int64_t* device_bytes) {
+  if (!p || p->kind != kStencil2DHost) return set_error(CS_EINVAL, "not a host-resident 2D plan");
+  if (band_rows) *band_rows = p->ring_rows;
+  if (device_bytes) *device_bytes = p->ring_bytes;
   return CS_OK;
 }
 
@@ -395,6 +586,12 @@ int cs_compute_host(cs_plan_t p, const void* h_in, void* h_out, void* stream) {
   if (!p) return set_error(CS_EINVAL, "null plan");
   if (p->kind == kCahnHilliard) return set_error(CS_EINVAL, "use cs_ch_step for a Cahn-Hilliard plan");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->kind == kStencil2DHost) {
+    if (!h_in || !h_out) return set_error(CS_EINVAL, "a host-resident plan needs both host buffers");
+    if (overlaps(h_in, h_out, static_cast<size_t>(p->elems) * p->elem_bytes))
+      return set_error(CS_EALIAS, "input and output buffers overlap");
+    return compute_host_streamed(p, h_in, h_out, s);
+  }
   const size_t bytes = static_cast<size_t>(p->elems) * p->elem_bytes;
   if (p->kind == kStencil2D && h_in && h_out && bytes >= kBandMinBytes && p->s2.ny >= 2 * kStencilBandAlign)
     return compute_host_banded(p, h_in, h_out, s);
@@ -411,6 +608,7 @@ int cs_compute_host(cs_plan_t p, const void* h_in, void* h_out, void* stream) {
 int cs_swap(cs_plan_t p) {
   if (!p) return set_error(CS_EINVAL, "null plan");
   if (p->kind == kCahnHilliard) return set_error(CS_EINVAL, "Cahn-Hilliard plans rotate their fields themselves");
+  if (p->kind == kStencil2DHost) return set_error(CS_EINVAL, "a host-resident plan binds no device buffers");
   const void* in = p->d_in;
   p->d_in = p->d_out;
   p->d_out = const_cast<void*>(in);
@@ -420,7 +618,7 @@ int cs_swap(cs_plan_t p) {
 
 int cs_set_buffers(cs_plan_t p, const void* d_in, void* d_out) {
   if (!p) return set_error(CS_EINVAL, "null plan");
-  if (p->kind == kCahnHilliard) return set_error(CS_EINVAL, "not a stencil plan");
+  if (p->kind == kCahnHilliard || p->kind == kStencil2DHost) return set_error(CS_EINVAL, "not a device-buffer stencil plan");
   const size_t bytes = static_cast<size_t>(p->elems) * p->elem_bytes;
   if (bytes && (!d_in || !d_out)) return set_error(CS_EINVAL, "null device buffer");
   if (bytes && (reinterpret_cast<uintptr_t>(d_in) % p->elem_bytes || reinterpret_cast<uintptr_t>(d_out) % p->elem_bytes))
@@ -433,7 +631,7 @@ int cs_set_buffers(cs_plan_t p, const void* d_in, void* d_out) {
 }
 
 int cs_plan_set_fp64_mode(cs_plan_t p, int32_t mode) {
-  if (!p || p->kind != kStencil2D) return set_error(CS_EINVAL, "not a 2D stencil plan");
+  if (!is_2d(p)) return set_error(CS_EINVAL, "not a 2D stencil plan");
   if (mode != CS_FP64_AUTO && mode != CS_FP64_NATIVE) return set_error(CS_EINVAL, "unknown FP64 mode %d", mode);
   p->s2.fp64_mode = mode;
   drop_graph(p);
@@ -441,7 +639,7 @@ int cs_plan_set_fp64_mode(cs_plan_t p, int32_t mode) {
 }
 
 int cs_plan_set_tile_choice(cs_plan_t p, int32_t choice) {
-  if (!p || p->kind != kStencil2D) return set_error(CS_EINVAL, "not a 2D stencil plan");
+  if (!is_2d(p)) return set_error(CS_EINVAL, "not a 2D stencil plan");
   if (choice < 0 || choice >= stencil2d_num_tile_choices()) return set_error(CS_EINVAL, "tile choice %d out of range", choice);
   stencil2d_set_tile_choice(&p->s2, choice);
   drop_graph(p);
@@ -449,14 +647,15 @@ int cs_plan_set_tile_choice(cs_plan_t p, int32_t choice) {
 }
 
 int cs_plan_get_tile_choice(cs_plan_t p, int32_t* choice) {
-  if (!p || p->kind != kStencil2D || !choice) return set_error(CS_EINVAL, "not a 2D stencil plan");
+  if (!is_2d(p) || !choice) return set_error(CS_EINVAL, "not a 2D stencil plan");
   *choice = p->s2.use_tma ? 2 : (p->s2.tile_rows == 32 ? 0 : 1);
   return CS_OK;
 }
 
 int cs_plan_use_graph(cs_plan_t p, int enable) {
   if (!p) return set_error(CS_EINVAL, "null plan");
-  if (p->kind == kCahnHilliard) return set_error(CS_EUNSUPPORTED, "graph replay is for stencil plans");
+  if (p->kind == kCahnHilliard || p->kind == kStencil2DHost)
+    return set_error(CS_EUNSUPPORTED, "graph replay is for device-buffer stencil plans");
   p->use_graph = enable != 0;
   if (!p->use_graph) drop_graph(p);
   return CS_OK;
@@ -465,6 +664,7 @@ int cs_plan_use_graph(cs_plan_t p, int enable) {
 int cs_autotune(cs_plan_t p, void* stream) {
   if (!p) return set_error(CS_EINVAL, "null plan");
   if (p->kind == kCahnHilliard) return ch_autotune(p->ch, static_cast<cudaStream_t>(stream));
+  if (p->kind == kStencil2DHost) return CS_OK;  // host-link bound: the tile choice stays as created
   if (p->elems == 0) return CS_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int nchoices = p->kind == kStencil2D ? stencil2d_num_tile_choices() : batch1d_num_choices();
@@ -521,7 +721,8 @@ int cs_destroy(cs_plan_t p) {
     for (auto& e : p->band_event) cudaEventDestroy(e);
     for (int i = 0; i < 2; ++i) cudaStreamDestroy(p->band_stream[i]);
   }
-  if (p->kind == kStencil2D) stencil2d_release(&p->s2);
+  if (p->kind == kStencil2DHost) ring_free(p);
+  if (p->kind == kStencil2D || p->kind == kStencil2DHost) stencil2d_release(&p->s2);
   if (p->kind == kBatch1D) batch1d_release(&p->b1);
   if (p->kind == kCahnHilliard) ch_destroy(p->ch);
   delete p;

@@ -103,6 +103,17 @@ def test_ch_fields_must_not_overlap(cs):
     assert rc_of(cs.cs_ch_create, d, 1 << 30, (1 << 30) + 64, 1 << 36) == cs.CS_EALIAS
 
 
+def test_host_resident_plan_rejected_on_host(cs):
+    """Validation of cs_plan_create_2d_host runs before any device allocation."""
+    kw = dict(dir=2, bc=1, left=1, right=1, top=1, bottom=1, weights=[0, 1, 0, 1, -4, 1, 0, 1, 0.0])
+    assert rc_of(cs.cs_plan_create_2d_host, cs.StencilDesc(nx=64, ny=127, dtype=0, **kw), 0) == cs.CS_EINVAL
+    assert rc_of(cs.cs_plan_create_2d_host, cs.StencilDesc(nx=64, ny=4096, dtype=0, **kw), -1) == cs.CS_EINVAL
+    # 3 slots x (in + out) x (64 + 64 + 80) rows x 64 x 8 bytes is the least budget; one byte less fails
+    least = 2 * 3 * (64 + 64 + 80) * 64 * 8
+    assert rc_of(cs.cs_plan_create_2d_host, cs.StencilDesc(nx=64, ny=4096, dtype=0, **kw), least - 1) == cs.CS_EINVAL
+    assert rc_of(cs.cs_plan_host_info, None) == cs.CS_EINVAL
+
+
 def test_wrong_plan_kind_rejected(cs):
     assert rc_of(cs.cs_ch_step, None, 1, False, 0) == cs.CS_EINVAL
     assert rc_of(cs.cs_ch_coarsening, None, 0) == cs.CS_EINVAL
