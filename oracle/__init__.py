@@ -15,6 +15,9 @@ What each routine computes, with the passage it follows:
 * ``ch_mass``, ``ch_energy`` -- the integral of C and the free energy F[C] of Eq. (1)
 * ``ch_coarsening_s``, ``ch_coarsening_k1`` -- the coarsening measures s(t) and k_1(t) of
   Sec. 5.1 "Numerical Results" (numpy; the FFT is numpy's)
+* ``weno5_hj``, ``weno5_derivatives``, ``weno_advection`` -- the periodic XY WENO advection variant
+  of Sec. 4.2 "Advection" (numpy), with the fifth-order Hamilton-Jacobi WENO derivatives of the
+  reference it cites (Osher & Fedkiw, Sec. 3.4)
 
 Fields are 2D numpy arrays of shape (ny, nx), row-major, x fastest.  FP32 inputs are widened to
 FP64 before the oracle sees them, so the oracle works on exactly the values the GPU read.
@@ -221,3 +224,56 @@ def ch_coarsening_k1(c) -> float:
     k[0, 0] = 1.0
     return float(p.sum() / (p / k).sum())
 
+
+
+# ---- WENO advection (Sec. 4.2 "Advection": the 2D periodic XY variant with inputs C, u, v) -------
+# The derivative approximations are the fifth-order WENO scheme for Hamilton-Jacobi equations of
+# Osher & Fedkiw, "Level Set Methods and Dynamic Implicit Surfaces" (the reference the paper
+# gives for its solver), Sec. 3.4, written out from its definitions in numpy, FP64.
+
+WENO_EPS_SCALE = 1e-6   # epsilon = 1e-6 * max(v_k^2) + 1e-99
+WENO_EPS_FLOOR = 1e-99
+
+
+def weno5_hj(v1, v2, v3, v4, v5, eps_scale: float = WENO_EPS_SCALE, eps_floor: float = WENO_EPS_FLOOR):
+    """The WENO5 derivative from the five one-sided differences v1..v5 (arrays or scalars): the
+    three third-order candidates, their smoothness indicators and the nonlinear weights built on
+    the optimal weights 0.1, 0.6, 0.3."""
+    v1, v2, v3, v4, v5 = (np.asarray(v, dtype=np.float64) for v in (v1, v2, v3, v4, v5))
+    phi1 = v1 / 3.0 - 7.0 * v2 / 6.0 + 11.0 * v3 / 6.0
+    phi2 = -v2 / 6.0 + 5.0 * v3 / 6.0 + v4 / 3.0
+    phi3 = v3 / 3.0 + 5.0 * v4 / 6.0 - v5 / 6.0
+    s1 = 13.0 / 12.0 * (v1 - 2.0 * v2 + v3) ** 2 + 0.25 * (v1 - 4.0 * v2 + 3.0 * v3) ** 2
+    s2 = 13.0 / 12.0 * (v2 - 2.0 * v3 + v4) ** 2 + 0.25 * (v2 - v4) ** 2
+    s3 = 13.0 / 12.0 * (v3 - 2.0 * v4 + v5) ** 2 + 0.25 * (3.0 * v3 - 4.0 * v4 + v5) ** 2
+    eps = eps_scale * np.maximum.reduce([v1 * v1, v2 * v2, v3 * v3, v4 * v4, v5 * v5]) + eps_floor
+    a1 = 0.1 / (s1 + eps) ** 2
+    a2 = 0.6 / (s2 + eps) ** 2
+    a3 = 0.3 / (s3 + eps) ** 2
+    return (a1 * phi1 + a2 * phi2 + a3 * phi3) / (a1 + a2 + a3)
+
+
+def _at(a, k: int, axis: int):
+    """a at index i + k along `axis`, periodic."""
+    return np.roll(a, -k, axis=axis)
+
+
+def weno5_derivatives(c, h: float, axis: int, **eps):
+    """(left-biased, right-biased) WENO5 approximations of dC/dx along `axis` (1: x, 0: y) on the
+    periodic grid: the first from the backward differences D-C at i-2 .. i+2, the second from the
+    forward differences D+C at i+2 .. i-2."""
+    c = _f64(c)
+    d = (_at(c, 1, axis) - c) / h  # d[i] = D+C at i = D-C at i+1
+    minus = weno5_hj(_at(d, -3, axis), _at(d, -2, axis), _at(d, -1, axis), d, _at(d, 1, axis), **eps)
+    plus = weno5_hj(_at(d, 2, axis), _at(d, 1, axis), d, _at(d, -1, axis), _at(d, -2, axis), **eps)
+    return minus, plus
+
+
+def weno_advection(c, u, v, hx: float, hy: float, **eps):
+    """The advection term u C_x + v C_y on the periodic grid, each derivative upwinded: the
+    left-biased WENO5 value where the velocity component is positive, the right-biased one where
+    it is negative (where it is zero the term is zero either way).  Rows are y, columns x."""
+    u, v = _f64(u), _f64(v)
+    cx_m, cx_p = weno5_derivatives(c, hx, 1, **eps)
+    cy_m, cy_p = weno5_derivatives(c, hy, 0, **eps)
+    return u * np.where(u > 0, cx_m, cx_p) + v * np.where(v > 0, cy_m, cy_p)
