@@ -12,7 +12,8 @@ Other parts of the metric are measured after the timed steps and reported beside
 Cahn-Hilliard ADI steps/s (N = 1024, 4096; FP64 and FP32 storage) and the ragged batched-1D
 sweep (65536 lines, log-uniform 64..4096, FP32, persistent launch replayed from a CUDA graph),
 the coarsening run of Sec. 5.1 (512^2 to t = 100, s(t) and k_1(t) on the device), and
-host-resident grids streamed through 256 MiB of device band slots.
+host-resident grids streamed through 256 MiB of device band slots, and the periodic XY WENO
+advection term (Sec. 4.2) at 8192^2.
 
 --impl reference runs the CPU oracle (the reference arm of this build: a plain FP64 C program)
 on a bounded sample of the same workload.
@@ -342,6 +343,7 @@ def run_ours(args):
         parts["serve"] = bench_serve(cs, torch)
         parts["coarsening"] = bench_coarsening(cs, torch, stream)
         parts["streamed"] = bench_streamed(cs, torch, stream)
+        parts["weno"] = bench_weno(cs, torch, stream, hbm_peak)
     for sw in sweeps:
         cs.cs_destroy(sw["plan"])
     line = {
@@ -467,6 +469,41 @@ def bench_streamed(cs, torch, stream, budget_mib=256, reps=5):
                     "link_gbs": round(2 * n * n * eb / t / 1e9, 1), "band_rows": rows,
                     "bands": -(-n // rows), "device_mib": round(held / 2 ** 20, 1)}
         del h_in, h_out
+    return out
+
+
+def bench_weno(cs, torch, stream, hbm_peak, reps=20):
+    """Periodic XY WENO advection (Sec. 4.2) at 8192^2, FP64 and FP32: one launch per sweep on
+    inputs larger than L2 (three 512 MB / 256 MB fields), timed with CUDA events; HBM bytes per
+    point = C, u, v read + the term written."""
+    out = {}
+    n = 8192
+    h = 2 * np.pi / n
+    x = torch.arange(n, dtype=torch.float64, device="cuda") * h
+    for dtype in (cs.CS_F64, cs.CS_F32):
+        tdt = torch.float64 if dtype == cs.CS_F64 else torch.float32
+        eb = 8 if dtype == cs.CS_F64 else 4
+        c = (torch.sin(3 * x)[None, :] * torch.cos(5 * x)[:, None]).to(tdt)
+        u = (torch.cos(x)[:, None] + 0.0 * x[None, :]).to(tdt)
+        v = (torch.sin(x)[None, :] - 0.2 + 0.0 * x[:, None]).to(tdt)
+        o = torch.empty_like(c)
+        plan = cs.cs_plan_create_weno_adv(n, n, dtype, h, h, c, u, v, o)
+        for _ in range(3):
+            cs.cs_compute(plan, stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for _ in range(reps):
+            cs.cs_compute(plan, stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / reps
+        cs.cs_destroy(plan)
+        gbs = 4 * eb * n * n / (ms * 1e-3) / 1e9
+        out["f64" if dtype == cs.CS_F64 else "f32"] = {
+            "ms": round(ms, 4), "gpts_per_s": round(n * n / (ms * 1e-3) / 1e9, 2),
+            "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 3)}
+        del c, u, v, o
     return out
 
 
@@ -640,7 +677,7 @@ def run_reference(args):
 
 def run_part(args):
     """One part of the metric on its own (used to profile it): --part ch:<n>:<f64|f32>:<steps>,
-    batch1d, serve, coarsening or streamed."""
+    batch1d, serve, coarsening, streamed or weno."""
     import torch
     import paper_1902_09931_gb300 as cs
     torch.cuda.set_device(0)
@@ -657,6 +694,8 @@ def run_part(args):
         res = bench_coarsening(cs, torch, stream)
     elif kind[0] == "streamed":
         res = bench_streamed(cs, torch, stream)
+    elif kind[0] == "weno":
+        res = bench_weno(cs, torch, stream, hbm_peak)
     else:
         res = bench_batch1d(cs, torch, stream, hbm_peak)
     print(json.dumps({"part": args.part, "result": res}), flush=True)
@@ -674,7 +713,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile-choice", type=int, default=-1, help="force a tile choice (0, 1, 2) instead of autotuning")
     ap.add_argument("--only", default="", help="profile one sweep: name,n,f64|f32,p|np")
-    ap.add_argument("--part", default="", help="run one part alone: ch:<n>:<f64|f32>:<steps>, batch1d, serve, coarsening or streamed")
+    ap.add_argument("--part", default="", help="run one part alone: ch:<n>:<f64|f32>:<steps>, batch1d, serve, coarsening, streamed or weno")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

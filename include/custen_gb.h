@@ -129,6 +129,29 @@ int cs_compute(cs_plan_t plan, void* cuda_stream);
  * loop to batch small sweeps.  Stream-ordered and asynchronous. */
 int cs_compute_group(const cs_plan_t* plans, int32_t count, void* cuda_stream);
 
+/* Periodic XY WENO advection (Sec. 4.2, "Advection"): the XY periodic stencil variant whose
+ * inputs are a field C and velocities u, v, and whose per-point solver is the fifth-order WENO
+ * scheme for Hamilton-Jacobi equations of the reference the paper cites (Osher & Fedkiw, Sec. 3.4).
+ * Compute writes the advection term
+ *     out = u * C_x + v * C_y
+ * with each derivative upwinded: the left-biased WENO5 approximation (points i-3 .. i+2) where
+ * the velocity component is > 0, the right-biased one (i-2 .. i+3) elsewhere; eps = 1e-6 *
+ * max(v_k^2) + 1e-99 over the five differences (the floor is left out with FP32 storage).  A
+ * time stepper advances C_t = -out.  All four fields are n_y x n_x, row-major (x fastest),
+ * periodic in both directions, of the description's dtype; arithmetic in that dtype.
+ *   hx, hy    grid spacings, in [1e-60, 1e60] (CS_EINVAL otherwise).
+ *   d_out     must not overlap d_c, d_u or d_v (CS_EALIAS); the three inputs are only read.
+ * cs_compute runs one kernel; graph replay applies; cs_swap, cs_set_buffers and
+ * cs_compute_host do not (CS_EINVAL); cs_autotune leaves the plan unchanged. */
+typedef struct {
+  int64_t nx, ny;
+  int32_t dtype;    /* CS_F64 or CS_F32 */
+  int32_t reserved;
+  double hx, hy;
+} cs_weno_desc;
+int cs_plan_create_weno_adv(cs_plan_t* plan, const cs_weno_desc* desc, const void* d_c,
+                            const void* d_u, const void* d_v, void* d_out);
+
 /* Create for a 2D grid that lives in host memory (Sec. 2's y-tile streaming of grids larger
  * than device memory).  The plan owns a ring of 3 band slots in device memory, each holding
  * input and output for a band of rows plus halo rows; cs_compute_host then streams the grid

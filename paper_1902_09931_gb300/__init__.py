@@ -56,6 +56,11 @@ class _CCHDesc(ctypes.Structure):
                 ("D", ctypes.c_double), ("gamma", ctypes.c_double), ("dt", ctypes.c_double)]
 
 
+class _CWenoDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("dtype", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("hx", ctypes.c_double), ("hy", ctypes.c_double)]
+
+
 @dataclass
 class StencilDesc:
     """Python mirror of ``cs_stencil_desc`` (Sec. 3 / Sec. 4.1 parameters)."""
@@ -89,6 +94,7 @@ _SYMBOLS = {
     "cs_plan_create_2d": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_CStencilDesc), ctypes.c_void_p, ctypes.c_void_p]),
     "cs_plan_create_2d_host": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_CStencilDesc), ctypes.c_int64]),
     "cs_plan_host_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "cs_plan_create_weno_adv": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_CWenoDesc), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_plan_create_1d_batch": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_CStencilDesc), ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_compute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "cs_compute_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -203,6 +209,15 @@ def cs_plan_host_info(plan):
     r, b = ctypes.c_int64(), ctypes.c_int64()
     _check(load().cs_plan_host_info(plan, ctypes.byref(r), ctypes.byref(b)))
     return r.value, b.value
+
+
+def cs_plan_create_weno_adv(nx: int, ny: int, dtype: int, hx: float, hy: float, d_c, d_u, d_v, d_out):
+    """Periodic XY WENO advection plan: cs_compute writes u C_x + v C_y into d_out."""
+    c = _CWenoDesc(nx=int(nx), ny=int(ny), dtype=int(dtype), reserved=0, hx=float(hx), hy=float(hy))
+    plan = ctypes.c_void_p()
+    _check(load().cs_plan_create_weno_adv(ctypes.byref(plan), ctypes.byref(c), _ptr(d_c), _ptr(d_u),
+                                          _ptr(d_v), _ptr(d_out)))
+    return plan
 
 
 def cs_plan_create_1d_batch(desc: StencilDesc, num_lines: int, d_offsets, total_len: int, d_in,

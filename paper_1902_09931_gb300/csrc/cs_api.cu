@@ -90,7 +90,7 @@ int flush_l2(cudaStream_t s) {
 }  // namespace autotune_detail
 }  // namespace cs
 
-enum PlanKind { kStencil2D = 1, kBatch1D = 2, kCahnHilliard = 3, kStencil2DHost = 4 };
+enum PlanKind { kStencil2D = 1, kBatch1D = 2, kCahnHilliard = 3, kStencil2DHost = 4, kWeno = 5 };
 
 // Band slots of a host-resident (out-of-core) 2D plan: one being copied in, one swept, one
 // copied out.
@@ -121,6 +121,10 @@ struct cs_plan {
   void* ring_out[kRingSlots];
   cs::Stencil2DConfig* ring_cfg;  // kRingSlots copies of s2 with ny = ring_ny (own tensor maps)
   int64_t ring_bytes;
+  // WENO advection plan: d_in = C, d_out = the advection term, plus the two velocity fields
+  cs::WenoConfig weno;
+  const void* d_u;
+  const void* d_v;
 };
 
 namespace {
@@ -144,6 +148,7 @@ int launch_direct(cs_plan* p, cudaStream_t s) {
   switch (p->kind) {
     case kStencil2D: return stencil2d_launch(&p->s2, p->d_in, p->d_out, s);
     case kBatch1D: return batch1d_launch(&p->b1, p->d_in, p->d_out, s);
+    case kWeno: return weno_launch(&p->weno, p->d_in, p->d_u, p->d_v, p->d_out, s);
     case kStencil2DHost: return set_error(CS_EINVAL, "a host-resident plan computes through cs_compute_host");
     default: return set_error(CS_EINVAL, "cs_compute: not a stencil plan");
   }
@@ -471,6 +476,43 @@ int cs_plan_create_2d_host(cs_plan_t* plan, const cs_stencil_desc* d, int64_t de
   return CS_OK;
 }
 
+int cs_plan_create_weno_adv(cs_plan_t* plan, const cs_weno_desc* d, const void* d_c, const void* d_u,
+                            const void* d_v, void* d_out) {
+  if (!plan) return set_error(CS_EINVAL, "null plan pointer");
+  *plan = nullptr;
+  if (!d) return set_error(CS_EINVAL, "null WENO description");
+  if (d->dtype != CS_F64 && d->dtype != CS_F32) return set_error(CS_EINVAL, "dtype must be CS_F64 or CS_F32");
+  if (d->nx < 0 || d->ny < 0) return set_error(CS_EINVAL, "nx, ny must be >= 0");
+  if (d->nx > (int64_t(1) << 40) / (d->ny > 0 ? d->ny : 1)) return set_error(CS_EINVAL, "grid too large");
+  if (!(d->hx >= 1e-60 && d->hx <= 1e60 && d->hy >= 1e-60 && d->hy <= 1e60))
+    return set_error(CS_EINVAL, "hx, hy must lie in [1e-60, 1e60]");
+  const size_t eb = d->dtype == CS_F32 ? 4 : 8;
+  const int64_t elems = d->nx * d->ny;
+  if (elems > 0) {
+    const void* f[4] = {d_c, d_u, d_v, d_out};
+    for (const void* q : f) {
+      if (!q) return set_error(CS_EINVAL, "null device buffer");
+      if (reinterpret_cast<uintptr_t>(q) % eb) return set_error(CS_EINVAL, "buffers must be aligned to the element size");
+    }
+    const size_t bytes = static_cast<size_t>(elems) * eb;
+    for (int i = 0; i < 3; ++i)
+      if (overlaps(f[i], d_out, bytes))
+        return set_error(CS_EALIAS, "the output must not overlap C, u or v (Sec. 2: blocks read overlapping halos)");
+  }
+  cs_plan* p = new_plan(kWeno);
+  if (!p) return set_error(CS_ENOMEM, "out of host memory");
+  p->weno.nx = d->nx;
+  p->weno.ny = d->ny;
+  p->weno.dtype = d->dtype;
+  p->weno.hx = d->hx;
+  p->weno.hy = d->hy;
+  p->d_in = d_c; p->d_u = d_u; p->d_v = d_v; p->d_out = d_out;
+  p->elem_bytes = eb;
+  p->elems = elems;
+  *plan = p;
+  return CS_OK;
+}
+
 int cs_plan_host_info(cs_plan_t p, int64_t* band_rows, int64_t* device_bytes) {
   if (!p || p->kind != kStencil2DHost) return set_error(CS_EINVAL, "not a host-resident 2D plan");
   if (band_rows) *band_rows = p->ring_rows;
@@ -584,6 +626,7 @@ int cs_compute_group(const cs_plan_t* plans, int32_t count, void* stream) {
 
 int cs_compute_host(cs_plan_t p, const void* h_in, void* h_out, void* stream) {
   if (!p) return set_error(CS_EINVAL, "null plan");
+  if (p->kind == kWeno) return set_error(CS_EINVAL, "a WENO plan computes on device buffers (cs_compute)");
   if (p->kind == kCahnHilliard) return set_error(CS_EINVAL, "use cs_ch_step for a Cahn-Hilliard plan");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (p->kind == kStencil2DHost) {
@@ -609,6 +652,7 @@ int cs_swap(cs_plan_t p) {
   if (!p) return set_error(CS_EINVAL, "null plan");
   if (p->kind == kCahnHilliard) return set_error(CS_EINVAL, "Cahn-Hilliard plans rotate their fields themselves");
   if (p->kind == kStencil2DHost) return set_error(CS_EINVAL, "a host-resident plan binds no device buffers");
+  if (p->kind == kWeno) return set_error(CS_EINVAL, "a WENO plan's output is the advection term, not a new field");
   const void* in = p->d_in;
   p->d_in = p->d_out;
   p->d_out = const_cast<void*>(in);
@@ -618,7 +662,8 @@ int cs_swap(cs_plan_t p) {
 
 int cs_set_buffers(cs_plan_t p, const void* d_in, void* d_out) {
   if (!p) return set_error(CS_EINVAL, "null plan");
-  if (p->kind == kCahnHilliard || p->kind == kStencil2DHost) return set_error(CS_EINVAL, "not a device-buffer stencil plan");
+  if (p->kind == kCahnHilliard || p->kind == kStencil2DHost || p->kind == kWeno)
+    return set_error(CS_EINVAL, "not a single-input device-buffer stencil plan");
   const size_t bytes = static_cast<size_t>(p->elems) * p->elem_bytes;
   if (bytes && (!d_in || !d_out)) return set_error(CS_EINVAL, "null device buffer");
   if (bytes && (reinterpret_cast<uintptr_t>(d_in) % p->elem_bytes || reinterpret_cast<uintptr_t>(d_out) % p->elem_bytes))
@@ -664,7 +709,7 @@ int cs_plan_use_graph(cs_plan_t p, int enable) {
 int cs_autotune(cs_plan_t p, void* stream) {
   if (!p) return set_error(CS_EINVAL, "null plan");
   if (p->kind == kCahnHilliard) return ch_autotune(p->ch, static_cast<cudaStream_t>(stream));
-  if (p->kind == kStencil2DHost) return CS_OK;  // host-link bound: the tile choice stays as created
+  if (p->kind == kStencil2DHost || p->kind == kWeno) return CS_OK;  // one launch shape: nothing to choose
   if (p->elems == 0) return CS_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int nchoices = p->kind == kStencil2D ? stencil2d_num_tile_choices() : batch1d_num_choices();

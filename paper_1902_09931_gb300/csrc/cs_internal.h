@@ -83,6 +83,14 @@ int batch1d_launch(const Batch1DConfig* cfg, const void* in, void* out, cudaStre
 int batch1d_num_choices();
 std::string batch1d_shape_key(const Batch1DConfig* cfg);
 
+// ---- periodic XY WENO advection (cs_weno.cu) ---------------------------------------------------
+struct WenoConfig {
+  int64_t nx, ny;
+  int dtype;
+  double hx, hy;
+};
+int weno_launch(const WenoConfig* cfg, const void* c, const void* u, const void* v, void* out, cudaStream_t s);
+
 // ---- Cahn-Hilliard ADI (cs_ch.cu) -------------------------------------------------------------
 struct CHPlan;
 int ch_create(CHPlan** out, const cs_ch_desc* d, void* prev, void* cur, void* next);

@@ -1,0 +1,184 @@
+// Periodic XY WENO advection (Sec. 4.2, "Advection"): the variant of the periodic XY stencil
+// whose inputs are the field C and the velocities u, v, and whose per-point computation is a
+// WENO solver instead of a weighted sum.  The output is the advection term
+//     a = u C_x + v C_y,
+// each derivative the fifth-order WENO approximation for Hamilton-Jacobi equations (Osher &
+// Fedkiw, "Level Set Methods and Dynamic Implicit Surfaces", Sec. 3.4 -- the reference the paper
+// gives for its solver), upwinded: the left-biased approximation where the velocity component is
+// positive, the right-biased one elsewhere.  The stencil is 3 points each way along x and along
+// y, no corners (the paper's variant drops the corner loads too).
+//
+// Tiles: 64 x 32 outputs per CTA of 256 threads; C (with a 3-point periodic halo) staged in
+// shared memory by the 2D stencil's tile loader; u and v read once per point from global memory.
+// A thread owns one column and walks 8 consecutive rows, keeping its 7-point y window in
+// registers.  Arithmetic in the storage type (FP64 for FP64 fields, FP32 for FP32 fields).
+//
+// The weights.  With v1..v5 the five one-sided differences, candidates phi_k, smoothness
+// indicators S_k and q_k = (S_k + eps)^2, the WENO value is
+//     sum_k g_k phi_k / q_k  /  sum_k g_k / q_k  =  sum_k g_k phi_k P_k / sum_k g_k P_k,
+// P_1 = q_2 q_3, P_2 = q_1 q_3, P_3 = q_1 q_2, g = (0.1, 0.6, 0.3): one division.  The differences
+// are first scaled by the power of two 2^-E that brings max|v_k| into [1, 2) (exact), so every
+// q_k lies in [1e-12, 2e4] and no product under- or overflows; the scheme is invariant under that
+// scaling except for eps's constant floor, which is scaled with it (1e-99 h^2 2^-2E).  Where the
+// floor is at least 1e19 times every S_k, the weights equal g to rounding and the linear
+// combination sum_k g_k phi_k is taken directly (this covers all-zero and tiny differences).
+
+#include <cmath>
+
+#include "cs_internal.h"
+#include "cs_stencil2d_kernels.cuh"
+
+namespace cs {
+namespace {
+
+constexpr int kWThreads = 256;
+constexpr int kWTX = 64;                        // columns per tile
+constexpr int kWTY = 32;                        // rows per tile
+constexpr int kWHalo = 3;                       // stencil reach along x and y
+constexpr int kWGroups = kWThreads / kWTX;      // row groups
+constexpr int kWRows = kWTY / kWGroups;         // rows per thread
+constexpr int kWLA = 4;                         // left halo, rounded up to 16 bytes in both types
+constexpr int kWCols = kWLA + kWTX + kWLA;
+constexpr int kWTileRows = kWTY + 2 * kWHalo;
+
+__device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+
+// The WENO value from the scaled differences w1..w5 (max |w_k| in [1, 2)), eps = 1e-6 max w^2 + fl.
+template <typename T>
+__device__ __forceinline__ T weno_scaled(T w1, T w2, T w3, T w4, T w5, T mw, T fl) {
+  const T phi1 = fma_(T(1.0 / 3.0), w1, fma_(T(-7.0 / 6.0), w2, T(11.0 / 6.0) * w3));
+  const T phi2 = fma_(T(-1.0 / 6.0), w2, fma_(T(5.0 / 6.0), w3, T(1.0 / 3.0) * w4));
+  const T phi3 = fma_(T(1.0 / 3.0), w3, fma_(T(5.0 / 6.0), w4, T(-1.0 / 6.0) * w5));
+  const T a1 = fma_(T(-2), w2, w1) + w3, b1 = fma_(T(-4), w2, w1) + T(3) * w3;
+  const T a2 = fma_(T(-2), w3, w2) + w4, b2 = w2 - w4;
+  const T a3 = fma_(T(-2), w4, w3) + w5, b3 = fma_(T(3), w3, fma_(T(-4), w4, w5));
+  const T s1 = fma_(T(13.0 / 12.0) * a1, a1, T(0.25) * b1 * b1);
+  const T s2 = fma_(T(13.0 / 12.0) * a2, a2, T(0.25) * b2 * b2);
+  const T s3 = fma_(T(13.0 / 12.0) * a3, a3, T(0.25) * b3 * b3);
+  const T eps = fma_(T(1e-6), mw * mw, fl);
+  const T t1 = s1 + eps, t2 = s2 + eps, t3 = s3 + eps;
+  const T q1 = t1 * t1, q2 = t2 * t2, q3 = t3 * t3;
+  const T p1 = T(0.1) * (q2 * q3), p2 = T(0.6) * (q1 * q3), p3 = T(0.3) * (q1 * q2);
+  const T num = fma_(p1, phi1, fma_(p2, phi2, p3 * phi3));
+  const T den = p1 + p2 + p3;
+  return num / den;
+}
+
+// sum_k g_k phi_k: the optimal-weight (linear) combination, (2 v1 - 13 v2 + 47 v3 + 27 v4 - 3 v5) / 60.
+template <typename T>
+__device__ __forceinline__ T weno_linear(T v1, T v2, T v3, T v4, T v5) {
+  const T phi1 = fma_(T(1.0 / 3.0), v1, fma_(T(-7.0 / 6.0), v2, T(11.0 / 6.0) * v3));
+  const T phi2 = fma_(T(-1.0 / 6.0), v2, fma_(T(5.0 / 6.0), v3, T(1.0 / 3.0) * v4));
+  const T phi3 = fma_(T(1.0 / 3.0), v3, fma_(T(5.0 / 6.0), v4, T(-1.0 / 6.0) * v5));
+  return fma_(T(0.1), phi1, fma_(T(0.6), phi2, T(0.3) * phi3));
+}
+
+// WENO value of unscaled differences v1..v5 (in units of C; the caller divides by h), with
+// floor_h2 = 1e-99 h^2 the eps floor in those units.
+__device__ __forceinline__ double weno5(double v1, double v2, double v3, double v4, double v5, double floor_h2) {
+  const double m = fmax(fmax(fmax(fabs(v1), fabs(v2)), fmax(fabs(v3), fabs(v4))), fabs(v5));
+  const int e = static_cast<int>(__double_as_longlong(m) >> 52);  // biased exponent of max |v|
+  // e < 600: max|v| < 2^-423 and the floor (>= 1e-99 * 1e-120 for h >= 1e-60) outweighs every
+  // S_k by far more than 1e19; e > 2045: inf / nan or next to overflow (kept linear)
+  if (e >= 600 && e <= 2045) {
+    const double sc = __longlong_as_double(static_cast<long long>(2046 - e) << 52);  // 2^(1023 - e)
+    const double fl = floor_h2 * sc * sc;
+    if (fl < 1e19) {
+      const double r = weno_scaled<double>(v1 * sc, v2 * sc, v3 * sc, v4 * sc, v5 * sc, m * sc, fl);
+      return r * __longlong_as_double(static_cast<long long>(e) << 52);  // * 2^(e - 1023)
+    }
+  }
+  return weno_linear<double>(v1, v2, v3, v4, v5);
+}
+
+// FP32: the floor (1e-99 h^2, below FP32's range) is left out; it changes eps by a relative
+// 1e-99 h^2 / (1e-6 max v^2), i.e. nothing unless the differences are denormal.
+__device__ __forceinline__ float weno5(float v1, float v2, float v3, float v4, float v5, float) {
+  const float m = fmaxf(fmaxf(fmaxf(fabsf(v1), fabsf(v2)), fmaxf(fabsf(v3), fabsf(v4))), fabsf(v5));
+  const int e = static_cast<int>(__float_as_uint(m) >> 23);
+  if (e >= 1 && e <= 253) {
+    const float sc = __uint_as_float(static_cast<unsigned>(254 - e) << 23);  // 2^(127 - e)
+    const float r = weno_scaled<float>(v1 * sc, v2 * sc, v3 * sc, v4 * sc, v5 * sc, m * sc, 0.f);
+    return r * __uint_as_float(static_cast<unsigned>(e) << 23);  // * 2^(e - 127)
+  }
+  return weno_linear<float>(v1, v2, v3, v4, v5);
+}
+
+// d[k] = C(i + k - 2) - C(i + k - 3), k = 0..5 (the differences at i - 3 .. i + 2); upwind
+// selection: left-biased (d0..d4) for a positive velocity, right-biased (d5..d1) otherwise.
+template <typename T>
+__device__ __forceinline__ T upwind(const T (&d)[6], bool pos, T floor_h2) {
+  const T v1 = pos ? d[0] : d[5];
+  const T v2 = pos ? d[1] : d[4];
+  const T v3 = pos ? d[2] : d[3];
+  const T v4 = pos ? d[3] : d[2];
+  const T v5 = pos ? d[4] : d[1];
+  return weno5(v1, v2, v3, v4, v5, floor_h2);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kWThreads)
+    k_weno_adv(const T* __restrict__ c, const T* __restrict__ u, const T* __restrict__ v, T* __restrict__ out,
+               int64_t nx, int64_t ny, int vec_ok, T inv_hx, T inv_hy, T floor_x, T floor_y) {
+  __shared__ __align__(16) T s[kWTileRows * kWCols];
+  const int64_t x0 = static_cast<int64_t>(blockIdx.x) * kWTX;
+  const int64_t y0 = static_cast<int64_t>(blockIdx.y) * kWTY;
+  s2d::load_tile<T>(s, c, nx, ny, true, vec_ok != 0, x0, y0, kWHalo, kWLA, kWCols, kWTileRows);
+  const int tx = threadIdx.x % kWTX;
+  const int r0 = (threadIdx.x / kWTX) * kWRows;
+  const int64_t gx = x0 + tx;
+  if (gx >= nx) return;
+  const T* colp = s + tx + kWLA;
+  T col[2 * kWHalo + 1];  // C at rows y - 3 .. y + 3 of this column
+#pragma unroll
+  for (int k = 0; k < 2 * kWHalo + 1; ++k) col[k] = colp[(r0 + k) * kWCols];
+#pragma unroll
+  for (int r = 0; r < kWRows; ++r) {
+    const int64_t gy = y0 + r0 + r;
+    if (gy >= ny) break;
+    const T* row = colp + (r0 + r + kWHalo) * kWCols;
+    T dx[6], dy[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      dx[k] = row[k - 2] - row[k - 3];
+      dy[k] = col[k + 1] - col[k];
+    }
+    const int64_t o = gy * nx + gx;
+    const T uu = u[o], vv = v[o];
+    const T fx = upwind<T>(dx, uu > T(0), floor_x) * inv_hx;
+    const T fy = upwind<T>(dy, vv > T(0), floor_y) * inv_hy;
+    out[o] = fma_(uu, fx, vv * fy);
+    if (r + 1 < kWRows) {
+#pragma unroll
+      for (int k = 0; k < 2 * kWHalo; ++k) col[k] = col[k + 1];
+      col[2 * kWHalo] = colp[(r0 + r + 2 * kWHalo + 1) * kWCols];
+    }
+  }
+}
+
+}  // namespace
+
+int weno_launch(const WenoConfig* cfg, const void* c, const void* u, const void* v, void* out, cudaStream_t st) {
+  if (cfg->nx == 0 || cfg->ny == 0) return CS_OK;
+  const size_t eb = cfg->dtype == CS_F32 ? 4 : 8;
+  const int vec_ok = reinterpret_cast<uintptr_t>(c) % 16 == 0 && (cfg->nx * eb) % 16 == 0;
+  const dim3 grid(static_cast<unsigned>((cfg->nx + kWTX - 1) / kWTX), static_cast<unsigned>((cfg->ny + kWTY - 1) / kWTY));
+  if (grid.y > 65535u) return set_error(CS_EUNSUPPORTED, "ny = %lld exceeds the WENO grid limit", (long long)cfg->ny);
+  const double fx = 1e-99 * cfg->hx * cfg->hx, fy = 1e-99 * cfg->hy * cfg->hy;
+  if (cfg->dtype == CS_F32) {
+    k_weno_adv<float><<<grid, kWThreads, 0, st>>>(static_cast<const float*>(c), static_cast<const float*>(u),
+                                                  static_cast<const float*>(v), static_cast<float*>(out), cfg->nx,
+                                                  cfg->ny, vec_ok, static_cast<float>(1.0 / cfg->hx),
+                                                  static_cast<float>(1.0 / cfg->hy), 0.f, 0.f);
+  } else {
+    k_weno_adv<double><<<grid, kWThreads, 0, st>>>(static_cast<const double*>(c), static_cast<const double*>(u),
+                                                   static_cast<const double*>(v), static_cast<double*>(out), cfg->nx,
+                                                   cfg->ny, vec_ok, 1.0 / cfg->hx, 1.0 / cfg->hy, fx, fy);
+  }
+  CS_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return CS_OK;
+}
+
+}  // namespace cs

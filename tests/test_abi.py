@@ -114,6 +114,16 @@ def test_host_resident_plan_rejected_on_host(cs):
     assert rc_of(cs.cs_plan_host_info, None) == cs.CS_EINVAL
 
 
+def test_weno_plan_rejected_on_host(cs):
+    ok = dict(nx=64, ny=64, dtype=0, hx=0.1, hy=0.1)
+    bad = [dict(ok, hx=0.0), dict(ok, hy=float("inf")), dict(ok, dtype=7), dict(ok, nx=-1)]
+    for d in bad:
+        assert rc_of(cs.cs_plan_create_weno_adv, *d.values(), 1 << 30, 1 << 31, 1 << 32, 1 << 33) == cs.CS_EINVAL
+    assert rc_of(cs.cs_plan_create_weno_adv, *ok.values(), 0, 1 << 31, 1 << 32, 1 << 33) == cs.CS_EINVAL
+    # output overlapping u
+    assert rc_of(cs.cs_plan_create_weno_adv, *ok.values(), 1 << 30, 1 << 31, 1 << 32, (1 << 31) + 64) == cs.CS_EALIAS
+
+
 def test_wrong_plan_kind_rejected(cs):
     assert rc_of(cs.cs_ch_step, None, 1, False, 0) == cs.CS_EINVAL
     assert rc_of(cs.cs_ch_coarsening, None, 0) == cs.CS_EINVAL
