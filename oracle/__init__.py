@@ -15,6 +15,9 @@ What each routine computes, with the passage it follows:
 * ``ch_mass``, ``ch_energy`` -- the integral of C and the free energy F[C] of Eq. (1)
 * ``ch_coarsening_s``, ``ch_coarsening_k1`` -- the coarsening measures s(t) and k_1(t) of
   Sec. 5.1 "Numerical Results" (numpy; the FFT is numpy's)
+* ``ch_rhs_noflux``, ``noflux_penta_solve``, ``ch_step_noflux``, ``ch_run_noflux``,
+  ``ch_energy_noflux`` -- the same ADI scheme with no-flux boundaries (reflected ghost cells,
+  non-cyclic line solves; numpy, scipy's banded solve)
 * ``weno5_hj``, ``weno5_derivatives``, ``weno_advection`` -- the periodic XY WENO advection variant
   of Sec. 4.2 "Advection" (numpy), with the fifth-order Hamilton-Jacobi WENO derivatives of the
   reference it cites (Osher & Fedkiw, Sec. 3.4)
@@ -277,3 +280,97 @@ def weno_advection(c, u, v, hx: float, hy: float, **eps):
     cx_m, cx_p = weno5_derivatives(c, hx, 1, **eps)
     cy_m, cy_p = weno5_derivatives(c, hy, 0, **eps)
     return u * np.where(u > 0, cx_m, cx_p) + v * np.where(v > 0, cy_m, cy_p)
+
+
+# ---- Cahn-Hilliard with no-flux boundaries (the ADI scheme of Sec. 5.1 on a bounded domain) -------
+# Cell-centred grid x_i = (i + 1/2) h, h = 2 pi / n, on [0, 2 pi]^2; every stencil reads ghost cells
+# by even reflection about the boundary (C_{-1-k} = C_k, C_{n+k} = C_{n-1-k}), which imposes
+# dC/dn = 0 and d(lap C)/dn = 0, so no mass crosses the boundary.  The line operator becomes
+# L = I + a D4 with D4 the reflected 5-point fourth difference (numpy and scipy, FP64).
+
+def _reflect(f, width: int) -> np.ndarray:
+    return np.pad(_f64(f), width, mode="symmetric")  # [b a | a b c | c b]: even reflection
+
+
+def ch_rhs_noflux(c_prev, c_cur, D: float, gamma: float, dt: float) -> np.ndarray:
+    """-(2/3)(C^n - C^{n-1}) - (2/3) D gamma dt lap4(Cbar) + (2/3) D dt lap2(C^3 - C)^n with
+    Cbar = 2 C^n - C^{n-1}, lap4 the 13-point dxxxx + 2 dxxyy + dyyyy and lap2 the 5-point
+    Laplacian (Eq. 5), ghost cells by reflection."""
+    p, c = _f64(c_prev), _f64(c_cur)
+    n = c.shape[0]
+    h = 2.0 * np.pi / n
+    cb = _reflect(2.0 * c - p, 2)
+    s = lambda dj, di: cb[2 + dj:2 + dj + n, 2 + di:2 + di + n]  # Cbar at (j + dj, i + di)
+    dxxxx = s(0, -2) - 4 * s(0, -1) + 6 * s(0, 0) - 4 * s(0, 1) + s(0, 2)
+    dyyyy = s(-2, 0) - 4 * s(-1, 0) + 6 * s(0, 0) - 4 * s(1, 0) + s(2, 0)
+    dxxyy = (s(-1, -1) - 2 * s(-1, 0) + s(-1, 1)) - 2 * (s(0, -1) - 2 * s(0, 0) + s(0, 1)) \
+        + (s(1, -1) - 2 * s(1, 0) + s(1, 1))
+    lap4 = (dxxxx + 2 * dxxyy + dyyyy) / h ** 4
+    nl = _reflect(c ** 3 - c, 1)
+    t = lambda dj, di: nl[1 + dj:1 + dj + n, 1 + di:1 + di + n]
+    lap2 = (t(0, -1) + t(0, 1) + t(-1, 0) + t(1, 0) - 4 * t(0, 0)) / h ** 2
+    return -(2.0 / 3.0) * (c - p) - (2.0 / 3.0) * D * gamma * dt * lap4 + (2.0 / 3.0) * D * dt * lap2
+
+
+def noflux_line_matrix(n: int, a: float) -> np.ndarray:
+    """L = I + a D2 D2 (dense), D2 the reflected second difference (rows (1, -2, 1), first and
+    last rows (-1, 1) and (1, -1)); D2 D2 is the reflected fourth difference."""
+    d2 = np.diag(np.full(n, -2.0)) + np.diag(np.ones(n - 1), 1) + np.diag(np.ones(n - 1), -1)
+    d2[0, 0] = d2[-1, -1] = -1.0
+    return np.eye(n) + a * (d2 @ d2)
+
+
+def noflux_penta_solve(b, a: float) -> np.ndarray:
+    """Solves L x = b along the last axis of b (every line), L = noflux_line_matrix (banded
+    solve of its five diagonals)."""
+    from scipy.linalg import solve_banded
+    b = _f64(b)
+    n = b.shape[-1]
+    L = noflux_line_matrix(n, a)
+    ab = np.zeros((5, n))
+    for k in range(-2, 3):  # ab[2 + i - j, j] = L[i, j]
+        diag = np.diagonal(L, k)
+        if k >= 0:
+            ab[2 - k, k:] = diag
+        else:
+            ab[2 - k, :n + k] = diag
+    flat = b.reshape(-1, n)
+    return solve_banded((2, 2), ab, flat.T).T.reshape(b.shape)
+
+
+def ch_step_noflux(c_prev, c_cur, D: float, gamma: float, dt: float) -> np.ndarray:
+    """One ADI step (Eq. ch_adi) with no-flux boundaries: L_x w = RHS, L_y v = w, C^{n+1} = Cbar + v."""
+    p, c = _f64(c_prev), _f64(c_cur)
+    n = c.shape[0]
+    if c.shape != (n, n) or p.shape != (n, n):
+        raise ValueError("Cahn-Hilliard fields must be square n x n")
+    a = ch_coefficient_a(n, D, gamma, dt)
+    rhs = ch_rhs_noflux(p, c, D, gamma, dt)
+    w = noflux_penta_solve(rhs, a)          # lines along x (rows)
+    v = noflux_penta_solve(w.T, a).T        # lines along y (columns)
+    return 2.0 * c - p + v
+
+
+def ch_energy_noflux(c, gamma: float) -> float:
+    """Free energy of Eq. (1) by the rectangle rule with forward differences, the difference
+    across the boundary being zero (reflected ghost)."""
+    c = _f64(c)
+    n = c.shape[0]
+    h = 2.0 * np.pi / n
+    e = _reflect(c, 1)[1:n + 2, 1:n + 2]
+    gx = (e[:n, 1:n + 1] - c) / h
+    gy = (e[1:n + 1, :n] - c) / h
+    return float(h * h * np.sum(0.25 * (c * c - 1.0) ** 2 + 0.5 * gamma * (gx * gx + gy * gy)))
+
+
+def ch_run_noflux(c0, D: float, gamma: float, dt: float, nsteps: int):
+    """The time loop (C^{-1} := C^0) with no-flux boundaries: (C_final, mass[], energy[])."""
+    prev = cur = _f64(c0)
+    n = cur.shape[0]
+    h = 2.0 * np.pi / n
+    mass, energy = np.empty(nsteps), np.empty(nsteps)
+    for s in range(nsteps):
+        prev, cur = cur, ch_step_noflux(prev, cur, D, gamma, dt)
+        mass[s] = h * h * cur.sum()
+        energy[s] = ch_energy_noflux(cur, gamma)
+    return cur, mass, energy
