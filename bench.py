@@ -13,7 +13,7 @@ Cahn-Hilliard ADI steps/s (N = 1024, 4096; FP64 and FP32 storage) and the ragged
 sweep (65536 lines, log-uniform 64..4096, FP32, persistent launch replayed from a CUDA graph),
 the coarsening run of Sec. 5.1 (512^2 to t = 100, s(t) and k_1(t) on the device), and
 host-resident grids streamed through 256 MiB of device band slots, and the periodic XY WENO
-advection term (Sec. 4.2) at 8192^2.
+advection term (Sec. 4.2) at 8192^2, and the Cahn-Hilliard step with no-flux boundaries at 4096^2.
 
 --impl reference runs the CPU oracle (the reference arm of this build: a plain FP64 C program)
 on a bounded sample of the same workload.
@@ -344,6 +344,8 @@ def run_ours(args):
         parts["coarsening"] = bench_coarsening(cs, torch, stream)
         parts["streamed"] = bench_streamed(cs, torch, stream)
         parts["weno"] = bench_weno(cs, torch, stream, hbm_peak)
+        parts["ch_noflux"] = bench_ch(cs, torch, stream, [(4096, cs.CS_F64, 30, cs.CS_CH_NOFLUX),
+                                                          (4096, cs.CS_F32, 30, cs.CS_CH_NOFLUX)])
     for sw in sweeps:
         cs.cs_destroy(sw["plan"])
     line = {
@@ -413,12 +415,15 @@ def bench_ch(cs, torch, stream, cases=None):
     out = {}
     if cases is None:
         cases = [(1024, cs.CS_F64, 200), (4096, cs.CS_F64, 30), (1024, cs.CS_F32, 200), (4096, cs.CS_F32, 30)]
-    for n, storage, steps in cases:
+    for case in cases:
+        n, storage, steps = case[:3]
+        boundary = case[3] if len(case) > 3 else cs.CS_CH_PERIODIC
         h = 2 * np.pi / n
         tdt = torch.float64 if storage == cs.CS_F64 else torch.float32
         c0 = torch.from_numpy(W.ch_initial(n, seed=5)).to("cuda", tdt)
         f = [c0.clone(), c0.clone(), torch.zeros_like(c0)]
-        plan = cs.cs_ch_create(cs.CHDesc(n=n, storage=storage, D=1.0, gamma=0.01, dt=0.1 * h), *f)
+        plan = cs.cs_ch_create(cs.CHDesc(n=n, storage=storage, D=1.0, gamma=0.01, dt=0.1 * h,
+                                         boundary=boundary), *f)
         cs.cs_autotune(plan, stream)  # chunks per line of the partitioned line solves
         cs.cs_ch_step(plan, 5, stream=stream)
         torch.cuda.synchronize()
@@ -430,7 +435,7 @@ def bench_ch(cs, torch, stream, cases=None):
         ms = e0.elapsed_time(e1) / steps
         chunks, m = cs.cs_ch_config(plan)
         cs.cs_destroy(plan)
-        key = f"n{n}_{'f64' if storage == cs.CS_F64 else 'f32'}"
+        key = f"n{n}_{'f64' if storage == cs.CS_F64 else 'f32'}" + ("_noflux" if boundary == cs.CS_CH_NOFLUX else "")
         fp64_ops = ch_fp64_ops_per_point(storage == cs.CS_F64, chunks, m) * n * n
         out[key] = {"ms_per_step": round(ms, 4), "steps_per_s": round(1e3 / ms, 1),
                     "fp64_gops": round(fp64_ops / (ms * 1e-3) / 1e9, 1),
@@ -676,7 +681,7 @@ def run_reference(args):
 
 
 def run_part(args):
-    """One part of the metric on its own (used to profile it): --part ch:<n>:<f64|f32>:<steps>,
+    """One part of the metric on its own (used to profile it): --part ch:<n>:<f64|f32>:<steps>[:noflux],
     batch1d, serve, coarsening, streamed or weno."""
     import torch
     import paper_1902_09931_gb300 as cs
@@ -687,7 +692,8 @@ def run_part(args):
     kind = args.part.split(":")
     if kind[0] == "ch":
         n, dt, steps = int(kind[1]), kind[2], int(kind[3])
-        res = bench_ch(cs, torch, stream, [(n, cs.CS_F64 if dt == "f64" else cs.CS_F32, steps)])
+        bnd = cs.CS_CH_NOFLUX if len(kind) > 4 and kind[4] == "noflux" else cs.CS_CH_PERIODIC
+        res = bench_ch(cs, torch, stream, [(n, cs.CS_F64 if dt == "f64" else cs.CS_F32, steps, bnd)])
     elif kind[0] == "serve":
         res = bench_serve(cs, torch)
     elif kind[0] == "coarsening":
@@ -713,7 +719,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile-choice", type=int, default=-1, help="force a tile choice (0, 1, 2) instead of autotuning")
     ap.add_argument("--only", default="", help="profile one sweep: name,n,f64|f32,p|np")
-    ap.add_argument("--part", default="", help="run one part alone: ch:<n>:<f64|f32>:<steps>, batch1d, serve, coarsening, streamed or weno")
+    ap.add_argument("--part", default="", help="run one part alone: ch:<n>:<f64|f32>:<steps>[:noflux], batch1d, serve, coarsening, streamed or weno")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -237,7 +237,7 @@ int cs_tune_load(const char* path);
  * caller's buffers.  Destroying NULL is a no-op. */
 int cs_destroy(cs_plan_t plan);
 
-/* ---- Cahn-Hilliard ADI (Sec. 5.1), periodic on (0, 2 pi)^2 ---------------------------------
+/* ---- Cahn-Hilliard ADI (Sec. 5.1) on (0, 2 pi)^2, periodic or with no-flux boundaries --------
  * One step:  Cbar = 2 C^n - C^{n-1};
  *            RHS = -(2/3)(C^n - C^{n-1}) - (2/3) D gamma dt lap4(Cbar) + (2/3) D dt lap2(C^3 - C)^n;
  *            L_x w = RHS;  L_y v = w;  C^{n+1} = Cbar + v;  L = I + (2/3) D gamma dt d^4
@@ -248,11 +248,20 @@ int cs_destroy(cs_plan_t plan);
  *   n        grid points per side (n x n), a multiple of 64 in [64, 65536]
  *   storage  CS_F64, or CS_F32 (fields stored in FP32, stencils in FP32, solves in FP64)
  *   D, gamma mobility and interface parameter (Sec. 5.3: 1.0 and 0.01)
- *   dt       time step (Sec. 5.3: 0.1 h) */
+ *   dt       time step (Sec. 5.3: 0.1 h)
+ *   boundary CS_CH_PERIODIC (0, the paper's case) or CS_CH_NOFLUX: the same scheme on a
+ *            bounded domain, the np stencils plus a boundary treatment (Sec. 4's pattern) --
+ *            cell-centred points x_i = (i + 1/2) h, every stencil reading ghost cells by even
+ *            reflection (C_{-1-k} = C_k, C_{n+k} = C_{n-1-k}: dC/dn = 0 and d(lap C)/dn = 0,
+ *            so no mass crosses the boundary), and non-cyclic line solves with
+ *            L = I + a D4, D4 the reflected fourth difference (rows (2,-3,1), (-3,6,-4,1),
+ *            then (1,-4,6,-4,1), mirrored at the far end).  Mass and energy are as for periodic
+ *            fields, the forward difference across the boundary being zero. */
+typedef enum { CS_CH_PERIODIC = 0, CS_CH_NOFLUX = 1 } cs_ch_boundary;
 typedef struct {
   int64_t n;
   int32_t storage;
-  int32_t reserved;
+  int32_t boundary; /* cs_ch_boundary */
   double D, gamma, dt;
 } cs_ch_desc;
 
@@ -278,7 +287,7 @@ int cs_ch_invariants(cs_plan_t plan, double* mass, double* energy, void* cuda_st
  *         weight 2 and every odd-index point weight 4, total 3 n per direction);
  *   *k1 = sum |C^(k)|^2 / sum |k|^-1 |C^(k)|^2 over the n x n discrete wavenumbers of the 2D DFT
  *         (signed, |k| <= n / 2), with k = (0, 0) left out of both sums.
- * Either output may be NULL.  Requires n a power of two and n <= 8192 (CS_EUNSUPPORTED
+ * Either output may be NULL.  Requires a periodic plan, n a power of two and n <= 8192 (CS_EUNSUPPORTED
  * otherwise); uses the plan's n x n scratch, so it may be called only between steps on the
  * plan's stream.  The first call allocates 4 n + 4 doubles of device memory (CS_ENOMEM on
  * failure), held until cs_destroy.  Synchronises the stream. */

@@ -31,6 +31,7 @@ CS_DIR_X, CS_DIR_Y, CS_DIR_XY = 0, 1, 2
 CS_BC_NONPERIODIC, CS_BC_PERIODIC = 0, 1
 CS_F64, CS_F32 = 0, 1
 CS_FN_NONE, CS_FN_CENTRAL_D2X, CS_FN_CH_NONLIN_LAP, CS_FN_CUBIC_MINUS_LAP = 0, 1, 2, 3
+CS_CH_PERIODIC, CS_CH_NOFLUX = 0, 1
 CS_FP64_AUTO, CS_FP64_NATIVE = 0, 1
 CS_MAX_EXTENT = 16
 
@@ -52,7 +53,7 @@ class _CStencilDesc(ctypes.Structure):
 
 
 class _CCHDesc(ctypes.Structure):
-    _fields_ = [("n", ctypes.c_int64), ("storage", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    _fields_ = [("n", ctypes.c_int64), ("storage", ctypes.c_int32), ("boundary", ctypes.c_int32),
                 ("D", ctypes.c_double), ("gamma", ctypes.c_double), ("dt", ctypes.c_double)]
 
 
@@ -86,6 +87,7 @@ class CHDesc:
     D: float = 1.0
     gamma: float = 0.01
     dt: float = 0.0
+    boundary: int = 0  # CS_CH_PERIODIC, or CS_CH_NOFLUX (reflected ghost cells)
 
 
 _lib = None
@@ -288,7 +290,7 @@ def cs_destroy(plan) -> None:
 
 def cs_ch_create(desc: CHDesc, d_c_prev, d_c_cur, d_c_next) -> ctypes.c_void_p:
     c = _CCHDesc()
-    c.n, c.storage, c.reserved, c.D, c.gamma, c.dt = desc.n, desc.storage, 0, desc.D, desc.gamma, desc.dt
+    c.n, c.storage, c.boundary, c.D, c.gamma, c.dt = desc.n, desc.storage, desc.boundary, desc.D, desc.gamma, desc.dt
     plan = ctypes.c_void_p()
     _check(load().cs_ch_create(ctypes.byref(plan), ctypes.byref(c), _ptr(d_c_prev), _ptr(d_c_cur),
                                _ptr(d_c_next)))

@@ -24,6 +24,15 @@
 // chunk ends; phase 2 forms the two end values of each neighbouring chunk from the recorded
 // ends (16 P FMAs) and corrects x = g - S_L t_{p-1} - S_R h_{p+1}.  This is exact (up to
 // rounding) and gives n * P independent threads instead of n sequential lines.
+//
+// No-flux boundaries (cs_ch_desc.boundary = CS_CH_NOFLUX): the same step on a cell-centred
+// grid whose stencils read ghost cells by even reflection.  Reflection commutes with the
+// 5-point Laplacian, so the factored right-hand side holds unchanged -- only the tile loader
+// mirrors indices instead of wrapping them.  The line operator is non-cyclic, I + a D4 with the
+// reflected fourth difference (first rows (1+2a, -3a, a), (-3a, 1+6a, -4a, a)): the first and
+// last chunks of a line get their own LU factors and spikes, the couplings are the same, and the
+// chunk-end system is inverted as a dense 4P x 4P matrix (no longer block-circulant; applying it
+// still takes 16 P FMAs per chunk).
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -55,6 +64,7 @@ struct CHPlan {
   cudaGraphExec_t graph3[3];  // three steps (one buffer rotation) per starting rotation phase
   int graph_kernels;
   double* diag;  // coarsening measures: n/2 twiddles (re, im), 2 n partial sums, 4 results
+  int noflux;    // CS_CH_NOFLUX: reflected ghost cells, non-cyclic line solves
 };
 
 void drop_graphs(CHPlan* p);
@@ -102,6 +112,12 @@ template <> __device__ __forceinline__ void store_as<float>(float* p, double v) 
 __device__ __forceinline__ int wrapn(int64_t k, int64_t n) {
   return static_cast<int>(k < 0 ? k + n : (k >= n ? k - n : k));
 }
+// even reflection about the boundary: -1 -> 0, -2 -> 1, n -> n - 1, n + 1 -> n - 2
+__device__ __forceinline__ int mirrorn(int64_t k, int64_t n) {
+  return static_cast<int>(k < 0 ? -1 - k : (k >= n ? 2 * n - 1 - k : k));
+}
+// line-solve chunk type: bit 0 the line's first chunk, bit 1 its last (no-flux tables)
+__device__ __forceinline__ int chunk_type(int p, int P) { return (p == 0 ? 1 : 0) | (p == P - 1 ? 2 : 0); }
 
 template <typename T>
 __device__ __forceinline__ void block_reduce2(double m, double e, double* out2) {
@@ -127,7 +143,7 @@ __device__ __forceinline__ void block_reduce2(double m, double e, double* out2) 
 template <typename T, typename RT>
 __global__ void __launch_bounds__(kThreads)
     k_ch_rhs(const T* __restrict__ cur, const T* __restrict__ prev, RT* __restrict__ rhs, int64_t n,
-             T alpha, T a, double half_gamma_over_h2, double* __restrict__ partials) {
+             T alpha, T a, double half_gamma_over_h2, double* __restrict__ partials, int noflux) {
   constexpr int HR = kTY + 4, HC = kTX + 4;  // halo-2 tiles
   constexpr int ZR = kTY + 2, ZC = kTX + 2;  // halo-1 tile
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -138,7 +154,9 @@ __global__ void __launch_bounds__(kThreads)
   const int64_t y0 = static_cast<int64_t>(blockIdx.y) * kTY;
   for (int idx = threadIdx.x; idx < HR * HC; idx += kThreads) {
     const int r = idx / HC, c = idx - r * HC;
-    const int64_t off = static_cast<int64_t>(wrapn(y0 - 2 + r, n)) * n + wrapn(x0 - 2 + c, n);
+    const int64_t gy = y0 - 2 + r, gx = x0 - 2 + c;
+    const int64_t off = noflux ? static_cast<int64_t>(mirrorn(gy, n)) * n + mirrorn(gx, n)
+                               : static_cast<int64_t>(wrapn(gy, n)) * n + wrapn(gx, n);
     const T cv = cur[off];
     sc[idx] = cv;
     sb[idx] = T(2) * cv - prev[off];
@@ -326,7 +344,8 @@ __device__ __forceinline__ void store_batch(double* __restrict__ p, int64_t at, 
 // Phase 1: A g = b on chunk p of a line (LU forward then backward), g over the scratch.
 // Coefficients (negated / pre-scaled): nl1, nl2, dinv, nu1, nu2 at coef[0..5m).  Elements are
 // processed in register batches of kU so that a batch's loads are in flight together.
-template <typename IT, bool CONTIG>
+// NF: no-flux tables, one set of 9 m coefficients per chunk type.
+template <typename IT, bool CONTIG, bool NF>
 __global__ void __launch_bounds__(kSolveThreads)
     k_solve_local(const IT* __restrict__ in, double* __restrict__ G, double* __restrict__ bnd,
                   const double* __restrict__ coef, int64_t n, int P, int m, int64_t line_stride,
@@ -336,6 +355,7 @@ __global__ void __launch_bounds__(kSolveThreads)
   const int64_t line = t % n;
   const int p = static_cast<int>(t / n);
   const int64_t es = CONTIG ? 1 : elem_stride;
+  if constexpr (NF) coef += static_cast<int64_t>(chunk_type(p, P)) * 9 * m;
   const double* nl1 = coef;
   const double* nl2 = coef + m;
   const double* dinv = coef + 2 * m;
@@ -385,31 +405,59 @@ __global__ void __launch_bounds__(kSolveThreads)
 // shared memory), then the spike correction.  MODE 0 writes w (FP64); MODE 1 writes
 // C^{n+1} = 2 C^n - C^{n-1} + x (for FP32 storage 2 C^n - C^{n-1} is formed in FP32, as in the
 // right-hand side).
-template <int MODE, typename T, bool CONTIG>
+// NF: no-flux tables (per chunk type) and the dense 4P x 4P chunk-end inverse, read through the
+// read-only cache; the line's first chunk has no left neighbour, its last no right one.
+template <int MODE, typename T, bool CONTIG, bool NF>
 __global__ void __launch_bounds__(kSolveThreads)
     k_solve_correct(const double* __restrict__ G, const double* __restrict__ bnd,
                     const double* __restrict__ coef, const double* __restrict__ K, int64_t n, int P,
                     int m, int64_t line_stride, int64_t elem_stride, double* __restrict__ w_out,
                     const T* __restrict__ cur, const T* __restrict__ prev, T* __restrict__ next) {
   extern __shared__ double sK[];
-  for (int i = threadIdx.x; i < 16 * P; i += blockDim.x) sK[i] = K[i];
-  __syncthreads();
+  if constexpr (!NF) {
+    for (int i = threadIdx.x; i < 16 * P; i += blockDim.x) sK[i] = K[i];
+    __syncthreads();
+  }
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= n * P) return;
   const int64_t line = t % n;
   const int p = static_cast<int>(t / n);
   const int64_t es = CONTIG ? 1 : elem_stride;
-  const int pm = (p + P - 1) % P, pp = (p + 1) % P;
   double t0 = 0.0, t1 = 0.0, h0 = 0.0, h1 = 0.0;
-  for (int q = 0; q < P; ++q) {
-    const double* b = bnd + static_cast<int64_t>(q) * 4 * n + line;
-    const double g0 = b[0], g1 = b[n], g2 = b[2 * n], g3 = b[3 * n];
-    const double* Kt = sK + ((pm - q + P) % P) * 16;  // K_{(p-1)-q}: rows 2, 3 give t_{p-1}
-    const double* Kh = sK + ((pp - q + P) % P) * 16;  // K_{(p+1)-q}: rows 0, 1 give h_{p+1}
-    t0 = fma(Kt[8], g0, fma(Kt[9], g1, fma(Kt[10], g2, fma(Kt[11], g3, t0))));
-    t1 = fma(Kt[12], g0, fma(Kt[13], g1, fma(Kt[14], g2, fma(Kt[15], g3, t1))));
-    h0 = fma(Kh[0], g0, fma(Kh[1], g1, fma(Kh[2], g2, fma(Kh[3], g3, h0))));
-    h1 = fma(Kh[4], g0, fma(Kh[5], g1, fma(Kh[6], g2, fma(Kh[7], g3, h1))));
+  if constexpr (NF) {
+    coef += static_cast<int64_t>(chunk_type(p, P)) * 9 * m;
+    const int64_t N4 = 4 * static_cast<int64_t>(P);
+    const bool left = p > 0, right = p + 1 < P;
+    const double* Kt = left ? K + (4 * static_cast<int64_t>(p - 1) + 2) * N4 : K;  // rows of x_{p-1}[m-2], [m-1]
+    const double* Kh = right ? K + (4 * static_cast<int64_t>(p + 1)) * N4 : K;     // rows of x_{p+1}[0], [1]
+    for (int q = 0; q < P; ++q) {
+      const double* b = bnd + static_cast<int64_t>(q) * 4 * n + line;
+      const double g0 = b[0], g1 = b[n], g2 = b[2 * n], g3 = b[3 * n];
+      if (left) {
+        const double* r2 = Kt + 4 * q;
+        const double* r3 = r2 + N4;
+        t0 = fma(__ldg(r2), g0, fma(__ldg(r2 + 1), g1, fma(__ldg(r2 + 2), g2, fma(__ldg(r2 + 3), g3, t0))));
+        t1 = fma(__ldg(r3), g0, fma(__ldg(r3 + 1), g1, fma(__ldg(r3 + 2), g2, fma(__ldg(r3 + 3), g3, t1))));
+      }
+      if (right) {
+        const double* r0 = Kh + 4 * q;
+        const double* r1 = r0 + N4;
+        h0 = fma(__ldg(r0), g0, fma(__ldg(r0 + 1), g1, fma(__ldg(r0 + 2), g2, fma(__ldg(r0 + 3), g3, h0))));
+        h1 = fma(__ldg(r1), g0, fma(__ldg(r1 + 1), g1, fma(__ldg(r1 + 2), g2, fma(__ldg(r1 + 3), g3, h1))));
+      }
+    }
+  } else {
+    const int pm = (p + P - 1) % P, pp = (p + 1) % P;
+    for (int q = 0; q < P; ++q) {
+      const double* b = bnd + static_cast<int64_t>(q) * 4 * n + line;
+      const double g0 = b[0], g1 = b[n], g2 = b[2 * n], g3 = b[3 * n];
+      const double* Kt = sK + ((pm - q + P) % P) * 16;  // K_{(p-1)-q}: rows 2, 3 give t_{p-1}
+      const double* Kh = sK + ((pp - q + P) % P) * 16;  // K_{(p+1)-q}: rows 0, 1 give h_{p+1}
+      t0 = fma(Kt[8], g0, fma(Kt[9], g1, fma(Kt[10], g2, fma(Kt[11], g3, t0))));
+      t1 = fma(Kt[12], g0, fma(Kt[13], g1, fma(Kt[14], g2, fma(Kt[15], g3, t1))));
+      h0 = fma(Kh[0], g0, fma(Kh[1], g1, fma(Kh[2], g2, fma(Kh[3], g3, h0))));
+      h1 = fma(Kh[4], g0, fma(Kh[5], g1, fma(Kh[6], g2, fma(Kh[7], g3, h1))));
+    }
   }
   const double* sl0 = coef + 5 * m;
   const double* sl1 = coef + 6 * m;
@@ -469,6 +517,22 @@ void block_lu(int m, double a, std::vector<double>& l1, std::vector<double>& l2,
   }
 }
 
+// LU (no pivoting) of an m x m pentadiagonal block given by its bands: sub2[k] = A(k, k-2),
+// sub1[k] = A(k, k-1), diag[k], sup1[k] = A(k, k+1), sup2[k] = A(k, k+2).
+void penta_lu(int m, const std::vector<double>& sub2, const std::vector<double>& sub1,
+              const std::vector<double>& diag, const std::vector<double>& sup1,
+              const std::vector<double>& sup2, std::vector<double>& l1, std::vector<double>& l2,
+              std::vector<double>& d, std::vector<double>& u1, std::vector<double>& u2) {
+  l1.assign(m, 0.0); l2.assign(m, 0.0); d.assign(m, 0.0); u1.assign(m, 0.0); u2.assign(m, 0.0);
+  for (int k = 0; k < m; ++k) {
+    l2[k] = k >= 2 ? sub2[k] / d[k - 2] : 0.0;
+    l1[k] = k >= 1 ? (sub1[k] - (k >= 2 ? l2[k] * u1[k - 2] : 0.0)) / d[k - 1] : 0.0;
+    d[k] = diag[k] - (k >= 2 ? l2[k] * u2[k - 2] : 0.0) - (k >= 1 ? l1[k] * u1[k - 1] : 0.0);
+    u1[k] = k + 1 < m ? sup1[k] - (k >= 1 ? l1[k] * u2[k - 1] : 0.0) : 0.0;
+    u2[k] = k + 2 < m ? sup2[k] : 0.0;
+  }
+}
+
 void block_solve(int m, const std::vector<double>& l1, const std::vector<double>& l2,
                  const std::vector<double>& d, const std::vector<double>& u1,
                  const std::vector<double>& u2, std::vector<double>& x) {
@@ -515,7 +579,7 @@ bool invert(int N, std::vector<double>& M, std::vector<double>& inv) {
   return true;
 }
 
-int build_tables(int64_t n, int P, double a, std::vector<double>& coef, std::vector<double>& K) {
+int build_tables_periodic(int64_t n, int P, double a, std::vector<double>& coef, std::vector<double>& K) {
   const int m = static_cast<int>(n / P);
   std::vector<double> l1, l2, d, u1, u2;
   block_lu(m, a, l1, l2, d, u1, u2);
@@ -560,6 +624,75 @@ int build_tables(int64_t n, int P, double a, std::vector<double>& coef, std::vec
   return CS_OK;
 }
 
+// No-flux tables: for each chunk type t (bit 0: the line's first chunk, bit 1: its last) the LU
+// of the chunk block of L = I + a D4 (reflected rows at the line's ends) and the four spikes, at
+// coef[9 m t ..]; K = the dense inverse of the 4P x 4P chunk-end system, row-major.
+int build_tables_noflux(int64_t n, int P, double a, std::vector<double>& coef, std::vector<double>& K) {
+  const int m = static_cast<int>(n / P);
+  coef.assign(static_cast<size_t>(4) * 9 * m, 0.0);
+  std::vector<double> spk[4][4];  // [type][spike]
+  for (int t = 0; t < 4; ++t) {
+    std::vector<double> sub2(m, a), sub1(m, -4.0 * a), diag(m, 1.0 + 6.0 * a), sup1(m, -4.0 * a), sup2(m, a);
+    if (t & 1) {  // rows 0, 1 of the line: (1 + 2a, -3a, a), (-3a, 1 + 6a, -4a, a)
+      diag[0] = 1.0 + 2.0 * a;
+      sup1[0] = -3.0 * a;
+      sub1[1] = -3.0 * a;
+    }
+    if (t & 2) {  // rows n-2, n-1: mirrored
+      diag[m - 1] = 1.0 + 2.0 * a;
+      sub1[m - 1] = -3.0 * a;
+      sup1[m - 2] = -3.0 * a;
+    }
+    std::vector<double> l1, l2, d, u1, u2;
+    penta_lu(m, sub2, sub1, diag, sup1, sup2, l1, l2, d, u1, u2);
+    double* c = coef.data() + static_cast<size_t>(9) * m * t;
+    for (int k = 0; k < m; ++k) {
+      c[k] = -l1[k];
+      c[m + k] = -l2[k];
+      c[2 * m + k] = 1.0 / d[k];
+      c[3 * m + k] = -u1[k] / d[k];
+      c[4 * m + k] = -u2[k] / d[k];
+    }
+    for (int q = 0; q < 4; ++q) spk[t][q].assign(m, 0.0);
+    if (!(t & 1)) {  // couplings to the previous chunk's last two values
+      spk[t][0][0] = a;
+      spk[t][1][0] = -4.0 * a; spk[t][1][1] = a;
+    }
+    if (!(t & 2)) {  // couplings to the next chunk's first two values
+      spk[t][2][m - 2] = a; spk[t][2][m - 1] = -4.0 * a;
+      spk[t][3][m - 1] = a;
+    }
+    for (int q = 0; q < 4; ++q) {
+      block_solve(m, l1, l2, d, u1, u2, spk[t][q]);
+      for (int k = 0; k < m; ++k) c[static_cast<size_t>(5 + q) * m + k] = spk[t][q][k];
+    }
+  }
+  const int rows[4] = {0, 1, m - 2, m - 1};
+  const int N4 = 4 * P;
+  std::vector<double> R(static_cast<size_t>(N4) * N4, 0.0);
+  for (int i = 0; i < N4; ++i) R[static_cast<size_t>(i) * N4 + i] = 1.0;
+  for (int p = 0; p < P; ++p) {
+    const int t = (p == 0 ? 1 : 0) | (p == P - 1 ? 2 : 0);
+    for (int r = 0; r < 4; ++r) {
+      const size_t row = static_cast<size_t>(4 * p + r) * N4;
+      if (p > 0) {
+        R[row + 4 * (p - 1) + 2] += spk[t][0][rows[r]];
+        R[row + 4 * (p - 1) + 3] += spk[t][1][rows[r]];
+      }
+      if (p + 1 < P) {
+        R[row + 4 * (p + 1) + 0] += spk[t][2][rows[r]];
+        R[row + 4 * (p + 1) + 1] += spk[t][3][rows[r]];
+      }
+    }
+  }
+  if (!invert(N4, R, K)) return set_error(CS_EINVAL, "Cahn-Hilliard chunk system is singular");
+  return CS_OK;
+}
+
+int build_tables(int64_t n, int P, double a, bool noflux, std::vector<double>& coef, std::vector<double>& K) {
+  return noflux ? build_tables_noflux(n, P, a, coef, K) : build_tables_periodic(n, P, a, coef, K);
+}
+
 // Valid partition: P divides n, chunks of at least 16 points in whole register batches.
 bool valid_chunks(int64_t n, int P) {
   return P >= 1 && P <= 64 && n % P == 0 && (n / P) >= 16 && (n / P) % kU == 0;
@@ -599,31 +732,37 @@ int launch_rhs(CHPlan* p, bool with_rhs, double* partials, cudaStream_t s) {
   T* rhs = with_rhs ? reinterpret_cast<T*>(p->A) : nullptr;
   k_ch_rhs<T, T><<<grid, kThreads, rhs_smem_bytes(p->storage), s>>>(
       cur, prev, rhs, p->n, static_cast<T>(p->alpha), static_cast<T>(p->a),
-      0.5 * p->gamma / (p->h * p->h), partials);
+      0.5 * p->gamma / (p->h * p->h), partials, p->noflux);
   CS_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return CS_OK;
+}
+
+template <typename T, bool NF>
+void launch_solves(CHPlan* p, cudaStream_t s) {
+  const int64_t n = p->n;
+  const unsigned sgrid = static_cast<unsigned>((n * p->P + kSolveThreads - 1) / kSolveThreads);
+  const size_t ksmem = NF ? 0 : static_cast<size_t>(16) * p->P * sizeof(double);
+  // x-sweep: lines are rows (line stride n, element stride 1)
+  k_solve_local<T, true, NF><<<sgrid, kSolveThreads, 0, s>>>(reinterpret_cast<const T*>(p->A), p->B, p->bnd,
+                                                             p->coef, n, p->P, p->m, n, 1);
+  k_solve_correct<0, T, true, NF><<<sgrid, kSolveThreads, ksmem, s>>>(p->B, p->bnd, p->coef, p->K, n, p->P,
+                                                                      p->m, n, 1, p->A, nullptr, nullptr, nullptr);
+  // y-sweep: lines are columns (line stride 1, element stride n), update fused
+  k_solve_local<double, false, NF><<<sgrid, kSolveThreads, 0, s>>>(p->A, p->B, p->bnd, p->coef, n, p->P,
+                                                                   p->m, 1, n);
+  k_solve_correct<1, T, false, NF><<<sgrid, kSolveThreads, ksmem, s>>>(
+      p->B, p->bnd, p->coef, p->K, n, p->P, p->m, 1, n, nullptr,
+      static_cast<const T*>(p->field[p->icur]), static_cast<const T*>(p->field[p->iprev]),
+      static_cast<T*>(p->field[p->inext]));
 }
 
 template <typename T>
 int launch_step(CHPlan* p, double* partials, cudaStream_t s) {
   int rc = launch_rhs<T>(p, true, partials, s);
   if (rc != CS_OK) return rc;
-  const int64_t n = p->n;
-  const unsigned sgrid = static_cast<unsigned>((n * p->P + kSolveThreads - 1) / kSolveThreads);
-  const size_t ksmem = static_cast<size_t>(16) * p->P * sizeof(double);
-  // x-sweep: lines are rows (line stride n, element stride 1)
-  k_solve_local<T, true><<<sgrid, kSolveThreads, 0, s>>>(reinterpret_cast<const T*>(p->A), p->B, p->bnd,
-                                                         p->coef, n, p->P, p->m, n, 1);
-  k_solve_correct<0, T, true><<<sgrid, kSolveThreads, ksmem, s>>>(p->B, p->bnd, p->coef, p->K, n, p->P,
-                                                                  p->m, n, 1, p->A, nullptr, nullptr, nullptr);
-  // y-sweep: lines are columns (line stride 1, element stride n), update fused
-  k_solve_local<double, false><<<sgrid, kSolveThreads, 0, s>>>(p->A, p->B, p->bnd, p->coef, n, p->P,
-                                                               p->m, 1, n);
-  k_solve_correct<1, T, false><<<sgrid, kSolveThreads, ksmem, s>>>(
-      p->B, p->bnd, p->coef, p->K, n, p->P, p->m, 1, n, nullptr,
-      static_cast<const T*>(p->field[p->icur]), static_cast<const T*>(p->field[p->iprev]),
-      static_cast<T*>(p->field[p->inext]));
+  if (p->noflux) launch_solves<T, true>(p, s);
+  else launch_solves<T, false>(p, s);
   CS_CUDA_TRY(cudaGetLastError());
   count_launches(4);
   return CS_OK;
@@ -663,6 +802,8 @@ int ch_create(CHPlan** out, const cs_ch_desc* d, void* prev, void* cur, void* ne
   if (d->n < 64 || d->n % 64 != 0 || d->n > 65536)
     return set_error(CS_EINVAL, "n must be a multiple of 64 in [64, 65536]");
   if (d->storage != CS_F64 && d->storage != CS_F32) return set_error(CS_EINVAL, "storage must be CS_F64 or CS_F32");
+  if (d->boundary != CS_CH_PERIODIC && d->boundary != CS_CH_NOFLUX)
+    return set_error(CS_EINVAL, "boundary must be CS_CH_PERIODIC or CS_CH_NOFLUX");
   if (!(d->D > 0) || !(d->gamma >= 0) || !(d->dt > 0) || !std::isfinite(d->D) || !std::isfinite(d->gamma) || !std::isfinite(d->dt))
     return set_error(CS_EINVAL, "D > 0, gamma >= 0, dt > 0 and finite are required");
   if (!prev || !cur || !next) return set_error(CS_EINVAL, "null field buffer");
@@ -682,6 +823,7 @@ int ch_create(CHPlan** out, const cs_ch_desc* d, void* prev, void* cur, void* ne
   memset(p, 0, sizeof *p);
   p->n = d->n;
   p->storage = d->storage;
+  p->noflux = d->boundary == CS_CH_NOFLUX;
   p->D = d->D; p->gamma = d->gamma; p->dt = d->dt;
   p->h = 2.0 * M_PI / static_cast<double>(d->n);
   const double h2 = p->h * p->h;
@@ -690,7 +832,8 @@ int ch_create(CHPlan** out, const cs_ch_desc* d, void* prev, void* cur, void* ne
   int P = default_chunks(d->n);
   int choice;
   char key[96];
-  snprintf(key, sizeof key, "ch|%s|n%lld|sm%d", d->storage == CS_F32 ? "f32" : "f64", (long long)d->n, num_sms());
+  snprintf(key, sizeof key, "ch|%s%s|n%lld|sm%d", d->storage == CS_F32 ? "f32" : "f64",
+           p->noflux ? "|noflux" : "", (long long)d->n, num_sms());
   if (tune_lookup(key, &choice) && valid_chunks(d->n, choice)) P = choice;
   p->P = P;
   p->m = static_cast<int>(d->n / P);
@@ -698,7 +841,7 @@ int ch_create(CHPlan** out, const cs_ch_desc* d, void* prev, void* cur, void* ne
   p->iprev = 0; p->icur = 1; p->inext = 2;
   p->rhs_blocks = static_cast<int>((d->n / kTX) * (d->n / kTY));
   std::vector<double> coef, K;
-  int rc = build_tables(d->n, P, p->a, coef, K);
+  int rc = build_tables(d->n, P, p->a, p->noflux != 0, coef, K);
   if (rc != CS_OK) { free_plan(p); return rc; }
   const size_t nn = static_cast<size_t>(d->n) * d->n;
   cudaError_t e = cudaSuccess;
@@ -976,6 +1119,7 @@ __global__ void k_coarsening_final(const double* __restrict__ simpson, const dou
 }  // namespace
 
 int ch_coarsening(CHPlan* p, double* s_out, double* k1_out, cudaStream_t st) {
+  if (p->noflux) return set_error(CS_EUNSUPPORTED, "the coarsening measures are defined on the periodic grid");
   const int64_t n = p->n;
   int logn = 0;
   while ((int64_t(1) << logn) < n) ++logn;
@@ -1046,7 +1190,7 @@ namespace {
 // (Re)builds the partition tables and chunk-end buffer for P chunks per line.
 int set_partition(CHPlan* p, int P) {
   std::vector<double> coef, K;
-  int rc = build_tables(p->n, P, p->a, coef, K);
+  int rc = build_tables(p->n, P, p->a, p->noflux != 0, coef, K);
   if (rc != CS_OK) return rc;
   double *bnd = nullptr, *dcoef = nullptr, *dK = nullptr;
   cudaError_t e = cudaMalloc(&bnd, static_cast<size_t>(4) * P * p->n * sizeof(double));
@@ -1114,7 +1258,8 @@ int ch_autotune(CHPlan* p, cudaStream_t s) {
   if (e1) cudaEventDestroy(e1);
   if (rc != CS_OK) return rc;
   char key[96];
-  snprintf(key, sizeof key, "ch|%s|n%lld|sm%d", p->storage == CS_F32 ? "f32" : "f64", (long long)p->n, num_sms());
+  snprintf(key, sizeof key, "ch|%s%s|n%lld|sm%d", p->storage == CS_F32 ? "f32" : "f64",
+           p->noflux ? "|noflux" : "", (long long)p->n, num_sms());
   tune_store(key, best);
   return CS_OK;
 }

@@ -124,6 +124,11 @@ def test_weno_plan_rejected_on_host(cs):
     assert rc_of(cs.cs_plan_create_weno_adv, *ok.values(), 1 << 30, 1 << 31, 1 << 32, (1 << 31) + 64) == cs.CS_EALIAS
 
 
+def test_ch_boundary_rejected_on_host(cs):
+    d = cs.CHDesc(n=64, storage=cs.CS_F64, D=1.0, gamma=0.01, dt=0.01, boundary=2)
+    assert rc_of(cs.cs_ch_create, d, 1 << 30, 1 << 31, 1 << 32) == cs.CS_EINVAL
+
+
 def test_wrong_plan_kind_rejected(cs):
     assert rc_of(cs.cs_ch_step, None, 1, False, 0) == cs.CS_EINVAL
     assert rc_of(cs.cs_ch_coarsening, None, 0) == cs.CS_EINVAL
