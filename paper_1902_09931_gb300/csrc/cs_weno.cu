@@ -75,8 +75,8 @@ __device__ __forceinline__ T weno_linear(T v1, T v2, T v3, T v4, T v5) {
 }
 
 // WENO value of unscaled differences v1..v5 (in units of C; the caller divides by h), with
-// floor_h2 = 1e-99 h^2 the eps floor in those units.
-__device__ __forceinline__ double weno5(double v1, double v2, double v3, double v4, double v5, double floor_h2) {
+// floor_h2 = 1e-99 h^2 the eps floor in those units: all in FP64.
+__device__ __forceinline__ double weno5_fp64(double v1, double v2, double v3, double v4, double v5, double floor_h2) {
   const double m = fmax(fmax(fmax(fabs(v1), fabs(v2)), fmax(fabs(v3), fabs(v4))), fabs(v5));
   const int e = static_cast<int>(__double_as_longlong(m) >> 52);  // biased exponent of max |v|
   // e < 600: max|v| < 2^-423 and the floor (>= 1e-99 * 1e-120 for h >= 1e-60) outweighs every
@@ -92,6 +92,118 @@ __device__ __forceinline__ double weno5(double v1, double v2, double v3, double 
   return weno_linear<double>(v1, v2, v3, v4, v5);
 }
 
+// ---- FP64 storage, mixed precision ------------------------------------------------------------
+// GB300 issues FP64 at 1/64 of the FP32 rate, so only the steps that need FP64's 53 bits stay on
+// the FP64 pipe: the one-sided differences and the second differences a_k, b_k of the smoothness
+// indicators, where the cancellation happens (the indicators amplify an input error by ~200 in
+// the weights when S ~ eps).  Every other step runs in double-float arithmetic (a value as an
+// unevaluated pair of floats, error-free products and sums; ~2^-46 relative per operation) on the
+// FP32 pipe: the indicators S' = 12 S = 13 a^2 + 3 b^2, the candidates Phi' = 6 phi, eps' = 12 eps,
+// (S' + eps')^2, the products with weights 1 : 6 : 3 (the common factors 12^2, 6 and 0.1 cancel in
+// the ratio) and the division.  The error stays below ~1e-13 of max|v|.
+
+struct dd { float hi, lo; };
+__device__ __forceinline__ dd two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ dd fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dd dd_add(dd x, dd y) {
+  const dd s = two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ dd dd_neg(dd x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ dd dd_mul(dd x, dd y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ dd dd_mulf(dd x, float c) {  // c a small integer
+  const float p = __fmul_rn(x.hi, c);
+  return fast_two_sum(p, __fmaf_rn(x.lo, c, __fmaf_rn(x.hi, c, -p)));
+}
+__device__ __forceinline__ dd dd_sqr(dd x) {
+  const float p = __fmul_rn(x.hi, x.hi);
+  return fast_two_sum(p, __fmaf_rn(__fmul_rn(2.0f, x.hi), x.lo, __fmaf_rn(x.hi, x.hi, -p)));
+}
+
+// v * 2^(1023 - e) as a float pair, exactly up to the last 6 of v's 52 mantissa bits (relative
+// error <= 2^-46), by integer operations only; |v| 2^(1023 - e) < 2^-100 (negligible beside the
+// largest difference, >= 1) gives zero.
+__device__ __forceinline__ dd split_scaled(double v, int e) {
+  const uint32_t hw = static_cast<uint32_t>(__double2hiint(v)), lw = static_cast<uint32_t>(__double2loint(v));
+  const int k = static_cast<int>((hw >> 20) & 0x7ffu) - e;  // exponent of the scaled value
+  if (((hw >> 20) & 0x7ffu) == 0u || k < -100) return {0.0f, 0.0f};
+  const uint32_t sign = hw & 0x80000000u;
+  const float hi = __uint_as_float(sign | (static_cast<uint32_t>(k + 127) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+  float lo = 0.0f;
+  if (k >= -80) {  // next 23 mantissa bits, scaled by 2^(k - 46) (a normal float)
+    const float r = __fsub_rn(__uint_as_float(0x4b000000u | ((lw & 0x1fffffffu) >> 6)), 8388608.0f);
+    lo = __uint_as_float(__float_as_uint(__fmul_rn(r, __uint_as_float(static_cast<uint32_t>(k + 81) << 23))) | sign);
+  }
+  return {hi, lo};
+}
+
+// 12e-6 as a float pair
+constexpr float kEps12Hi = 1.2e-5f;
+constexpr float kEps12Lo = static_cast<float>(1.2e-5 - static_cast<double>(1.2e-5f));
+
+__device__ __forceinline__ double weno5(double v1, double v2, double v3, double v4, double v5, double floor_h2) {
+  // exact max |v|: non-negative doubles order as their bit patterns
+  const unsigned long long mask = 0x7fffffffffffffffull;
+  unsigned long long mb = static_cast<unsigned long long>(__double_as_longlong(v1)) & mask;
+  mb = max(mb, static_cast<unsigned long long>(__double_as_longlong(v2)) & mask);
+  mb = max(mb, static_cast<unsigned long long>(__double_as_longlong(v3)) & mask);
+  mb = max(mb, static_cast<unsigned long long>(__double_as_longlong(v4)) & mask);
+  mb = max(mb, static_cast<unsigned long long>(__double_as_longlong(v5)) & mask);
+  const int e = static_cast<int>(mb >> 52);
+  // fl = floor_h2 2^(2 (1023 - e)), by exponent arithmetic (floor_h2 is a normal double: h >= 1e-60)
+  const unsigned long long fb = static_cast<unsigned long long>(__double_as_longlong(floor_h2));
+  const int fe = static_cast<int>(fb >> 52) + 2 * (1023 - e);  // biased exponent of fl
+  // fl >= 2^19 (the floor outweighs the indicators), or max|v| outside the scaled range: FP64
+  if (e < 600 || e > 2045 || fe >= 1023 + 19) return weno5_fp64(v1, v2, v3, v4, v5, floor_h2);
+  const double fl = fe >= 1 ? __longlong_as_double(static_cast<long long>((fb & 0xfffffffffffffull) |
+                                                                        (static_cast<unsigned long long>(fe) << 52)))
+                            : 0.0;
+  // FP64: the second differences of the indicators
+  const double a1 = fma(-2.0, v2, v1) + v3, b1 = fma(3.0, v3, fma(-4.0, v2, v1));
+  const double a2 = fma(-2.0, v3, v2) + v4, b2 = v2 - v4;
+  const double a3 = fma(-2.0, v4, v3) + v5, b3 = fma(3.0, v3, fma(-4.0, v4, v5));
+  // double-float from here, on values scaled by 2^(1023 - e)
+  const dd w1 = split_scaled(v1, e), w2 = split_scaled(v2, e), w3 = split_scaled(v3, e);
+  const dd w4 = split_scaled(v4, e), w5 = split_scaled(v5, e);
+  auto ind = [&](double a, double b) {  // 12 S = 13 a^2 + 3 b^2
+    return dd_add(dd_mulf(dd_sqr(split_scaled(a, e)), 13.0f), dd_mulf(dd_sqr(split_scaled(b, e)), 3.0f));
+  };
+  const dd s1 = ind(a1, b1), s2 = ind(a2, b2), s3 = ind(a3, b3);
+  // 6 phi_k
+  const dd p1 = dd_add(dd_add({__fmul_rn(2.0f, w1.hi), __fmul_rn(2.0f, w1.lo)}, dd_mulf(w2, -7.0f)), dd_mulf(w3, 11.0f));
+  const dd p2 = dd_add(dd_add(dd_neg(w2), dd_mulf(w3, 5.0f)), {__fmul_rn(2.0f, w4.hi), __fmul_rn(2.0f, w4.lo)});
+  const dd p3 = dd_add(dd_add({__fmul_rn(2.0f, w3.hi), __fmul_rn(2.0f, w3.lo)}, dd_mulf(w4, 5.0f)), dd_neg(w5));
+  // 12 eps = 12e-6 max w^2 + 12 floor
+  const dd mw = split_scaled(__longlong_as_double(static_cast<long long>(mb)), e);
+  dd eps = dd_mul(dd_sqr(mw), {kEps12Hi, kEps12Lo});
+  eps = dd_add(eps, dd_mulf(split_scaled(fl, 1023), 12.0f));
+  const dd q1 = dd_sqr(dd_add(s1, eps)), q2 = dd_sqr(dd_add(s2, eps)), q3 = dd_sqr(dd_add(s3, eps));
+  const dd P1 = dd_mul(q2, q3), P2 = dd_mulf(dd_mul(q1, q3), 6.0f), P3 = dd_mulf(dd_mul(q1, q2), 3.0f);
+  const dd num = dd_add(dd_add(dd_mul(P1, p1), dd_mul(P2, p2)), dd_mul(P3, p3));
+  const dd den = dd_add(dd_add(P1, P2), P3);
+  // num / den: one correction step on a correctly rounded reciprocal
+  const float rcp = __frcp_rn(den.hi);
+  const float y1 = __fmul_rn(num.hi, rcp);
+  const dd r = dd_add(num, dd_neg(dd_mulf(den, y1)));
+  const dd y = fast_two_sum(y1, __fmul_rn(r.hi, rcp));
+  // back to FP64: (hi + lo) * 2^(e - 1023) / 6
+  const double sixth = __longlong_as_double(static_cast<long long>(0x3fc5555555555555ull + (static_cast<unsigned long long>(e - 1023) << 52)));
+  return (s2d::f2d_exact(y.hi) + s2d::f2d_exact(y.lo)) * sixth;
+}
+
 // FP32: the floor (1e-99 h^2, below FP32's range) is left out; it changes eps by a relative
 // 1e-99 h^2 / (1e-6 max v^2), i.e. nothing unless the differences are denormal.
 __device__ __forceinline__ float weno5(float v1, float v2, float v3, float v4, float v5, float) {
@@ -104,6 +216,11 @@ __device__ __forceinline__ float weno5(float v1, float v2, float v3, float v4, f
   }
   return weno_linear<float>(v1, v2, v3, v4, v5);
 }
+
+// u > 0 by the bit pattern (integer compare; a nan with the sign bit clear counts as positive,
+// which changes nothing: the term is nan either way)
+__device__ __forceinline__ bool positive(double u) { return __double_as_longlong(u) > 0; }
+__device__ __forceinline__ bool positive(float u) { return __float_as_int(u) > 0; }
 
 // d[k] = C(i + k - 2) - C(i + k - 3), k = 0..5 (the differences at i - 3 .. i + 2); upwind
 // selection: left-biased (d0..d4) for a positive velocity, right-biased (d5..d1) otherwise.
@@ -146,8 +263,8 @@ __global__ void __launch_bounds__(kWThreads)
     }
     const int64_t o = gy * nx + gx;
     const T uu = u[o], vv = v[o];
-    const T fx = upwind<T>(dx, uu > T(0), floor_x) * inv_hx;
-    const T fy = upwind<T>(dy, vv > T(0), floor_y) * inv_hy;
+    const T fx = upwind<T>(dx, positive(uu), floor_x) * inv_hx;
+    const T fy = upwind<T>(dy, positive(vv), floor_y) * inv_hy;
     out[o] = fma_(uu, fx, vv * fy);
     if (r + 1 < kWRows) {
 #pragma unroll
