@@ -24,6 +24,7 @@
 // combination sum_k g_k phi_k is taken directly (this covers all-zero and tiny differences).
 
 #include <cmath>
+#include <cstring>
 
 #include "cs_internal.h"
 #include "cs_stencil2d_kernels.cuh"
@@ -76,7 +77,7 @@ __device__ __forceinline__ T weno_linear(T v1, T v2, T v3, T v4, T v5) {
 
 // WENO value of unscaled differences v1..v5 (in units of C; the caller divides by h), with
 // floor_h2 = 1e-99 h^2 the eps floor in those units: all in FP64.
-__device__ __forceinline__ double weno5_fp64(double v1, double v2, double v3, double v4, double v5, double floor_h2) {
+__device__ __noinline__ double weno5_fp64(double v1, double v2, double v3, double v4, double v5, double floor_h2) {
   const double m = fmax(fmax(fmax(fabs(v1), fabs(v2)), fmax(fabs(v3), fabs(v4))), fabs(v5));
   const int e = static_cast<int>(__double_as_longlong(m) >> 52);  // biased exponent of max |v|
   // e < 600: max|v| < 2^-423 and the floor (>= 1e-99 * 1e-120 for h >= 1e-60) outweighs every
@@ -150,6 +151,51 @@ __device__ __forceinline__ dd split_scaled(double v, int e) {
   return {hi, lo};
 }
 
+// ---- exact second differences on the integer pipe ----
+// v * 2^(1082 - e) truncated to an integer (|v| < 2^(e - 1022) gives |I| < 2^60, so the indicator
+// combinations, at most 8 I in size, stay below 2^63); bits below 2^-60 of max|v| are dropped.
+__host__ __device__ __forceinline__ long long fixed_of(unsigned long long bits, int e) {
+  const int ev = static_cast<int>((bits >> 52) & 0x7ffu);
+  if (ev == 0) return 0;
+  const unsigned long long mant = (bits & 0xfffffffffffffull) | (1ull << 52);
+  const int sh = ev - e + 7;  // <= 7
+  const unsigned long long u = sh >= 0 ? (mant << sh) : (sh > -53 ? (mant >> -sh) : 0ull);
+  return (bits >> 63) ? -static_cast<long long>(u) : static_cast<long long>(u);
+}
+
+__host__ __device__ __forceinline__ int clz64(unsigned long long x) {
+#ifdef __CUDA_ARCH__
+  return __clzll(static_cast<long long>(x));
+#else
+  return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
+__host__ __device__ __forceinline__ float float_of_bits(unsigned int b) {
+  float f;
+  memcpy(&f, &b, sizeof f);
+  return f;
+}
+
+// The integer A (|A| < 2^63) times 2^-59 as a float pair: the leading 24 bits, then the next 24
+// (relative error <= 2^-48 of |A|).  A = I-combinations of fixed_of values, so A 2^-59 is the
+// combination of the values scaled by 2^(1023 - e).
+__host__ __device__ __forceinline__ void dd_of_fixed(long long A, float& hi, float& lo) {
+  hi = lo = 0.0f;
+  if (A == 0) return;
+  const unsigned int sign = A < 0 ? 0x80000000u : 0u;
+  unsigned long long U = A < 0 ? static_cast<unsigned long long>(-A) : static_cast<unsigned long long>(A);
+  const int p = 63 - clz64(U);  // leading bit
+  unsigned long long H = p >= 23 ? (U >> (p - 23)) : (U << (23 - p));
+  hi = float_of_bits(sign | (static_cast<unsigned int>(p + 68) << 23) | static_cast<unsigned int>(H & 0x7fffffu));
+  if (p <= 23) return;  // no bits left
+  const unsigned long long R = U - (H << (p - 23));
+  if (R == 0) return;
+  const int q = 63 - clz64(R);
+  const unsigned long long L = q >= 23 ? (R >> (q - 23)) : (R << (23 - q));
+  lo = float_of_bits(sign | (static_cast<unsigned int>(q + 68) << 23) | static_cast<unsigned int>(L & 0x7fffffu));
+}
+
 // 12e-6 as a float pair
 constexpr float kEps12Hi = 1.2e-5f;
 constexpr float kEps12Lo = static_cast<float>(1.2e-5 - static_cast<double>(1.2e-5f));
@@ -171,17 +217,24 @@ __device__ __forceinline__ double weno5(double v1, double v2, double v3, double 
   const double fl = fe >= 1 ? __longlong_as_double(static_cast<long long>((fb & 0xfffffffffffffull) |
                                                                         (static_cast<unsigned long long>(fe) << 52)))
                             : 0.0;
-  // FP64: the second differences of the indicators
-  const double a1 = fma(-2.0, v2, v1) + v3, b1 = fma(3.0, v3, fma(-4.0, v2, v1));
-  const double a2 = fma(-2.0, v3, v2) + v4, b2 = v2 - v4;
-  const double a3 = fma(-2.0, v4, v3) + v5, b3 = fma(3.0, v3, fma(-4.0, v4, v5));
+  // the second differences of the indicators, exactly, in 64-bit integers
+  const long long i1 = fixed_of(static_cast<unsigned long long>(__double_as_longlong(v1)), e);
+  const long long i2 = fixed_of(static_cast<unsigned long long>(__double_as_longlong(v2)), e);
+  const long long i3 = fixed_of(static_cast<unsigned long long>(__double_as_longlong(v3)), e);
+  const long long i4 = fixed_of(static_cast<unsigned long long>(__double_as_longlong(v4)), e);
+  const long long i5 = fixed_of(static_cast<unsigned long long>(__double_as_longlong(v5)), e);
   // double-float from here, on values scaled by 2^(1023 - e)
   const dd w1 = split_scaled(v1, e), w2 = split_scaled(v2, e), w3 = split_scaled(v3, e);
   const dd w4 = split_scaled(v4, e), w5 = split_scaled(v5, e);
-  auto ind = [&](double a, double b) {  // 12 S = 13 a^2 + 3 b^2
-    return dd_add(dd_mulf(dd_sqr(split_scaled(a, e)), 13.0f), dd_mulf(dd_sqr(split_scaled(b, e)), 3.0f));
+  auto ind = [&](long long a, long long b) {  // 12 S = 13 a^2 + 3 b^2
+    dd da, db;
+    dd_of_fixed(a, da.hi, da.lo);
+    dd_of_fixed(b, db.hi, db.lo);
+    return dd_add(dd_mulf(dd_sqr(da), 13.0f), dd_mulf(dd_sqr(db), 3.0f));
   };
-  const dd s1 = ind(a1, b1), s2 = ind(a2, b2), s3 = ind(a3, b3);
+  const dd s1 = ind(i1 - 2 * i2 + i3, i1 - 4 * i2 + 3 * i3);
+  const dd s2 = ind(i2 - 2 * i3 + i4, i2 - i4);
+  const dd s3 = ind(i3 - 2 * i4 + i5, 3 * i3 - 4 * i4 + i5);
   // 6 phi_k
   const dd p1 = dd_add(dd_add({__fmul_rn(2.0f, w1.hi), __fmul_rn(2.0f, w1.lo)}, dd_mulf(w2, -7.0f)), dd_mulf(w3, 11.0f));
   const dd p2 = dd_add(dd_add(dd_neg(w2), dd_mulf(w3, 5.0f)), {__fmul_rn(2.0f, w4.hi), __fmul_rn(2.0f, w4.lo)});
@@ -250,7 +303,9 @@ __global__ void __launch_bounds__(kWThreads)
   T col[2 * kWHalo + 1];  // C at rows y - 3 .. y + 3 of this column
 #pragma unroll
   for (int k = 0; k < 2 * kWHalo + 1; ++k) col[k] = colp[(r0 + k) * kWCols];
-#pragma unroll
+  // the row loop stays rolled for FP64 storage: its double-float body is large, and unrolled
+  // copies overflow the instruction cache
+#pragma unroll(sizeof(T) == 4 ? kWRows : 1)
   for (int r = 0; r < kWRows; ++r) {
     const int64_t gy = y0 + r0 + r;
     if (gy >= ny) break;
