@@ -11,7 +11,9 @@
 // Tiles: 64 x 32 outputs per CTA of 256 threads; C (with a 3-point periodic halo) staged in
 // shared memory by the 2D stencil's tile loader; u and v read once per point from global memory.
 // A thread owns one column and walks 8 consecutive rows, keeping its 7-point y window in
-// registers.  Arithmetic in the storage type (FP64 for FP64 fields, FP32 for FP32 fields).
+// registers.  FP32 fields: FP32 arithmetic.  FP64 fields: the differences and the output in FP64,
+// the weights in exact integer and double-float arithmetic (below), with the all-FP64 formula
+// kept for points outside that path's range.
 //
 // The weights.  With v1..v5 the five one-sided differences, candidates phi_k, smoothness
 // indicators S_k and q_k = (S_k + eps)^2, the WENO value is
