@@ -1,0 +1,165 @@
+"""Decomposition of one grid over several GPUs (one process per GPU, torch.distributed).
+
+The paper sketches the multi-GPU extension as non-periodic stencils plus halo swaps between
+ranks (Sec. 6.2, MPI).  Here:
+
+* 2D stencils: the grid is cut into contiguous row bands along y (the layout of the paper's
+  y-tiles, Sec. 2).  Before a sweep each rank receives the ``top`` rows above its band and the
+  ``bottom`` rows below it from its neighbours; with periodic rows the last and first ranks are
+  neighbours.  The sweep then runs on the padded band; the halo rows' own outputs are dropped.
+* Cahn-Hilliard ADI (Sec. 5.1): the right-hand side needs a 2-row halo of C^n and C^{n-1}; the
+  x-line solves are local to a row band; the y-line solves run after an all-to-all transpose that
+  gives every rank a band of columns, and a second transpose brings the result back.  Mass and
+  energy are sums of per-rank FP64 partials (an allreduce).
+
+Everything here is communication and index bookkeeping: the arithmetic of a band is a callable
+the caller supplies (a device plan of this library on the GPU path).  Point-to-point exchanges use
+``isend`` / ``irecv``, so any backend works (gloo for CPU tensors, NCCL for CUDA tensors).
+"""
+from __future__ import annotations
+
+from typing import Callable
+
+import torch
+import torch.distributed as dist
+
+_TAG_TOP, _TAG_BOTTOM, _TAG_T = 11, 12, 13
+
+
+def band(n: int, world: int, rank: int) -> tuple[int, int]:
+    """Rows [r0, r1) of rank `rank` when n rows are cut into `world` contiguous bands whose sizes
+    differ by at most one (the first n % world bands take the extra row)."""
+    base, extra = divmod(n, world)
+    r0 = rank * base + min(rank, extra)
+    return r0, r0 + base + (1 if rank < extra else 0)
+
+
+def exchange_halo(local: torch.Tensor, top: int, bottom: int, periodic: bool, group=None):
+    """The band `local` (rows x nx) with the `top` rows of the band above and the `bottom` rows of
+    the band below stacked on.  Non-periodic grids have no neighbour beyond their first and last
+    bands, and those bands get no halo on that side.  Returns (padded, top_rows, bottom_rows): the
+    halo rows actually added on each side."""
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    rows, nx = local.shape
+    if rows < max(top, bottom):
+        raise ValueError(f"band of {rows} rows is thinner than the stencil's reach ({top}, {bottom})")
+    has_top = top > 0 and (periodic or rank > 0)
+    has_bottom = bottom > 0 and (periodic or rank < world - 1)
+    up, down = (rank - 1) % world, (rank + 1) % world
+    if world == 1:  # the only band is its own neighbour
+        t = local[rows - top:] if has_top else local[:0]
+        b = local[:bottom] if has_bottom else local[:0]
+        return torch.cat([t, local, b]), (top if has_top else 0), (bottom if has_bottom else 0)
+    recv_top = torch.empty((top, nx), dtype=local.dtype, device=local.device) if has_top else None
+    recv_bottom = torch.empty((bottom, nx), dtype=local.dtype, device=local.device) if has_bottom else None
+    reqs = []
+    if has_top:
+        reqs.append(dist.irecv(recv_top, src=up, group=group, tag=_TAG_TOP))
+    if has_bottom:
+        reqs.append(dist.irecv(recv_bottom, src=down, group=group, tag=_TAG_BOTTOM))
+    # my last `top` rows are the top halo of the band below; my first `bottom` rows the bottom
+    # halo of the band above
+    if top > 0 and (periodic or rank < world - 1):
+        reqs.append(dist.isend(local[rows - top:].contiguous(), dst=down, group=group, tag=_TAG_TOP))
+    if bottom > 0 and (periodic or rank > 0):
+        reqs.append(dist.isend(local[:bottom].contiguous(), dst=up, group=group, tag=_TAG_BOTTOM))
+    for r in reqs:
+        r.wait()
+    parts = ([recv_top] if has_top else []) + [local] + ([recv_bottom] if has_bottom else [])
+    return torch.cat(parts), (top if has_top else 0), (bottom if has_bottom else 0)
+
+
+def sharded_sweep(local: torch.Tensor, compute: Callable[[torch.Tensor], torch.Tensor], top: int,
+                  bottom: int, periodic: bool, group=None) -> torch.Tensor:
+    """One stencil sweep of a row band: halo exchange, then `compute` on the padded band (a
+    stencil with the grid's x boundary; its rows' wrap or untouched edges only reach halo rows),
+    then the band's own rows of the result."""
+    padded, t, _ = exchange_halo(local, top, bottom, periodic, group)
+    out = compute(padded)
+    return out[t:t + local.shape[0]]
+
+
+def transpose_bands(local: torch.Tensor, n: int, group=None) -> torch.Tensor:
+    """Row band -> column band of an n x n field: rank q holds rows band(n, world, q) of A and
+    receives rows band(n, world, q) of A^T (the columns of its band, as rows)."""
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    r0, r1 = band(n, world, rank)
+    if local.shape != (r1 - r0, n):
+        raise ValueError(f"band of shape {tuple(local.shape)}, expected {(r1 - r0, n)}")
+    out = torch.empty((r1 - r0, n), dtype=local.dtype, device=local.device)
+    out[:, r0:r1] = local[:, r0:r1].t()  # my rows x my columns
+    # from every other rank q: its rows x my columns, transposed into my rows of A^T
+    reqs = []
+    recv = {}
+    for q in range(world):
+        if q == rank:
+            continue
+        q0, q1 = band(n, world, q)
+        recv[q] = torch.empty((q1 - q0, r1 - r0), dtype=local.dtype, device=local.device)
+        reqs.append(dist.irecv(recv[q], src=q, group=group, tag=_TAG_T))
+    for q in range(world):
+        if q == rank:
+            continue
+        c0, c1 = band(n, world, q)
+        reqs.append(dist.isend(local[:, c0:c1].contiguous(), dst=q, group=group, tag=_TAG_T))
+    for r in reqs:
+        r.wait()
+    for q, blk in recv.items():
+        q0, q1 = band(n, world, q)
+        out[:, q0:q1] = blk.t()
+    return out
+
+
+def allreduce_sum(values: torch.Tensor, group=None) -> torch.Tensor:
+    """Sum over ranks of per-rank FP64 partial sums (mass, energy)."""
+    t = values.to(torch.float64).clone()
+    dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    return t
+
+
+def sharded_ch_step(prev: torch.Tensor, cur: torch.Tensor, n: int,
+                    rhs: Callable[[torch.Tensor, torch.Tensor], torch.Tensor],
+                    line_solve: Callable[[torch.Tensor], torch.Tensor], group=None) -> torch.Tensor:
+    """One ADI step (Sec. 5.1) of row bands of C^{n-1}, C^n of an n x n periodic grid.
+    `rhs(prev_padded, cur_padded)` returns the right-hand side of the band from the bands padded
+    with 2 rows each side; `line_solve(b)` solves (I + a P) x = b along the last axis of b."""
+    pp, _, _ = exchange_halo(prev, 2, 2, True, group)
+    cp, _, _ = exchange_halo(cur, 2, 2, True, group)
+    w = line_solve(rhs(pp, cp))                       # x-lines: rows of the band
+    v = line_solve(transpose_bands(w, n, group))      # y-lines: columns, as rows
+    return 2 * cur - prev + transpose_bands(v, n, group)
+
+
+class DeviceBandSweep:
+    """`compute` for sharded_sweep on the GPU: a 2D plan of this library over the padded band
+    (created on first use and kept while the padded shape stays the same; its output buffer starts
+    at zero, so cells a non-periodic sweep leaves untouched come back as zeros).  `desc_kw` are the
+    StencilDesc fields other than nx, ny."""
+
+    def __init__(self, desc_kw: dict, stream=None):
+        from . import StencilDesc, cs_plan_create_2d
+        self._desc_kw = dict(desc_kw)
+        self._make = lambda nx, ny, i, o: cs_plan_create_2d(StencilDesc(nx=nx, ny=ny, **self._desc_kw), i, o)
+        self._stream = stream
+        self._plan = None
+        self._bufs = None
+
+    def __call__(self, padded: torch.Tensor) -> torch.Tensor:
+        from . import cs_compute
+        ny, nx = padded.shape
+        if self._bufs is None or self._bufs[0].shape != padded.shape or self._bufs[0].dtype != padded.dtype:
+            self.close()
+            self._bufs = (torch.empty_like(padded), torch.zeros_like(padded))
+            self._plan = self._make(nx, ny, self._bufs[0], self._bufs[1])
+        self._bufs[0].copy_(padded)
+        cs_compute(self._plan, self._stream)
+        return self._bufs[1].clone()
+
+    def close(self):
+        if self._plan is not None:
+            from . import cs_destroy
+            cs_destroy(self._plan)
+        self._plan = None
+        self._bufs = None

@@ -1,0 +1,162 @@
+"""The multi-GPU decomposition (row bands with halo exchange; the CH step's all-to-all
+transposes and allreduced invariants) on CPU ranks over gloo: a sharded oracle must equal the
+unsharded one.  World sizes 2 and 3, band heights that differ by one row, periodic and
+non-periodic stencils, and the transpose on its own."""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _init(rank, world, port):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    return dist
+
+
+STENCILS = [  # (name, L, R, T, B, dir)
+    ("lap9", 1, 1, 1, 1, 2), ("biharm13", 2, 2, 2, 2, 2), ("ddy4", 0, 0, 2, 2, 1),
+    ("asym", 3, 1, 0, 2, 2), ("generic", 2, 3, 4, 1, 2),
+]
+
+
+def _stencil_worker(rank, world, port, q):
+    dist = _init(rank, world, port)
+    import torch
+    import oracle
+    import workloads as W
+    from paper_1902_09931_gb300 import distributed as D
+    ny, nx = 47, 36
+    u = W.sines_field(nx, seed=3, ny=ny)
+    rng = np.random.default_rng(5)
+    r0, r1 = D.band(ny, world, rank)
+    ok = []
+    for name, L, R, T, B, d in STENCILS:
+        w = rng.uniform(-1, 1, (L + R + 1) * (T + B + 1))
+        for bc in (0, 1):
+            full = oracle.stencil2d(u, w, d, bc, L, R, T, B)
+            compute = lambda padded: torch.from_numpy(oracle.stencil2d(padded.numpy(), w, d, bc, L, R, T, B))
+            got = D.sharded_sweep(torch.from_numpy(u[r0:r1].copy()), compute, T, B, bc == 1)
+            ok.append((name, bc, bool(np.array_equal(got.numpy(), full[r0:r1]))))
+    q.put((rank, ok))
+    dist.destroy_process_group()
+
+
+def _ch_worker(rank, world, port, q):
+    dist = _init(rank, world, port)
+    import torch
+    import oracle
+    import workloads as W
+    from paper_1902_09931_gb300 import distributed as D
+    n, Dm, G = 48, 1.0, 0.01
+    h = 2 * np.pi / n
+    dt = 0.1 * h
+    a = oracle.ch_coefficient_a(n, Dm, G, dt)
+    prev = W.ch_initial(n, seed=8)
+    cur = prev + 0.01 * W.ch_initial(n, seed=9)
+    r0, r1 = D.band(n, world, rank)
+    lap5 = np.array([0, 1, 0, 1, -4, 1, 0, 1, 0.0]) / h ** 2
+    bih = np.zeros((5, 5))
+    bih[2, 2] = 20
+    bih[1, 2] = bih[3, 2] = bih[2, 1] = bih[2, 3] = -8
+    bih[1, 1] = bih[1, 3] = bih[3, 1] = bih[3, 3] = 2
+    bih[0, 2] = bih[4, 2] = bih[2, 0] = bih[2, 4] = 1
+    bih = bih.ravel() / h ** 4
+
+    def rhs(pp, cp):  # the right-hand side of Sec. 5.1 on a band padded by 2 rows
+        p, c = pp.numpy(), cp.numpy()
+        cbar = 2 * c - p
+        b4 = oracle.stencil2d(cbar, bih, 2, 1, 2, 2, 2, 2)[2:-2]
+        l2 = oracle.stencil2d(c ** 3 - c, lap5, 2, 1, 1, 1, 1, 1)[2:-2]
+        r = -(2 / 3) * (c[2:-2] - p[2:-2]) - (2 / 3) * Dm * G * dt * b4 + (2 / 3) * Dm * dt * l2
+        return torch.from_numpy(r)
+
+    solve = lambda b: torch.from_numpy(oracle.cyclic_penta_solve(b.numpy(), a))
+    got = D.sharded_ch_step(torch.from_numpy(prev[r0:r1].copy()), torch.from_numpy(cur[r0:r1].copy()), n, rhs, solve)
+    ref = oracle.ch_step(prev, cur, Dm, G, dt)
+    err = float(np.abs(got.numpy() - ref[r0:r1]).max())
+    v = ref - (2 * cur - prev)  # the per-step bound of the CH parity tests
+    tol = 1e-12 * (np.abs(cur).max() + np.abs(oracle.ch_rhs(prev, cur, Dm, G, dt)).max() + (1 + 16 * a) * np.abs(v).max())
+    # invariants of the new field from per-rank partials
+    g = got.numpy()
+    e_loc = np.vstack([g, D.exchange_halo(got, 0, 1, True)[0].numpy()[-1:]])  # one row below for D+y
+    gx = (np.roll(g, -1, axis=1) - g) / h
+    gy = (e_loc[1:] - e_loc[:-1]) / h
+    part = torch.tensor([h * h * g.sum(), h * h * np.sum(0.25 * (g * g - 1) ** 2 + 0.5 * G * (gx ** 2 + gy ** 2))])
+    tot = D.allreduce_sum(part).numpy()
+    q.put((rank, err, tol, tot.tolist(), oracle.ch_mass(ref), oracle.ch_energy(ref, G)))
+    dist.destroy_process_group()
+
+
+def _transpose_worker(rank, world, port, q):
+    dist = _init(rank, world, port)
+    import torch
+    from paper_1902_09931_gb300 import distributed as D
+    n = 23
+    A = np.arange(n * n, dtype=np.float64).reshape(n, n)
+    r0, r1 = D.band(n, world, rank)
+    t = D.transpose_bands(torch.from_numpy(A[r0:r1].copy()), n)
+    q.put((rank, bool(np.array_equal(t.numpy(), A.T[r0:r1]))))
+    dist.destroy_process_group()
+
+
+def _run(target, world):
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=target, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=240) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    return sorted(out)
+
+
+def test_band_partition():
+    sys.path.insert(0, ROOT)
+    from paper_1902_09931_gb300 import distributed as D
+    for n in (1, 7, 47, 64):
+        for world in (1, 2, 3, 8):
+            bands = [D.band(n, world, r) for r in range(world)]
+            assert bands[0][0] == 0 and bands[-1][1] == n
+            assert all(bands[i][1] == bands[i + 1][0] for i in range(world - 1))
+            sizes = [b - a for a, b in bands]
+            assert max(sizes) - min(sizes) <= 1
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_stencil_equals_unsharded_oracle(world):
+    for rank, ok in _run(_stencil_worker, world):
+        bad = [x for x in ok if not x[2]]
+        assert not bad, (rank, bad)
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_transpose_bands(world):
+    assert all(ok for _, ok in _run(_transpose_worker, world))
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_ch_step_equals_unsharded_oracle(world):
+    """x-solves on row bands, an all-to-all transpose, y-solves, the transpose back; mass and
+    energy of the result from allreduced per-rank partials."""
+    for rank, err, tol, tot, mass, energy in _run(_ch_worker, world):
+        assert err <= tol, (rank, err, tol)
+        assert tot[0] == pytest.approx(mass, rel=1e-12, abs=1e-13)
+        assert tot[1] == pytest.approx(energy, rel=1e-12)
