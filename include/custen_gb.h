@@ -141,8 +141,9 @@ int cs_compute_group(const cs_plan_t* plans, int32_t count, void* cuda_stream);
  * periodic in both directions, of the description's dtype; arithmetic in that dtype.
  *   hx, hy    grid spacings, in [1e-60, 1e60] (CS_EINVAL otherwise).
  *   d_out     must not overlap d_c, d_u or d_v (CS_EALIAS); the three inputs are only read.
- * cs_compute runs one kernel; graph replay applies; cs_swap, cs_set_buffers and
- * cs_compute_host do not (CS_EINVAL); cs_autotune leaves the plan unchanged. */
+ * cs_compute runs one kernel (CS_EUNSUPPORTED when ny > 2,097,120 rows, the launch's limit);
+ * graph replay applies; cs_swap, cs_set_buffers and cs_compute_host do not (CS_EINVAL);
+ * cs_autotune leaves the plan unchanged. */
 typedef struct {
   int64_t nx, ny;
   int32_t dtype;    /* CS_F64 or CS_F32 */

@@ -337,8 +337,10 @@ int weno_launch(const WenoConfig* cfg, const void* c, const void* u, const void*
   if (cfg->nx == 0 || cfg->ny == 0) return CS_OK;
   const size_t eb = cfg->dtype == CS_F32 ? 4 : 8;
   const int vec_ok = reinterpret_cast<uintptr_t>(c) % 16 == 0 && (cfg->nx * eb) % 16 == 0;
-  const dim3 grid(static_cast<unsigned>((cfg->nx + kWTX - 1) / kWTX), static_cast<unsigned>((cfg->ny + kWTY - 1) / kWTY));
-  if (grid.y > 65535u) return set_error(CS_EUNSUPPORTED, "ny = %lld exceeds the WENO grid limit", (long long)cfg->ny);
+  const int64_t gx = (cfg->nx + kWTX - 1) / kWTX, gy = (cfg->ny + kWTY - 1) / kWTY;
+  if (gx > 0x7fffffff || gy > 65535)
+    return set_error(CS_EUNSUPPORTED, "grid %lld x %lld exceeds the WENO launch limits", (long long)cfg->nx, (long long)cfg->ny);
+  const dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy));
   const double fx = 1e-99 * cfg->hx * cfg->hx, fy = 1e-99 * cfg->hy * cfg->hy;
   if (cfg->dtype == CS_F32) {
     k_weno_adv<float><<<grid, kWThreads, 0, st>>>(static_cast<const float*>(c), static_cast<const float*>(u),
