@@ -104,7 +104,9 @@ typedef struct {
 /* Create (Sec. 3): validates the description, copies weights / coefficients, picks the kernel
  * variant and tile shape, and binds the caller's device buffers d_in (read) and d_out
  * (written).  d_in and d_out must not overlap (CS_EALIAS): blocks read overlapping halos, so
- * outputs cannot be written in place (Sec. 2). */
+ * outputs cannot be written in place (Sec. 2).  One compute covers the grid in one launch:
+ * ny <= 2,097,120 rows (cs_compute returns CS_EUNSUPPORTED beyond; cs_plan_create_2d_host
+ * streams taller grids in bands). */
 int cs_plan_create_2d(cs_plan_t* plan, const cs_stencil_desc* desc, const void* d_in, void* d_out);
 
 /* Create for a ragged batch of 1D lines (Abstract; Sec. 5.4's batched 1D problems): line m

@@ -224,6 +224,11 @@ int stencil2d_group(const Stencil2DConfig* const* cfgs, const void* const* ins, 
 
 int stencil2d_launch(const Stencil2DConfig* cfg, const void* in, void* out, cudaStream_t s) {
   if (cfg->nx == 0 || cfg->ny == 0) return CS_OK;
+  // one launch covers the grid: column tiles (>= 64 columns) in grid.x, row tiles (>= 32 rows) in
+  // grid.y, whose limit is 65535
+  if ((cfg->nx + 63) / 64 > 0x7fffffff || (cfg->ny + 31) / 32 > 65535)
+    return set_error(CS_EUNSUPPORTED, "grid %lld x %lld exceeds one launch (ny <= 2097120); a host-resident plan streams taller grids",
+                     (long long)cfg->nx, (long long)cfg->ny);
   return cfg->dtype == CS_F32 ? stencil2d_launch_f32(cfg, in, out, s)
                               : stencil2d_launch_f64(cfg, in, out, s);
 }
