@@ -244,7 +244,7 @@ __device__ __forceinline__ double weno5(double v1, double v2, double v3, double 
   // 12 eps = 12e-6 max w^2 + 12 floor
   const dd mw = split_scaled(__longlong_as_double(static_cast<long long>(mb)), e);
   dd eps = dd_mul(dd_sqr(mw), {kEps12Hi, kEps12Lo});
-  eps = dd_add(eps, dd_mulf(split_scaled(fl, 1023), 12.0f));
+  if (fe >= 1023 - 100) eps = dd_add(eps, dd_mulf(split_scaled(fl, 1023), 12.0f));  // else < 2^-99: below eps's last bit
   const dd q1 = dd_sqr(dd_add(s1, eps)), q2 = dd_sqr(dd_add(s2, eps)), q3 = dd_sqr(dd_add(s3, eps));
   const dd P1 = dd_mul(q2, q3), P2 = dd_mulf(dd_mul(q1, q3), 6.0f), P3 = dd_mulf(dd_mul(q1, q2), 3.0f);
   const dd num = dd_add(dd_add(dd_mul(P1, p1), dd_mul(P2, p2)), dd_mul(P3, p3));
