@@ -363,6 +363,8 @@ def run_ours(args):
     }
     if rank == 0 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        if not args.skip_parts:
+            line["cpu_baseline"]["rows"] = cpu_rows()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -648,6 +650,49 @@ def cpu_sample(seconds: float):
     desc = (f"oracle (C, 1 thread) on {rows}-row bands of the 4096^2 and 8192^2 grids, all 10 "
             f"stencil/bc combinations, {done} passes")
     return pts, t_total, desc
+
+
+def cpu_rows(seconds_each: float = 2.0):
+    """The oracle on bounded samples of the other rows' workloads (the same code the parity tests
+    trust, as it stands): units per second on the host, 1 thread for the C parts, numpy/scipy's
+    defaults for the rest.  Each sample repeats until `seconds_each` have passed."""
+    import oracle
+    oracle.build()
+
+    def timed(fn):
+        reps, t = 0, 0.0
+        while t < seconds_each:
+            t0 = time.perf_counter()
+            fn()
+            t += time.perf_counter() - t0
+            reps += 1
+        return reps, t
+
+    out = {}
+    n = 512
+    h = 2 * np.pi / n
+    c0 = W.ch_initial(n, seed=5)
+    reps, t = timed(lambda: oracle.ch_step(c0, c0, 1.0, 0.01, 0.1 * h))
+    out["ch_adi_f64"] = {"steps_per_s_at_512": round(reps / t, 2),
+                         "steps_per_s_at_4096_scaled": round(reps / t * (n / 4096) ** 2, 4)}
+    reps, t = timed(lambda: oracle.ch_step_noflux(c0, c0, 1.0, 0.01, 0.1 * h))
+    out["ch_noflux_f64"] = {"steps_per_s_at_512": round(reps / t, 2),
+                            "steps_per_s_at_4096_scaled": round(reps / t * (n / 4096) ** 2, 4)}
+    reps, t = timed(lambda: (oracle.ch_coarsening_s(c0), oracle.ch_coarsening_k1(c0)))
+    out["coarsening_measure_at_512"] = {"ms": round(t / reps * 1e3, 3)}
+    m = 1024
+    hw = 2 * np.pi / m
+    cw = W.sines_field(m, seed=61)
+    uw, vw = np.cos(cw), np.sin(cw)
+    reps, t = timed(lambda: oracle.weno_advection(cw, uw, vw, hw, hw))
+    out["weno_f64"] = {"gpts_per_s": round(reps * m * m / t / 1e9, 6), "sample": "1024^2"}
+    offs = W.ragged_offsets(2048, seed=7)
+    packed = W.sines_lines(offs, seed=8)
+    wts = np.array([-1, 16, -30, 16, -1.0]) / 12.0
+    reps, t = timed(lambda: oracle.stencil1d_batch(packed, offs, wts, 1, 2, 2))
+    out["batch1d_f64"] = {"gpts_per_s": round(reps * int(offs[-1]) / t / 1e9, 6), "sample": "2048 ragged lines"}
+    out["threads"] = "C parts 1; numpy / scipy default"
+    return out
 
 
 def cpu_baseline(seconds: float):
