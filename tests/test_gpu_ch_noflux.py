@@ -95,6 +95,23 @@ def test_full_size_single_step(env, n):
     assert np.abs(c2 - ref2).max() <= step_tolerance(orc, p1, c1, ref2, n, dt, 1e-12)
 
 
+def test_full_size_single_step_fp32_storage(env):
+    """4096^2 with FP32 fields (the bench's FP32 configuration), against the FP64 oracle fed the
+    same FP32-rounded state."""
+    cs, torch, orc = env
+    n = 4096
+    h = 2 * np.pi / n
+    dt = 0.1 * h
+    prev = W.ch_initial(n, seed=1904).astype(np.float32).astype(np.float64)
+    cur = (prev + 0.01 * W.ch_initial(n, seed=1905)).astype(np.float32).astype(np.float64)
+    r = Run(cs, torch, prev, cur, 1, dt)
+    r.step(1)
+    _, got, _ = r.state()
+    r.close()
+    ref = orc.ch_step_noflux(prev, cur, D, GAMMA, dt)
+    assert np.abs(got - ref).max() <= step_tolerance(orc, prev, cur, ref, n, dt, TOL[1])
+
+
 @pytest.mark.parametrize("k,l", [(1, 0), (3, 2), (20, 1), (63, 63)])
 def test_linear_limit_cosine_modes_on_gpu(env, k, l):
     """cos(k pi (i + 1/2) / n) cos(l pi (j + 1/2) / n), amplitude 1e-8: the amplitude follows the

@@ -156,3 +156,17 @@ def test_homogeneous_beyond_the_oracles_range(env):
     b = run(cs, torch, c * 2.0 ** 498, u, v, hx, hy, 0)
     assert np.all(np.isfinite(b))
     assert np.abs(b * 2.0 ** -498 - a).max() <= 1e-12 * scale_of(c, u, v, hx, hy)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("h", [1e-30, 1e30])
+def test_extreme_grid_spacings(env, dtype, h):
+    """eps's floor is 1e-99 in units of the differences over h: scaled by h^2 where the kernel
+    works on differences, so very fine and very coarse spacings keep their weights."""
+    cs, torch, orc = env
+    c, u, v, _, _ = fields(64, 96, seed=12, kind="disc")
+    if dtype == 1:
+        c, u, v = (a.astype(np.float32).astype(np.float64) for a in (c, u, v))
+    got = run(cs, torch, c, u, v, h, 2 * h, dtype)
+    ref = orc.weno_advection(c, u, v, h, 2 * h)
+    assert np.abs(got - ref).max() <= TOL[dtype] * scale_of(c, u, v, h, 2 * h)
