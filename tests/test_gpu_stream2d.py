@@ -55,11 +55,13 @@ FAMILIES = ("lap9", "biharm13", "ddx4", "d2y8", "asym3102", "generic5", "box5x5"
 
 @pytest.mark.parametrize("dtype", [0, 1])
 @pytest.mark.parametrize("bc", [0, 1])
-def test_streamed_equals_device_sweep(env, dtype, bc):
+@pytest.mark.parametrize("nx", [300, 301])
+def test_streamed_equals_device_sweep(env, dtype, bc, nx):
     """1000 x 300 grid (neither a multiple of the tile), bands of 64 rows: 16 bands through 3
-    slots, a ragged last band, wrapped or zero halos at both grid ends."""
+    slots, a ragged last band, wrapped or zero halos at both grid ends; 301 columns make rows that
+    are not a multiple of 16 bytes (the element-wise loader)."""
     cs, torch, _ = env
-    ny, nx = 1000, 300
+    ny = 1000
     h = 2 * np.pi / nx
     u = W.sines_field(nx, seed=51, ny=ny)
     eb = 8 if dtype == 0 else 4
