@@ -65,7 +65,10 @@ __device__ __forceinline__ T weno_scaled(T w1, T w2, T w3, T w4, T w5, T mw, T f
   const T p1 = T(0.1) * (q2 * q3), p2 = T(0.6) * (q1 * q3), p3 = T(0.3) * (q1 * q2);
   const T num = fma_(p1, phi1, fma_(p2, phi2, p3 * phi3));
   const T den = p1 + p2 + p3;
-  return num / den;
+  // FP32: the fast division (2 ulp; den lies in [1e-24, 3e8], inside its range) -- FP32 storage
+  // is held to 1e-5
+  if constexpr (sizeof(T) == 4) return __fdividef(num, den);
+  else return num / den;
 }
 
 // sum_k g_k phi_k: the optimal-weight (linear) combination, (2 v1 - 13 v2 + 47 v3 + 27 v4 - 3 v5) / 60.
