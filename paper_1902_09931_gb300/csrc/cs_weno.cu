@@ -292,8 +292,10 @@ __device__ __forceinline__ T upwind(const T (&d)[6], bool pos, T floor_h2) {
   return weno5(v1, v2, v3, v4, v5, floor_h2);
 }
 
+// FP64 storage: at least 4 CTAs per SM (the mixed-precision body then fits 63 registers without
+// spilling; measured 2.6 % faster than the compiler's 69 registers and 3 CTAs).
 template <typename T>
-__global__ void __launch_bounds__(kWThreads)
+__global__ void __launch_bounds__(kWThreads, sizeof(T) == 8 ? 4 : 1)
     k_weno_adv(const T* __restrict__ c, const T* __restrict__ u, const T* __restrict__ v, T* __restrict__ out,
                int64_t nx, int64_t ny, int vec_ok, T inv_hx, T inv_hy, T floor_x, T floor_y) {
   __shared__ __align__(16) T s[kWTileRows * kWCols];
