@@ -160,3 +160,33 @@ def test_sharded_ch_step_equals_unsharded_oracle(world):
         assert err <= tol, (rank, err, tol)
         assert tot[0] == pytest.approx(mass, rel=1e-12, abs=1e-13)
         assert tot[1] == pytest.approx(energy, rel=1e-12)
+
+
+def _errors_worker(rank, world, port, q):
+    dist = _init(rank, world, port)
+    import torch
+    from paper_1902_09931_gb300 import distributed as D
+    out = {}
+    try:
+        D.exchange_halo(torch.zeros(1, 8, dtype=torch.float64), 2, 2, True)
+        out["thin"] = False
+    except ValueError:
+        out["thin"] = True
+    try:
+        D.transpose_bands(torch.zeros(3, 8, dtype=torch.float64), 8)
+        out["shape"] = False
+    except ValueError:
+        out["shape"] = True
+    # one rank: the halo of a periodic band is its own wrap; a non-periodic band gets none
+    x = torch.arange(20, dtype=torch.float64).reshape(5, 4)
+    p, t, b = D.exchange_halo(x, 2, 1, True)
+    out["wrap"] = bool(t == 2 and b == 1 and torch.equal(p, torch.cat([x[3:], x, x[:1]])))
+    p, t, b = D.exchange_halo(x, 2, 1, False)
+    out["nowrap"] = bool(t == 0 and b == 0 and torch.equal(p, x))
+    q.put((rank, out))
+    dist.destroy_process_group()
+
+
+def test_single_rank_halo_and_errors():
+    (rank, out), = _run(_errors_worker, 1)
+    assert out == {"thin": True, "shape": True, "wrap": True, "nowrap": True}
