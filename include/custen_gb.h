@@ -43,7 +43,7 @@ typedef enum {
   CS_ENOMEM = -3,       /* library-owned workspace could not be allocated */
   CS_ECUDA = -4,        /* a CUDA runtime call failed */
   CS_EUNSUPPORTED = -5, /* valid request that this build does not implement */
-  CS_ETIMEOUT = -6      /* a bounded device-side wait ran out (reserved) */
+  CS_ETIMEOUT = -6      /* a bounded device-side wait ran out (cs_plan_check, cs_compute_host) */
 } cs_status;
 
 /* Direction of a 2D stencil (Sec. 3: X, Y, XY).  XY stencils read corner halos. */
@@ -123,12 +123,17 @@ int cs_plan_create_1d_batch(cs_plan_t* plan, const cs_stencil_desc* desc, int64_
 /* Compute (Sec. 3): applies the stencil, d_in -> d_out, stream-ordered and asynchronous. */
 int cs_compute(cs_plan_t plan, void* cuda_stream);
 
-/* Grouped Compute: applies `count` 2D stencil plans -- independent grids of any sizes -- in as
- * few kernel launches as possible (one launch per 16 plans).  The plans must share dtype,
- * stencil shape (left/right/top/bottom and the non-zero tap pattern, i.e. the same specialised
- * kernel) and tile shape; CS_EINVAL otherwise, CS_EUNSUPPORTED for plans on the generic
- * kernel.  Storage-type arithmetic (FP64 plans use native FP64 here).  Used by the serving
- * loop to batch small sweeps.  Stream-ordered and asynchronous. */
+/* Grouped Compute: applies `count` 2D stencil plans -- independent grids of any sizes -- in one
+ * persistent kernel launch per 64 plans: the launch has as many CTAs as the GPU holds at once,
+ * and each walks the tiles of all grids in turn.  The plans must share dtype, stencil shape
+ * (left/right/top/bottom and the non-zero tap pattern, i.e. the same specialised kernel) and
+ * tile shape; CS_EINVAL otherwise, CS_EUNSUPPORTED for plans on the generic kernel.  Each tile
+ * is evaluated as cs_compute's cp.async tiles of the same height evaluate it, so results are
+ * those of the plans computed alone with that tile choice, bit for bit: FP32 storage in FP32, FP64
+ * storage on the exact digit path when every plan allows it (integer weight ratios, or the cubic
+ * user function; CS_FP64_AUTO), else in native FP64.  Allocates nothing and never synchronises,
+ * so the call can be captured into a CUDA graph (the graph keeps the plans' buffers of capture
+ * time).  Used by the serving loop to batch small sweeps.  Stream-ordered and asynchronous. */
 int cs_compute_group(const cs_plan_t* plans, int32_t count, void* cuda_stream);
 
 /* Periodic XY WENO advection (Sec. 4.2, "Advection"): the XY periodic stencil variant whose
@@ -193,11 +198,11 @@ int cs_swap(cs_plan_t plan);
 /* Arithmetic used for CS_F64 stencils (GB300 issues FP64 at 1/64 of the FP32 rate).
  * CS_FP64_AUTO (default), for the specialised stencils:
  *   - weights w_k = c * n_k with integers n_k, sum |n_k| <= 64 (every stencil of the paper):
- *     exact digit evaluation -- each value cut into three 18-bit digits on a grid set by the
- *     largest value of its tile (tile = 64 x TY outputs plus halo), digit sums exact in FP32,
- *     their combination rounded to 2^-46 of the tile's largest value and scaled with one FP64
- *     FMA; error at most 2^-45 / sum|n_k| of sum|w| * (largest |value| in the tile and its
- *     halo);
+ *     exact digit evaluation -- each value cut into two signed 25-bit integer digits on a grid
+ *     set by the largest value of its tile (tile = 64 x TY outputs plus halo; bits below 2^-50
+ *     of the grid's top dropped), digit sums exact in int32, their combination rounded to 2^-46
+ *     of the grid's top and scaled with one FP64 FMA; error at most (2^-49 + 2^-46 / sum|n_k|)
+ *     of sum|w| * (largest |value| in the tile and its halo);
  *   - other weights: double-float arithmetic (values as unevaluated float pairs, error-free
  *     products and sums on the FP32 pipes); error below ~2^-46 of sum|w| * max|in|;
  *   tiles holding inf / nan or values outside the methods' exponent ranges, and weights
@@ -215,6 +220,21 @@ int cs_plan_set_fp64_mode(cs_plan_t plan, int32_t mode);
  *      nx is a multiple of 16 bytes / element size and d_in is 16-byte aligned, else 1). */
 int cs_plan_set_tile_choice(cs_plan_t plan, int32_t choice);
 int cs_plan_get_tile_choice(cs_plan_t plan, int32_t* choice);
+
+/* Completion check of a plan's work (no counterpart in the paper: it reports the bounded waits
+ * of this library's TMA pipeline).  Waits for cuda_stream, then returns CS_ETIMEOUT if, since
+ * the previous check, a TMA-pipelined sweep of this 2D plan (tile choice 2) had an mbarrier wait
+ * run out: the CTAs concerned returned early and part of that sweep's output was not written.
+ * The count lives in a 4-byte device word the plan owns, so plans (and the streams they run on)
+ * do not mask one another.  cs_compute_host runs this check itself.  Returns CS_OK otherwise,
+ * for every plan kind. */
+int cs_plan_check(cs_plan_t plan, void* cuda_stream);
+
+/* Test hook for cs_plan_check (no counterpart in the paper): from CTA-local tile index `tile`
+ * on, the TMA sweep of this 2D device plan issues no copies, so each CTA's wait for such a tile
+ * runs out (after a short bounded wait, with no copy in flight) and the sweep returns early;
+ * tile < 0 (the default) turns it off.  CS_EINVAL for other plans. */
+int cs_plan_debug_stall(cs_plan_t plan, int32_t tile);
 
 /* Rebinds the device buffers of a stencil plan without re-planning (same sizes and dtype). */
 int cs_set_buffers(cs_plan_t plan, const void* d_in, void* d_out);
@@ -309,6 +329,16 @@ int cs_ch_set_fields(cs_plan_t plan, void* d_c_prev, void* d_c_cur, void* d_c_ne
  * *chunks pieces of *chunk_len points (see cs_ch_create); either output may be NULL. */
 int cs_ch_config(cs_plan_t plan, int32_t* chunks, int32_t* chunk_len);
 
+/* Self-check of the line solver (no counterpart in the paper; host code only, no GPU needed):
+ * builds the partitioned-solve tables cs_ch_create would build for lines of n points split into
+ * `chunks` chunks with coefficient a = (2/3) D gamma dt / h^4 and the given boundary
+ * (cs_ch_boundary), replays the two device phases on the host in the kernels' order of operations
+ * for a fixed pseudo-random right-hand side b in [-1, 1), and writes the backward error
+ * ||L x - b||_inf / ((1 + 16 a) ||x||_inf) of the result against the line operator L = I + a D4
+ * itself.  CS_EINVAL for an invalid partition (n / chunks >= 16, a multiple of 8, chunks <= 64),
+ * a < 0 or a non-finite a. */
+int cs_ch_solver_check(int64_t n, int32_t chunks, double a, int32_t boundary, double* residual);
+
 /* Allocation-free batched 1D sweep.  The paper has no counterpart: this entry point exists for
  * callers that cannot let a library allocate device memory -- code running under a fixed
  * device-memory budget or inside an arena owned by another runtime, latency-critical loops that
@@ -324,8 +354,9 @@ int cs_ch_config(cs_plan_t plan, int32_t* chunks, int32_t* chunk_len);
  *   that device current; make that first call before any stream capture.
  *   Every call shares the array and overwrites it: calls that overlap on the GPU (different
  *   streams, or host threads) race and must be serialised by the caller.
- *   The offsets are validated on the device first (the call synchronises the stream once to
- *   read the result); invalid offsets return CS_EINVAL and leave d_out untouched. */
+ *   The offsets are validated on the device first: every call synchronises the stream once,
+ *   to read the result of that check back to the host; invalid offsets return CS_EINVAL and
+ *   leave d_out untouched. */
 int cs_batch1d_compute_noalloc(const cs_stencil_desc* desc, int64_t num_lines,
                                const int64_t* d_offsets, int64_t total_len, const void* d_in,
                                void* d_out, void* cuda_stream);

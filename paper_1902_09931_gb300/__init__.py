@@ -107,6 +107,8 @@ _SYMBOLS = {
     "cs_plan_set_fp64_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "cs_plan_set_tile_choice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "cs_plan_get_tile_choice": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
+    "cs_plan_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "cs_plan_debug_stall": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "cs_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "cs_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
     "cs_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
@@ -118,6 +120,7 @@ _SYMBOLS = {
     "cs_ch_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)]),
     "cs_ch_set_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_ch_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "cs_ch_solver_check": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "cs_batch1d_compute_noalloc": (ctypes.c_int, [ctypes.POINTER(_CStencilDesc), ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_last_error": (ctypes.c_char_p, []),
     "cs_launch_count": (ctypes.c_int64, []),
@@ -267,6 +270,17 @@ def cs_plan_get_tile_choice(plan) -> int:
     return c.value
 
 
+def cs_plan_check(plan, stream=None) -> None:
+    """Waits for the stream; raises CSError(CS_ETIMEOUT) if a TMA sweep of the plan had a bounded
+    wait run out since the last check."""
+    _check(load().cs_plan_check(plan, _stream(stream)))
+
+
+def cs_plan_debug_stall(plan, tile: int) -> None:
+    """Test hook: the plan's TMA sweep issues no copies from CTA-local tile `tile` on (< 0: off)."""
+    _check(load().cs_plan_debug_stall(plan, int(tile)))
+
+
 def cs_plan_use_graph(plan, enable: bool = True) -> None:
     _check(load().cs_plan_use_graph(plan, 1 if enable else 0))
 
@@ -338,6 +352,13 @@ def cs_ch_config(plan):
     c, m = ctypes.c_int32(), ctypes.c_int32()
     _check(load().cs_ch_config(plan, ctypes.byref(c), ctypes.byref(m)))
     return c.value, m.value
+
+
+def cs_ch_solver_check(n: int, chunks: int, a: float, boundary: int) -> float:
+    """Backward error of the line solver's host replay on its own tables (no GPU needed)."""
+    r = ctypes.c_double()
+    _check(load().cs_ch_solver_check(int(n), int(chunks), float(a), int(boundary), ctypes.byref(r)))
+    return r.value
 
 
 def cs_batch1d_compute_noalloc(desc: StencilDesc, num_lines: int, d_offsets, total_len: int, d_in,

@@ -633,18 +633,37 @@ int cs_compute_host(cs_plan_t p, const void* h_in, void* h_out, void* stream) {
     if (!h_in || !h_out) return set_error(CS_EINVAL, "a host-resident plan needs both host buffers");
     if (overlaps(h_in, h_out, static_cast<size_t>(p->elems) * p->elem_bytes))
       return set_error(CS_EALIAS, "input and output buffers overlap");
-    return compute_host_streamed(p, h_in, h_out, s);
+    int rc = compute_host_streamed(p, h_in, h_out, s);
+    return rc != CS_OK ? rc : stencil2d_check(&p->s2, s);
   }
   const size_t bytes = static_cast<size_t>(p->elems) * p->elem_bytes;
-  if (p->kind == kStencil2D && h_in && h_out && bytes >= kBandMinBytes && p->s2.ny >= 2 * kStencilBandAlign)
-    return compute_host_banded(p, h_in, h_out, s);
+  if (p->kind == kStencil2D && h_in && h_out && bytes >= kBandMinBytes && p->s2.ny >= 2 * kStencilBandAlign) {
+    int rc = compute_host_banded(p, h_in, h_out, s);
+    return rc != CS_OK ? rc : stencil2d_check(&p->s2, s);
+  }
   if (h_in && bytes) CS_CUDA_TRY(cudaMemcpyAsync(const_cast<void*>(p->d_in), h_in, bytes, cudaMemcpyHostToDevice, s));
   int rc = cs_compute(p, stream);
   if (rc != CS_OK) return rc;
   if (h_out && bytes) {
     CS_CUDA_TRY(cudaMemcpyAsync(h_out, p->d_out, bytes, cudaMemcpyDeviceToHost, s));
     CS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (p->kind == kStencil2D) return stencil2d_check(&p->s2, s);
   }
+  return CS_OK;
+}
+
+int cs_plan_check(cs_plan_t p, void* stream) {
+  if (!p) return set_error(CS_EINVAL, "null plan");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->kind == kStencil2D || p->kind == kStencil2DHost) return stencil2d_check(&p->s2, s);
+  CS_CUDA_TRY(cudaStreamSynchronize(s));
+  return CS_OK;
+}
+
+int cs_plan_debug_stall(cs_plan_t p, int32_t tile) {
+  if (!p || p->kind != kStencil2D) return set_error(CS_EINVAL, "not a 2D stencil plan on device buffers");
+  p->s2.stall_from = tile < 0 ? -1 : tile;
+  drop_graph(p);
   return CS_OK;
 }
 
@@ -808,6 +827,11 @@ int cs_ch_fields(cs_plan_t p, void** prev, void** cur, int64_t* steps) {
 int cs_ch_set_fields(cs_plan_t p, void* prev, void* cur, void* next) {
   if (!p || p->kind != kCahnHilliard) return set_error(CS_EINVAL, "not a Cahn-Hilliard plan");
   return ch_set_fields(p->ch, prev, cur, next);
+}
+
+int cs_ch_solver_check(int64_t n, int32_t chunks, double a, int32_t boundary, double* residual) {
+  if (boundary != CS_CH_PERIODIC && boundary != CS_CH_NOFLUX) return set_error(CS_EINVAL, "unknown boundary %d", boundary);
+  return ch_solver_check(n, chunks, a, boundary == CS_CH_NOFLUX, residual);
 }
 
 int cs_ch_config(cs_plan_t p, int32_t* chunks, int32_t* chunk_len) {

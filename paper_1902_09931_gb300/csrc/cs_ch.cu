@@ -9,9 +9,11 @@
 // evaluated in the factored form
 //   Z   = (2/3) D dt / h^2 * N - a * (sum of 4 neighbours of Cbar - 4 Cbar)
 //   RHS = -(2/3)(C^n - C^{n-1}) + (sum of 4 neighbours of Z - 4 Z)
-// which needs 16 instead of 24 FP64 operations per point (FP64 is the bound on GB300); with FP64
-// storage the two Laplacians are exact digit sums on the FP32 / integer pipes, each scaled by one
-// FP64 FMA, which leaves about 10.
+// which needs 16 instead of 24 FP64 operations per point (FP64 is the bound on GB300); the two
+// Laplacians are exact integer-digit sums, each scaled by one FP64 FMA (the first carrying -a), which
+// leaves about 8.6.  FP32 storage evaluates the right-hand side the same way, on exactly widened
+// values: its terms reach ~64 a |Cbar| and the solves cancel them back down to |C|, so FP32
+// arithmetic there would lose every digit of C at n = 4096 (a = 1.8e5).
 //
 // Line solves (the paper uses cuPentBatch with the periodic corners treated as in Navon's
 // PENT).  Here each periodic line of length n is cut into P chunks of m = n / P points; since
@@ -33,6 +35,7 @@
 // last chunks of a line get their own LU factors and spikes, the couplings are the same, and the
 // chunk-end system is inverted as a dense 4P x 4P matrix (no longer block-circulant; applying it
 // still takes 16 P FMAs per chunk).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -117,7 +120,7 @@ __device__ __forceinline__ int mirrorn(int64_t k, int64_t n) {
   return static_cast<int>(k < 0 ? -1 - k : (k >= n ? 2 * n - 1 - k : k));
 }
 // line-solve chunk type: bit 0 the line's first chunk, bit 1 its last (no-flux tables)
-__device__ __forceinline__ int chunk_type(int p, int P) { return (p == 0 ? 1 : 0) | (p == P - 1 ? 2 : 0); }
+__host__ __device__ __forceinline__ int chunk_type(int p, int P) { return (p == 0 ? 1 : 0) | (p == P - 1 ? 2 : 0); }
 
 template <typename T>
 __device__ __forceinline__ void block_reduce2(double m, double e, double* out2) {
@@ -137,19 +140,21 @@ __device__ __forceinline__ void block_reduce2(double m, double e, double* out2) 
   }
 }
 
-// RHS of the x-sweep (storage T, stencil arithmetic T) and, when partials != nullptr, the
-// per-block FP64 sums of C and of the free-energy density of C^n.  rhs == nullptr computes the
-// sums only.
-template <typename T, typename RT>
+// RHS of the x-sweep and, when partials != nullptr, the per-block FP64 sums of C and of the
+// free-energy density of C^n.  rhs == nullptr computes the sums only.  The tile is staged in FP64
+// whatever the storage type T (FP32 values widen exactly): the right-hand side carries terms of
+// size ~64 a |Cbar| (a = 1.8e5 at n = 4096) that the solves cancel back down to |C|, so it needs
+// FP64 precision; evaluated in FP32 it loses all of C's digits at the large grids.
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
-    k_ch_rhs(const T* __restrict__ cur, const T* __restrict__ prev, RT* __restrict__ rhs, int64_t n,
-             T alpha, T a, double half_gamma_over_h2, double* __restrict__ partials, int noflux) {
+    k_ch_rhs(const T* __restrict__ cur, const T* __restrict__ prev, double* __restrict__ rhs, int64_t n,
+             double alpha, double a, double half_gamma_over_h2, double* __restrict__ partials, int noflux) {
   constexpr int HR = kTY + 4, HC = kTX + 4;  // halo-2 tiles
   constexpr int ZR = kTY + 2, ZC = kTX + 2;  // halo-1 tile
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sc = reinterpret_cast<T*>(smem_raw);  // C^n
-  T* sb = sc + HR * HC;                    // Cbar
-  T* sz = sb + HR * HC;                    // Z
+  double* sc = reinterpret_cast<double*>(smem_raw);  // C^n
+  double* sb = sc + HR * HC;                         // Cbar
+  double* sz = sb + HR * HC;                         // Z
   const int64_t x0 = static_cast<int64_t>(blockIdx.x) * kTX;
   const int64_t y0 = static_cast<int64_t>(blockIdx.y) * kTY;
   for (int idx = threadIdx.x; idx < HR * HC; idx += kThreads) {
@@ -157,114 +162,82 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t gy = y0 - 2 + r, gx = x0 - 2 + c;
     const int64_t off = noflux ? static_cast<int64_t>(mirrorn(gy, n)) * n + mirrorn(gx, n)
                                : static_cast<int64_t>(wrapn(gy, n)) * n + wrapn(gx, n);
-    const T cv = cur[off];
+    const double cv = widen(cur[off]);
     sc[idx] = cv;
-    sb[idx] = T(2) * cv - prev[off];
+    sb[idx] = 2.0 * cv - widen(prev[off]);
   }
   __syncthreads();
-  if constexpr (sizeof(T) == 8) {
-    if (rhs) {
-      // FP64 storage: both 5-point Laplacians as exact digit sums (integer weights 1, 1, 1, 1, -4)
-      // scaled with one FP64 FMA each, so the FP64 pipe keeps only Cbar, N, Z, the two scalings and
-      // the final combination (10 instead of 16.5 FP64 operations per point).  A tile whose values
-      // leave the digit range takes the FP64 formula for that Laplacian.
-      float* s2 = reinterpret_cast<float*>(sz + ZR * ZC);  // third digits (Cbar, then Z)
-      __shared__ unsigned s_red[kThreads / 32];
-      auto lap5 = [&](const double* t, int i, int pitch) {
-        return (t[i - pitch] + t[i + pitch]) + (t[i - 1] + t[i + 1]) - 4.0 * t[i];
-      };
-      // digit sums of the 5-point Laplacian at i of a split tile (d0, d1 pairs over t, d2 in s2)
-      auto lap5_digits = [&](const double* t, int i, int pitch, float& q0, float& q1, float& q2) {
-        const float2* d = reinterpret_cast<const float2*>(t);
-        const float2 qa = __fadd2_rn(__fadd2_rn(d[i - pitch], d[i + pitch]), __fadd2_rn(d[i - 1], d[i + 1]));
-        const float2 qb = __ffma2_rn(make_float2(-4.0f, -4.0f), d[i], qa);
-        q0 = qb.x;
-        q1 = qb.y;
-        q2 = __fmaf_rn(-4.0f, s2[i], (s2[i - pitch] + s2[i + pitch]) + (s2[i - 1] + s2[i + 1]));
-      };
-      auto tile_scale = [](int tile_e) { return tile_e == 0 ? 0.0 : ldexp(1.0, tile_e - 1022 - 3 * ixd::kDigitBits); };
-      auto words = [](double v, uint32_t& hi, uint32_t& lo) {
-        hi = static_cast<uint32_t>(__double2hiint(v));
-        lo = static_cast<uint32_t>(__double2loint(v));
-      };
-      double* cb = reinterpret_cast<double*>(sb);
-      double* zt = reinterpret_cast<double*>(sz);
-      const double* cn = reinterpret_cast<const double*>(sc);
-      {
-        const int te = static_cast<int>(ixd::ix_tile_max_hi<kThreads>(cb, HR * HC, s_red) >> 20);
-        const double scale = tile_scale(te);
-        const bool dig = ixd::ix_tile_ok(te, scale);  // uniform over the block
-        if (dig) {
-          ixd::ix_split_tile<kThreads>(cb, s2, HR * HC, te);
-          __syncthreads();
-        }
-        uint32_t sh, sl, ch, cl;
-        words(scale * 0x1p8, sh, sl);
-        words(-scale * 0x1p60, ch, cl);
-        for (int idx = threadIdx.x; idx < ZR * ZC; idx += kThreads) {
-          const int r = idx / ZC, c = idx - r * ZC;
-          const int hidx = (r + 1) * HC + (c + 1);
-          double lap_cb;
-          if (dig) {
-            float q0, q1, q2;
-            lap5_digits(cb, hidx, HC, q0, q1, q2);
-            lap_cb = ixd::ix_combine(q0, q1, q2, sh, sl, ch, cl);
-          } else {
-            lap_cb = lap5(cb, hidx, HC);
-          }
-          const double u = cn[hidx];
-          const double nl = u * u * u - u;
-          zt[idx] = static_cast<double>(alpha) * nl - static_cast<double>(a) * lap_cb;
-        }
+  if (rhs) {
+    // Both 5-point Laplacians as exact integer-digit sums (weights 1, 1, 1, 1, -4; 28-bit digits, which
+    // hold every bit of a value within a factor 8 of its tile's largest, so neighbouring tiles,
+    // which evaluate Z on each other's border, agree on it to 2^-56 of the tile's scale and the sum
+    // of the Laplacian over the grid stays zero to that level: mass is conserved), each scaled with
+    // one FP64 FMA; the first one's scaling carries -a, so the FP64 pipe keeps only Cbar, u u,
+    // N, Z, the two scalings, C^n - C^{n-1} and the final combination (8.6 FP64 operations per
+    // point).  A tile whose values leave the digit range takes the FP64 formula for that Laplacian.
+    __shared__ unsigned s_red[kThreads / 32];
+    auto lap5 = [&](const double* t, int i, int pitch) {
+      return (t[i - pitch] + t[i + pitch]) + (t[i - 1] + t[i + 1]) - 4.0 * t[i];
+    };
+    // digit sums of the 5-point Laplacian at i of a split tile (int2 digits over t's slots)
+    auto lap5_digits = [&](const double* t, int i, int pitch, int& q0, int& q1) {
+      const int2* d = reinterpret_cast<const int2*>(t);
+      const int2 u = d[i - pitch], v = d[i + pitch], w = d[i - 1], x = d[i + 1], c = d[i];
+      q0 = (u.x + v.x) + (w.x + x.x) - 4 * c.x;
+      q1 = (u.y + v.y) + (w.y + x.y) - 4 * c.y;
+    };
+    // the one-FMA scaling of a digit sum by m 2^(G - 56) (ixi_consts); false: the FP64 formula
+    double* cb = sb;
+    double* zt = sz;
+    const double* cn = sc;
+    {
+      const int te = static_cast<int>(ixd::ix_tile_max_hi<kThreads>(cb, HR * HC, s_red) >> 20);
+      uint32_t w[4];
+      const bool dig = ixd::ixi_consts<28>(-a, te, w);  // uniform over the block
+      if (dig) {
+        ixd::ixi_split_tile<kThreads, 28>(cb, HR * HC, te);
         __syncthreads();
       }
-      {
-        const int te = static_cast<int>(ixd::ix_tile_max_hi<kThreads>(zt, ZR * ZC, s_red) >> 20);
-        const double scale = tile_scale(te);
-        const bool dig = ixd::ix_tile_ok(te, scale);
+      for (int idx = threadIdx.x; idx < ZR * ZC; idx += kThreads) {
+        const int r = idx / ZC, c = idx - r * ZC;
+        const int hidx = (r + 1) * HC + (c + 1);
+        double lap_a;  // -a * Laplacian(Cbar)
         if (dig) {
-          ixd::ix_split_tile<kThreads>(zt, s2, ZR * ZC, te);
-          __syncthreads();
+          int q0, q1;
+          lap5_digits(cb, hidx, HC, q0, q1);
+          lap_a = ixd::ixi_combine<28>(q0, q1, w);
+        } else {
+          lap_a = -a * lap5(cb, hidx, HC);
         }
-        uint32_t sh, sl, ch, cl;
-        words(scale * 0x1p8, sh, sl);
-        words(-scale * 0x1p60, ch, cl);
-        for (int idx = threadIdx.x; idx < kTY * kTX; idx += kThreads) {
-          const int r = idx / kTX, c = idx - r * kTX;
-          const int zidx = (r + 1) * ZC + (c + 1);
-          const int hidx = (r + 2) * HC + (c + 2);
-          double lap_z;
-          if (dig) {
-            float q0, q1, q2;
-            lap5_digits(zt, zidx, ZC, q0, q1, q2);
-            lap_z = ixd::ix_combine(q0, q1, q2, sh, sl, ch, cl);
-          } else {
-            lap_z = lap5(zt, zidx, ZC);
-          }
-          const int64_t o = (y0 + r) * n + x0 + c;
-          const double diff = cn[hidx] - static_cast<double>(prev[o]);  // C^n - C^{n-1}
-          rhs[o] = static_cast<RT>(-2.0 / 3.0 * diff + lap_z);
-        }
+        const double u = cn[hidx];
+        zt[idx] = fma(alpha, fma(u * u, u, -u), lap_a);
       }
+      __syncthreads();
     }
-  } else if (rhs) {
-    for (int idx = threadIdx.x; idx < ZR * ZC; idx += kThreads) {
-      const int r = idx / ZC, c = idx - r * ZC;
-      const int hidx = (r + 1) * HC + (c + 1);
-      const T cb = sb[hidx];
-      const T lap_cb = (sb[hidx - HC] + sb[hidx + HC]) + (sb[hidx - 1] + sb[hidx + 1]) - T(4) * cb;
-      const T u = sc[hidx];
-      const T nl = u * u * u - u;
-      sz[idx] = alpha * nl - a * lap_cb;
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < kTY * kTX; idx += kThreads) {
-      const int r = idx / kTX, c = idx - r * kTX;
-      const int zidx = (r + 1) * ZC + (c + 1);
-      const int hidx = (r + 2) * HC + (c + 2);
-      const T lap_z = (sz[zidx - ZC] + sz[zidx + ZC]) + (sz[zidx - 1] + sz[zidx + 1]) - T(4) * sz[zidx];
-      const T diff = sb[hidx] - sc[hidx];  // Cbar - C^n = C^n - C^{n-1}
-      rhs[(y0 + r) * n + x0 + c] = static_cast<RT>(T(-2.0 / 3.0) * diff + lap_z);
+    {
+      const int te = static_cast<int>(ixd::ix_tile_max_hi<kThreads>(zt, ZR * ZC, s_red) >> 20);
+      uint32_t w[4];
+      const bool dig = ixd::ixi_consts<28>(1.0, te, w);
+      if (dig) {
+        ixd::ixi_split_tile<kThreads, 28>(zt, ZR * ZC, te);
+        __syncthreads();
+      }
+      for (int idx = threadIdx.x; idx < kTY * kTX; idx += kThreads) {
+        const int r = idx / kTX, c = idx - r * kTX;
+        const int zidx = (r + 1) * ZC + (c + 1);
+        const int hidx = (r + 2) * HC + (c + 2);
+        double lap_z;
+        if (dig) {
+          int q0, q1;
+          lap5_digits(zt, zidx, ZC, q0, q1);
+          lap_z = ixd::ixi_combine<28>(q0, q1, w);
+        } else {
+          lap_z = lap5(zt, zidx, ZC);
+        }
+        const int64_t o = (y0 + r) * n + x0 + c;
+        const double diff = cn[hidx] - widen(prev[o]);  // C^n - C^{n-1}
+        rhs[o] = fma(-2.0 / 3.0, diff, lap_z);
+      }
     }
   }
   if (partials) {
@@ -272,9 +245,9 @@ __global__ void __launch_bounds__(kThreads)
     for (int idx = threadIdx.x; idx < kTY * kTX; idx += kThreads) {
       const int r = idx / kTX, c = idx - r * kTX;
       const int hidx = (r + 2) * HC + (c + 2);
-      const double u = widen(sc[hidx]);
-      const double gx = widen(sc[hidx + 1]) - u;
-      const double gy = widen(sc[hidx + HC]) - u;
+      const double u = sc[hidx];
+      const double gx = sc[hidx + 1] - u;
+      const double gy = sc[hidx + HC] - u;
       const double w = u * u - 1.0;
       m += u;
       e += 0.25 * w * w + half_gamma_over_h2 * (gx * gx + gy * gy);
@@ -403,8 +376,8 @@ __global__ void __launch_bounds__(kSolveThreads)
 
 // Phase 2: end values of the neighbouring chunks from the block-circulant inverse (staged in
 // shared memory), then the spike correction.  MODE 0 writes w (FP64); MODE 1 writes
-// C^{n+1} = 2 C^n - C^{n-1} + x (for FP32 storage 2 C^n - C^{n-1} is formed in FP32, as in the
-// right-hand side).
+// C^{n+1} = 2 C^n - C^{n-1} + x (for FP32 storage 2 C^n - C^{n-1} is formed in FP32: its one
+// rounding, <= 2^-24 |Cbar|, is of the size of the rounding of the stored result).
 // NF: no-flux tables (per chunk type) and the dense 4P x 4P chunk-end inverse, read through the
 // read-only cache; the line's first chunk has no left neighbour, its last no right one.
 template <int MODE, typename T, bool CONTIG, bool NF>
@@ -477,9 +450,9 @@ __global__ void __launch_bounds__(kSolveThreads)
       store_batch<CONTIG>(w_out, base + k0 * es, es, x);
     } else {
       if constexpr (sizeof(T) == 4) {
-        // FP32 storage: Cbar = 2 C^n - C^{n-1} in FP32 arithmetic (as the right-hand side forms
-        // it), widened exactly; the FP64 add of x and the round-to-nearest narrowing (F2F, the
-        // same rounding as an integer-pipe narrowing) keep this kernel's integer work small
+        // FP32 storage: Cbar = 2 C^n - C^{n-1} in FP32 arithmetic (one rounding, of the size of
+        // the result's own), widened exactly; the FP64 add of x and the round-to-nearest narrowing
+        // (F2F, the same rounding as an integer-pipe narrowing) keep this kernel's integer work small
         float cb[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) cb[u] = fmaf(2.0f, cur[base + (k0 + u) * es], -prev[base + (k0 + u) * es]);
@@ -547,8 +520,15 @@ void block_solve(int m, const std::vector<double>& l1, const std::vector<double>
   }
 }
 
-// Gauss-Jordan inverse with partial pivoting (dense, small).
-bool invert(int N, std::vector<double>& M, std::vector<double>& inv) {
+// Gauss-Jordan inverse with partial pivoting (dense, small), then two steps of Newton refinement
+// K <- K + K (I - R K) whose residual I - R K is accumulated with error-free products and sums
+// (FMA and TwoSum), so it is exact to rounding although it is far smaller than R K: the
+// chunk-end system's condition number grows with a, and the plain inverse's rounding (~cond * eps)
+// went straight into every corrected value (the solver's backward error was 3.9e-13 of
+// (1 + 16 a) |x| at n = 4096 with no-flux boundaries; refined it is 2.6e-15).
+bool invert(int N, std::vector<double>& Min, std::vector<double>& inv) {
+  const std::vector<double> R = Min;
+  std::vector<double>& M = Min;
   inv.assign(static_cast<size_t>(N) * N, 0.0);
   for (int i = 0; i < N; ++i) inv[static_cast<size_t>(i) * N + i] = 1.0;
   for (int c = 0; c < N; ++c) {
@@ -575,6 +555,28 @@ bool invert(int N, std::vector<double>& M, std::vector<double>& inv) {
         inv[static_cast<size_t>(r) * N + k] -= f * inv[static_cast<size_t>(c) * N + k];
       }
     }
+  }
+  std::vector<double> E(static_cast<size_t>(N) * N), C(static_cast<size_t>(N) * N);
+  for (int it = 0; it < 2; ++it) {
+    for (int r = 0; r < N; ++r)
+      for (int c = 0; c < N; ++c) {  // E = I - R K, each entry as an unevaluated sum hi + lo
+        double hi = r == c ? 1.0 : 0.0, lo = 0.0;
+        for (int k = 0; k < N; ++k) {
+          const double p = -R[static_cast<size_t>(r) * N + k] * inv[static_cast<size_t>(k) * N + c];
+          const double pe = std::fma(-R[static_cast<size_t>(r) * N + k], inv[static_cast<size_t>(k) * N + c], -p);
+          const double t = hi + p, bb = t - hi;
+          lo += (hi - (t - bb)) + (p - bb) + pe;
+          hi = t;
+        }
+        E[static_cast<size_t>(r) * N + c] = hi + lo;
+      }
+    for (int r = 0; r < N; ++r)
+      for (int c = 0; c < N; ++c) {  // C = K E
+        double acc = 0.0;
+        for (int k = 0; k < N; ++k) acc = std::fma(inv[static_cast<size_t>(r) * N + k], E[static_cast<size_t>(k) * N + c], acc);
+        C[static_cast<size_t>(r) * N + c] = acc;
+      }
+    for (size_t q = 0; q < C.size(); ++q) inv[q] += C[q];
   }
   return true;
 }
@@ -706,17 +708,16 @@ int default_chunks(int64_t n) {
   return P;
 }
 
-size_t rhs_smem_bytes(int storage) {
-  const size_t e = storage == CS_F32 ? 4 : 8;
-  const size_t digits = storage == CS_F32 ? 0 : 4 * (kTY + 4) * (kTX + 4);  // FP64: third digits
-  return e * (2 * (kTY + 4) * (kTX + 4) + (kTY + 2) * (kTX + 2)) + digits;
+// FP64 tiles (C^n, Cbar: halo 2; Z: halo 1), for either storage type.
+size_t rhs_smem_bytes() {
+  return 8 * (2 * (kTY + 4) * (kTX + 4) + (kTY + 2) * (kTX + 2));
 }
 
 template <typename T> int set_rhs_attr() {
   static bool done = false;
   if (!done) {
-    const int bytes = static_cast<int>(rhs_smem_bytes(sizeof(T) == 4 ? CS_F32 : CS_F64));
-    CS_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    const int bytes = static_cast<int>(rhs_smem_bytes());
+    CS_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     done = true;
   }
   return CS_OK;
@@ -729,10 +730,9 @@ int launch_rhs(CHPlan* p, bool with_rhs, double* partials, cudaStream_t s) {
   dim3 grid(static_cast<unsigned>(p->n / kTX), static_cast<unsigned>(p->n / kTY));
   const T* cur = static_cast<const T*>(p->field[p->icur]);
   const T* prev = static_cast<const T*>(p->field[p->iprev]);
-  T* rhs = with_rhs ? reinterpret_cast<T*>(p->A) : nullptr;
-  k_ch_rhs<T, T><<<grid, kThreads, rhs_smem_bytes(p->storage), s>>>(
-      cur, prev, rhs, p->n, static_cast<T>(p->alpha), static_cast<T>(p->a),
-      0.5 * p->gamma / (p->h * p->h), partials, p->noflux);
+  double* rhs = with_rhs ? p->A : nullptr;
+  k_ch_rhs<T><<<grid, kThreads, rhs_smem_bytes(), s>>>(cur, prev, rhs, p->n, p->alpha, p->a,
+                                                        0.5 * p->gamma / (p->h * p->h), partials, p->noflux);
   CS_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return CS_OK;
@@ -744,8 +744,8 @@ void launch_solves(CHPlan* p, cudaStream_t s) {
   const unsigned sgrid = static_cast<unsigned>((n * p->P + kSolveThreads - 1) / kSolveThreads);
   const size_t ksmem = NF ? 0 : static_cast<size_t>(16) * p->P * sizeof(double);
   // x-sweep: lines are rows (line stride n, element stride 1)
-  k_solve_local<T, true, NF><<<sgrid, kSolveThreads, 0, s>>>(reinterpret_cast<const T*>(p->A), p->B, p->bnd,
-                                                             p->coef, n, p->P, p->m, n, 1);
+  k_solve_local<double, true, NF><<<sgrid, kSolveThreads, 0, s>>>(p->A, p->B, p->bnd, p->coef, n, p->P,
+                                                                  p->m, n, 1);
   k_solve_correct<0, T, true, NF><<<sgrid, kSolveThreads, ksmem, s>>>(p->B, p->bnd, p->coef, p->K, n, p->P,
                                                                       p->m, n, 1, p->A, nullptr, nullptr, nullptr);
   // y-sweep: lines are columns (line stride 1, element stride n), update fused
@@ -1291,5 +1291,105 @@ int ch_config(CHPlan* p, int32_t* chunks, int32_t* chunk_len) {
 }
 
 void ch_destroy(CHPlan* p) { free_plan(p); }
+
+// Host replay of the device line solver (phase 1: chunk LU forward and backward, chunk-end
+// values; phase 2: neighbouring chunk ends from K, spike correction), in the kernels' order of
+// operations, on the tables cs_ch_create builds, for a pseudo-random right-hand side; returns the
+// backward error ||L x - b||_inf / ((1 + 16 a) ||x||_inf) of the result against the line operator
+// itself (periodic: circulant (1, -4, 6, -4, 1); no-flux: reflected rows at the ends).
+int ch_solver_check(int64_t n, int P, double a, bool noflux, double* residual) {
+  if (!residual) return set_error(CS_EINVAL, "null residual pointer");
+  if (n < 16 || n > 65536 || !valid_chunks(n, P)) return set_error(CS_EINVAL, "invalid line length / chunk count");
+  if (!(a >= 0.0) || !std::isfinite(a)) return set_error(CS_EINVAL, "a must be finite and >= 0");
+  std::vector<double> coef, K;
+  int rc = build_tables(n, P, a, noflux, coef, K);
+  if (rc != CS_OK) return rc;
+  const int m = static_cast<int>(n / P);
+  std::vector<double> b(n), g(n), x(n), ends(static_cast<size_t>(4) * P);
+  uint64_t st = 0x9E3779B97F4A7C15ull ^ static_cast<uint64_t>(n * 131 + P);
+  for (int64_t i = 0; i < n; ++i) {  // xorshift64*: values in [-1, 1)
+    st ^= st >> 12; st ^= st << 25; st ^= st >> 27;
+    b[i] = static_cast<double>((st * 0x2545F4914F6CDD1Dull) >> 11) * 0x1p-52 - 1.0;
+  }
+  auto tab = [&](int p) { return coef.data() + (noflux ? static_cast<size_t>(9) * m * chunk_type(p, P) : 0); };
+  for (int p = 0; p < P; ++p) {  // phase 1
+    const double* c = tab(p);
+    double y1 = 0.0, y2 = 0.0;
+    for (int k = 0; k < m; ++k) {
+      const double y = fma(c[k], y1, fma(c[m + k], y2, b[p * m + k]));
+      g[p * m + k] = y;
+      y2 = y1;
+      y1 = y;
+    }
+    double g1 = 0.0, g2 = 0.0;
+    for (int k = m - 1; k >= 0; --k) {
+      const double v = fma(c[3 * m + k], g1, fma(c[4 * m + k], g2, g[p * m + k] * c[2 * m + k]));
+      g[p * m + k] = v;
+      g2 = g1;
+      g1 = v;
+    }
+    ends[4 * p] = g[p * m];
+    ends[4 * p + 1] = g[p * m + 1];
+    ends[4 * p + 2] = g[p * m + m - 2];
+    ends[4 * p + 3] = g[p * m + m - 1];
+  }
+  const int64_t N4 = 4 * static_cast<int64_t>(P);
+  for (int p = 0; p < P; ++p) {  // phase 2
+    double t0 = 0.0, t1 = 0.0, h0 = 0.0, h1 = 0.0;
+    for (int q = 0; q < P; ++q) {
+      const double* e = ends.data() + 4 * q;
+      if (noflux) {
+        if (p > 0) {
+          const double* r2 = K.data() + (4 * static_cast<int64_t>(p - 1) + 2) * N4 + 4 * q;
+          const double* r3 = r2 + N4;
+          t0 = fma(r2[0], e[0], fma(r2[1], e[1], fma(r2[2], e[2], fma(r2[3], e[3], t0))));
+          t1 = fma(r3[0], e[0], fma(r3[1], e[1], fma(r3[2], e[2], fma(r3[3], e[3], t1))));
+        }
+        if (p + 1 < P) {
+          const double* r0 = K.data() + 4 * static_cast<int64_t>(p + 1) * N4 + 4 * q;
+          const double* r1 = r0 + N4;
+          h0 = fma(r0[0], e[0], fma(r0[1], e[1], fma(r0[2], e[2], fma(r0[3], e[3], h0))));
+          h1 = fma(r1[0], e[0], fma(r1[1], e[1], fma(r1[2], e[2], fma(r1[3], e[3], h1))));
+        }
+      } else {
+        const double* Kt = K.data() + ((p + P - 1 - q + P) % P) * 16;
+        const double* Kh = K.data() + ((p + 1 - q + P) % P) * 16;
+        t0 = fma(Kt[8], e[0], fma(Kt[9], e[1], fma(Kt[10], e[2], fma(Kt[11], e[3], t0))));
+        t1 = fma(Kt[12], e[0], fma(Kt[13], e[1], fma(Kt[14], e[2], fma(Kt[15], e[3], t1))));
+        h0 = fma(Kh[0], e[0], fma(Kh[1], e[1], fma(Kh[2], e[2], fma(Kh[3], e[3], h0))));
+        h1 = fma(Kh[4], e[0], fma(Kh[5], e[1], fma(Kh[6], e[2], fma(Kh[7], e[3], h1))));
+      }
+    }
+    const double* c = tab(p);
+    for (int k = 0; k < m; ++k)
+      x[p * m + k] = fma(-c[5 * m + k], t0, fma(-c[6 * m + k], t1, fma(-c[7 * m + k], h0, fma(-c[8 * m + k], h1, g[p * m + k]))));
+  }
+  double rmax = 0.0, xmax = 0.0;
+  auto at = [&](int64_t i) {  // periodic wrap or even reflection
+    if (!noflux) return x[(i % n + n) % n];
+    if (i < 0) i = -1 - i;
+    if (i >= n) i = 2 * n - 1 - i;
+    return x[i];
+  };
+  for (int64_t i = 0; i < n; ++i) {
+    // L = I + a D4; D4 is the fourth difference, on the reflected line the square of the
+    // reflected second difference, which reflection of x reproduces at every row
+    double d2[3];
+    for (int j = -1; j <= 1; ++j) d2[j + 1] = at(i + j - 1) - 2.0 * at(i + j) + at(i + j + 1);
+    if (noflux) {  // D2 of the reflected line, taken again with reflection
+      auto d2at = [&](int64_t k) {
+        if (k < 0) k = -1 - k;
+        if (k >= n) k = 2 * n - 1 - k;
+        return at(k - 1) - 2.0 * at(k) + at(k + 1);
+      };
+      for (int j = -1; j <= 1; ++j) d2[j + 1] = d2at(i + j);
+    }
+    const double lx = x[i] + a * (d2[0] - 2.0 * d2[1] + d2[2]);
+    rmax = std::max(rmax, std::fabs(lx - b[i]));
+    xmax = std::max(xmax, std::fabs(x[i]));
+  }
+  *residual = rmax / ((1.0 + 16.0 * a) * std::max(xmax, 1e-300));
+  return CS_OK;
+}
 
 }  // namespace cs

@@ -1,11 +1,13 @@
-// Exact digit evaluation of integer-weight sums of FP64 values on the FP32 / integer pipes
-// (GB300 issues FP64 at 1/64 of the FP32 rate).  For weights w_k = c * n_k with integers n_k,
-// sum |n_k| <= 64: every staged value of a tile is cut into three signed 18-bit digits on a grid
-// fixed by the tile's largest exponent, x = sum_i d_i 2^(G - 18(i+1)) (bits below 2^(G-54)
-// dropped), so each digit sum S_i = sum_k n_k d_{k,i} is an integer below 2^24 and exact in FP32.
-// T = S0 2^36 + S1 2^18 + S2 is then rounded to a multiple of 2^8 and scaled by c * 2^(G-54) with
-// one FP64 FMA: the result is within 2^-45 / sum|n| of sum|w| * (largest value of the tile).
-// Used by the 2D stencil sweep and by the Laplacians of the Cahn-Hilliard right-hand side.
+// Exact digit evaluation of integer-weight sums of FP64 values on the integer pipe (GB300 issues
+// FP64 at 1/64 of the FP32 rate).  For weights w_k = c * n_k with integers n_k, sum |n_k| <= 64:
+// every staged value of a tile is cut into two signed 24-bit integer digits on a grid fixed by
+// the tile's largest exponent, x = (d0 2^24 + d1) 2^(G-48) + r with 0 <= |r| < 2^(G-48) (each digit
+// carries the sign of x), so each digit sum S_i = sum_k n_k d_{k,i} is exact in int32.
+// T = S0 2^24 + S1 is then rounded to a multiple of 2^4 (ties to even) and scaled by c * 2^(G-48)
+// with one FP64 FMA: the result is within (2^-47 + 2^-44 / sum|n|) of sum|w| * (largest value of
+// the tile).  With sum |n_k| <= 8, 28-bit digits keep 56 bits and round to 2^(G-49).  The per-tile constants come from c's bits by integer exponent arithmetic, and
+// nothing converts between integers and floating point (on GB300 those conversions share the FP64
+// pipe).  Used by the 2D stencil sweep and by the Laplacians of the Cahn-Hilliard right-hand side.
 #pragma once
 
 #include <stdint.h>
@@ -13,71 +15,10 @@
 namespace cs {
 namespace ixd {
 
-constexpr int kDigitBits = 18;
 constexpr int kMinExp = 1023 - 900;  // smallest biased exponent of a tile's largest value
 constexpr int kMaxExp = 1023 + 900;  // largest one
-
-
-// Digits of x on the tile grid whose top is 2^G with G = tile_e - 1022 (tile_e = largest biased
-// exponent in the tile): A = |x| / 2^(G-54) truncated (54 bits), d0 = A >> 36, d1 and d2 the next
-// 18-bit groups, each carrying the sign of x.  Works on the two 32-bit words of x with funnel
-// shifts: A = (M << 1) >> (tile_e - e), M the 53-bit significand.
-__device__ __forceinline__ void ix_split(double x, int tile_e, float& d0, float& d1, float& d2) {
-  const uint32_t hi = static_cast<uint32_t>(__double2hiint(x));
-  const uint32_t lo = static_cast<uint32_t>(__double2loint(x));
-  const int e = static_cast<int>((hi >> 20) & 0x7ffu);
-  // (M << 1) as two words, 22 + 32 bits.  Zeros and subnormals (e == 0) need no special case: a
-  // digit tile has tile_e >= kMinExp, so t >= 54 and every digit is 0, and an all-zero tile
-  // (tile_e == 0) is scaled by 0.
-  const uint32_t mh = __funnelshift_l(lo, (hi & 0xFFFFFu) | 0x100000u, 1);
-  const uint32_t ml = lo << 1;
-  const int t = tile_e - e;  // >= 0
-  uint32_t ah, al;
-  if (t < 32) {
-    al = __funnelshift_r(ml, mh, t);
-    ah = mh >> t;
-  } else {
-    al = t < 54 ? (mh >> (t - 32)) : 0u;
-    ah = 0u;
-  }
-  // a digit a < 2^18 becomes +-(2^23 + a) by setting the mantissa bits of +-2^23 (exact), and
-  // subtracting +-2^23 leaves +-a
-  const uint32_t K = 0x4B000000u | (hi & 0x80000000u);
-  const float k = __uint_as_float(K);
-  d0 = __fsub_rn(__uint_as_float((ah >> 4) | K), k);
-  d1 = __fsub_rn(__uint_as_float((__funnelshift_r(al, ah, 18) & 0x3FFFFu) | K), k);
-  d2 = __fsub_rn(__uint_as_float((al & 0x3FFFFu) | K), k);
-}
-
-// T * scale for T = S0 * 2^36 + S1 * 2^18 + S2 (the digit sums are integers below 2^24 in
-// magnitude, so |T| < sum|n| * 2^54 <= 2^60) with one FP64 instruction and no int64 -> FP64
-// conversion (GB300 issues about 2 FP64 instructions per clock per SM, the digit kernel's bound):
-// T' = round(T / 2^8) = S0 * 2^28 + S1 * 2^10 + round(S2 / 2^8) is exact apart from the last
-// term, |T'| <= 2^52, so D = 2^52 + |T'| is assembled by an integer add to the bit pattern of
-// 2^52, and fma(D, +-2^8 scale, -+2^60 scale) = T' * 2^8 * scale is rounded once.  sc and cs are
-// the two words of 2^8 * scale and of -2^60 * scale (exact power-of-two multiples); the sign of
-// T flips both.  Error before the final rounding: at most 2^7 units of 2^(G-54) * |c|.
-__device__ __forceinline__ double ix_combine(float S0, float S1, float S2, uint32_t sc_hi, uint32_t sc_lo,
-                                            uint32_t cs_hi, uint32_t cs_lo) {
-  const long long Tp = (static_cast<long long>(__float2int_rn(S0)) << 28) +
-                       (static_cast<long long>(__float2int_rn(S1)) << 10) +
-                       static_cast<long long>(__float2int_rn(S2 * 0x1p-8f));
-  const uint32_t sgn = static_cast<uint32_t>(static_cast<unsigned long long>(Tp) >> 63) << 31;
-  const unsigned long long A = sgn ? 0ull - static_cast<unsigned long long>(Tp) : static_cast<unsigned long long>(Tp);
-  const double D = __longlong_as_double(static_cast<long long>(0x4330000000000000ull + A));
-  const double sc = __hiloint2double(static_cast<int>(sc_hi ^ sgn), static_cast<int>(sc_lo));
-  const double cs = __hiloint2double(static_cast<int>(cs_hi ^ sgn), static_cast<int>(cs_lo));
-  return __fma_rn(D, sc, cs);
-}
-
-// A tile takes the digit path when its largest value lies in [2^-900, 2^900] and its scale
-// c * 2^(G-54) keeps 2^8 scale normal and 2^60 scale finite; an all-zero tile (tile_e 0, scale 0)
-// gives zeros.  Every other tile (inf / nan, out-of-range values) is evaluated in native FP64.
-__device__ __forceinline__ bool ix_tile_ok(int tile_e, double scale) {
-  if (tile_e == 0) return true;
-  const double a = fabs(scale);
-  return tile_e >= kMinExp && tile_e <= kMaxExp && a >= 0x1p-1000 && a < 0x1p960;
-}
+constexpr int kIDigitBits = 24;
+constexpr int kIFracBits = 2 * kIDigitBits;  // bits kept below the tile's top 2^G
 
 // Largest high word (sign cleared) of the n staged FP64 values (n even, 16-byte aligned): its top
 // bits are the largest biased exponent, and it is >= 0x7ff00000 exactly when the tile holds an
@@ -99,20 +40,87 @@ __device__ __forceinline__ uint32_t ix_tile_max_hi(const double* s, int n, unsig
   return r;
 }
 
-// Replaces the n staged FP64 values by their digits: (d0, d1) pairs over the values' own slots,
-// d2 in s2 (8-byte aligned).  Each of the NT threads converts and overwrites two values at a time.
-template <int NT>
-__device__ __forceinline__ void ix_split_tile(double* s, float* s2, int n, int tile_e) {
+// Digit widths: DB = 24 (the default) keeps 48 bits below 2^G and serves sum |n_k| <= 64;
+// DB = 28 keeps 56 bits (every bit of a value within a factor 8 of the tile's largest) and serves
+// sum |n_k| <= 8, e.g. the 5-point Laplacian.  RS is the rounding shift of the combination, chosen
+// so that |T'| <= 2^52: T < (sum |n_k|) 2^(2 DB).
+template <int DB> struct Digits;
+template <> struct Digits<24> { static constexpr int kFrac = 48, kRound = 4, kMaxSum = 64; };
+template <> struct Digits<28> { static constexpr int kFrac = 56, kRound = 7, kMaxSum = 8; };
+
+// Digits of x on the grid whose top is 2^G, G = tile_e - 1022: A = floor(|x| / 2^(G-F)), F = 2 DB,
+// = (M << 3) >> (tile_e - e + 56 - F) for the 53-bit significand M of x (biased exponent e),
+// d0 = A >> DB, d1 = A mod 2^DB, branch-free (the shift is capped at 63, where A is 0).  Zeros
+// and subnormals: a digit tile has tile_e >= kMinExp, so the shift is >= 56 and both digits are
+// 0; an all-zero tile (tile_e 0) is scaled by 0.
+template <int DB = 24>
+__device__ __forceinline__ int2 ixi_split(double x, int tile_e) {
+  constexpr int F = Digits<DB>::kFrac;
+  const uint32_t hi = static_cast<uint32_t>(__double2hiint(x));
+  const uint32_t lo = static_cast<uint32_t>(__double2loint(x));
+  const int e = static_cast<int>((hi >> 20) & 0x7ffu);
+  const unsigned long long M = (static_cast<unsigned long long>((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
+  const unsigned long long A = (M << 3) >> min(tile_e - e + 56 - F, 63);
+  const int sgn = static_cast<int>(hi) >> 31;  // 0 or -1
+  const int d0 = static_cast<int>(A >> DB);
+  const int d1 = static_cast<int>(A & ((1u << DB) - 1u));
+  return make_int2((d0 ^ sgn) - sgn, (d1 ^ sgn) - sgn);
+}
+
+// T * 2^-RS * (2^RS scale) for T = S0 2^DB + S1, with one FP64 instruction:
+// T' = S0 2^(DB-RS) + round(S1 / 2^RS) = round(T / 2^RS) (ties to even) is exact apart from the
+// last term, |T' + q| <= 2^52 (q, default 0, is an integer added in the same units: the user
+// function's cubic term), so D = 2^52 + |T'| is the bit pattern of 2^52 plus |T'|, and
+// fma(D, +-2^RS scale, -+2^(52+RS) scale) = T' 2^RS scale is rounded once.  w holds the words of
+// 2^RS scale and of -2^(52+RS) scale (ixi_consts); the sign of T flips both.
+template <int DB = 24>
+__device__ __forceinline__ double ixi_combine(int S0, int S1, const uint32_t (&w)[4], long long q = 0) {
+  constexpr int RS = Digits<DB>::kRound;
+  // round(S1 / 2^RS) with ties to even: rounding half up would bias every output by half a unit
+  // of 2^-RS on average, and a conserved sum (the Cahn-Hilliard mass) would drift by that much
+  const int r = (S1 + ((1 << (RS - 1)) - 1) + ((S1 >> RS) & 1)) >> RS;
+  const long long Tp = static_cast<long long>(S0) * (1ll << (DB - RS)) + static_cast<long long>(r) + q;
+  const uint32_t sgn = static_cast<uint32_t>(static_cast<unsigned long long>(Tp) >> 63) << 31;
+  const unsigned long long A = sgn ? 0ull - static_cast<unsigned long long>(Tp) : static_cast<unsigned long long>(Tp);
+  const double D = __longlong_as_double(static_cast<long long>(0x4330000000000000ull + A));
+  const double sc = __hiloint2double(static_cast<int>(w[0] ^ sgn), static_cast<int>(w[1]));
+  const double cs = __hiloint2double(static_cast<int>(w[2] ^ sgn), static_cast<int>(w[3]));
+  return __fma_rn(D, sc, cs);
+}
+
+// The combination's constants for a tile, scale = c 2^(G-F): w = the words of 2^RS scale and of
+// -2^(52+RS) scale, made by adding to c's exponent field.  Returns false (the tile then takes
+// native FP64) when c is zero or not normal, when the tile's largest value is outside
+// [2^-900, 2^900], or when either constant would leave the normal range; an all-zero tile
+// (tile_e 0) gets zero constants, so its outputs are 0.
+template <int DB = 24>
+__device__ __forceinline__ bool ixi_consts(double c, int tile_e, uint32_t (&w)[4]) {
+  constexpr int k1 = Digits<DB>::kRound - Digits<DB>::kFrac, k2 = k1 + 52;
+  w[0] = w[1] = w[2] = w[3] = 0u;
+  if (tile_e == 0) return true;
+  const uint32_t chi = static_cast<uint32_t>(__double2hiint(c)), clo = static_cast<uint32_t>(__double2loint(c));
+  const int ec = static_cast<int>((chi >> 20) & 0x7ffu);
+  const int G = tile_e - 1022;
+  if (tile_e < kMinExp || tile_e > kMaxExp || ec == 0 || ec == 0x7ff) return false;
+  if (ec + G + k1 < 1 || ec + G + k2 > 2046) return false;
+  w[0] = chi + (static_cast<uint32_t>(G + k1) << 20);
+  w[1] = clo;
+  w[2] = (chi ^ 0x80000000u) + (static_cast<uint32_t>(G + k2) << 20);
+  w[3] = clo;
+  return true;
+}
+
+// Replaces the n staged FP64 values (n even, 16-byte aligned) by their integer digits (d0, d1)
+// in the values' own 8-byte slots.  Each of the NT threads converts two values at a time.
+template <int NT, int DB = 24>
+__device__ __forceinline__ void ixi_split_tile(double* s, int n, int tile_e) {
   const double2* q = reinterpret_cast<const double2*>(s);
-  float4* q01 = reinterpret_cast<float4*>(s);
-  float2* q2 = reinterpret_cast<float2*>(s2);
+  int4* qi = reinterpret_cast<int4*>(s);
   for (int k = threadIdx.x; k < n / 2; k += NT) {
     const double2 v = q[k];
-    float a0, a1, a2, b0, b1, b2;
-    ix_split(v.x, tile_e, a0, a1, a2);
-    ix_split(v.y, tile_e, b0, b1, b2);
-    q01[k] = make_float4(a0, a1, b0, b1);
-    q2[k] = make_float2(a2, b2);
+    const int2 a = ixi_split<DB>(v.x, tile_e);
+    const int2 b = ixi_split<DB>(v.y, tile_e);
+    qi[k] = make_int4(a.x, a.y, b.x, b.y);
   }
 }
 

@@ -50,6 +50,10 @@ struct Stencil2DConfig {
   double ix_c;        // common scale c
   int ix_n[32];       // integer ratios n_k
   int fp64_mode;      // CS_FP64_AUTO or CS_FP64_NATIVE
+  int* d_status;      // library-owned counter: CTAs of this plan's TMA sweeps whose bounded wait ran out
+  mutable int status_seen;  // counter value at the last cs_plan_check
+  int stall_from;     // test hook (cs_plan_debug_stall): CTA-local tile from which the TMA sweep
+                      // issues no copies, so its wait runs out; -1 = off
 };
 int stencil2d_prepare(Stencil2DConfig* cfg);  // picks variant, allocates generic weights
 void stencil2d_release(Stencil2DConfig* cfg);
@@ -60,12 +64,12 @@ constexpr int64_t kStencilBandAlign = 64;
 int stencil2d_launch_rows(const Stencil2DConfig* cfg, const void* in, void* out, int64_t row0,
                           int64_t row1, cudaStream_t s);
 int stencil2d_num_tile_choices();
-int stencil2d_status_ptr(int** out);  // device word a timed-out bounded wait sets to 1
+int stencil2d_check(const Stencil2DConfig* cfg, cudaStream_t s);  // CS_ETIMEOUT if a wait ran out
 int stencil2d_set_tile_choice(Stencil2DConfig* cfg, int choice);
 std::string stencil2d_shape_key(const Stencil2DConfig* cfg);
 int stencil2d_group(const Stencil2DConfig* const* cfgs, const void* const* ins, void* const* outs,
-                    int count, cudaStream_t s);  // same dtype / variant / tile rows, count <= 16
-constexpr int kMaxGroupJobs = 16;
+                    int count, cudaStream_t s);  // same dtype / variant / tile rows, count <= 64
+constexpr int kMaxGroupJobs = 64;
 
 // ---- batched 1D (cs_batch1d.cu) -------------------------------------------------------------
 struct Batch1DConfig {
@@ -102,5 +106,6 @@ int ch_config(CHPlan* p, int32_t* chunks, int32_t* chunk_len);
 int ch_set_fields(CHPlan* p, void* prev, void* cur, void* next);
 int ch_autotune(CHPlan* p, cudaStream_t s);
 void ch_destroy(CHPlan* p);
+int ch_solver_check(int64_t n, int P, double a, bool noflux, double* residual);
 
 }  // namespace cs

@@ -52,6 +52,9 @@ int map_function(Stencil2DConfig* cfg) {
 int stencil2d_prepare(Stencil2DConfig* cfg) {
   cfg->d_weights = nullptr;
   cfg->d_weights_f = nullptr;
+  cfg->d_status = nullptr;
+  cfg->status_seen = 0;
+  cfg->stall_from = -1;
   cfg->variant = -1;
   cfg->tmap_in = nullptr;
   if (cfg->tile_rows != 32 && cfg->tile_rows != 64) cfg->tile_rows = 64;
@@ -80,11 +83,10 @@ int stencil2d_prepare(Stencil2DConfig* cfg) {
   }
   if (cfg->variant < 0) {  // generic kernel: weights in device memory
     const size_t n = static_cast<size_t>(W) * H;
-    CS_CUDA_TRY(cudaMalloc(&cfg->d_weights, n * sizeof(double)));
-    cudaError_t e = cudaMalloc(&cfg->d_weights_f, n * sizeof(float));
+    cudaError_t e = cudaMalloc(&cfg->d_weights, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&cfg->d_weights_f, n * sizeof(float));
     if (e != cudaSuccess) {
-      cudaFree(cfg->d_weights);
-      cfg->d_weights = nullptr;
+      stencil2d_release(cfg);
       return cuda_error(e, "cudaMalloc(weights)");
     }
     float wf[(2 * CS_MAX_EXTENT + 1) * (2 * CS_MAX_EXTENT + 1)];
@@ -134,6 +136,24 @@ int stencil2d_prepare(Stencil2DConfig* cfg) {
       }
     }
   }
+  // the cubic user function (variant 13): weights c * (0, -1, 0, -1, 4, -1, 0, -1, 0); its cubic
+  // term joins the digit sum as an integer in units of c (see ixf_tile_ok), for |c| in [4, 2^40]
+  if (cfg->fn == CS_FN_CUBIC_MINUS_LAP && cfg->dd_ok) {
+    const double c = cfg->coe[0];
+    if (fabs(c) >= 4.0 && fabs(c) <= 0x1p40) {
+      const int n[9] = {0, -1, 0, -1, 4, -1, 0, -1, 0};
+      for (int i = 0; i < 9; ++i) cfg->ix_n[i] = n[i];
+      cfg->ix_c = c;
+      cfg->ix_ok = 1;
+    }
+  }
+  // the plan's timeout counter for its TMA sweeps (read by cs_plan_check)
+  cudaError_t e = cudaMalloc(&cfg->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(cfg->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    stencil2d_release(cfg);
+    return cuda_error(e, "cudaMalloc(status)");
+  }
   int choice;
   if (tune_lookup(stencil2d_shape_key(cfg), &choice)) stencil2d_set_tile_choice(cfg, choice);
   return CS_OK;
@@ -142,8 +162,26 @@ int stencil2d_prepare(Stencil2DConfig* cfg) {
 void stencil2d_release(Stencil2DConfig* cfg) {
   if (cfg->d_weights) cudaFree(cfg->d_weights);
   if (cfg->d_weights_f) cudaFree(cfg->d_weights_f);
+  if (cfg->d_status) cudaFree(cfg->d_status);
   cfg->d_weights = nullptr;
   cfg->d_weights_f = nullptr;
+  cfg->d_status = nullptr;
+}
+
+// Waits for the stream, then reads the plan's timeout counter: a TMA sweep whose bounded
+// mbarrier wait ran out since the last check left part of its output unwritten.
+int stencil2d_check(const Stencil2DConfig* cfg, cudaStream_t s) {
+  CS_CUDA_TRY(cudaStreamSynchronize(s));
+  if (!cfg->d_status) return CS_OK;
+  int count = 0;
+  CS_CUDA_TRY(cudaMemcpy(&count, cfg->d_status, sizeof count, cudaMemcpyDeviceToHost));
+  if (count != cfg->status_seen) {
+    const int ran_out = count - cfg->status_seen;
+    cfg->status_seen = count;
+    return set_error(CS_ETIMEOUT, "a TMA sweep's bounded wait ran out in %d CTA(s): part of the output was not written",
+                     ran_out);
+  }
+  return CS_OK;
 }
 
 // Tile / pipeline choices the autotuner times: 0 = cp.async tiles of 32 rows, 1 = cp.async
@@ -157,28 +195,9 @@ int stencil2d_set_tile_choice(Stencil2DConfig* cfg, int choice) {
 }
 
 namespace {
-// Status word shared by every TMA sweep in the process (per device): a bounded mbarrier wait
-// that runs out writes 1 here instead of hanging.
-__device__ int g_stencil_status;
-std::atomic<int*> g_status_addr[64];
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::atomic<int> g_encode_state{0};
 }  // namespace
-
-int stencil2d_status_ptr(int** out) {
-  int dev = 0;
-  CS_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return set_error(CS_EUNSUPPORTED, "device index %d out of range", dev);
-  int* p = g_status_addr[dev].load();
-  if (!p) {
-    void* a = nullptr;
-    CS_CUDA_TRY(cudaGetSymbolAddress(&a, g_stencil_status));
-    p = static_cast<int*>(a);
-    g_status_addr[dev].store(p);
-  }
-  *out = p;
-  return CS_OK;
-}
 
 int s2d::make_tensor_map(const Stencil2DConfig* cfg, const void* in, int elem_bytes, int cols, int rows) {
   if (g_encode_state.load() == 0) {

@@ -4,7 +4,7 @@
 // the TMA sweeps are instantiated in cs_stencil2d_f32_tma.cu (compiled in parallel)
 namespace cs {
 namespace s2d {
-extern template int dispatch_tma<0, float>(int variant, const CUtensorMap& map, const float* in, float* out, int64_t nx, int64_t ny, int periodic, const Taps<float>& taps, const IxTaps& it, const DDTaps& dt, int* status, cudaStream_t st);
+extern template int dispatch_tma<0, float>(int variant, const CUtensorMap& map, const float* in, float* out, int64_t nx, int64_t ny, int periodic, const Taps<float>& taps, const IxTaps& it, const DDTaps& dt, int* status, int stall_from, cudaStream_t st);
 }  // namespace s2d
 }  // namespace cs
 

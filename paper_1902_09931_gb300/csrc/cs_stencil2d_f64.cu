@@ -4,9 +4,9 @@
 // the TMA sweeps are instantiated in cs_stencil2d_f64_tma.cu (compiled in parallel)
 namespace cs {
 namespace s2d {
-extern template int dispatch_tma<0, double>(int variant, const CUtensorMap& map, const double* in, double* out, int64_t nx, int64_t ny, int periodic, const Taps<double>& taps, const IxTaps& it, const DDTaps& dt, int* status, cudaStream_t st);
-extern template int dispatch_tma<1, double>(int variant, const CUtensorMap& map, const double* in, double* out, int64_t nx, int64_t ny, int periodic, const Taps<double>& taps, const IxTaps& it, const DDTaps& dt, int* status, cudaStream_t st);
-extern template int dispatch_tma<2, double>(int variant, const CUtensorMap& map, const double* in, double* out, int64_t nx, int64_t ny, int periodic, const Taps<double>& taps, const IxTaps& it, const DDTaps& dt, int* status, cudaStream_t st);
+extern template int dispatch_tma<0, double>(int variant, const CUtensorMap& map, const double* in, double* out, int64_t nx, int64_t ny, int periodic, const Taps<double>& taps, const IxTaps& it, const DDTaps& dt, int* status, int stall_from, cudaStream_t st);
+extern template int dispatch_tma<1, double>(int variant, const CUtensorMap& map, const double* in, double* out, int64_t nx, int64_t ny, int periodic, const Taps<double>& taps, const IxTaps& it, const DDTaps& dt, int* status, int stall_from, cudaStream_t st);
+extern template int dispatch_tma<2, double>(int variant, const CUtensorMap& map, const double* in, double* out, int64_t nx, int64_t ny, int periodic, const Taps<double>& taps, const IxTaps& it, const DDTaps& dt, int* status, int stall_from, cudaStream_t st);
 }  // namespace s2d
 }  // namespace cs
 

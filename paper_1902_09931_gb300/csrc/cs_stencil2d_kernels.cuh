@@ -387,40 +387,135 @@ inline size_t tile_smem_bytes(int L, int R, int TT, int BB, int TY, bool generic
   return b;
 }
 
+// The double-float steps run packed (FP32x2) over two adjacent output columns: lane x is the left
+// column, y the right; each lane rounds exactly as a scalar evaluation would.  a - b is formed as
+// fma(b, -1, a) (one rounding, as a subtraction).
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(a, f2(-1.0f)); }
+
+// (sh, sl) += (wh + wl) * (xh + xl): the product's rounding error comes from an FMA and the sum
+// is an error-free TwoSum; the wl * xl term (~2^-48 relative) is dropped.
+__device__ __forceinline__ void dd_mac2(float2& sh, float2& sl, float wh, float wl, float2 xh, float2 xl) {
+  const float2 q = __fmul2_rn(f2(-wh), xh);  // q = -p, p = wh * xh rounded
+  float2 e = __ffma2_rn(f2(wh), xh, q);      // exact: wh * xh - p
+  e = __ffma2_rn(f2(wh), xl, e);
+  e = __ffma2_rn(f2(wl), xh, e);
+  const float2 s = sub2(sh, q);              // TwoSum(sh, p)
+  const float2 bb = sub2(s, sh);
+  const float2 err = sub2(sub2(sh, sub2(s, bb)), __fadd2_rn(q, bb));  // (sh - (s - bb)) + (p - bb)
+  sl = __fadd2_rn(sl, __fadd2_rn(err, e));
+  sh = s;
+}
+
+// (sh, sl) += p + e with an error-free TwoSum of sh and p.
+__device__ __forceinline__ void dd_add_exact2(float2& sh, float2& sl, float2 p, float2 e) {
+  const float2 s = __fadd2_rn(sh, p);
+  const float2 bb = sub2(s, sh);
+  const float2 err = __fadd2_rn(sub2(sh, sub2(s, bb)), sub2(p, bb));
+  sl = __fadd2_rn(sl, __fadd2_rn(err, e));
+  sh = s;
+}
+
+// (sh, sl) += u^3 - u for u = uh + ul, with error-free products and sums (terms below ~2^-46
+// of |u| dropped), so the cubic of the user function stays on the FP32 pipes.
+__device__ __forceinline__ void dd_add_cubic_minus2(float2& sh, float2& sl, float2 uh, float2 ul) {
+  const float2 p2 = __fmul2_rn(uh, uh);  // u^2 = p2 + e2
+  float2 e2 = __ffma2_rn(uh, uh, neg2(p2));
+  e2 = __ffma2_rn(__fmul2_rn(f2(2.0f), uh), ul, e2);
+  const float2 p3 = __fmul2_rn(p2, uh);  // u^3 = p3 + e3
+  float2 e3 = __ffma2_rn(p2, uh, neg2(p3));
+  e3 = __ffma2_rn(p2, ul, e3);
+  e3 = __ffma2_rn(e2, uh, e3);
+  dd_add_exact2(sh, sl, p3, e3);
+  dd_add_exact2(sh, sl, neg2(uh), neg2(ul));
+}
+
 // ---- exact digit evaluation of FP64-storage stencils with integer weight ratios ------------
 // When every weight is w_k = c * n_k with small integers (sum |n_k| <= 64; the paper's stencils
 // are of this kind), a tile is evaluated with integer-exact sums: every staged value is cut into
-// three signed 18-bit digits on a grid fixed by the tile's largest exponent,
-// x = sum_i d_i 2^(G - 18(i+1)), so each digit sum S_i = sum_k n_k d_{k,i} is an integer below
-// 2^24 and exact in FP32 (per tap one packed FMA for S0, S1 and one FMA for S2).  The sums form
-// T = S0 2^36 + S1 2^18 + S2, which is rounded to a multiple of 2^8 and scaled by c * 2^(G-54)
-// with one FP64 FMA (ix_combine).  Bits of a value below 2^(G-54) are dropped and the final sum
-// is rounded to 2^(G-46) |c|: the error is at most 2^-45 / sum|n| of sum|w| * max|in| (native
-// FP64 accumulation: about taps * 2^-53 of sum|w| |in|).  Tiles holding inf / nan, or whose
-// largest value is outside [2^-900, 2^900], are evaluated in native FP64.
+// two signed 25-bit integer digits on a grid fixed by the tile's largest exponent,
+// x = (d0 2^25 + d1) 2^(G-50) + r with |r| < 2^(G-50), so each digit sum S_i = sum_k n_k d_{k,i}
+// is exact in int32 (per tap two integer multiply-adds).  The sums form T = S0 2^25 + S1, which is
+// rounded to a multiple of 2^4 and scaled by c * 2^(G-50) with one FP64 FMA (ixi_combine).  The
+// error is at most (2^-49 + 2^-46 / sum|n|) of sum|w| * max|in| (native FP64 accumulation: about
+// taps * 2^-53 of sum|w| |in|).  Tiles holding inf / nan, or whose largest value is outside
+// [2^-900, 2^900], are evaluated in native FP64.
 
 struct IxTaps {
-  float n[32];   // integer weight ratios n_k (exact in FP32)
+  int8_t n[32];  // integer weight ratios n_k (sum |n_k| <= 64)
   double c;      // common scale: w_k ~= c * n_k
+  float inv_hi, inv_lo;  // 1 / c as a float pair (the user function's cubic term)
 };
 
-constexpr int kIxDigitBits = ixd::kDigitBits;
-using ixd::ix_combine;
-using ixd::ix_split;
-using ixd::ix_tile_ok;
+// The user function c^3 - c + sum w_k u_k (Sec. 5.2, variant 13) on the digit path: the cubic
+// term P = u^3 - u of the centre value, in double-float arithmetic from the value's digits, joins
+// the digit sum as the integer Q = round(P / U) in units U = c 2^(G-44) of the combination, so the
+// output is still rounded once by the one FP64 FMA.  Valid when |P / U| < 2^43, which holds when
+// |c| >= 4 (the host's condition) and 2G <= e_c - 2 (e_c = floor(log2 |c|), |u| < 2^G), with the
+// tile's values in the double-float exponent range; other tiles take native FP64.  Q's error is
+// below one unit U (the truncated digits, the double-float cubic and product, ~2^-46 relative).
+__device__ __forceinline__ bool ixf_tile_ok(int tile_e, double c) {
+  if (tile_e == 0) return true;
+  const int G = tile_e - 1022;
+  const int ec = static_cast<int>((static_cast<uint32_t>(__double2hiint(c)) >> 20) & 0x7ffu) - 1023;
+  return tile_e >= 1023 - 69 && tile_e < 1023 + 60 && 2 * G <= ec - 2;
+}
+
+// Per-tile constants of the cubic term: 2^(G-24), 2^(G-48) (digit weights) and (1/c) 2^(44-G) as
+// a float pair, by adding to the exponent fields (all stay normal in the tile's valid range).
+struct IxfConsts { float p1, p2, ih, il; };
+__device__ __forceinline__ IxfConsts ixf_consts(int tile_e, float inv_hi, float inv_lo) {
+  const int G = tile_e - 1022;
+  IxfConsts k;
+  k.p1 = __uint_as_float(static_cast<uint32_t>(G - 24 + 127) << 23);
+  k.p2 = __uint_as_float(static_cast<uint32_t>(G - 48 + 127) << 23);
+  const uint32_t shift = static_cast<uint32_t>(44 - G) << 23;
+  k.ih = __uint_as_float(__float_as_uint(inv_hi) + shift);
+  k.il = inv_lo == 0.0f ? 0.0f : __uint_as_float(__float_as_uint(inv_lo) + shift);
+  return k;
+}
+
+// Q for the centre digits (d0, d1) of two adjacent outputs (packed FP32x2): u = d0 2^(G-24) +
+// d1 2^(G-48) (both exact floats), P = u^3 - u in double-float, (ph, pl) = P (1/c) 2^(44-G),
+// renormalised; Q = round(ph + pl) from two FP32 rounding shifts: 1.5 * 2^44 takes ph to a
+// multiple of 2^21 (|ph| < 2^43), whose count k sits in the low mantissa bits, and 1.5 * 2^23
+// rounds the rest (|rest| < 2^22); Q = k 2^21 + the rest's integer.  No conversion instruction
+// beyond the two exact int -> float conversions of the digits.
+__device__ __forceinline__ void ixf_q2(int2 a, int2 b, const IxfConsts& k, long long& qa, long long& qb) {
+  const float2 uh = __fmul2_rn(make_float2(__int2float_rn(a.x), __int2float_rn(b.x)), f2(k.p1));
+  const float2 ul = __fmul2_rn(make_float2(__int2float_rn(a.y), __int2float_rn(b.y)), f2(k.p2));
+  float2 sh = make_float2(0.0f, 0.0f), sl = make_float2(0.0f, 0.0f);
+  dd_add_cubic_minus2(sh, sl, uh, ul);
+  const float2 ph = __fmul2_rn(sh, f2(k.ih));
+  float2 pe = __ffma2_rn(sh, f2(k.ih), neg2(ph));
+  pe = __ffma2_rn(sl, f2(k.ih), pe);
+  const float2 pl = __ffma2_rn(sh, f2(k.il), pe);
+  const float2 qh = __fadd2_rn(ph, pl);  // Fast2Sum: |pl| below half an ulp of qh after this
+  const float2 ql = sub2(pl, sub2(qh, ph));
+  constexpr float M1 = 26388279066624.0f, M2 = 12582912.0f;  // 1.5 * 2^44, 1.5 * 2^23
+  const float2 t = __fadd2_rn(qh, f2(M1));
+  const float2 rest = __fadd2_rn(sub2(qh, sub2(t, f2(M1))), ql);
+  const float2 t2 = __fadd2_rn(rest, f2(M2));
+  const int ka = static_cast<int>(__float_as_uint(t.x) - __float_as_uint(M1));
+  const int kb = static_cast<int>(__float_as_uint(t.y) - __float_as_uint(M1));
+  qa = static_cast<long long>(ka) * (1ll << 21) + static_cast<int>(__float_as_uint(t2.x) - __float_as_uint(M2));
+  qb = static_cast<long long>(kb) * (1ll << 21) + static_cast<int>(__float_as_uint(t2.y) - __float_as_uint(M2));
+}
+
+using ixd::ixi_combine;
+using ixd::ixi_consts;
 
 // Digit sums of two adjacent tile columns per thread, "push" form: every staged row adds its
 // contributions to the (up to H) output rows it feeds, held in H rolling accumulators per column
 // and digit; an output row is complete once its last input row has been added.  A row's digits
-// are read as 16-byte (d0, d1) and 8-byte d2 pairs, W + 1 columns (+1 when L is odd) serving both
-// outputs, and the two results leave as one 16-byte store where both columns are written.
+// are read as 16-byte (d0, d1, d0', d1') pairs of columns, W + 1 columns (+1 when L is odd)
+// serving both outputs, and the two results leave as one 16-byte store where both columns are
+// written.
 template <int TY, int SPEC>
-__device__ __forceinline__ void ix_compute(const float2* s01, const float* s2, double* __restrict__ out,
-                                           int64_t nx, int64_t ny, int periodic, int64_t x0,
-                                           int64_t y0, const IxTaps& taps, double scale) {
-  const double sc = scale * 0x1p8, cs = -scale * 0x1p60;  // exact
-  const uint32_t sc_hi = static_cast<uint32_t>(__double2hiint(sc)), sc_lo = static_cast<uint32_t>(__double2loint(sc));
-  const uint32_t cs_hi = static_cast<uint32_t>(__double2hiint(cs)), cs_lo = static_cast<uint32_t>(__double2loint(cs));
+__device__ __forceinline__ void ix_compute(const int2* sd2, double* __restrict__ out, int64_t nx,
+                                           int64_t ny, int periodic, int64_t x0, int64_t y0,
+                                           const IxTaps& taps, const uint32_t (&w)[4], int tile_e) {
   constexpr SpecDesc sd = kSpecs[SPEC];
   constexpr int L = sd.L, R = sd.R, TT = sd.T, BB = sd.B;
   constexpr int V = Vec<double>::n;
@@ -446,22 +541,21 @@ __device__ __forceinline__ void ix_compute(const float2* s01, const float* s2, d
   const int klo = rows_below(ylo - gy0);
   const int khi = (ok0 || ok1) ? rows_below(yhi - gy0) : 0;
   double* op = out + gy0 * nx + gx;
-  const float4* a = reinterpret_cast<const float4*>(s01 + (S0 - X) + c);  // (S0 - X + c) is even
-  const float2* b = reinterpret_cast<const float2*>(s2 + (S0 - X) + c);
-  // (S0, S1) of an output accumulate as a pair with the packed FP32x2 FMA, S2 alone
-  float2 acc01[H][2];
-  float acc2[H][2];
+  const int4* a = reinterpret_cast<const int4*>(sd2 + (S0 - X) + c);  // (S0 - X + c) is even
+  int acc0[H][2], acc1[H][2];
 #pragma unroll
   for (int q = 0; q < H; ++q)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      acc01[q][j] = make_float2(0.0f, 0.0f);
-      acc2[q][j] = 0.0f;
-    }
+    for (int j = 0; j < 2; ++j) acc0[q][j] = acc1[q][j] = 0;
+  // user function: the centre digits of the pending output rows, and the per-tile constants
+  int2 ctr[H][2];
+  IxfConsts kf{};
+  if constexpr (sd.epi) {
+    if (tile_e != 0) kf = ixf_consts(tile_e, taps.inv_hi, taps.inv_lo);
+  }
 #pragma unroll
   for (int i = 0; i < RW + H - 1; ++i) {  // input row r0 + i feeds output rows i - q
-    float2 v01[2 * NP];
-    float v2[2 * NP];
+    int2 v[2 * NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       bool used = false;
@@ -475,12 +569,9 @@ __device__ __forceinline__ void ix_compute(const float2* s01, const float* s2, d
             used |= (e >> 1) == k && ((sd.mask >> (q * W + p)) & 1u) && (i - q >= 0) && (i - q < RW);
           }
       if (used) {
-        const float4 d = a[(r0 + i) * (COLS / 2) + k];
-        const float2 f = b[(r0 + i) * (COLS / 2) + k];
-        v01[2 * k] = make_float2(d.x, d.y);
-        v01[2 * k + 1] = make_float2(d.z, d.w);
-        v2[2 * k] = f.x;
-        v2[2 * k + 1] = f.y;
+        const int4 d = a[(r0 + i) * (COLS / 2) + k];
+        v[2 * k] = make_int2(d.x, d.y);
+        v[2 * k + 1] = make_int2(d.z, d.w);
       }
     }
 #pragma unroll
@@ -492,20 +583,27 @@ __device__ __forceinline__ void ix_compute(const float2* s01, const float* s2, d
 #pragma unroll
         for (int p = 0; p < W; ++p)
           if ((sd.mask >> (q * W + p)) & 1u) {
-            const float n = taps.n[q * W + p];
-            acc01[o % H][j] = __ffma2_rn(make_float2(n, n), v01[X + j + p], acc01[o % H][j]);
-            acc2[o % H][j] = __fmaf_rn(n, v2[X + j + p], acc2[o % H][j]);
+            const int n = static_cast<int>(taps.n[q * W + p]);
+            acc0[o % H][j] += n * v[X + j + p].x;
+            acc1[o % H][j] += n * v[X + j + p].y;
           }
+      }
+    }
+    if constexpr (sd.epi) {  // this row is the centre row of output row i - TT
+      if (i - TT >= 0 && i - TT < RW) {
+        ctr[(i - TT) % H][0] = v[X + L];
+        ctr[(i - TT) % H][1] = v[X + 1 + L];
       }
     }
     const int done = i - (H - 1);  // output row complete after its last input row
     if (done >= 0) {
-      const float2 p0 = acc01[done % H][0], p1 = acc01[done % H][1];
-      const float q0 = acc2[done % H][0], q1 = acc2[done % H][1];
-      const double val0 = ix_combine(p0.x, p0.y, q0, sc_hi, sc_lo, cs_hi, cs_lo);
-      const double val1 = ix_combine(p1.x, p1.y, q1, sc_hi, sc_lo, cs_hi, cs_lo);
-      acc01[done % H][0] = acc01[done % H][1] = make_float2(0.0f, 0.0f);
-      acc2[done % H][0] = acc2[done % H][1] = 0.0f;
+      long long q0 = 0, q1 = 0;
+      if constexpr (sd.epi) {
+        if (tile_e != 0) ixf_q2(ctr[done % H][0], ctr[done % H][1], kf, q0, q1);
+      }
+      const double val0 = ixi_combine(acc0[done % H][0], acc1[done % H][0], w, q0);
+      const double val1 = ixi_combine(acc0[done % H][1], acc1[done % H][1], w, q1);
+      acc0[done % H][0] = acc0[done % H][1] = acc1[done % H][0] = acc1[done % H][1] = 0;
       if (done >= klo && done < khi) {
         if (both) {
           *reinterpret_cast<double2*>(op) = make_double2(val0, val1);
@@ -519,8 +617,7 @@ __device__ __forceinline__ void ix_compute(const float2* s01, const float* s2, d
   }
 }
 
-// At least 3 resident CTAs: a register budget of 85 per thread (measured: the 13-point kernel then
-// takes 64 registers and issues 3 % fewer instructions than with the compiler's default of 48).
+// At least 3 resident CTAs: a register budget of 85 per thread.
 template <int TY, int SPEC>
 __global__ void __launch_bounds__(kThreads, 3)
     k_stencil2d_ix(const double* __restrict__ in, double* __restrict__ out, int64_t nx, int64_t ny,
@@ -530,10 +627,9 @@ __global__ void __launch_bounds__(kThreads, 3)
   constexpr int TX = tile_x<double>();
   constexpr int LA = (sd.L + V - 1) / V * V, RA = (sd.R + V - 1) / V * V;
   constexpr int COLS = LA + TX + RA, ROWS = TY + sd.T + sd.B;
-  static_assert(!sd.xform && !sd.epi, "digit kernel covers plain weighted stencils");
+  static_assert(!sd.xform, "digit kernel covers weighted stencils and the cubic user function");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* s = reinterpret_cast<double*>(smem_raw);
-  float* s2 = reinterpret_cast<float*>(s + ROWS * COLS);
   __shared__ unsigned s_red[kThreads / 32];
   static_assert(COLS % 2 == 0, "digit passes take values in pairs");
   const int64_t x0 = static_cast<int64_t>(blockIdx.x) * TX;
@@ -543,17 +639,15 @@ __global__ void __launch_bounds__(kThreads, 3)
   // native FP64
   const uint32_t mhi = ixd::ix_tile_max_hi<kThreads>(s, ROWS * COLS, s_red);
   const int tile_e = static_cast<int>(mhi >> 20);
-  // scale = c * 2^(G - 54) with G = tile_e - 1022
-  const double scale = tile_e == 0 ? 0.0 : itaps.c * ldexp(1.0, tile_e - 1022 - 3 * kIxDigitBits);
-  if (!ix_tile_ok(tile_e, scale)) {
+  uint32_t w[4];
+  if (!ixi_consts(itaps.c, tile_e, w) || (sd.epi && !ixf_tile_ok(tile_e, itaps.c))) {
     spec_compute<double, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
     return;
   }
-  // pass 2: digits, d0 and d1 over the double's own slot, d2 in the float tile
-  ixd::ix_split_tile<kThreads>(s, s2, ROWS * COLS, tile_e);
+  // pass 2: integer digits over the values' own slots
+  ixd::ixi_split_tile<kThreads>(s, ROWS * COLS, tile_e);
   __syncthreads();
-  const float2* s01 = reinterpret_cast<const float2*>(s);
-  ix_compute<TY, SPEC>(s01, s2, out, nx, ny, periodic, x0, y0, itaps, scale);
+  ix_compute<TY, SPEC>(reinterpret_cast<const int2*>(s), out, nx, ny, periodic, x0, y0, itaps, w, tile_e);
 }
 
 // Output rows [row0, row1) of the next launches on this host thread (row0 a multiple of 64, so
@@ -577,7 +671,7 @@ template <int TY, int SPEC>
 int launch_ix(const double* in, double* out, int64_t nx, int64_t ny, int periodic, int vec_ok,
               const Taps<double>& taps, const IxTaps& itaps, cudaStream_t st) {
   constexpr SpecDesc sd = kSpecs[SPEC];
-  const size_t smem = tile_smem_bytes<double>(sd.L, sd.R, sd.T, sd.B, TY, false) * 3 / 2;
+  const size_t smem = tile_smem_bytes<double>(sd.L, sd.R, sd.T, sd.B, TY, false);
   auto kern = k_stencil2d_ix<TY, SPEC>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -602,17 +696,22 @@ int dispatch_ix(int variant, const double* in, double* out, int64_t nx, int64_t 
   case I: return launch_ix<TY, I>(in, out, nx, ny, periodic, vec_ok, taps, itaps, st);
     CS_IX_CASE(0) CS_IX_CASE(1) CS_IX_CASE(2) CS_IX_CASE(3) CS_IX_CASE(4)
     CS_IX_CASE(5) CS_IX_CASE(6) CS_IX_CASE(7) CS_IX_CASE(8) CS_IX_CASE(9)
-    CS_IX_CASE(10) CS_IX_CASE(11)
+    CS_IX_CASE(10) CS_IX_CASE(11) CS_IX_CASE(13)
 #undef CS_IX_CASE
     default: return set_error(CS_EINVAL, "internal: variant %d has no digit kernel", variant);
   }
 }
 
-// ---- grouped launch: several independent grids, one kernel ---------------------------------
+// ---- grouped launch: several independent grids, one persistent kernel ---------------------
 // The job table travels as a __grid_constant__ kernel parameter (kept in the constant bank,
-// indexable without a local copy).  CTA b belongs to the job whose tile range holds b; inside
-// the job it is an ordinary tile of the specialised kernel (storage-type arithmetic).
-constexpr int kMaxGroup = 16;
+// indexable without a local copy; up to kMaxGroup jobs per launch).  The grid is sized to the
+// resident CTAs of the GPU; CTA b walks the tiles b, b + gridDim.x, ... of all jobs in order,
+// advancing its job index as the tile index passes each job's range, and evaluates each tile as
+// the specialised kernel does: storage-type arithmetic (MODE 0), or for FP64 storage the exact
+// digit path (MODE 1, every job's weights integer ratios; tiles out of its range take native
+// FP64).  Nothing is allocated and nothing synchronises, so a grouped launch can be captured in a
+// CUDA graph.
+constexpr int kMaxGroup = 64;
 
 template <typename T> struct GroupJob {
   const T* in;
@@ -620,13 +719,14 @@ template <typename T> struct GroupJob {
   int64_t nx, ny;
   int tiles_x, tile_begin, periodic, vec_ok;
   Taps<T> taps;
+  IxTaps itaps;
 };
 template <typename T> struct GroupTable {
   int count, total_tiles;
   GroupJob<T> job[kMaxGroup];
 };
 
-template <typename T, int TY, int SPEC>
+template <typename T, int TY, int SPEC, int MODE>
 __global__ void __launch_bounds__(kThreads) k_stencil2d_group(const __grid_constant__ GroupTable<T> tab) {
   constexpr SpecDesc sd = kSpecs[SPEC];
   constexpr int V = Vec<T>::n;
@@ -634,39 +734,61 @@ __global__ void __launch_bounds__(kThreads) k_stencil2d_group(const __grid_const
   constexpr int LA = (sd.L + V - 1) / V * V, RA = (sd.R + V - 1) / V * V;
   constexpr int COLS = LA + TX + RA, ROWS = TY + sd.T + sd.B;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ unsigned s_red[kThreads / 32];
   T* s = reinterpret_cast<T*>(smem_raw);
   int j = 0;
-  while (j + 1 < tab.count && static_cast<int>(blockIdx.x) >= tab.job[j + 1].tile_begin) ++j;
-  const GroupJob<T>& g = tab.job[j];
-  const int t = static_cast<int>(blockIdx.x) - g.tile_begin;
-  const int64_t x0 = static_cast<int64_t>(t % g.tiles_x) * TX;
-  const int64_t y0 = static_cast<int64_t>(t / g.tiles_x) * TY;
-  load_tile_ct<T, ROWS, COLS>(s, g.in, g.nx, g.ny, g.periodic != 0, g.vec_ok != 0, x0, y0, sd.T, LA);
-  if constexpr (sd.xform) xform_tile<T>(s, ROWS * COLS);
-  spec_compute<T, TY, SPEC>(s, g.out, g.nx, g.ny, g.periodic, x0, y0, g.taps);
+  for (int b = static_cast<int>(blockIdx.x); b < tab.total_tiles; b += static_cast<int>(gridDim.x)) {
+    while (j + 1 < tab.count && b >= tab.job[j + 1].tile_begin) ++j;
+    const GroupJob<T>& g = tab.job[j];
+    const int t = b - g.tile_begin;
+    const int64_t x0 = static_cast<int64_t>(t % g.tiles_x) * TX;
+    const int64_t y0 = static_cast<int64_t>(t / g.tiles_x) * TY;
+    __syncthreads();  // the previous tile's reads of s are done
+    load_tile_ct<T, ROWS, COLS>(s, g.in, g.nx, g.ny, g.periodic != 0, g.vec_ok != 0, x0, y0, sd.T, LA);
+    if constexpr (MODE == 1 && !sd.xform && sizeof(T) == 8) {
+      const uint32_t mhi = ixd::ix_tile_max_hi<kThreads>(s, ROWS * COLS, s_red);
+      const int tile_e = static_cast<int>(mhi >> 20);
+      uint32_t w[4];
+      if (!ixi_consts(g.itaps.c, tile_e, w) || (sd.epi && !ixf_tile_ok(tile_e, g.itaps.c))) {
+        spec_compute<double, TY, SPEC>(s, g.out, g.nx, g.ny, g.periodic, x0, y0, g.taps);
+      } else {
+        ixd::ixi_split_tile<kThreads>(s, ROWS * COLS, tile_e);
+        __syncthreads();
+        ix_compute<TY, SPEC>(reinterpret_cast<const int2*>(s), g.out, g.nx, g.ny, g.periodic, x0, y0, g.itaps,
+                             w, tile_e);
+      }
+    } else {
+      if constexpr (sd.xform) xform_tile<T>(s, ROWS * COLS);
+      spec_compute<T, TY, SPEC>(s, g.out, g.nx, g.ny, g.periodic, x0, y0, g.taps);
+    }
+  }
 }
 
-template <typename T, int TY, int SPEC>
+template <typename T, int TY, int SPEC, int MODE>
 int launch_group(const GroupTable<T>& tab, cudaStream_t st) {
   constexpr SpecDesc sd = kSpecs[SPEC];
   const size_t smem = tile_smem_bytes<T>(sd.L, sd.R, sd.T, sd.B, TY, false);
-  auto kern = k_stencil2d_group<T, TY, SPEC>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  auto kern = k_stencil2d_group<T, TY, SPEC, MODE>;
+  static int per_sm = 0;  // resident CTAs per SM of this instantiation (set on first use)
+  if (per_sm == 0) {
     CS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-    attr_set = true;
+    int occ = 0;
+    CS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem));
+    per_sm = occ > 0 ? occ : -1;
   }
-  kern<<<static_cast<unsigned>(tab.total_tiles), kThreads, smem, st>>>(tab);
+  if (per_sm < 0) return set_error(CS_EUNSUPPORTED, "grouped stencil kernel does not fit on an SM");
+  const int grid = static_cast<int>(std::min<int64_t>(tab.total_tiles, static_cast<int64_t>(num_sms()) * per_sm));
+  kern<<<static_cast<unsigned>(grid), kThreads, smem, st>>>(tab);
   CS_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return CS_OK;
 }
 
-template <typename T, int TY>
+template <typename T, int TY, int MODE>
 int dispatch_group(int variant, const GroupTable<T>& tab, cudaStream_t st) {
   switch (variant) {
 #define CS_GR_CASE(I) \
-  case I: return launch_group<T, TY, I>(tab, st);
+  case I: return launch_group<T, TY, I, MODE>(tab, st);
     CS_GR_CASE(0) CS_GR_CASE(1) CS_GR_CASE(2) CS_GR_CASE(3) CS_GR_CASE(4)
     CS_GR_CASE(5) CS_GR_CASE(6) CS_GR_CASE(7) CS_GR_CASE(8) CS_GR_CASE(9)
     CS_GR_CASE(10) CS_GR_CASE(11) CS_GR_CASE(12) CS_GR_CASE(13)
@@ -676,12 +798,17 @@ int dispatch_group(int variant, const GroupTable<T>& tab, cudaStream_t st) {
 }
 
 // Launches up to kMaxGroup plans (same dtype, specialised variant and tile rows) as one grid.
+// FP64 plans take the digit path when every plan in the group allows it (integer weight ratios,
+// FP64 mode auto), else native FP64.
 template <typename T>
 int launch_group_t(const Stencil2DConfig* const* cfgs, const void* const* ins, void* const* outs,
                    int count, cudaStream_t st) {
   GroupTable<T> tab;
   memset(&tab, 0, sizeof tab);
   const int variant = cfgs[0]->variant, TY = cfgs[0]->tile_rows;
+  const SpecDesc& sd = kSpecs[variant];
+  const int nt = (sd.L + sd.R + 1) * (sd.T + sd.B + 1);
+  bool digits = sizeof(T) == 8 && !sd.xform;
   int tiles = 0;
   for (int j = 0; j < count; ++j) {
     const Stencil2DConfig* c = cfgs[j];
@@ -699,14 +826,23 @@ int launch_group_t(const Stencil2DConfig* const* cfgs, const void* const* ins, v
     tiles += static_cast<int>(g.tiles_x * ty);
     g.periodic = c->bc == CS_BC_PERIODIC;
     g.vec_ok = (c->nx % Vec<T>::n == 0) && (reinterpret_cast<uintptr_t>(ins[j]) % 16 == 0);
-    const SpecDesc& sd = kSpecs[variant];
-    const int nt = (sd.L + sd.R + 1) * (sd.T + sd.B + 1);
     for (int i = 0; i < 32; ++i) g.taps.w[i] = i < nt ? static_cast<T>(c->weights[i]) : T(0);
+    digits = digits && c->ix_ok && c->fp64_mode == CS_FP64_AUTO;
+    for (int i = 0; i < 32; ++i) g.itaps.n[i] = static_cast<int8_t>(i < nt && c->ix_ok ? c->ix_n[i] : 0);
+    g.itaps.c = c->ix_c;
+    if (c->ix_ok) {
+      g.itaps.inv_hi = static_cast<float>(1.0 / c->ix_c);
+      g.itaps.inv_lo = static_cast<float>(1.0 / c->ix_c - static_cast<double>(g.itaps.inv_hi));
+    }
     ++tab.count;
   }
   tab.total_tiles = tiles;
   if (tab.count == 0) return CS_OK;
-  return TY == 32 ? dispatch_group<T, 32>(variant, tab, st) : dispatch_group<T, 64>(variant, tab, st);
+  if constexpr (sizeof(T) == 8) {
+    if (digits)
+      return TY == 32 ? dispatch_group<T, 32, 1>(variant, tab, st) : dispatch_group<T, 64, 1>(variant, tab, st);
+  }
+  return TY == 32 ? dispatch_group<T, 32, 0>(variant, tab, st) : dispatch_group<T, 64, 0>(variant, tab, st);
 }
 
 // ---- double-float evaluation of FP64-storage stencils ---------------------------------------
@@ -760,50 +896,6 @@ __device__ __forceinline__ double f2d_exact(float f) {
   const uint64_t d = (static_cast<uint64_t>(b & 0x80000000u) << 32) | (static_cast<uint64_t>(e + 896u) << 52) |
                      (static_cast<uint64_t>(b & 0x7fffffu) << 29);
   return __longlong_as_double(static_cast<long long>(d));
-}
-
-// The double-float steps run packed (FP32x2) over two adjacent output columns: lane x is the left
-// column, y the right; each lane rounds exactly as a scalar evaluation would.  a - b is formed as
-// fma(b, -1, a) (one rounding, as a subtraction).
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
-__device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(a, f2(-1.0f)); }
-
-// (sh, sl) += (wh + wl) * (xh + xl): the product's rounding error comes from an FMA and the sum
-// is an error-free TwoSum; the wl * xl term (~2^-48 relative) is dropped.
-__device__ __forceinline__ void dd_mac2(float2& sh, float2& sl, float wh, float wl, float2 xh, float2 xl) {
-  const float2 q = __fmul2_rn(f2(-wh), xh);  // q = -p, p = wh * xh rounded
-  float2 e = __ffma2_rn(f2(wh), xh, q);      // exact: wh * xh - p
-  e = __ffma2_rn(f2(wh), xl, e);
-  e = __ffma2_rn(f2(wl), xh, e);
-  const float2 s = sub2(sh, q);              // TwoSum(sh, p)
-  const float2 bb = sub2(s, sh);
-  const float2 err = sub2(sub2(sh, sub2(s, bb)), __fadd2_rn(q, bb));  // (sh - (s - bb)) + (p - bb)
-  sl = __fadd2_rn(sl, __fadd2_rn(err, e));
-  sh = s;
-}
-
-// (sh, sl) += p + e with an error-free TwoSum of sh and p.
-__device__ __forceinline__ void dd_add_exact2(float2& sh, float2& sl, float2 p, float2 e) {
-  const float2 s = __fadd2_rn(sh, p);
-  const float2 bb = sub2(s, sh);
-  const float2 err = __fadd2_rn(sub2(sh, sub2(s, bb)), sub2(p, bb));
-  sl = __fadd2_rn(sl, __fadd2_rn(err, e));
-  sh = s;
-}
-
-// (sh, sl) += u^3 - u for u = uh + ul, with error-free products and sums (terms below ~2^-46
-// of |u| dropped), so the cubic of the user function stays on the FP32 pipes.
-__device__ __forceinline__ void dd_add_cubic_minus2(float2& sh, float2& sl, float2 uh, float2 ul) {
-  const float2 p2 = __fmul2_rn(uh, uh);  // u^2 = p2 + e2
-  float2 e2 = __ffma2_rn(uh, uh, neg2(p2));
-  e2 = __ffma2_rn(__fmul2_rn(f2(2.0f), uh), ul, e2);
-  const float2 p3 = __fmul2_rn(p2, uh);  // u^3 = p3 + e3
-  float2 e3 = __ffma2_rn(p2, uh, neg2(p3));
-  e3 = __ffma2_rn(p2, ul, e3);
-  e3 = __ffma2_rn(e2, uh, e3);
-  dd_add_exact2(sh, sl, p3, e3);
-  dd_add_exact2(sh, sl, neg2(uh), neg2(ul));
 }
 
 // Splits the N staged FP64 values (N even) in place: each 16-byte pair of values becomes
@@ -1009,10 +1101,16 @@ int dispatch_dd(int variant, const double* in, double* out, int64_t nx, int64_t 
 // grid; for periodic boundaries the threads of an edge tile then overwrite those cells with the
 // wrapped values.  MODE 0 computes in the storage type, MODE 1 is the exact digit path and
 // MODE 2 the double-float path of FP64 storage (each with its native-FP64 tile fallback).
-// Every mbarrier wait is bounded: when it runs out the kernel records 1 in *status and returns.
+// Every mbarrier wait is bounded.  When one runs out (in any thread: the decision is made
+// block-wide), thread 0 adds 1 to the plan's *status counter and waits, bounded again, for the
+// copies this CTA still has in flight; then the CTA returns with its remaining tiles unwritten.
+// The host reads the counter with cs_plan_check.  stall_from (a test hook, INT_MAX when off)
+// makes the CTA issue no copy for its tiles from that index on, so the wait for such a tile runs
+// out with nothing in flight; those waits use the short kStallWaitLimit.
 
 constexpr int kStages = 2;
 constexpr long long kWaitLimit = 1ll << 22;
+constexpr long long kStallWaitLimit = 1ll << 10;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -1036,8 +1134,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (long long it = 0; it < kWaitLimit; ++it)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
+  for (long long it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -1088,7 +1186,7 @@ struct TmaGeom {
   static constexpr int COLS = LA + TX + RA, ROWS = TY + sd.T + sd.B;
   static constexpr int SE = ROWS * COLS;
   static constexpr size_t STAGE_BYTES = (SE * sizeof(T) + 127) / 128 * 128;
-  static constexpr size_t EXTRA_BYTES = MODE == 1 ? SE * sizeof(float) : 0;
+  static constexpr size_t EXTRA_BYTES = 0;
   static constexpr size_t SMEM = kStages * STAGE_BYTES + EXTRA_BYTES;
 };
 
@@ -1096,14 +1194,14 @@ template <int MODE, typename T, int SPEC>
 __global__ void __launch_bounds__(kThreads)
     k_stencil2d_tma(const __grid_constant__ CUtensorMap tmap, const T* __restrict__ in,
                     T* __restrict__ out, int64_t nx, int64_t ny, int periodic, int tiles_x,
-                    int tiles, int ty0, Taps<T> taps, IxTaps itaps, DDTaps dtaps, int* status) {
+                    int tiles, int ty0, Taps<T> taps, IxTaps itaps, DDTaps dtaps, int* status,
+                    int stall_from) {
   using G = TmaGeom<MODE, T, SPEC>;
   constexpr SpecDesc sd = kSpecs[SPEC];
   constexpr int TY = G::TY, TX = G::TX, COLS = G::COLS, ROWS = G::ROWS, SE = G::SE;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar[kStages];
   __shared__ int s_wmax[kThreads / 32];
-  unsigned char* extra = smem_raw + kStages * G::STAGE_BYTES;
   const int tid = threadIdx.x;
   if (blockIdx.x >= tiles) return;
   const int my_tiles = (tiles - 1 - static_cast<int>(blockIdx.x)) / static_cast<int>(gridDim.x) + 1;
@@ -1120,15 +1218,19 @@ __global__ void __launch_bounds__(kThreads)
     tma_load_2d(smem_raw + st * G::STAGE_BYTES, &tmap, bx * TX - G::LA, by * TY - sd.T, &mbar[st]);
   };
   if (tid == 0)
-    for (int st = 0; st < kStages && st < my_tiles; ++st) issue(st, st);
+    for (int st = 0; st < kStages && st < my_tiles && st < stall_from; ++st) issue(st, st);
 
   for (int i = 0; i < my_tiles; ++i) {
     const int st = i % kStages;
-    if (!mbar_wait_bounded(&mbar[st], static_cast<uint32_t>((i / kStages) & 1))) {
-      if (tid == 0) atomicExch(status, 1);
-      // let the copies already issued into this CTA's stages land before leaving
-      for (int j = i + 1; j < i + kStages && j < my_tiles; ++j)
-        mbar_wait_bounded(&mbar[j % kStages], static_cast<uint32_t>((j / kStages) & 1));
+    const bool ok = mbar_wait_bounded(&mbar[st], static_cast<uint32_t>((i / kStages) & 1),
+                                      i < stall_from ? kWaitLimit : kStallWaitLimit);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicAdd(status, 1);
+        // the copies issued into this CTA's stages (tiles i .. i + kStages - 1) land before it leaves
+        for (int j = i; j < i + kStages && j < my_tiles && j < stall_from; ++j)
+          mbar_wait_bounded(&mbar[j % kStages], static_cast<uint32_t>((j / kStages) & 1), kWaitLimit);
+      }
       return;
     }
     T* s = reinterpret_cast<T*>(smem_raw + st * G::STAGE_BYTES);
@@ -1147,15 +1249,13 @@ __global__ void __launch_bounds__(kThreads)
       static_assert(COLS % 2 == 0, "digit passes take values in pairs");
       const uint32_t mhi = ixd::ix_tile_max_hi<kThreads>(s, SE, reinterpret_cast<unsigned*>(s_wmax));
       const int tile_e = static_cast<int>(mhi >> 20);
-      const double scale = tile_e == 0 ? 0.0 : itaps.c * ldexp(1.0, tile_e - 1022 - 3 * kIxDigitBits);
-      if (!ix_tile_ok(tile_e, scale)) {
+      uint32_t w[4];
+      if (!ixi_consts(itaps.c, tile_e, w) || (sd.epi && !ixf_tile_ok(tile_e, itaps.c))) {
         spec_compute<double, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
       } else {
-        float* s2 = reinterpret_cast<float*>(extra);
-        ixd::ix_split_tile<kThreads>(s, s2, SE, tile_e);
+        ixd::ixi_split_tile<kThreads>(s, SE, tile_e);
         __syncthreads();
-        const float2* s01 = reinterpret_cast<const float2*>(s);
-        ix_compute<TY, SPEC>(s01, s2, out, nx, ny, periodic, x0, y0, itaps, scale);
+        ix_compute<TY, SPEC>(reinterpret_cast<const int2*>(s), out, nx, ny, periodic, x0, y0, itaps, w, tile_e);
       }
     } else {
       static_assert(COLS % 2 == 0, "the split takes values in pairs");
@@ -1165,14 +1265,15 @@ __global__ void __launch_bounds__(kThreads)
       else
         spec_compute<double, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
     }
-    __syncthreads();  // every thread is done with stage st (and the extra buffer)
-    if (tid == 0 && i + kStages < my_tiles) issue(i + kStages, st);
+    __syncthreads();  // every thread is done with stage st
+    if (tid == 0 && i + kStages < my_tiles && i + kStages < stall_from) issue(i + kStages, st);
   }
 }
 
 template <int MODE, typename T, int SPEC>
 int launch_tma(const CUtensorMap& map, const T* in, T* out, int64_t nx, int64_t ny, int periodic,
-               const Taps<T>& taps, const IxTaps& it, const DDTaps& dt, int* status, cudaStream_t st) {
+               const Taps<T>& taps, const IxTaps& it, const DDTaps& dt, int* status, int stall_from,
+               cudaStream_t st) {
   using G = TmaGeom<MODE, T, SPEC>;
   auto kern = k_stencil2d_tma<MODE, T, SPEC>;
   static int per_sm = 0;  // resident CTAs per SM for this instantiation (set on first use)
@@ -1192,7 +1293,7 @@ int launch_tma(const CUtensorMap& map, const T* in, T* out, int64_t nx, int64_t 
   const int64_t grid = std::min<int64_t>(tiles, static_cast<int64_t>(num_sms()) * per_sm);
   kern<<<static_cast<unsigned>(grid), kThreads, G::SMEM, st>>>(map, in, out, nx, ny, periodic,
                                                                static_cast<int>(tiles_x), static_cast<int>(tiles),
-                                                               ty0, taps, it, dt, status);
+                                                               ty0, taps, it, dt, status, stall_from);
   CS_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return CS_OK;
@@ -1201,14 +1302,14 @@ int launch_tma(const CUtensorMap& map, const T* in, T* out, int64_t nx, int64_t 
 template <int MODE, typename T>
 int dispatch_tma(int variant, const CUtensorMap& map, const T* in, T* out, int64_t nx, int64_t ny,
                  int periodic, const Taps<T>& taps, const IxTaps& it, const DDTaps& dt, int* status,
-                 cudaStream_t st) {
+                 int stall_from, cudaStream_t st) {
   switch (variant) {
 #define CS_TMA_CASE(I)                                                                          \
   case I:                                                                                       \
-    if constexpr (MODE == 1 && (kSpecs[I].xform || kSpecs[I].epi))                              \
+    if constexpr (MODE == 1 && kSpecs[I].xform)                                                 \
       return set_error(CS_EINVAL, "internal: no digit kernel for variant %d", I);               \
     else                                                                                        \
-      return launch_tma<MODE, T, I>(map, in, out, nx, ny, periodic, taps, it, dt, status, st);
+      return launch_tma<MODE, T, I>(map, in, out, nx, ny, periodic, taps, it, dt, status, stall_from, st);
     CS_TMA_CASE(0) CS_TMA_CASE(1) CS_TMA_CASE(2) CS_TMA_CASE(3) CS_TMA_CASE(4)
     CS_TMA_CASE(5) CS_TMA_CASE(6) CS_TMA_CASE(7) CS_TMA_CASE(8) CS_TMA_CASE(9)
     CS_TMA_CASE(10) CS_TMA_CASE(11) CS_TMA_CASE(12) CS_TMA_CASE(13)
@@ -1342,17 +1443,19 @@ int launch_stencil2d_t(const Stencil2DConfig* cfg, const void* vin, void* vout, 
         int rc = make_tensor_map(cfg, vin, sizeof(T), cols, rows);
         if (rc != CS_OK) return rc;
       }
-      int* status = nullptr;
-      int rc = stencil2d_status_ptr(&status);
-      if (rc != CS_OK) return rc;
+      int* status = cfg->d_status;
+      if (!status) return set_error(CS_EINVAL, "internal: plan without a status word");
+      const int stall = cfg->stall_from < 0 ? 0x7fffffff : cfg->stall_from;
       IxTaps it{};
       DDTaps dt{};
       int mode = 0;
       if constexpr (sizeof(T) == 8) {
         if (cfg->fp64_mode == CS_FP64_AUTO && cfg->ix_ok) {
           mode = 1;
-          for (int i = 0; i < 32; ++i) it.n[i] = i < nt ? static_cast<float>(cfg->ix_n[i]) : 0.0f;
+          for (int i = 0; i < 32; ++i) it.n[i] = static_cast<int8_t>(i < nt ? cfg->ix_n[i] : 0);
           it.c = cfg->ix_c;
+          it.inv_hi = static_cast<float>(1.0 / cfg->ix_c);
+          it.inv_lo = static_cast<float>(1.0 / cfg->ix_c - static_cast<double>(it.inv_hi));
         } else if (cfg->fp64_mode == CS_FP64_AUTO && cfg->dd_ok) {
           mode = 2;
           for (int i = 0; i < 32; ++i) {
@@ -1364,17 +1467,19 @@ int launch_stencil2d_t(const Stencil2DConfig* cfg, const void* vin, void* vout, 
       }
       if constexpr (sizeof(T) == 8) {
         if (mode == 1)
-          return dispatch_tma<1, T>(cfg->variant, cfg->tmap, in, out, cfg->nx, cfg->ny, periodic, taps, it, dt, status, st);
+          return dispatch_tma<1, T>(cfg->variant, cfg->tmap, in, out, cfg->nx, cfg->ny, periodic, taps, it, dt, status, stall, st);
         if (mode == 2)
-          return dispatch_tma<2, T>(cfg->variant, cfg->tmap, in, out, cfg->nx, cfg->ny, periodic, taps, it, dt, status, st);
+          return dispatch_tma<2, T>(cfg->variant, cfg->tmap, in, out, cfg->nx, cfg->ny, periodic, taps, it, dt, status, stall, st);
       }
-      return dispatch_tma<0, T>(cfg->variant, cfg->tmap, in, out, cfg->nx, cfg->ny, periodic, taps, it, dt, status, st);
+      return dispatch_tma<0, T>(cfg->variant, cfg->tmap, in, out, cfg->nx, cfg->ny, periodic, taps, it, dt, status, stall, st);
     }
     if constexpr (sizeof(T) == 8) {
       if (cfg->ix_ok && cfg->fp64_mode == CS_FP64_AUTO) {
         IxTaps it;
-        for (int i = 0; i < 32; ++i) it.n[i] = i < nt ? static_cast<float>(cfg->ix_n[i]) : 0.0f;
+        for (int i = 0; i < 32; ++i) it.n[i] = static_cast<int8_t>(i < nt ? cfg->ix_n[i] : 0);
         it.c = cfg->ix_c;
+        it.inv_hi = static_cast<float>(1.0 / cfg->ix_c);
+        it.inv_lo = static_cast<float>(1.0 / cfg->ix_c - static_cast<double>(it.inv_hi));
         if (cfg->tile_rows == 32)
           return dispatch_ix<32>(cfg->variant, in, out, cfg->nx, cfg->ny, periodic, vec_ok, taps, it, st);
         return dispatch_ix<64>(cfg->variant, in, out, cfg->nx, cfg->ny, periodic, vec_ok, taps, it, st);

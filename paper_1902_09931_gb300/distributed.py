@@ -154,7 +154,12 @@ class DeviceBandSweep:
             self._bufs = (torch.empty_like(padded), torch.zeros_like(padded))
             self._plan = self._make(nx, ny, self._bufs[0], self._bufs[1])
         self._bufs[0].copy_(padded)
+        cur = torch.cuda.current_stream()
+        if self._stream is not None:  # the copy above ran on the current stream
+            self._stream.wait_stream(cur)
         cs_compute(self._plan, self._stream)
+        if self._stream is not None:  # the clone below runs on the current stream
+            cur.wait_stream(self._stream)
         return self._bufs[1].clone()
 
     def close(self):

@@ -87,3 +87,48 @@ def scaled_err(got, ref, weights, field):
     """Error normalised by the size of the terms the stencil sums (sum |w| * max |in|)."""
     scale = np.abs(np.asarray(weights)).sum() * max(np.abs(field).max(), 1e-300)
     return np.abs(got - ref).max() / scale
+
+
+CH_D, CH_GAMMA = 1.0, 0.01
+EPS64 = 2.0 ** -52
+
+
+def ch_step_bound(orc, prev, cur, nxt_ref, n, dt, storage, noflux=False):
+    """Rounding bound for one Cahn-Hilliard ADI step (Sec. 5.1) taken by two FP64 implementations
+    from the same state (C^{n-1}, C^n): (tolerance, B).
+
+    B = eps (S + kappa max|v|), eps = 2^-52: S = max|C^n| + max|C^{n-1}| + 64 a max|Cbar| +
+    8 alpha max|N| is the size of the right-hand side's terms (the 13-point biharmonic's weights
+    sum to 64 in units of a = (2/3) D gamma dt / h^4, the 5-point Laplacian's to 8 in units of
+    alpha = (2/3) D dt / h^2), whose roundings reach C^{n+1} undamped at low wavenumbers since
+    ||L^-1|| <= 1; the backward-stable y-solve adds at most kappa eps |v|, kappa = 1 + 16 a,
+    v = C^{n+1} - Cbar.  (The x-solve's own rounding, of size kappa eps |w| before L_y^-1, lies
+    in the rows' high wavenumbers that L_y^-1 damps; measured, the total stays near B.)  The
+    tolerance is 8 B, plus 2^-24 (max|Cbar| + max|C^{n+1}|) for FP32 storage (Cbar in the update
+    and the stored result are rounded to FP32)."""
+    h = 2 * np.pi / n
+    a = orc.ch_coefficient_a(n, CH_D, CH_GAMMA, dt)
+    alpha = (2.0 / 3.0) * CH_D * dt / h ** 2
+    cbar = 2 * cur - prev
+    S = (np.abs(cur).max() + np.abs(prev).max() + 64 * a * np.abs(cbar).max()
+         + 8 * alpha * np.abs(cur ** 3 - cur).max())
+    v = nxt_ref - cbar
+    B = EPS64 * (S + (1 + 16 * a) * np.abs(v).max())
+    tol = 8 * B
+    if storage == 1:
+        tol += 2.0 ** -24 * (np.abs(cbar).max() + np.abs(nxt_ref).max())
+    return tol, B
+
+
+def check_ch_step(orc, prev, cur, got, n, dt, storage, what, noflux=False):
+    """Compares one device step with the oracle's from the same state; prints err / B."""
+    step = orc.ch_step_noflux if noflux else orc.ch_step
+    ref = step(prev, cur, CH_D, CH_GAMMA, dt)
+    tol, B = ch_step_bound(orc, prev, cur, ref, n, dt, storage, noflux)
+    err = np.abs(got - ref).max()
+    print(f"[ch step{' noflux' if noflux else ''}] {what} n={n} storage={'f32' if storage else 'f64'}: "
+          f"err {err:.3e} = {err / B:.3f} B (B = {B:.3e}), {err / np.abs(ref).max():.3e} of max|C|")
+    assert err <= tol, (what, err, tol, err / B)
+    if storage == 1:
+        assert err <= 1e-5 * np.abs(ref).max(), (what, err / np.abs(ref).max())
+    return ref

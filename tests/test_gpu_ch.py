@@ -1,23 +1,29 @@
 """GPU parity of the Cahn-Hilliard ADI step (Sec. 5.1) against the CPU oracle, through the C ABI.
 
-Per-step tolerance.  From an identical state (C^{n-1}, C^n), every stage of the step is held to
-the 1e-12 relative FP64 bound, taken relative to the magnitude it works at:
-    |C_gpu - C_oracle| <= 1e-12 * (max|C^n| + max|RHS| + kappa * max|v|),
-with RHS the x-sweep right-hand side, v = C^{n+1} - Cbar the solve result, and
-kappa = 1 + 16 a the condition number of L = I + a P (its forward error bound); for small grids
-(a << 1) this is plain 1e-12 relative.  FP32 storage uses 1e-5 in the same form, against the
-FP64 oracle fed with the same FP32-rounded state.  Whole trajectories are compared on the
-invariants (mass conserved to rounding, energy) and on fields with a growth-aware tolerance.
+Per-step tolerance.  From an identical state (C^{n-1}, C^n) both implementations evaluate the same
+FP64 arithmetic, so they differ by rounding alone.  Its size follows from the step's terms:
+  * the right-hand side sums terms of size S = max|C^n| + max|C^{n-1}| + 64 a max|Cbar|
+    + 8 alpha max|N| (the 13-point biharmonic's weights sum to 64 in units of a = (2/3) D gamma
+    dt / h^4, the 5-point Laplacian's to 8 in units of alpha = (2/3) D dt / h^2), each rounded at
+    eps = 2^-52 relative; L^-1 has norm <= 1 (its eigenvalues are >= 1), so these errors reach
+    C^{n+1} undamped at the low wavenumbers;
+  * the y line solve is backward stable, so it adds at most kappa eps |v| (kappa = 1 + 16 a,
+    v = L_y^-1 w); the x-solve's rounding lies in high wavenumbers that L_y^-1 damps.
+The bound is B = eps (S + kappa max|v|) (gpu_helpers.ch_step_bound); the tests allow 8 B and
+print the measured error as a multiple of B.  FP32 storage
+adds two roundings to FP32 (Cbar in the update and the stored result), 2^-24 (max|Cbar| +
+max|C^{n+1}|), and must stay within 1e-5 max|C^{n+1}|.  Whole trajectories are compared on the
+invariants and on fields with a growth-aware tolerance.
 """
 import numpy as np
 import pytest
 
 import workloads as W
+from gpu_helpers import check_ch_step
 
 pytestmark = pytest.mark.gpu
 
 D, GAMMA = 1.0, 0.01
-TOL = {0: 1e-12, 1: 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -54,14 +60,6 @@ class Run:
         self.cs.cs_destroy(self.plan)
 
 
-def step_tolerance(orc, prev, cur, nxt_ref, n, dt, tol):
-    h = 2 * np.pi / n
-    a = orc.ch_coefficient_a(n, D, GAMMA, dt)
-    rhs = orc.ch_rhs(prev, cur, D, GAMMA, dt)
-    v = nxt_ref - (2 * cur - prev)
-    return tol * (np.abs(cur).max() + np.abs(rhs).max() + (1 + 16 * a) * np.abs(v).max())
-
-
 @pytest.mark.parametrize("storage", [0, 1])
 @pytest.mark.parametrize("n", [64, 128, 256, 512])
 def test_single_step_from_identical_state(env, storage, n):
@@ -77,30 +75,32 @@ def test_single_step_from_identical_state(env, storage, n):
     r.step(1)
     _, got, steps = r.state()
     r.close()
-    ref = orc.ch_step(prev, cur, D, GAMMA, dt)
-    tol = step_tolerance(orc, prev, cur, ref, n, dt, TOL[storage])
     assert steps == 1
-    assert np.abs(got - ref).max() <= tol, (np.abs(got - ref).max(), tol)
+    check_ch_step(orc, prev, cur, got, n, dt, storage, "two-level state")
 
 
+@pytest.mark.parametrize("storage", [0, 1])
 @pytest.mark.parametrize("n", [1024, 4096])
-def test_full_size_single_step(env, n):
-    """The benchmark grids (N = 1024, 4096; dt = 0.1 h): one FP64 step from the deep-quench
+def test_full_size_single_step(env, n, storage):
+    """The benchmark grids (N = 1024, 4096; dt = 0.1 h), FP64 and FP32 storage, with the line-solve
+    partition the autotuner picks (as the benchmark runs it): one step from the deep-quench
     initial condition (C^{-1} = C^0) and a second step from the resulting two-level state."""
     cs, torch, orc = env
     h = 2 * np.pi / n
     dt = 0.1 * h
     c0 = W.ch_initial(n, seed=1902)
-    r = Run(cs, torch, c0, c0, 0, dt)
+    if storage == 1:
+        c0 = c0.astype(np.float32).astype(np.float64)
+    r = Run(cs, torch, c0, c0, storage, dt)
+    cs.cs_autotune(r.plan)
+    torch.cuda.synchronize()
     r.step(1)
     p1, c1, _ = r.state()
-    ref1 = orc.ch_step(c0, c0, D, GAMMA, dt)
-    assert np.abs(c1 - ref1).max() <= step_tolerance(orc, c0, c0, ref1, n, dt, 1e-12)
+    check_ch_step(orc, c0, c0, c1, n, dt, storage, "first step")
     r.step(1)
     _, c2, _ = r.state()
     r.close()
-    ref2 = orc.ch_step(p1, c1, D, GAMMA, dt)
-    assert np.abs(c2 - ref2).max() <= step_tolerance(orc, p1, c1, ref2, n, dt, 1e-12)
+    check_ch_step(orc, p1, c1, c2, n, dt, storage, "second step")
 
 
 @pytest.mark.parametrize("k,l", [(1, 0), (3, 2), (20, 1)])
@@ -207,5 +207,4 @@ def test_autotune_restores_state_and_keeps_parity(env, storage):
     r.step(1)
     _, got, _ = r.state()
     r.close()
-    ref = orc.ch_step(prev, cur, D, GAMMA, dt)
-    assert np.abs(got - ref).max() <= step_tolerance(orc, prev, cur, ref, n, dt, TOL[storage])
+    check_ch_step(orc, prev, cur, got, n, dt, storage, "after autotune")

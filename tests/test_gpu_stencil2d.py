@@ -313,8 +313,9 @@ def test_full_size_configs(env, n, dtype):
 
 @pytest.mark.parametrize("dtype", [0, 1])
 def test_grouped_launch_equals_individual_plans(env, dtype):
-    """cs_compute_group over grids of different sizes (one launch) gives bit-for-bit the results
-    of computing each plan alone with the same arithmetic."""
+    """cs_compute_group over grids of different sizes (one persistent launch) gives bit-for-bit
+    the results of computing each plan alone: storage-type arithmetic for FP32, the exact digit
+    path for FP64 (integer weight ratios), on the same 64-row tiles."""
     cs, torch, orc = env
     tdt = torch.float64 if dtype == 0 else torch.float32
     sizes = [(64, 64), (100, 260), (257, 129), (31, 517), (128, 128)]
@@ -327,7 +328,7 @@ def test_grouped_launch_equals_individual_plans(env, dtype):
         w = biharm13(h)
         desc = cs.StencilDesc(nx=nx, ny=ny, dir=2, bc=k % 2, dtype=dtype, left=2, right=2, top=2, bottom=2, weights=w)
         p_alone = cs.cs_plan_create_2d(desc, x, r)
-        cs.cs_plan_set_fp64_mode(p_alone, cs.CS_FP64_NATIVE)
+        cs.cs_plan_set_tile_choice(p_alone, 1)
         cs.cs_compute(p_alone)
         cs.cs_destroy(p_alone)
         plans.append(cs.cs_plan_create_2d(desc, x, y))
@@ -338,6 +339,64 @@ def test_grouped_launch_equals_individual_plans(env, dtype):
         cs.cs_destroy(p)
     for y, r in zip(outs, refs):
         assert torch.equal(y, r)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("fn", [None, 3])
+def test_grouped_launch_many_grids_and_graph(env, dtype, fn):
+    """150 grids of the serving size mix (more than one launch's job table), weighted 9-point
+    Laplacian or the cubic user function: grouped results equal the plans computed alone bit
+    for bit, and a CUDA graph captured around cs_compute_group replays to the same bits on new
+    inputs written into the same buffers."""
+    cs, torch, orc = env
+    tdt = torch.float64 if dtype == 0 else torch.float32
+    rng = np.random.Generator(np.random.PCG64(5))
+    ns = rng.choice([16, 32, 64, 128, 200, 256], size=150)
+    xs, ys, refs, plans = [], [], [], []
+    for k, n in enumerate(ns):
+        h = 2 * np.pi / n
+        x = torch.from_numpy(W.sines_field(int(n), seed=300 + k)).to("cuda", tdt)
+        y = torch.full_like(x, 7.0)
+        r = torch.full_like(x, 7.0)
+        if fn is None:
+            kw = dict(dir=2, left=1, right=1, top=1, bottom=1, weights=lap9(h))
+        else:
+            kw = dict(dir=2, left=1, right=1, top=1, bottom=1, fn=fn, coe=[1 / h ** 2])
+        desc = cs.StencilDesc(nx=int(n), ny=int(n), bc=k % 2, dtype=dtype, **kw)
+        p_alone = cs.cs_plan_create_2d(desc, x, r)
+        cs.cs_plan_set_tile_choice(p_alone, 1)
+        cs.cs_compute(p_alone)
+        cs.cs_destroy(p_alone)
+        plans.append(cs.cs_plan_create_2d(desc, x, y))
+        xs.append(x); ys.append(y); refs.append(r)
+    before = cs.cs_launch_count()
+    cs.cs_compute_group(plans)
+    torch.cuda.synchronize()
+    assert cs.cs_launch_count() - before == 3  # 150 plans, 64 per launch
+    for y, r in zip(ys, refs):
+        assert torch.equal(y, r)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        cs.cs_compute_group(plans, torch.cuda.current_stream())
+    for x in xs:
+        x.mul_(-0.5)
+    for y in ys:
+        y.fill_(7.0)
+    g.replay()
+    torch.cuda.synchronize()
+    for k, (x, y) in enumerate(zip(xs, ys)):
+        r = torch.full_like(x, 7.0)
+        p = cs.cs_plan_create_2d(cs.StencilDesc(nx=x.shape[1], ny=x.shape[0], bc=k % 2, dtype=dtype,
+                                                **(dict(dir=2, left=1, right=1, top=1, bottom=1,
+                                                        weights=lap9(2 * np.pi / x.shape[1])) if fn is None else
+                                                   dict(dir=2, left=1, right=1, top=1, bottom=1, fn=fn,
+                                                        coe=[1 / (2 * np.pi / x.shape[1]) ** 2]))), x, r)
+        cs.cs_plan_set_tile_choice(p, 1)
+        cs.cs_compute(p)
+        cs.cs_destroy(p)
+        assert torch.equal(y, r), k
+    for p in plans:
+        cs.cs_destroy(p)
 
 
 @pytest.mark.parametrize("case", ["plain", "wide_range", "nan_inf", "huge_tile", "zeros"])
@@ -439,9 +498,9 @@ def test_unaligned_buffers_match_oracle(env, dtype, offsets, bc):
                                            (2.0 ** -50, 2.0 ** 800), (1e200, 1e100)])
 def test_exact_digit_path_extreme_scales(env, wscale, uscale):
     """Integer-ratio weights near the ends of the fast-path weight range [2^-60, 2^50) on values
-    near the ends of the digit range [2^-900, 2^900]: tiles whose scale c * 2^(G - 54) leaves the
+    near the ends of the digit range [2^-900, 2^900]: tiles whose scale c * 2^(G - 50) leaves the
     range of the one-FMA conversion take native FP64, the others the digit path (with constants
-    up to 2^60 scale); weights outside the range take native FP64 throughout.  Every output meets
+    up to 2^56 scale); weights outside the range take native FP64 throughout.  Every output meets
     the FP64 tolerance against the oracle."""
     cs, torch, orc = env
     ny, nx = 130, 200

@@ -56,6 +56,28 @@ def test_noalloc_matches_plan_two_calls(env, dtype):
         assert err <= TOL[dtype], (seed, err)
 
 
+def test_noalloc_allocates_no_device_memory(env):
+    """The device's free memory is the same before and after a run of calls on a batch shape
+    the entry point has not seen (inputs created and the first call made beforehand)."""
+    cs, torch = env
+    w = np.array([-1.0, 16.0, -30.0, 16.0, -1.0]) / 12.0
+    desc = cs.StencilDesc(dir=cs.CS_DIR_X, bc=cs.CS_BC_PERIODIC, dtype=cs.CS_F32, left=2, right=2, weights=w)
+    warm = W.ragged_offsets(100, seed=40)
+    warm_x = torch.from_numpy(W.sines_lines(warm, seed=41).astype(np.float32)).cuda()
+    cs.cs_batch1d_compute_noalloc(desc, 100, torch.from_numpy(warm).cuda(), int(warm[-1]), warm_x,
+                                  torch.empty_like(warm_x))
+    off = W.ragged_offsets(40000, seed=42)
+    off_d = torch.from_numpy(off).cuda()
+    x_d = torch.from_numpy(W.sines_lines(off, seed=43).astype(np.float32)).cuda()
+    out = torch.empty_like(x_d)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(5):
+        cs.cs_batch1d_compute_noalloc(desc, 40000, off_d, int(off[-1]), x_d, out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
 def test_noalloc_rejects_oversize_and_bad_offsets(env):
     cs, torch = env
     w = np.array([1.0, -2.0, 1.0])
