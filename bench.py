@@ -305,25 +305,27 @@ def run_ours(args):
     value = whole_job_gpts(world, pts_per_step, ms_per_step)
     hbm_gbs = world * bytes_per_step / (ms_per_step * 1e-3) / 1e9
 
-    # dominant kernel: largest share of the step
+    # dominant kernel: largest share of the step.  Its roofline is the method's algorithmic work:
+    # one read and one write of every grid point (2 s bytes, s the element size), against the
+    # measured HBM copy rate; halo re-reads and the arithmetic formulation are not algorithmic.
     shares = {k: statistics.mean(v) for k, v in per.items()}
     dom_key = max(shares, key=shares.get)
     dom = [sw for sw in sweeps if f'{sw["name"]}|{sw["n"]}|{sw["dtype"]}|{sw["bc"]}' == dom_key][0]
     dom_ms = shares[dom_key]
-    if dom["eb"] == 8:  # FP64 storage, double-float arithmetic: bound by FP32-lane issue
+    achieved = dom["bytes"] / (dom_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(achieved / hbm_peak, 4), "peak_kind": peak_kind, "kernel": dom_key,
+            "bytes_per_launch": dom["bytes"], "launch_ms": round(dom_ms, 4),
+            "traffic": traffic_for(dom_key)}
+    if dom["eb"] == 8:
+        # FP64 storage is evaluated on the FP32 / integer pipes (exact digits or double-float):
+        # the formulation's own lane-operation count, against the derived FP32/INT lane peak
         ops = dd_ops_per_point(dom["taps"], dom["name"]) * dom["points"]
-        achieved = ops / (dom_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_LANE_PEAK_TOPS, 3),
-                "unit": "Tops/s (FP32/INT lane ops)", "frac": round(achieved / FP32_LANE_PEAK_TOPS, 4),
-                "peak_kind": "derived: 152 SM x 128 lanes x 2.07 GHz",
-                "ops_per_point": dd_ops_per_point(dom["taps"], dom["name"]), "kernel": dom_key,
-                "hbm_gbs": round(dom["bytes"] / (dom_ms * 1e-3) / 1e9, 1),
-                "traffic": traffic_for(dom_key)}
-    else:
-        achieved = dom["bytes"] / (dom_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 4), "peak_kind": peak_kind, "kernel": dom_key,
-                "traffic": traffic_for(dom_key)}
+        lane = ops / (dom_ms * 1e-3) / 1e12
+        roof["formulation"] = {"ops_per_point": dd_ops_per_point(dom["taps"], dom["name"]),
+                               "achieved_tops": round(lane, 3), "peak_tops": round(FP32_LANE_PEAK_TOPS, 3),
+                               "frac": round(lane / FP32_LANE_PEAK_TOPS, 4),
+                               "peak_kind": "derived: 152 SM x 128 lanes x 2.07 GHz"}
 
     # every sweep against the HBM roofline
     f32 = {}
@@ -335,10 +337,24 @@ def run_ours(args):
                   "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 3),
                   "tile_choice": cs.cs_plan_get_tile_choice(sw["plan"])}
 
+    by_dtype = {}
+    for dt in ("f64", "f32"):
+        sel = [(k, v) for k, v in shares.items() if k.split("|")[2] == dt]
+        if not sel:
+            continue
+        ms_dt = sum(v for _, v in sel)
+        pts_dt = sum(sw["points"] for sw in sweeps if sw["dtype"] == dt)
+        bytes_dt = sum(sw["bytes"] for sw in sweeps if sw["dtype"] == dt)
+        by_dtype[dt] = {"gpts": round(world * pts_dt / (ms_dt * 1e-3) / 1e9, 2), "ms_per_step": round(ms_dt, 4),
+                        "hbm_gbs": round(world * bytes_dt / (ms_dt * 1e-3) / 1e9, 1),
+                        "hbm_frac": round(bytes_dt / (ms_dt * 1e-3) / 1e9 / hbm_peak, 4)}
     e2e = e2e_host(cs, torch, sweeps, stream, max(1, min(args.steps, 2)), world)
     parts = {}
     if not args.skip_parts:
+        parts["single_call"] = bench_single_call(cs, torch, stream)
+        parts["group"] = bench_group(cs, torch, stream)
         parts["ch_adi"] = bench_ch(cs, torch, stream)
+        parts["ch_runs"] = bench_ch_runs(cs, torch, stream)
         parts["batch1d"] = bench_batch1d(cs, torch, stream, hbm_peak)
         parts["serve"] = bench_serve(cs, torch)
         parts["coarsening"] = bench_coarsening(cs, torch, stream)
@@ -358,6 +374,9 @@ def run_ours(args):
                    "parallelism": f"replicas x{world} (independent grids per GPU)"},
         "hbm_gbs": round(hbm_gbs, 1), "hbm_frac_of_measured": round(hbm_gbs / hbm_peak, 4),
         "hbm_frac_of_8tbs": round(hbm_gbs / 8000.0, 4),
+        "gpts_f64": by_dtype.get("f64", {}).get("gpts"), "gpts_f32": by_dtype.get("f32", {}).get("gpts"),
+        "hbm_frac_f64": by_dtype.get("f64", {}).get("hbm_frac"), "hbm_frac_f32": by_dtype.get("f32", {}).get("hbm_frac"),
+        "by_dtype": by_dtype,
         "roofline": roof, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
         "per_sweep": f32, "parts": parts,
     }
@@ -413,7 +432,7 @@ def e2e_host(cs, torch, sweeps, stream, steps, world):
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": steps}
 
 
-def bench_ch(cs, torch, stream, cases=None):
+def bench_ch(cs, torch, stream, cases=None, autotune=True):
     out = {}
     if cases is None:
         cases = [(1024, cs.CS_F64, 200), (4096, cs.CS_F64, 30), (1024, cs.CS_F32, 200), (4096, cs.CS_F32, 30)]
@@ -426,7 +445,8 @@ def bench_ch(cs, torch, stream, cases=None):
         f = [c0.clone(), c0.clone(), torch.zeros_like(c0)]
         plan = cs.cs_ch_create(cs.CHDesc(n=n, storage=storage, D=1.0, gamma=0.01, dt=0.1 * h,
                                          boundary=boundary), *f)
-        cs.cs_autotune(plan, stream)  # chunks per line of the partitioned line solves
+        if autotune:
+            cs.cs_autotune(plan, stream)  # chunks per line of the partitioned line solves
         cs.cs_ch_step(plan, 5, stream=stream)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -438,11 +458,142 @@ def bench_ch(cs, torch, stream, cases=None):
         chunks, m = cs.cs_ch_config(plan)
         cs.cs_destroy(plan)
         key = f"n{n}_{'f64' if storage == cs.CS_F64 else 'f32'}" + ("_noflux" if boundary == cs.CS_CH_NOFLUX else "")
-        fp64_ops = ch_fp64_ops_per_point(storage == cs.CS_F64, chunks, m) * n * n
+        fp64_ops = ch_fp64_ops_per_point(chunks, m) * n * n
         out[key] = {"ms_per_step": round(ms, 4), "steps_per_s": round(1e3 / ms, 1),
                     "fp64_gops": round(fp64_ops / (ms * 1e-3) / 1e9, 1),
                     "fp64_frac": round(fp64_ops / (ms * 1e-3) / 1e9 / FP64_PEAK_GOPS, 3),
                     "chunks_per_line": chunks}
+    return out
+
+
+def bench_single_call(cs, torch, stream, n=256, calls=2000):
+    """One compute call on a 256^2 periodic grid, FP64, 5-point Laplacian, h = 2 pi / 256, input
+    U[-1, 1]: microseconds per call launched directly and replayed from a CUDA graph, each the
+    mean of `calls` back-to-back calls between two CUDA events (the 1 MiB grid stays in L2, so
+    this measures launch and latency, not HBM)."""
+    h = 2 * np.pi / n
+    x = torch.from_numpy(W.uniform_field(n, n, seed=256)).to("cuda", torch.float64)
+    y = torch.zeros_like(x)
+    w = np.array([0, 1, 0, 1, -4, 1, 0, 1, 0.0]) / h ** 2
+    desc = cs.StencilDesc(nx=n, ny=n, dir=cs.CS_DIR_XY, bc=cs.CS_BC_PERIODIC, dtype=cs.CS_F64,
+                          left=1, right=1, top=1, bottom=1, weights=w)
+    plan = cs.cs_plan_create_2d(desc, x, y)
+    cs.cs_autotune(plan, stream)
+    out = {"n": n, "stencil": "5-point Laplacian, FP64, periodic", "calls": calls,
+           "tile_choice": cs.cs_plan_get_tile_choice(plan)}
+    for mode in ("plain", "graph"):
+        cs.cs_plan_use_graph(plan, mode == "graph")
+        for _ in range(20):
+            cs.cs_compute(plan, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(calls):
+            cs.cs_compute(plan, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / calls
+        out[mode] = {"us_per_call": round(us, 3), "gpts_per_s": round(n * n / (us * 1e-6) / 1e9, 2)}
+    cs.cs_destroy(plan)
+    return out
+
+
+def bench_ch_runs(cs, torch, stream, steps=1000):
+    """The 1000-step Cahn-Hilliard runs of the configuration (n = 1024, 4096; FP64 and FP32
+    storage; deep quench C0 ~ U[-0.1, 0.1] with the mean removed, D = 1, gamma = 0.01,
+    dt = 0.1 h) with the mass and free energy read back after every step: steps/s with the
+    per-step invariants, the largest mass drift (of h^2 sum |C0|), and the energy's behaviour
+    (steps where it rose, the first one, the largest rise), reported as they come."""
+    out = {}
+    for n in (1024, 4096):
+        h = 2 * np.pi / n
+        for storage in (cs.CS_F64, cs.CS_F32):
+            tdt = torch.float64 if storage == cs.CS_F64 else torch.float32
+            c0 = torch.from_numpy(W.ch_initial(n, seed=1902)).to("cuda", tdt)
+            f = [c0.clone(), c0.clone(), torch.zeros_like(c0)]
+            plan = cs.cs_ch_create(cs.CHDesc(n=n, storage=storage, D=1.0, gamma=0.01, dt=0.1 * h), *f)
+            cs.cs_autotune(plan, stream)
+            m0, e0 = cs.cs_ch_invariants(plan, stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mass, energy = cs.cs_ch_step(plan, steps, invariants=True, stream=stream)
+            dt_s = time.perf_counter() - t0
+            cs.cs_destroy(plan)
+            scale = h * h * float(c0.double().abs().sum().item())
+            e = np.concatenate([[e0], energy])
+            de = np.diff(e)
+            key = f"n{n}_{'f64' if storage == cs.CS_F64 else 'f32'}"
+            out[key] = {"steps": steps, "steps_per_s_with_invariants": round(steps / dt_s, 1),
+                        "mass_drift_max": float(f"{np.abs(mass - m0).max() / scale:.3e}"),
+                        "energy_start": round(float(e0), 6), "energy_end": round(float(e[-1]), 6),
+                        "energy_rises": int((de > 0).sum()),
+                        "first_rise_step": int(np.argmax(de > 0)) + 1 if (de > 0).any() else None,
+                        "largest_rise_rel": float(f"{(de / np.abs(e[:-1])).max():.3e}")}
+            del c0, f
+    return out
+
+
+def bench_group(cs, torch, stream, reps=50):
+    """Small 2D grids in one persistent launch against one launch per grid: 64 grids drawn from
+    {32, 64, 128, 256, 512}^2 (seeded), periodic xy 9-point Laplacian, FP32 and FP64 storage.
+    Arms: a plain cs_compute per grid, each grid's own CUDA graph, one grouped launch
+    (cs_compute_group), and that grouped launch captured in a CUDA graph.  Time per batch of
+    all 64 sweeps: mean over `reps` back-to-back batches between CUDA events (the grids, 83 MB
+    in FP64, sit in L2: this is the launch- and latency-bound regime that batching targets)."""
+    rng = np.random.Generator(np.random.PCG64(64))
+    ns = [int(v) for v in rng.choice([32, 64, 128, 256, 512], size=64)]
+    pts = sum(n * n for n in ns)
+    out = {"grids": len(ns), "sizes": "n in {32, 64, 128, 256, 512}", "points": pts}
+    for dtype in (cs.CS_F32, cs.CS_F64):
+        tdt = torch.float64 if dtype == cs.CS_F64 else torch.float32
+        plans, keep = [], []
+        for k, n in enumerate(ns):
+            h = 2 * np.pi / n
+            x = torch.from_numpy(W.sines_field(n, seed=900 + k)).to("cuda", tdt)
+            y = torch.zeros_like(x)
+            keep += [x, y]
+            w = np.array([1, 4, 1, 4, -20, 4, 1, 4, 1.0]) / (6 * h * h)
+            desc = cs.StencilDesc(nx=n, ny=n, dir=cs.CS_DIR_XY, bc=cs.CS_BC_PERIODIC, dtype=dtype,
+                                  left=1, right=1, top=1, bottom=1, weights=w)
+            p = cs.cs_plan_create_2d(desc, x, y)
+            cs.cs_plan_set_tile_choice(p, 1)
+            plans.append(p)
+
+        def timed(fn):
+            for _ in range(5):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) * 1e3 / reps
+
+        def per_call():
+            for p in plans:
+                cs.cs_compute(p, stream)
+
+        res = {"per_call_us": timed(per_call)}
+        for p in plans:
+            cs.cs_plan_use_graph(p, True)
+        res["per_call_graph_us"] = timed(per_call)
+        for p in plans:
+            cs.cs_plan_use_graph(p, False)
+        res["grouped_us"] = timed(lambda: cs.cs_compute_group(plans, stream))
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            cs.cs_compute_group(plans, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        res["grouped_graph_us"] = timed(g.replay)
+        del g
+        for p in plans:
+            cs.cs_destroy(p)
+        res = {k: round(v, 2) for k, v in res.items()}
+        res["grouped_graph_gpts"] = round(pts / (res["grouped_graph_us"] * 1e-6) / 1e9, 2)
+        res["speedup_vs_per_call"] = round(res["per_call_us"] / res["grouped_graph_us"], 2)
+        out["f64" if dtype == cs.CS_F64 else "f32"] = res
     return out
 
 
@@ -581,45 +732,96 @@ def bench_serve(cs, torch, factors=(0.5, 0.9, 1.5), count=120, seed=2026):
     return out
 
 
-def ch_fp64_ops_per_point(rhs_in_fp64: bool, chunks: int, m: int) -> float:
-    """FP64 operations per grid point of one ADI step as the kernels perform them: RHS 9.7
-    (Cbar on the halo-2 tile: 1.2; on the halo-1 tile the digit Laplacian's scaling, N and Z:
-    5 x 1.1; the outer digit Laplacian's scaling, C^n - C^{n-1} and the combination: 3; done in
-    FP32 for FP32 storage), two sweeps of local LU (5) + spike correction (4) + chunk-end system
-    (16 chunks / m), and the update (2: Cbar and the add; for FP32 storage Cbar is formed in FP32
-    and the add is the one FP64 operation)."""
+def ch_fp64_ops_per_point(chunks: int, m: int) -> float:
+    """FP64-pipe operations per grid point of one ADI step as the kernels perform them, for either
+    storage: the right-hand side 8.6 (Cbar on the halo-2 tile: 1.2; on the halo-1 tile u u, N,
+    the first digit Laplacian's scaling (carrying -a) and Z: 4 x 1.1; the second scaling,
+    C^n - C^{n-1} and the final combination: 3), two sweeps of local LU (5) + spike correction (4)
+    + chunk-end system (16 chunks / m), and the update (2: FP64 storage Cbar and the add; FP32
+    storage the add and the narrowing conversion, which runs on the FP64 pipe)."""
     per_sweep = 5 + 4 + 16.0 * chunks / m
-    return (9.7 if rhs_in_fp64 else 0.0) + 2 * per_sweep + (2 if rhs_in_fp64 else 1)
+    return 8.6 + 2 * per_sweep + 2
 
 
-def bench_batch1d(cs, torch, stream, hbm_peak):
-    off = W.ragged_offsets(65536, seed=2019)
-    x = W.sines_lines(off, seed=2020).astype(np.float32)
-    d_off = torch.from_numpy(off).cuda()
-    d_in = torch.from_numpy(x).cuda()
-    d_out = torch.zeros_like(d_in)
-    w = np.array([-1, 16, -30, 16, -1.0]) / 12.0
-    desc = cs.StencilDesc(dir=cs.CS_DIR_X, bc=cs.CS_BC_PERIODIC, dtype=cs.CS_F32, left=2, right=2, weights=w)
-    plan = cs.cs_plan_create_1d_batch(desc, off.size - 1, d_off, int(off[-1]), d_in, d_out)
-    cs.cs_autotune(plan, stream)
-    cs.cs_plan_use_graph(plan, True)
-    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+def _median_event_ms(torch, stream, launch, flush, reps=12, skip=2):
     times = []
-    for r in range(12):
+    for _ in range(reps):
         flush_l2(flush)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        cs.cs_compute(plan, stream)
+        launch()
         e1.record(stream)
         times.append((e0, e1))
     torch.cuda.synchronize()
-    ms = statistics.median([a.elapsed_time(b) for a, b in times[2:]])
-    cs.cs_destroy(plan)
+    return statistics.median([a.elapsed_time(b) for a, b in times[skip:]])
+
+
+def bench_batch1d(cs, torch, stream, hbm_peak):
+    """The ragged batch (65,536 lines, lengths log-uniform in 64..4096, 4th-order second
+    derivative, periodic per line), L2 evicted before every launch, CUDA events:
+      * persistent: FP32 storage, one persistent launch replayed from a CUDA graph, launch shape
+        from the autotuner (the configuration's form);
+      * fp64_plain: the same lines in FP64 storage, one plain launch per call, default shape;
+      * per_length_class: FP32, one plain launch per length class [2^k, 2^(k+1)) over that
+        class's lines packed contiguously (7 launches; the naive batching baseline)."""
+    off = W.ragged_offsets(65536, seed=2019)
+    x64 = W.sines_lines(off, seed=2020)
+    x = x64.astype(np.float32)
+    d_off = torch.from_numpy(off).cuda()
+    w = np.array([-1, 16, -30, 16, -1.0]) / 12.0
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     total = int(off[-1])
-    nbytes = 8 * total + 8 * off.size
-    return {"lines": off.size - 1, "points": total, "ms": round(ms, 4),
-            "gpts_per_s": round(total / (ms * 1e-3) / 1e9, 2),
-            "hbm_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1), "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / hbm_peak, 3)}
+    nbytes32 = 8 * total + 8 * off.size
+    out = {"lines": off.size - 1, "points": total}
+
+    def arm(ms, eb):
+        nb = 2 * eb * total + 8 * off.size
+        return {"ms": round(ms, 4), "gpts_per_s": round(total / (ms * 1e-3) / 1e9, 2),
+                "hbm_gbs": round(nb / (ms * 1e-3) / 1e9, 1), "hbm_frac": round(nb / (ms * 1e-3) / 1e9 / hbm_peak, 3)}
+
+    d_in = torch.from_numpy(x).cuda()
+    d_out = torch.zeros_like(d_in)
+    desc = cs.StencilDesc(dir=cs.CS_DIR_X, bc=cs.CS_BC_PERIODIC, dtype=cs.CS_F32, left=2, right=2, weights=w)
+    plan = cs.cs_plan_create_1d_batch(desc, off.size - 1, d_off, total, d_in, d_out)
+    cs.cs_autotune(plan, stream)
+    cs.cs_plan_use_graph(plan, True)
+    ms = _median_event_ms(torch, stream, lambda: cs.cs_compute(plan, stream), flush)
+    cs.cs_destroy(plan)
+    out.update({"ms": round(ms, 4), "gpts_per_s": round(total / (ms * 1e-3) / 1e9, 2),
+                "hbm_gbs": round(nbytes32 / (ms * 1e-3) / 1e9, 1),
+                "hbm_frac": round(nbytes32 / (ms * 1e-3) / 1e9 / hbm_peak, 3)})
+    out["persistent"] = arm(ms, 4)
+
+    d_in64 = torch.from_numpy(x64).cuda()
+    d_out64 = torch.zeros_like(d_in64)
+    desc64 = cs.StencilDesc(dir=cs.CS_DIR_X, bc=cs.CS_BC_PERIODIC, dtype=cs.CS_F64, left=2, right=2, weights=w)
+    plan64 = cs.cs_plan_create_1d_batch(desc64, off.size - 1, d_off, total, d_in64, d_out64)
+    ms64 = _median_event_ms(torch, stream, lambda: cs.cs_compute(plan64, stream), flush)
+    cs.cs_destroy(plan64)
+    out["fp64_plain"] = arm(ms64, 8)
+    del d_in64, d_out64
+
+    lens = np.diff(off)
+    cls = np.floor(np.log2(lens)).astype(int)
+    plans, keep = [], []
+    for k in sorted(set(cls.tolist())):
+        sel = np.nonzero(cls == k)[0]
+        o = np.concatenate([[0], np.cumsum(lens[sel])]).astype(np.int64)
+        xs = np.concatenate([x[off[m]:off[m + 1]] for m in sel])
+        ci, co, cof = torch.from_numpy(xs).cuda(), torch.zeros(xs.size, dtype=torch.float32, device="cuda"), \
+            torch.from_numpy(o).cuda()
+        keep += [ci, co, cof]
+        plans.append(cs.cs_plan_create_1d_batch(desc, sel.size, cof, int(o[-1]), ci, co))
+
+    def per_class():
+        for p in plans:
+            cs.cs_compute(p, stream)
+
+    msc = _median_event_ms(torch, stream, per_class, flush)
+    for p in plans:
+        cs.cs_destroy(p)
+    out["per_length_class"] = arm(msc, 4) | {"launches": len(plans)}
+    return out
 
 
 # --------------------------------------------------------------------------------------------
@@ -695,10 +897,49 @@ def cpu_rows(seconds_each: float = 2.0):
     return out
 
 
+def cpu_parallel(seconds: float):
+    """The same oracle sample on every host core at once: one thread per core, each calling the
+    C oracle (ctypes releases the interpreter lock during the call) on its own row bands for
+    `seconds`; throughput = all points / wall time.  The second form of the CPU baseline."""
+    import concurrent.futures as cf
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    rows = 16
+    bands = []
+    for n in SIZES:
+        h = 2 * np.pi / n
+        bands.append((W.sines_field(n, seed=1902 + n, ny=rows), stencil_suite(h)))
+
+    def worker(_):
+        pts = 0
+        deadline = time.perf_counter() + seconds
+        while time.perf_counter() < deadline:
+            for band, suite in bands:
+                for name, d, L, R, T, B, w, fn, coe, taps in suite:
+                    for bc in (1, 0):
+                        if fn:
+                            oracle.stencil2d_fn(band, fn, coe, bc)
+                        else:
+                            oracle.stencil2d(band, w, d, bc, L, R, T, B)
+                        pts += band.size
+        return pts
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        pts = sum(ex.map(worker, range(cores)))
+    wall = time.perf_counter() - t0
+    return {"value": round(pts / wall / 1e9, 6), "unit": "Gpts/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle (C) on {rows}-row bands of the 4096^2 and 8192^2 grids, all 10 stencil/bc "
+                      f"combinations, one thread per host core for {seconds:.0f} s",
+            "seconds": round(wall, 2)}
+
+
 def cpu_baseline(seconds: float):
     pts, t, desc = cpu_sample(seconds)
     return {"value": round(pts / t / 1e9, 6), "unit": "Gpts/s", "cores": 1, "kind": "oracle",
-            "sample": desc, "seconds": round(t, 2), "host_cores_available": os.cpu_count()}
+            "sample": desc, "seconds": round(t, 2), "host_cores_available": os.cpu_count(),
+            "all_cores": cpu_parallel(max(2.0, seconds / 3))}
 
 
 def run_reference(args):
@@ -738,9 +979,16 @@ def run_part(args):
     if kind[0] == "ch":
         n, dt, steps = int(kind[1]), kind[2], int(kind[3])
         bnd = cs.CS_CH_NOFLUX if len(kind) > 4 and kind[4] == "noflux" else cs.CS_CH_PERIODIC
-        res = bench_ch(cs, torch, stream, [(n, cs.CS_F64 if dt == "f64" else cs.CS_F32, steps, bnd)])
+        res = bench_ch(cs, torch, stream, [(n, cs.CS_F64 if dt == "f64" else cs.CS_F32, steps, bnd)],
+                       autotune=not args.no_autotune)
     elif kind[0] == "serve":
         res = bench_serve(cs, torch)
+    elif kind[0] == "single_call":
+        res = bench_single_call(cs, torch, stream)
+    elif kind[0] == "group":
+        res = bench_group(cs, torch, stream)
+    elif kind[0] == "ch_runs":
+        res = bench_ch_runs(cs, torch, stream)
     elif kind[0] == "coarsening":
         res = bench_coarsening(cs, torch, stream)
     elif kind[0] == "streamed":
@@ -764,7 +1012,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile-choice", type=int, default=-1, help="force a tile choice (0, 1, 2) instead of autotuning")
     ap.add_argument("--only", default="", help="profile one sweep: name,n,f64|f32,p|np")
-    ap.add_argument("--part", default="", help="run one part alone: ch:<n>:<f64|f32>:<steps>[:noflux], batch1d, serve, coarsening, streamed or weno")
+    ap.add_argument("--part", default="", help="run one part alone: ch:<n>:<f64|f32>:<steps>[:noflux], ch_runs, single_call, group, batch1d, serve, coarsening, streamed or weno")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
