@@ -11,6 +11,7 @@
 #pragma once
 
 #include <stdint.h>
+#include <string.h>
 
 namespace cs {
 namespace ixd {
@@ -27,6 +28,7 @@ template <int NT>
 __device__ __forceinline__ uint32_t ix_tile_max_hi(const double* s, int n, unsigned* s_red) {
   const uint4* q = reinterpret_cast<const uint4*>(s);
   uint32_t m = 0u;
+#pragma unroll 4
   for (int k = threadIdx.x; k < n / 2; k += NT) {
     const uint4 v = q[k];
     m = __vimax3_u32(m, v.y & 0x7fffffffu, v.w & 0x7fffffffu);
@@ -46,7 +48,17 @@ __device__ __forceinline__ uint32_t ix_tile_max_hi(const double* s, int n, unsig
 // so that |T'| <= 2^52: T < (sum |n_k|) 2^(2 DB).
 template <int DB> struct Digits;
 template <> struct Digits<24> { static constexpr int kFrac = 48, kRound = 4, kMaxSum = 64; };
-template <> struct Digits<28> { static constexpr int kFrac = 56, kRound = 7, kMaxSum = 8; };
+template <> struct Digits<28> { static constexpr int kFrac = 56, kRound = 8, kMaxSum = 8; };
+
+// The common weight scale c as the combination uses it: rounded to 51 significant bits (a relative
+// change below 2^-52, the size of the weights' own FP64 rounding), so that 1.5 c is exact too.
+__host__ __device__ inline double ixi_round51(double c) {
+  unsigned long long b;
+  memcpy(&b, &c, sizeof b);
+  b = (b + 2ull) & ~3ull;  // nearest on the two lowest significand bits; a carry moves the exponent
+  memcpy(&c, &b, sizeof b);
+  return c;
+}
 
 // Digits of x on the grid whose top is 2^G, G = tile_e - 1022: A = floor(|x| / 2^(G-F)), F = 2 DB,
 // = (M << 3) >> (tile_e - e + 56 - F) for the 53-bit significand M of x (biased exponent e),
@@ -69,44 +81,46 @@ __device__ __forceinline__ int2 ixi_split(double x, int tile_e) {
 
 // T * 2^-RS * (2^RS scale) for T = S0 2^DB + S1, with one FP64 instruction:
 // T' = S0 2^(DB-RS) + round(S1 / 2^RS) = round(T / 2^RS) (ties to even) is exact apart from the
-// last term, |T' + q| <= 2^52 (q, default 0, is an integer added in the same units: the user
-// function's cubic term), so D = 2^52 + |T'| is the bit pattern of 2^52 plus |T'|, and
-// fma(D, +-2^RS scale, -+2^(52+RS) scale) = T' 2^RS scale is rounded once.  w holds the words of
-// 2^RS scale and of -2^(52+RS) scale (ixi_consts); the sign of T flips both.
+// last term, |T' + q| < 2^51 (q, default 0, is an integer added in the same units: the user
+// function's cubic term).  V = T' + q + 2^51 lies in [0, 2^52), so D = 2^52 + V is the bit
+// pattern of 2^52 plus V, and fma(D, 2^RS scale, -1.5 2^(52+RS) scale) = (V - 2^51) 2^RS scale is
+// rounded once; both constants are exact (ixi_consts, with c rounded to 51 bits).  w holds their
+// words.
 template <int DB = 24>
 __device__ __forceinline__ double ixi_combine(int S0, int S1, const uint32_t (&w)[4], long long q = 0) {
   constexpr int RS = Digits<DB>::kRound;
   // round(S1 / 2^RS) with ties to even: rounding half up would bias every output by half a unit
   // of 2^-RS on average, and a conserved sum (the Cahn-Hilliard mass) would drift by that much
   const int r = (S1 + ((1 << (RS - 1)) - 1) + ((S1 >> RS) & 1)) >> RS;
-  const long long Tp = static_cast<long long>(S0) * (1ll << (DB - RS)) + static_cast<long long>(r) + q;
-  const uint32_t sgn = static_cast<uint32_t>(static_cast<unsigned long long>(Tp) >> 63) << 31;
-  const unsigned long long A = sgn ? 0ull - static_cast<unsigned long long>(Tp) : static_cast<unsigned long long>(Tp);
-  const double D = __longlong_as_double(static_cast<long long>(0x4330000000000000ull + A));
-  const double sc = __hiloint2double(static_cast<int>(w[0] ^ sgn), static_cast<int>(w[1]));
-  const double cs = __hiloint2double(static_cast<int>(w[2] ^ sgn), static_cast<int>(w[3]));
+  const long long V = static_cast<long long>(S0) * (1ll << (DB - RS)) + static_cast<long long>(r) +
+                      (q + (1ll << 51));
+  const double D = __longlong_as_double(static_cast<long long>(0x4330000000000000ull) + V);
+  const double sc = __hiloint2double(static_cast<int>(w[0]), static_cast<int>(w[1]));
+  const double cs = __hiloint2double(static_cast<int>(w[2]), static_cast<int>(w[3]));
   return __fma_rn(D, sc, cs);
 }
 
 // The combination's constants for a tile, scale = c 2^(G-F): w = the words of 2^RS scale and of
-// -2^(52+RS) scale, made by adding to c's exponent field.  Returns false (the tile then takes
-// native FP64) when c is zero or not normal, when the tile's largest value is outside
-// [2^-900, 2^900], or when either constant would leave the normal range; an all-zero tile
-// (tile_e 0) gets zero constants, so its outputs are 0.
+// -1.5 2^(52+RS) scale, made by adding to the exponent fields of c and of c15 = -1.5 c (c rounded
+// to 51 bits by ixi_round51, so c15 is exact).  Returns false (the tile then takes native FP64)
+// when c is zero or not normal, when the tile's largest value is outside [2^-900, 2^900], or when
+// either constant would leave the normal range; an all-zero tile (tile_e 0) gets zero constants,
+// so its outputs are 0.
 template <int DB = 24>
-__device__ __forceinline__ bool ixi_consts(double c, int tile_e, uint32_t (&w)[4]) {
+__device__ __forceinline__ bool ixi_consts(double c, double c15, int tile_e, uint32_t (&w)[4]) {
   constexpr int k1 = Digits<DB>::kRound - Digits<DB>::kFrac, k2 = k1 + 52;
   w[0] = w[1] = w[2] = w[3] = 0u;
   if (tile_e == 0) return true;
   const uint32_t chi = static_cast<uint32_t>(__double2hiint(c)), clo = static_cast<uint32_t>(__double2loint(c));
-  const int ec = static_cast<int>((chi >> 20) & 0x7ffu);
+  const uint32_t dhi = static_cast<uint32_t>(__double2hiint(c15)), dlo = static_cast<uint32_t>(__double2loint(c15));
+  const int ec = static_cast<int>((chi >> 20) & 0x7ffu), ed = static_cast<int>((dhi >> 20) & 0x7ffu);
   const int G = tile_e - 1022;
   if (tile_e < kMinExp || tile_e > kMaxExp || ec == 0 || ec == 0x7ff) return false;
-  if (ec + G + k1 < 1 || ec + G + k2 > 2046) return false;
+  if (ec + G + k1 < 1 || ed + G + k2 > 2046) return false;
   w[0] = chi + (static_cast<uint32_t>(G + k1) << 20);
   w[1] = clo;
-  w[2] = (chi ^ 0x80000000u) + (static_cast<uint32_t>(G + k2) << 20);
-  w[3] = clo;
+  w[2] = dhi + (static_cast<uint32_t>(G + k2) << 20);
+  w[3] = dlo;
   return true;
 }
 
@@ -116,6 +130,7 @@ template <int NT, int DB = 24>
 __device__ __forceinline__ void ixi_split_tile(double* s, int n, int tile_e) {
   const double2* q = reinterpret_cast<const double2*>(s);
   int4* qi = reinterpret_cast<int4*>(s);
+#pragma unroll 4
   for (int k = threadIdx.x; k < n / 2; k += NT) {
     const double2 v = q[k];
     const int2 a = ixi_split<DB>(v.x, tile_e);

@@ -444,7 +444,8 @@ __device__ __forceinline__ void dd_add_cubic_minus2(float2& sh, float2& sl, floa
 
 struct IxTaps {
   int8_t n[32];  // integer weight ratios n_k (sum |n_k| <= 64)
-  double c;      // common scale: w_k ~= c * n_k
+  double c;      // common scale, w_k ~= c * n_k, rounded to 51 bits (ixi_round51)
+  double c15;    // -1.5 c (exact)
   float inv_hi, inv_lo;  // 1 / c as a float pair (the user function's cubic term)
 };
 
@@ -640,7 +641,7 @@ __global__ void __launch_bounds__(kThreads, 3)
   const uint32_t mhi = ixd::ix_tile_max_hi<kThreads>(s, ROWS * COLS, s_red);
   const int tile_e = static_cast<int>(mhi >> 20);
   uint32_t w[4];
-  if (!ixi_consts(itaps.c, tile_e, w) || (sd.epi && !ixf_tile_ok(tile_e, itaps.c))) {
+  if (!ixi_consts(itaps.c, itaps.c15, tile_e, w) || (sd.epi && !ixf_tile_ok(tile_e, itaps.c))) {
     spec_compute<double, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
     return;
   }
@@ -749,7 +750,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil2d_group(const __grid_const
       const uint32_t mhi = ixd::ix_tile_max_hi<kThreads>(s, ROWS * COLS, s_red);
       const int tile_e = static_cast<int>(mhi >> 20);
       uint32_t w[4];
-      if (!ixi_consts(g.itaps.c, tile_e, w) || (sd.epi && !ixf_tile_ok(tile_e, g.itaps.c))) {
+      if (!ixi_consts(g.itaps.c, g.itaps.c15, tile_e, w) || (sd.epi && !ixf_tile_ok(tile_e, g.itaps.c))) {
         spec_compute<double, TY, SPEC>(s, g.out, g.nx, g.ny, g.periodic, x0, y0, g.taps);
       } else {
         ixd::ixi_split_tile<kThreads>(s, ROWS * COLS, tile_e);
@@ -829,7 +830,8 @@ int launch_group_t(const Stencil2DConfig* const* cfgs, const void* const* ins, v
     for (int i = 0; i < 32; ++i) g.taps.w[i] = i < nt ? static_cast<T>(c->weights[i]) : T(0);
     digits = digits && c->ix_ok && c->fp64_mode == CS_FP64_AUTO;
     for (int i = 0; i < 32; ++i) g.itaps.n[i] = static_cast<int8_t>(i < nt && c->ix_ok ? c->ix_n[i] : 0);
-    g.itaps.c = c->ix_c;
+    g.itaps.c = ixd::ixi_round51(c->ix_c);
+    g.itaps.c15 = -1.5 * g.itaps.c;
     if (c->ix_ok) {
       g.itaps.inv_hi = static_cast<float>(1.0 / c->ix_c);
       g.itaps.inv_lo = static_cast<float>(1.0 / c->ix_c - static_cast<double>(g.itaps.inv_hi));
@@ -1250,7 +1252,7 @@ __global__ void __launch_bounds__(kThreads)
       const uint32_t mhi = ixd::ix_tile_max_hi<kThreads>(s, SE, reinterpret_cast<unsigned*>(s_wmax));
       const int tile_e = static_cast<int>(mhi >> 20);
       uint32_t w[4];
-      if (!ixi_consts(itaps.c, tile_e, w) || (sd.epi && !ixf_tile_ok(tile_e, itaps.c))) {
+      if (!ixi_consts(itaps.c, itaps.c15, tile_e, w) || (sd.epi && !ixf_tile_ok(tile_e, itaps.c))) {
         spec_compute<double, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
       } else {
         ixd::ixi_split_tile<kThreads>(s, SE, tile_e);
@@ -1453,7 +1455,8 @@ int launch_stencil2d_t(const Stencil2DConfig* cfg, const void* vin, void* vout, 
         if (cfg->fp64_mode == CS_FP64_AUTO && cfg->ix_ok) {
           mode = 1;
           for (int i = 0; i < 32; ++i) it.n[i] = static_cast<int8_t>(i < nt ? cfg->ix_n[i] : 0);
-          it.c = cfg->ix_c;
+          it.c = ixd::ixi_round51(cfg->ix_c);
+          it.c15 = -1.5 * it.c;
           it.inv_hi = static_cast<float>(1.0 / cfg->ix_c);
           it.inv_lo = static_cast<float>(1.0 / cfg->ix_c - static_cast<double>(it.inv_hi));
         } else if (cfg->fp64_mode == CS_FP64_AUTO && cfg->dd_ok) {
@@ -1477,7 +1480,8 @@ int launch_stencil2d_t(const Stencil2DConfig* cfg, const void* vin, void* vout, 
       if (cfg->ix_ok && cfg->fp64_mode == CS_FP64_AUTO) {
         IxTaps it;
         for (int i = 0; i < 32; ++i) it.n[i] = static_cast<int8_t>(i < nt ? cfg->ix_n[i] : 0);
-        it.c = cfg->ix_c;
+        it.c = ixd::ixi_round51(cfg->ix_c);
+        it.c15 = -1.5 * it.c;
         it.inv_hi = static_cast<float>(1.0 / cfg->ix_c);
         it.inv_lo = static_cast<float>(1.0 / cfg->ix_c - static_cast<double>(it.inv_hi));
         if (cfg->tile_rows == 32)
