@@ -966,6 +966,54 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sharded(args):
+    """--sharded: one periodic CH grid (n = 4096 by default, FP64) split into row bands over the
+    ranks (one GPU each; NCCL, or a single gloo rank on one GPU), stepped with the library's band
+    entry points: halo exchange, band right-hand side, x solves, all-to-all transpose, y solves,
+    transpose back, update (strong scaling: the grid is fixed).  Prints one JSON line."""
+    import torch
+    import torch.distributed as dist
+    import paper_1902_09931_gb300 as cs
+    from paper_1902_09931_gb300 import distributed as DD
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    else:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29533")
+        dist.init_process_group("gloo", rank=0, world_size=1)
+    cs.load()
+    n = args.sharded_n
+    h = 2 * np.pi / n
+    r0, r1 = DD.band(n, world, rank)
+    c0 = torch.from_numpy(W.ch_initial(n, seed=1902)[r0:r1].copy()).cuda()
+    b = DD.DeviceCHBand(n, cs.CS_F64, 1.0, 0.01, 0.1 * h, c0)
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.step(args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    dist.barrier()
+    ms = max_over_ranks(world, e0.elapsed_time(e1) / args.steps) if world > 1 else e0.elapsed_time(e1) / args.steps
+    mass, energy = b.invariants()
+    b.close()
+    if rank == 0:
+        print(json.dumps({"metric": "CH-ADI steps/s, one periodic grid in row bands", "value": round(1e3 / ms, 1),
+                          "unit": "steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "strong",
+                          "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": f"CH-ADI periodic {n}^2, FP64, row bands of {r1 - r0} rows",
+                                     "parallelism": f"row bands x{world}"},
+                          "mass": mass, "energy": energy}), flush=True)
+    dist.destroy_process_group()
+
+
 def run_part(args):
     """One part of the metric on its own (used to profile it): --part ch:<n>:<f64|f32>:<steps>[:noflux],
     batch1d, serve, coarsening, streamed or weno."""
@@ -1012,11 +1060,15 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile-choice", type=int, default=-1, help="force a tile choice (0, 1, 2) instead of autotuning")
     ap.add_argument("--only", default="", help="profile one sweep: name,n,f64|f32,p|np")
+    ap.add_argument("--sharded", action="store_true", help="one CH grid split into row bands over the ranks")
+    ap.add_argument("--sharded-n", type=int, default=4096)
     ap.add_argument("--part", default="", help="run one part alone: ch:<n>:<f64|f32>:<steps>[:noflux], ch_runs, single_call, group, batch1d, serve, coarsening, streamed or weno")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.part:
+    if args.sharded:
+        run_sharded(args)
+    elif args.part:
         run_part(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -120,6 +120,10 @@ _SYMBOLS = {
     "cs_ch_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)]),
     "cs_ch_set_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_ch_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "cs_ch_band_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(_CCHDesc), ctypes.c_int64]),
+    "cs_ch_band_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "cs_ch_band_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "cs_ch_band_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_ch_solver_check": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "cs_batch1d_compute_noalloc": (ctypes.c_int, [ctypes.POINTER(_CStencilDesc), ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_last_error": (ctypes.c_char_p, []),
@@ -352,6 +356,27 @@ def cs_ch_config(plan):
     c, m = ctypes.c_int32(), ctypes.c_int32()
     _check(load().cs_ch_config(plan, ctypes.byref(c), ctypes.byref(m)))
     return c.value, m.value
+
+
+def cs_ch_band_create(desc: CHDesc, rows: int) -> ctypes.c_void_p:
+    plan = ctypes.c_void_p()
+    c = _CCHDesc()
+    c.n, c.storage, c.D, c.gamma, c.dt = desc.n, desc.storage, desc.D, desc.gamma, desc.dt
+    c.boundary = desc.boundary
+    _check(load().cs_ch_band_create(ctypes.byref(plan), ctypes.byref(c), int(rows)))
+    return plan
+
+
+def cs_ch_band_rhs(plan, d_prev, d_cur, d_rhs, d_sums=None, stream=None) -> None:
+    _check(load().cs_ch_band_rhs(plan, _ptr(d_prev), _ptr(d_cur), _ptr(d_rhs), _ptr(d_sums), _stream(stream)))
+
+
+def cs_ch_band_solve(plan, d_in, d_out, stream=None) -> None:
+    _check(load().cs_ch_band_solve(plan, _ptr(d_in), _ptr(d_out), _stream(stream)))
+
+
+def cs_ch_band_update(plan, d_prev, d_cur, d_v, d_next, stream=None) -> None:
+    _check(load().cs_ch_band_update(plan, _ptr(d_prev), _ptr(d_cur), _ptr(d_v), _ptr(d_next), _stream(stream)))
 
 
 def cs_ch_solver_check(n: int, chunks: int, a: float, boundary: int) -> float:

@@ -90,7 +90,7 @@ int flush_l2(cudaStream_t s) {
 }  // namespace autotune_detail
 }  // namespace cs
 
-enum PlanKind { kStencil2D = 1, kBatch1D = 2, kCahnHilliard = 3, kStencil2DHost = 4, kWeno = 5 };
+enum PlanKind { kStencil2D = 1, kBatch1D = 2, kCahnHilliard = 3, kStencil2DHost = 4, kWeno = 5, kCHBand = 6 };
 
 // Band slots of a host-resident (out-of-core) 2D plan: one being copied in, one swept, one
 // copied out.
@@ -105,6 +105,7 @@ struct cs_plan {
   cs::Stencil2DConfig s2;
   cs::Batch1DConfig b1;
   cs::CHPlan* ch;
+  cs::CHBand* chb;
   // graph replay
   int use_graph;
   cudaGraph_t graph;
@@ -789,6 +790,7 @@ int cs_destroy(cs_plan_t p) {
   if (p->kind == kStencil2D || p->kind == kStencil2DHost) stencil2d_release(&p->s2);
   if (p->kind == kBatch1D) batch1d_release(&p->b1);
   if (p->kind == kCahnHilliard) ch_destroy(p->ch);
+  if (p->kind == kCHBand) ch_band_destroy(p->chb);
   delete p;
   return CS_OK;
 }
@@ -802,6 +804,33 @@ int cs_ch_create(cs_plan_t* plan, const cs_ch_desc* d, void* prev, void* cur, vo
   if (rc != CS_OK) { delete p; return rc; }
   *plan = p;
   return CS_OK;
+}
+
+int cs_ch_band_create(cs_plan_t* plan, const cs_ch_desc* d, int64_t rows) {
+  if (!plan) return set_error(CS_EINVAL, "null plan pointer");
+  *plan = nullptr;
+  cs_plan* p = new_plan(kCHBand);
+  if (!p) return set_error(CS_ENOMEM, "out of host memory");
+  int rc = ch_band_create(&p->chb, d, rows);
+  if (rc != CS_OK) { delete p; return rc; }
+  *plan = p;
+  return CS_OK;
+}
+
+int cs_ch_band_rhs(cs_plan_t p, const void* d_prev, const void* d_cur, double* d_rhs, double* d_sums, void* stream) {
+  if (!p || p->kind != kCHBand) return set_error(CS_EINVAL, "not a Cahn-Hilliard band plan");
+  return ch_band_rhs(p->chb, d_prev, d_cur, d_rhs, d_sums, static_cast<cudaStream_t>(stream));
+}
+
+int cs_ch_band_solve(cs_plan_t p, const double* d_in, double* d_out, void* stream) {
+  if (!p || p->kind != kCHBand) return set_error(CS_EINVAL, "not a Cahn-Hilliard band plan");
+  return ch_band_solve(p->chb, d_in, d_out, static_cast<cudaStream_t>(stream));
+}
+
+int cs_ch_band_update(cs_plan_t p, const void* d_prev, const void* d_cur, const double* d_v, void* d_next,
+                      void* stream) {
+  if (!p || p->kind != kCHBand) return set_error(CS_EINVAL, "not a Cahn-Hilliard band plan");
+  return ch_band_update(p->chb, d_prev, d_cur, d_v, d_next, static_cast<cudaStream_t>(stream));
 }
 
 int cs_ch_step(cs_plan_t p, int64_t nsteps, double* h_mass, double* h_energy, void* stream) {

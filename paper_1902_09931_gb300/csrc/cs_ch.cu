@@ -148,7 +148,8 @@ __device__ __forceinline__ void block_reduce2(double m, double e, double* out2) 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_ch_rhs(const T* __restrict__ cur, const T* __restrict__ prev, double* __restrict__ rhs, int64_t n,
-             double alpha, double a, double half_gamma_over_h2, double* __restrict__ partials, int noflux) {
+             double alpha, double a, double half_gamma_over_h2, double* __restrict__ partials, int noflux,
+             double am51, int band) {
   constexpr int HR = kTY + 4, HC = kTX + 4;  // halo-2 tiles
   constexpr int ZR = kTY + 2, ZC = kTX + 2;  // halo-1 tile
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -157,11 +158,14 @@ __global__ void __launch_bounds__(kThreads)
   double* sz = sb + HR * HC;                         // Z
   const int64_t x0 = static_cast<int64_t>(blockIdx.x) * kTX;
   const int64_t y0 = static_cast<int64_t>(blockIdx.y) * kTY;
+  // band != 0: cur and prev are row bands padded with the 2 rows above and the 2 rows below (the
+  // neighbours' rows, exchanged by the caller); output row r of the band is padded row r + 2
   for (int idx = threadIdx.x; idx < HR * HC; idx += kThreads) {
     const int r = idx / HC, c = idx - r * HC;
     const int64_t gy = y0 - 2 + r, gx = x0 - 2 + c;
-    const int64_t off = noflux ? static_cast<int64_t>(mirrorn(gy, n)) * n + mirrorn(gx, n)
-                               : static_cast<int64_t>(wrapn(gy, n)) * n + wrapn(gx, n);
+    const int64_t off = band      ? (gy + 2) * n + wrapn(gx, n)
+                        : noflux  ? static_cast<int64_t>(mirrorn(gy, n)) * n + mirrorn(gx, n)
+                                  : static_cast<int64_t>(wrapn(gy, n)) * n + wrapn(gx, n);
     const double cv = widen(cur[off]);
     sc[idx] = cv;
     sb[idx] = 2.0 * cv - widen(prev[off]);
@@ -193,7 +197,7 @@ __global__ void __launch_bounds__(kThreads)
     {
       const int te = static_cast<int>(ixd::ix_tile_max_hi<kThreads>(cb, HR * HC, s_red) >> 20);
       uint32_t w[4];
-      const bool dig = ixd::ixi_consts<28>(-a, te, w);  // uniform over the block
+      const bool dig = ixd::ixi_consts<28>(am51, -1.5 * am51, te, w);  // uniform over the block
       if (dig) {
         ixd::ixi_split_tile<kThreads, 28>(cb, HR * HC, te);
         __syncthreads();
@@ -217,7 +221,7 @@ __global__ void __launch_bounds__(kThreads)
     {
       const int te = static_cast<int>(ixd::ix_tile_max_hi<kThreads>(zt, ZR * ZC, s_red) >> 20);
       uint32_t w[4];
-      const bool dig = ixd::ixi_consts<28>(1.0, te, w);
+      const bool dig = ixd::ixi_consts<28>(1.0, -1.5, te, w);
       if (dig) {
         ixd::ixi_split_tile<kThreads, 28>(zt, ZR * ZC, te);
         __syncthreads();
@@ -235,7 +239,7 @@ __global__ void __launch_bounds__(kThreads)
           lap_z = lap5(zt, zidx, ZC);
         }
         const int64_t o = (y0 + r) * n + x0 + c;
-        const double diff = cn[hidx] - widen(prev[o]);  // C^n - C^{n-1}
+        const double diff = cn[hidx] - widen(prev[band ? o + 2 * n : o]);  // C^n - C^{n-1}
         rhs[o] = fma(-2.0 / 3.0, diff, lap_z);
       }
     }
@@ -732,7 +736,8 @@ int launch_rhs(CHPlan* p, bool with_rhs, double* partials, cudaStream_t s) {
   const T* prev = static_cast<const T*>(p->field[p->iprev]);
   double* rhs = with_rhs ? p->A : nullptr;
   k_ch_rhs<T><<<grid, kThreads, rhs_smem_bytes(), s>>>(cur, prev, rhs, p->n, p->alpha, p->a,
-                                                        0.5 * p->gamma / (p->h * p->h), partials, p->noflux);
+                                                        0.5 * p->gamma / (p->h * p->h), partials, p->noflux,
+                                                        ixd::ixi_round51(-p->a), 0);
   CS_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return CS_OK;
@@ -1291,6 +1296,148 @@ int ch_config(CHPlan* p, int32_t* chunks, int32_t* chunk_len) {
 }
 
 void ch_destroy(CHPlan* p) { free_plan(p); }
+
+// ---- a row band of a periodic grid decomposed over several GPUs -----------------------------------
+// The pieces of the ADI step that a caller runs on its own band of rows (Sec. 6.2's decomposition):
+// the right-hand side and invariant sums of the band from padded C^n, C^{n-1} (2 halo rows each
+// side, exchanged by the caller), line solves along the rows of a buffer (the x lines of the band,
+// or after a transpose the y lines of a band of columns), and the update C^{n+1} = Cbar + v on the
+// band.  The kernels are the full-grid step's own, so the decomposed step gives the same values.
+struct CHBand {
+  int64_t n, rows;
+  int storage;
+  double D, gamma, dt, h, a, alpha;
+  int P, m;
+  double* coef;
+  double* K;
+  double* B;         // rows * n scratch (local solutions)
+  double* bnd;       // 4 * P * rows chunk-end values
+  double* partials;  // 2 per RHS block
+  int rhs_blocks;
+};
+
+namespace {
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_ch_band_update(const T* __restrict__ prev, const T* __restrict__ cur, const double* __restrict__ v,
+                     T* __restrict__ next, int64_t n, int64_t count) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int64_t o = i + 2 * n;  // padded row r + 2
+  if constexpr (sizeof(T) == 4) {
+    const float cb = fmaf(2.0f, cur[o], -prev[o]);  // as the full-grid update forms it
+    next[o] = __double2float_rn(widen(cb) + v[i]);
+  } else {
+    next[o] = fma(2.0, cur[o], -prev[o]) + v[i];
+  }
+}
+
+void free_band(CHBand* b) {
+  if (!b) return;
+  cudaFree(b->coef); cudaFree(b->K); cudaFree(b->B); cudaFree(b->bnd); cudaFree(b->partials);
+  delete b;
+}
+}  // namespace
+
+int ch_band_create(CHBand** out, const cs_ch_desc* d, int64_t rows) {
+  *out = nullptr;
+  if (!d) return set_error(CS_EINVAL, "null Cahn-Hilliard description");
+  if (d->boundary != CS_CH_PERIODIC) return set_error(CS_EUNSUPPORTED, "row bands are for the periodic domain");
+  if (d->n < 64 || d->n % 64 != 0 || d->n > 65536) return set_error(CS_EINVAL, "n must be a multiple of 64 in [64, 65536]");
+  if (rows < kTY || rows % kTY != 0 || rows > d->n) return set_error(CS_EINVAL, "band rows must be a multiple of %d in [%d, n]", kTY, kTY);
+  if (d->storage != CS_F64 && d->storage != CS_F32) return set_error(CS_EINVAL, "storage must be CS_F64 or CS_F32");
+  if (!(d->D > 0) || !(d->gamma >= 0) || !(d->dt > 0) || !std::isfinite(d->D) || !std::isfinite(d->gamma) || !std::isfinite(d->dt))
+    return set_error(CS_EINVAL, "D > 0, gamma >= 0, dt > 0 and finite are required");
+  CHBand* b = new (std::nothrow) CHBand;
+  if (!b) return set_error(CS_ENOMEM, "out of host memory");
+  memset(b, 0, sizeof *b);
+  b->n = d->n; b->rows = rows; b->storage = d->storage;
+  b->D = d->D; b->gamma = d->gamma; b->dt = d->dt;
+  b->h = 2.0 * M_PI / static_cast<double>(d->n);
+  const double h2 = b->h * b->h;
+  b->a = (2.0 / 3.0) * d->D * d->gamma * d->dt / (h2 * h2);
+  b->alpha = (2.0 / 3.0) * d->D * d->dt / h2;
+  int P = default_chunks(d->n), choice;
+  char key[96];
+  snprintf(key, sizeof key, "ch|%s|n%lld|sm%d", d->storage == CS_F32 ? "f32" : "f64", (long long)d->n, num_sms());
+  if (tune_lookup(key, &choice) && valid_chunks(d->n, choice)) P = choice;
+  b->P = P;
+  b->m = static_cast<int>(d->n / P);
+  b->rhs_blocks = static_cast<int>((d->n / kTX) * (rows / kTY));
+  std::vector<double> coef, K;
+  int rc = build_tables(d->n, P, b->a, false, coef, K);
+  if (rc != CS_OK) { free_band(b); return rc; }
+  cudaError_t e = cudaMalloc(&b->coef, coef.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&b->K, K.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&b->B, static_cast<size_t>(rows) * d->n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&b->bnd, static_cast<size_t>(4) * P * rows * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&b->partials, static_cast<size_t>(2) * b->rhs_blocks * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(b->coef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->K, K.data(), K.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    free_band(b);
+    return e == cudaErrorMemoryAllocation ? set_error(CS_ENOMEM, "band workspace: %s", cudaGetErrorString(e))
+                                          : cuda_error(e, "band workspace");
+  }
+  rc = d->storage == CS_F32 ? set_rhs_attr<float>() : set_rhs_attr<double>();
+  if (rc != CS_OK) { free_band(b); return rc; }
+  *out = b;
+  return CS_OK;
+}
+
+int ch_band_rhs(CHBand* b, const void* prev, const void* cur, double* rhs, double* sums, cudaStream_t s) {
+  if (!prev || !cur || (!rhs && !sums)) return set_error(CS_EINVAL, "null buffer");
+  dim3 grid(static_cast<unsigned>(b->n / kTX), static_cast<unsigned>(b->rows / kTY));
+  const double hg = 0.5 * b->gamma / (b->h * b->h);
+  double* part = sums ? b->partials : nullptr;
+  if (b->storage == CS_F32)
+    k_ch_rhs<float><<<grid, kThreads, rhs_smem_bytes(), s>>>(static_cast<const float*>(cur), static_cast<const float*>(prev),
+                                                              rhs, b->n, b->alpha, b->a, hg, part, 0,
+                                                              ixd::ixi_round51(-b->a), 1);
+  else
+    k_ch_rhs<double><<<grid, kThreads, rhs_smem_bytes(), s>>>(static_cast<const double*>(cur), static_cast<const double*>(prev),
+                                                               rhs, b->n, b->alpha, b->a, hg, part, 0,
+                                                               ixd::ixi_round51(-b->a), 1);
+  CS_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  if (sums) {
+    k_reduce_final<<<1, 256, 0, s>>>(b->partials, b->rhs_blocks, b->h * b->h, sums);
+    CS_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+  }
+  return CS_OK;
+}
+
+int ch_band_solve(CHBand* b, const double* in, double* out, cudaStream_t s) {
+  if (!in || !out) return set_error(CS_EINVAL, "null buffer");
+  const unsigned sgrid = static_cast<unsigned>((b->rows * b->P + kSolveThreads - 1) / kSolveThreads);
+  const size_t ksmem = static_cast<size_t>(16) * b->P * sizeof(double);
+  // rows lines of n points, line stride n, element stride 1 (the kernels' line count is `rows`)
+  k_solve_local<double, true, false><<<sgrid, kSolveThreads, 0, s>>>(in, b->B, b->bnd, b->coef, b->rows, b->P, b->m,
+                                                                    b->n, 1);
+  k_solve_correct<0, double, true, false><<<sgrid, kSolveThreads, ksmem, s>>>(
+      b->B, b->bnd, b->coef, b->K, b->rows, b->P, b->m, b->n, 1, out, nullptr, nullptr, nullptr);
+  CS_CUDA_TRY(cudaGetLastError());
+  count_launches(2);
+  return CS_OK;
+}
+
+int ch_band_update(CHBand* b, const void* prev, const void* cur, const double* v, void* next, cudaStream_t s) {
+  if (!prev || !cur || !v || !next) return set_error(CS_EINVAL, "null buffer");
+  const int64_t count = b->rows * b->n;
+  const unsigned grid = static_cast<unsigned>((count + 255) / 256);
+  if (b->storage == CS_F32)
+    k_ch_band_update<float><<<grid, 256, 0, s>>>(static_cast<const float*>(prev), static_cast<const float*>(cur), v,
+                                                 static_cast<float*>(next), b->n, count);
+  else
+    k_ch_band_update<double><<<grid, 256, 0, s>>>(static_cast<const double*>(prev), static_cast<const double*>(cur), v,
+                                                  static_cast<double*>(next), b->n, count);
+  CS_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return CS_OK;
+}
+
+void ch_band_destroy(CHBand* b) { free_band(b); }
 
 // Host replay of the device line solver (phase 1: chunk LU forward and backward, chunk-end
 // values; phase 2: neighbouring chunk ends from K, spike correction), in the kernels' order of

@@ -107,5 +107,11 @@ int ch_set_fields(CHPlan* p, void* prev, void* cur, void* next);
 int ch_autotune(CHPlan* p, cudaStream_t s);
 void ch_destroy(CHPlan* p);
 int ch_solver_check(int64_t n, int P, double a, bool noflux, double* residual);
+struct CHBand;
+int ch_band_create(CHBand** out, const cs_ch_desc* d, int64_t rows);
+int ch_band_rhs(CHBand* b, const void* prev, const void* cur, double* rhs, double* sums, cudaStream_t s);
+int ch_band_solve(CHBand* b, const double* in, double* out, cudaStream_t s);
+int ch_band_update(CHBand* b, const void* prev, const void* cur, const double* v, void* next, cudaStream_t s);
+void ch_band_destroy(CHBand* b);
 
 }  // namespace cs

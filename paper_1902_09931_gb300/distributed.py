@@ -168,3 +168,109 @@ class DeviceBandSweep:
             cs_destroy(self._plan)
         self._plan = None
         self._bufs = None
+
+
+def _stage(t: torch.Tensor, group) -> torch.Tensor:
+    """gloo moves CPU tensors only: a device tensor travels through host memory there."""
+    return t.cpu() if t.is_cuda and dist.get_backend(group) == "gloo" else t
+
+
+def exchange_halo_inplace(padded: torch.Tensor, halo: int, group=None) -> None:
+    """Fills the `halo` rows above and below the band held in padded[halo:-halo] (periodic rows:
+    the first band's neighbour above is the last band) with the neighbours' rows, in place, so the
+    band never moves."""
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    rows = padded.shape[0] - 2 * halo
+    if rows < halo:
+        raise ValueError(f"band of {rows} rows is thinner than the halo ({halo})")
+    if world == 1:
+        padded[:halo] = padded[rows:rows + halo]
+        padded[rows + halo:] = padded[halo:2 * halo]
+        return
+    up, down = (rank - 1) % world, (rank + 1) % world
+    top = _stage(torch.empty_like(padded[:halo]), group)
+    bottom = _stage(torch.empty_like(padded[:halo]), group)
+    reqs = [dist.irecv(top, src=up, group=group, tag=_TAG_TOP),
+            dist.irecv(bottom, src=down, group=group, tag=_TAG_BOTTOM),
+            dist.isend(_stage(padded[rows:rows + halo].contiguous(), group), dst=down, group=group, tag=_TAG_TOP),
+            dist.isend(_stage(padded[halo:2 * halo].contiguous(), group), dst=up, group=group, tag=_TAG_BOTTOM)]
+    for r in reqs:
+        r.wait()
+    padded[:halo].copy_(top)
+    padded[rows + halo:].copy_(bottom)
+
+
+def transpose_bands_device(local: torch.Tensor, n: int, group=None) -> torch.Tensor:
+    """transpose_bands for device tensors on any backend: a single rank transposes in device memory;
+    gloo ranks exchange through host memory, NCCL ranks device to device."""
+    if dist.get_world_size(group) == 1:
+        return local.t().contiguous()
+    if local.is_cuda and dist.get_backend(group) == "gloo":
+        return transpose_bands(local.cpu(), n, group).to(local.device)
+    return transpose_bands(local, n, group)
+
+
+class DeviceCHBand:
+    """The periodic Cahn-Hilliard ADI step (Sec. 5.1) of an n x n grid split into row bands over
+    the ranks of `group`, one band per rank, computed by this library's band entry points
+    (cs_ch_band_*): halo exchange of C^n and C^{n-1} (2 rows, in place in padded buffers), the
+    band's right-hand side, the x line solves, an all-to-all transpose, the y line solves, the
+    transpose back and the update.  `c0` is this rank's band of the initial field (rows x n, on
+    the GPU; C^{-1} = C^0).  The three padded fields rotate as in cs_ch_step."""
+
+    HALO = 2
+
+    def __init__(self, n: int, storage: int, D: float, gamma: float, dt: float, c0: torch.Tensor, group=None):
+        from . import CHDesc, CS_F64, cs_ch_band_create
+        self.group = group
+        self.n = n
+        world = dist.get_world_size(group)
+        rank = dist.get_rank(group)
+        r0, r1 = band(n, world, rank)
+        self.rows = r1 - r0
+        if tuple(c0.shape) != (self.rows, n):
+            raise ValueError(f"band of shape {tuple(c0.shape)}, expected {(self.rows, n)}")
+        tdt = torch.float64 if storage == CS_F64 else torch.float32
+        self.f = [torch.zeros(self.rows + 2 * self.HALO, n, dtype=tdt, device=c0.device) for _ in range(3)]
+        for k in (0, 1):
+            self.f[k][self.HALO:self.HALO + self.rows] = c0.to(tdt)
+        self.ip, self.ic, self.inext = 0, 1, 2
+        self.rhs = torch.empty(self.rows, n, dtype=torch.float64, device=c0.device)
+        self.sums = torch.zeros(2, dtype=torch.float64, device=c0.device)
+        self.plan = cs_ch_band_create(CHDesc(n=n, storage=storage, D=D, gamma=gamma, dt=dt), self.rows)
+        self.steps = 0
+
+    def _halos(self):
+        exchange_halo_inplace(self.f[self.ip], self.HALO, self.group)
+        exchange_halo_inplace(self.f[self.ic], self.HALO, self.group)
+
+    def invariants(self):
+        """(mass, energy) of the current field: the bands' FP64 sums, allreduced."""
+        from . import cs_ch_band_rhs
+        self._halos()
+        cs_ch_band_rhs(self.plan, self.f[self.ip], self.f[self.ic], None, self.sums)
+        return tuple(float(v) for v in allreduce_sum(_stage(self.sums, self.group), self.group))
+
+    def step(self, nsteps: int = 1) -> None:
+        from . import cs_ch_band_rhs, cs_ch_band_solve, cs_ch_band_update
+        for _ in range(nsteps):
+            self._halos()
+            cs_ch_band_rhs(self.plan, self.f[self.ip], self.f[self.ic], self.rhs)
+            cs_ch_band_solve(self.plan, self.rhs, self.rhs)                   # x lines: the band's rows
+            wt = transpose_bands_device(self.rhs, self.n, self.group)         # a band of columns, as rows
+            cs_ch_band_solve(self.plan, wt, wt)                               # y lines
+            v = transpose_bands_device(wt, self.n, self.group)
+            cs_ch_band_update(self.plan, self.f[self.ip], self.f[self.ic], v, self.f[self.inext])
+            self.ip, self.ic, self.inext = self.ic, self.inext, self.ip
+            self.steps += 1
+
+    def field(self) -> torch.Tensor:
+        """This rank's band of the current field C^n (a view of its padded buffer)."""
+        return self.f[self.ic][self.HALO:self.HALO + self.rows]
+
+    def close(self) -> None:
+        from . import cs_destroy
+        if self.plan is not None:
+            cs_destroy(self.plan)
+        self.plan = None
