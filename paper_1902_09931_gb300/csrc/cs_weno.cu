@@ -336,22 +336,138 @@ __global__ void __launch_bounds__(kWThreads, sizeof(T) == 8 ? 4 : 1)
   }
 }
 
+// ---- FP32 storage: two adjacent columns per thread in packed FP32x2 arithmetic -----------------
+// The WENO weights of two neighbouring outputs run as one chain of FP32x2 instructions (each lane
+// rounds as the scalar form would); the upwind choice, the exponent of max|v| and the division
+// stay per lane.  Tiles of 128 x 32 outputs: 64 column pairs x 4 row groups of 8 rows; a row's
+// x window (10 values) is read as five 8-byte loads, the y windows roll in registers.
+constexpr int kW2TX = 128, kW2Cols = kWLA + kW2TX + kWLA, kW2Groups = kWThreads / (kW2TX / 2);
+constexpr int kW2Rows = kWTY / kW2Groups;
+
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+
+// weno_scaled<float> on two lanes (w* already scaled by each lane's own 2^(127 - e))
+__device__ __forceinline__ float2 weno_scaled2(float2 w1, float2 w2, float2 w3, float2 w4, float2 w5, float2 mw) {
+  const float2 phi1 = __ffma2_rn(f2s(1.0f / 3.0f), w1, __ffma2_rn(f2s(-7.0f / 6.0f), w2, __fmul2_rn(f2s(11.0f / 6.0f), w3)));
+  const float2 phi2 = __ffma2_rn(f2s(-1.0f / 6.0f), w2, __ffma2_rn(f2s(5.0f / 6.0f), w3, __fmul2_rn(f2s(1.0f / 3.0f), w4)));
+  const float2 phi3 = __ffma2_rn(f2s(1.0f / 3.0f), w3, __ffma2_rn(f2s(5.0f / 6.0f), w4, __fmul2_rn(f2s(-1.0f / 6.0f), w5)));
+  const float2 a1 = __fadd2_rn(__ffma2_rn(f2s(-2.0f), w2, w1), w3), b1 = __fadd2_rn(__ffma2_rn(f2s(-4.0f), w2, w1), __fmul2_rn(f2s(3.0f), w3));
+  const float2 a2 = __fadd2_rn(__ffma2_rn(f2s(-2.0f), w3, w2), w4), b2 = __ffma2_rn(w4, f2s(-1.0f), w2);
+  const float2 a3 = __fadd2_rn(__ffma2_rn(f2s(-2.0f), w4, w3), w5), b3 = __ffma2_rn(f2s(3.0f), w3, __ffma2_rn(f2s(-4.0f), w4, w5));
+  const float2 s1 = __ffma2_rn(__fmul2_rn(f2s(13.0f / 12.0f), a1), a1, __fmul2_rn(__fmul2_rn(f2s(0.25f), b1), b1));
+  const float2 s2 = __ffma2_rn(__fmul2_rn(f2s(13.0f / 12.0f), a2), a2, __fmul2_rn(__fmul2_rn(f2s(0.25f), b2), b2));
+  const float2 s3 = __ffma2_rn(__fmul2_rn(f2s(13.0f / 12.0f), a3), a3, __fmul2_rn(__fmul2_rn(f2s(0.25f), b3), b3));
+  const float2 eps = __fmul2_rn(f2s(1e-6f), __fmul2_rn(mw, mw));
+  const float2 t1 = __fadd2_rn(s1, eps), t2 = __fadd2_rn(s2, eps), t3 = __fadd2_rn(s3, eps);
+  const float2 q1 = __fmul2_rn(t1, t1), q2 = __fmul2_rn(t2, t2), q3 = __fmul2_rn(t3, t3);
+  const float2 p1 = __fmul2_rn(f2s(0.1f), __fmul2_rn(q2, q3)), p2 = __fmul2_rn(f2s(0.6f), __fmul2_rn(q1, q3));
+  const float2 p3 = __fmul2_rn(f2s(0.3f), __fmul2_rn(q1, q2));
+  const float2 num = __ffma2_rn(p1, phi1, __ffma2_rn(p2, phi2, __fmul2_rn(p3, phi3)));
+  const float2 den = __fadd2_rn(__fadd2_rn(p1, p2), p3);
+  return make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
+}
+
+// upwinded WENO derivative (unscaled: the caller divides by h) of two lanes; d[k] the differences
+// at k = 0..5 as for upwind(), pos the lanes' velocity signs
+__device__ __forceinline__ float2 upwind2(const float2 (&d)[6], bool posx, bool posy) {
+  auto pick = [&](int a, int b) { return make_float2(posx ? d[a].x : d[b].x, posy ? d[a].y : d[b].y); };
+  const float2 v1 = pick(0, 5), v2 = pick(1, 4), v3 = pick(2, 3), v4 = pick(3, 2), v5 = pick(4, 1);
+  auto lane_max = [](float a, float b, float c, float d_, float e) {
+    return fmaxf(fmaxf(fmaxf(fabsf(a), fabsf(b)), fmaxf(fabsf(c), fabsf(d_))), fabsf(e));
+  };
+  const float mx = lane_max(v1.x, v2.x, v3.x, v4.x, v5.x), my = lane_max(v1.y, v2.y, v3.y, v4.y, v5.y);
+  const int ex = static_cast<int>(__float_as_uint(mx) >> 23), ey = static_cast<int>(__float_as_uint(my) >> 23);
+  if (ex >= 1 && ex <= 253 && ey >= 1 && ey <= 253) {
+    const float2 sc = make_float2(__uint_as_float(static_cast<unsigned>(254 - ex) << 23),
+                                  __uint_as_float(static_cast<unsigned>(254 - ey) << 23));
+    const float2 r = weno_scaled2(__fmul2_rn(v1, sc), __fmul2_rn(v2, sc), __fmul2_rn(v3, sc), __fmul2_rn(v4, sc),
+                                  __fmul2_rn(v5, sc), __fmul2_rn(make_float2(mx, my), sc));
+    return __fmul2_rn(r, make_float2(__uint_as_float(static_cast<unsigned>(ex) << 23),
+                                     __uint_as_float(static_cast<unsigned>(ey) << 23)));
+  }
+  return make_float2(weno5(v1.x, v2.x, v3.x, v4.x, v5.x, 0.0f), weno5(v1.y, v2.y, v3.y, v4.y, v5.y, 0.0f));
+}
+
+__global__ void __launch_bounds__(kWThreads)
+    k_weno_adv_f32x2(const float* __restrict__ c, const float* __restrict__ u, const float* __restrict__ v,
+                     float* __restrict__ out, int64_t nx, int64_t ny, int vec_ok, float inv_hx, float inv_hy) {
+  __shared__ __align__(16) float s[kWTileRows * kW2Cols];
+  const int64_t x0 = static_cast<int64_t>(blockIdx.x) * kW2TX;
+  const int64_t y0 = static_cast<int64_t>(blockIdx.y) * kWTY;
+  s2d::load_tile<float>(s, c, nx, ny, true, vec_ok != 0, x0, y0, kWHalo, kWLA, kW2Cols, kWTileRows);
+  const int cx = 2 * (threadIdx.x % (kW2TX / 2));
+  const int r0 = (threadIdx.x / (kW2TX / 2)) * kW2Rows;
+  const int64_t gx = x0 + cx;
+  if (gx >= nx) return;
+  const bool two = gx + 1 < nx;
+  // both outputs' stores as one 8-byte store where the row start keeps 8-byte alignment
+  const bool pair_store = two && (nx % 2 == 0) && (reinterpret_cast<uintptr_t>(out) % 8 == 0) &&
+                          (reinterpret_cast<uintptr_t>(u) % 8 == 0) && (reinterpret_cast<uintptr_t>(v) % 8 == 0);
+  const float* colp = s + cx + kWLA;  // this thread's first column
+  float2 col[2 * kWHalo + 1];         // the two columns at rows y - 3 .. y + 3
+#pragma unroll
+  for (int k = 0; k < 2 * kWHalo + 1; ++k) col[k] = *reinterpret_cast<const float2*>(colp + (r0 + k) * kW2Cols);
+#pragma unroll
+  for (int r = 0; r < kW2Rows; ++r) {
+    const int64_t gy = y0 + r0 + r;
+    if (gy >= ny) break;
+    const float* row = colp + (r0 + r + kWHalo) * kW2Cols;
+    float w[10];  // columns cx - 4 .. cx + 5 (8-byte aligned pairs)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const float2 t = *reinterpret_cast<const float2*>(row - 4 + 2 * k);
+      w[2 * k] = t.x;
+      w[2 * k + 1] = t.y;
+    }
+    float2 dx[6], dy[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {  // C(i + j) is w[4 + j] for lane 0 (column cx), w[5 + j] for lane 1
+      dx[k] = make_float2(w[k + 2] - w[k + 1], w[k + 3] - w[k + 2]);
+      dy[k] = __ffma2_rn(col[k], f2s(-1.0f), col[k + 1]);
+    }
+    const int64_t o = gy * nx + gx;
+    float2 uu, vv;
+    if (pair_store) {
+      uu = *reinterpret_cast<const float2*>(u + o);
+      vv = *reinterpret_cast<const float2*>(v + o);
+    } else {
+      uu = make_float2(u[o], two ? u[o + 1] : 0.0f);
+      vv = make_float2(v[o], two ? v[o + 1] : 0.0f);
+    }
+    const float2 fx = __fmul2_rn(upwind2(dx, positive(uu.x), positive(uu.y)), f2s(inv_hx));
+    const float2 fy = __fmul2_rn(upwind2(dy, positive(vv.x), positive(vv.y)), f2s(inv_hy));
+    const float2 res = __ffma2_rn(uu, fx, __fmul2_rn(vv, fy));
+    if (pair_store) {
+      *reinterpret_cast<float2*>(out + o) = res;
+    } else {
+      out[o] = res.x;
+      if (two) out[o + 1] = res.y;
+    }
+    if (r + 1 < kW2Rows) {
+#pragma unroll
+      for (int k = 0; k < 2 * kWHalo; ++k) col[k] = col[k + 1];
+      col[2 * kWHalo] = *reinterpret_cast<const float2*>(colp + (r0 + r + 2 * kWHalo + 1) * kW2Cols);
+    }
+  }
+}
+
 }  // namespace
 
 int weno_launch(const WenoConfig* cfg, const void* c, const void* u, const void* v, void* out, cudaStream_t st) {
   if (cfg->nx == 0 || cfg->ny == 0) return CS_OK;
   const size_t eb = cfg->dtype == CS_F32 ? 4 : 8;
   const int vec_ok = reinterpret_cast<uintptr_t>(c) % 16 == 0 && (cfg->nx * eb) % 16 == 0;
-  const int64_t gx = (cfg->nx + kWTX - 1) / kWTX, gy = (cfg->ny + kWTY - 1) / kWTY;
+  const int64_t tx = cfg->dtype == CS_F32 ? kW2TX : kWTX;
+  const int64_t gx = (cfg->nx + tx - 1) / tx, gy = (cfg->ny + kWTY - 1) / kWTY;
   if (gx > 0x7fffffff || gy > 65535)
     return set_error(CS_EUNSUPPORTED, "grid %lld x %lld exceeds the WENO launch limits", (long long)cfg->nx, (long long)cfg->ny);
   const dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy));
   const double fx = 1e-99 * cfg->hx * cfg->hx, fy = 1e-99 * cfg->hy * cfg->hy;
   if (cfg->dtype == CS_F32) {
-    k_weno_adv<float><<<grid, kWThreads, 0, st>>>(static_cast<const float*>(c), static_cast<const float*>(u),
-                                                  static_cast<const float*>(v), static_cast<float*>(out), cfg->nx,
-                                                  cfg->ny, vec_ok, static_cast<float>(1.0 / cfg->hx),
-                                                  static_cast<float>(1.0 / cfg->hy), 0.f, 0.f);
+    k_weno_adv_f32x2<<<grid, kWThreads, 0, st>>>(static_cast<const float*>(c), static_cast<const float*>(u),
+                                                 static_cast<const float*>(v), static_cast<float*>(out), cfg->nx,
+                                                 cfg->ny, vec_ok, static_cast<float>(1.0 / cfg->hx),
+                                                 static_cast<float>(1.0 / cfg->hy));
   } else {
     k_weno_adv<double><<<grid, kWThreads, 0, st>>>(static_cast<const double*>(c), static_cast<const double*>(u),
                                                    static_cast<const double*>(v), static_cast<double*>(out), cfg->nx,
