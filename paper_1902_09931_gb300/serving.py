@@ -185,6 +185,9 @@ class GpuBackend:
         self.pool_streams = [torch.cuda.Stream() for _ in range(streams)]
         self.free_streams = list(self.pool_streams)
         self.ch_plans: Dict[int, list] = collections.defaultdict(list)
+        # sweep plans are reused (rebound to each job's buffers): creating and destroying a plan
+        # per job allocates and frees device memory, and a free synchronises the device
+        self.sweep_plans: Dict[tuple, list] = collections.defaultdict(list)
         self.ch_dt_factor, self.D, self.gamma = ch_dt_factor, D, gamma
 
     # -- resources -------------------------------------------------------------------------
@@ -193,13 +196,27 @@ class GpuBackend:
         return int(0.5 * free)
 
     def warmup(self, sizes, copies: int = 2):
-        """Creates Cahn-Hilliard plans (and their device workspace) ahead of the run."""
+        """Creates Cahn-Hilliard plans (and their device workspace) and sweep plans of every
+        stencil of the mix ahead of the run."""
         made = []
         for n in sizes:
             for _ in range(copies):
                 made.append((n, self._new_ch_plan(n)))
         for n, p in made:
             self.ch_plans[n].append(p)
+        t = self.torch
+        for n in sizes:
+            x = t.zeros(n, n, dtype=t.float32, device=self.dev)
+            y = t.zeros_like(x)
+            for st in SWEEP_STENCILS:
+                for _ in range(copies):
+                    self.sweep_plans[(n, st)].append(self._new_sweep_plan(n, st, x, y))
+
+    def _new_sweep_plan(self, n, stencil, x, y):
+        cs = self.cs
+        name, d, L, R, T, B, w = sweep_stencil(stencil, 2 * np.pi / n)
+        return cs.cs_plan_create_2d(cs.StencilDesc(nx=n, ny=n, dir=d, bc=cs.CS_BC_PERIODIC, dtype=cs.CS_F32,
+                                                   left=L, right=R, top=T, bottom=B, weights=w), x, y)
 
     def _new_ch_plan(self, n):
         t = self.torch
@@ -216,10 +233,12 @@ class GpuBackend:
         if job.kind == "sweep":
             x = W.device_uniform((n, n), job.seed, -1.0, 1.0, self.dev, t.float32)
             y = t.zeros_like(x)
-            h = 2 * np.pi / n
-            name, d, L, R, T, B, w = sweep_stencil(job.stencil, h)
-            plan = cs.cs_plan_create_2d(cs.StencilDesc(nx=n, ny=n, dir=d, bc=cs.CS_BC_PERIODIC, dtype=cs.CS_F32,
-                                                       left=L, right=R, top=T, bottom=B, weights=w), x, y)
+            pool = self.sweep_plans[(n, job.stencil)]
+            if pool:
+                plan = pool.pop()
+                cs.cs_set_buffers(plan, x, y)
+            else:
+                plan = self._new_sweep_plan(n, job.stencil, x, y)
             job.res = {"plan": plan, "x": x}
             job.output = y
         else:
@@ -273,7 +292,7 @@ class GpuBackend:
 
     def release(self, job: Job):
         if job.kind == "sweep":
-            self.cs.cs_destroy(job.res["plan"])
+            self.sweep_plans[(job.n, job.stencil)].append(job.res["plan"])
         else:
             plan = job.res["plan"]
             _, cur, _ = self.cs.cs_ch_fields(plan)
@@ -284,8 +303,14 @@ class GpuBackend:
         job.res = {}
 
     def idle_until(self, t_abs: float, clock):
-        while clock() < t_abs:
-            pass
+        """Waits for the next arrival: sleeps while more than 0.2 ms remain, then spins (a sleep
+        alone overshoots by tens of microseconds)."""
+        while True:
+            left = t_abs - clock()
+            if left <= 0:
+                return
+            if left > 2e-4:
+                time.sleep(left - 1.5e-4)
 
 
 def sweep_stencil(name: str, h: float):
