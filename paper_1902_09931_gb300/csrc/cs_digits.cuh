@@ -81,19 +81,20 @@ __device__ __forceinline__ int2 ixi_split(double x, int tile_e) {
 
 // T * 2^-RS * (2^RS scale) for T = S0 2^DB + S1, with one FP64 instruction:
 // T' = S0 2^(DB-RS) + round(S1 / 2^RS) = round(T / 2^RS) (ties to even) is exact apart from the
-// last term, |T' + q| < 2^51 (q, default 0, is an integer added in the same units: the user
-// function's cubic term).  V = T' + q + 2^51 lies in [0, 2^52), so D = 2^52 + V is the bit
+// last term.  q = qa 2^(DB-RS) + qb (default 0) is an integer added in the same units (the user
+// function's cubic term), split so that it joins the two 32-bit parts before the one 64-bit
+// multiply-add; |T' + q| < 2^51.  V = T' + q + 2^51 lies in [0, 2^52), so D = 2^52 + V is the bit
 // pattern of 2^52 plus V, and fma(D, 2^RS scale, -1.5 2^(52+RS) scale) = (V - 2^51) 2^RS scale is
 // rounded once; both constants are exact (ixi_consts, with c rounded to 51 bits).  w holds their
 // words.
 template <int DB = 24>
-__device__ __forceinline__ double ixi_combine(int S0, int S1, const uint32_t (&w)[4], long long q = 0) {
+__device__ __forceinline__ double ixi_combine(int S0, int S1, const uint32_t (&w)[4], int qa = 0, int qb = 0) {
   constexpr int RS = Digits<DB>::kRound;
   // round(S1 / 2^RS) with ties to even: rounding half up would bias every output by half a unit
   // of 2^-RS on average, and a conserved sum (the Cahn-Hilliard mass) would drift by that much
   const int r = (S1 + ((1 << (RS - 1)) - 1) + ((S1 >> RS) & 1)) >> RS;
-  const long long V = static_cast<long long>(S0) * (1ll << (DB - RS)) + static_cast<long long>(r) +
-                      (q + (1ll << 51));
+  const long long V = static_cast<long long>(S0 + qa) * (1ll << (DB - RS)) + static_cast<long long>(r + qb) +
+                      (1ll << 51);
   const double D = __longlong_as_double(static_cast<long long>(0x4330000000000000ull) + V);
   const double sc = __hiloint2double(static_cast<int>(w[0]), static_cast<int>(w[1]));
   const double cs = __hiloint2double(static_cast<int>(w[2]), static_cast<int>(w[3]));

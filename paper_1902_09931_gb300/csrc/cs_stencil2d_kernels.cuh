@@ -434,11 +434,11 @@ __device__ __forceinline__ void dd_add_cubic_minus2(float2& sh, float2& sl, floa
 // ---- exact digit evaluation of FP64-storage stencils with integer weight ratios ------------
 // When every weight is w_k = c * n_k with small integers (sum |n_k| <= 64; the paper's stencils
 // are of this kind), a tile is evaluated with integer-exact sums: every staged value is cut into
-// two signed 25-bit integer digits on a grid fixed by the tile's largest exponent,
-// x = (d0 2^25 + d1) 2^(G-50) + r with |r| < 2^(G-50), so each digit sum S_i = sum_k n_k d_{k,i}
-// is exact in int32 (per tap two integer multiply-adds).  The sums form T = S0 2^25 + S1, which is
-// rounded to a multiple of 2^4 and scaled by c * 2^(G-50) with one FP64 FMA (ixi_combine).  The
-// error is at most (2^-49 + 2^-46 / sum|n|) of sum|w| * max|in| (native FP64 accumulation: about
+// two signed 24-bit integer digits on a grid fixed by the tile's largest exponent,
+// x = (d0 2^24 + d1) 2^(G-48) + r with |r| < 2^(G-48), so each digit sum S_i = sum_k n_k d_{k,i}
+// is exact in int32 (per tap two integer multiply-adds).  The sums form T = S0 2^24 + S1, which is
+// rounded to a multiple of 2^4 and scaled by c * 2^(G-48) with one FP64 FMA (ixi_combine).  The
+// error is at most (2^-47 + 2^-44 / sum|n|) of sum|w| * max|in| (native FP64 accumulation: about
 // taps * 2^-53 of sum|w| |in|).  Tiles holding inf / nan, or whose largest value is outside
 // [2^-900, 2^900], are evaluated in native FP64.
 
@@ -477,31 +477,50 @@ __device__ __forceinline__ IxfConsts ixf_consts(int tile_e, float inv_hi, float 
   return k;
 }
 
-// Q for the centre digits (d0, d1) of two adjacent outputs (packed FP32x2): u = d0 2^(G-24) +
-// d1 2^(G-48) (both exact floats), P = u^3 - u in double-float, (ph, pl) = P (1/c) 2^(44-G),
-// renormalised; Q = round(ph + pl) from two FP32 rounding shifts: 1.5 * 2^44 takes ph to a
-// multiple of 2^21 (|ph| < 2^43), whose count k sits in the low mantissa bits, and 1.5 * 2^23
-// rounds the rest (|rest| < 2^22); Q = k 2^21 + the rest's integer.  No conversion instruction
-// beyond the two exact int -> float conversions of the digits.
-__device__ __forceinline__ void ixf_q2(int2 a, int2 b, const IxfConsts& k, long long& qa, long long& qb) {
-  const float2 uh = __fmul2_rn(make_float2(__int2float_rn(a.x), __int2float_rn(b.x)), f2(k.p1));
-  const float2 ul = __fmul2_rn(make_float2(__int2float_rn(a.y), __int2float_rn(b.y)), f2(k.p2));
-  float2 sh = make_float2(0.0f, 0.0f), sl = make_float2(0.0f, 0.0f);
-  dd_add_cubic_minus2(sh, sl, uh, ul);
-  const float2 ph = __fmul2_rn(sh, f2(k.ih));
-  float2 pe = __ffma2_rn(sh, f2(k.ih), neg2(ph));
-  pe = __ffma2_rn(sl, f2(k.ih), pe);
-  const float2 pl = __ffma2_rn(sh, f2(k.il), pe);
-  const float2 qh = __fadd2_rn(ph, pl);  // Fast2Sum: |pl| below half an ulp of qh after this
-  const float2 ql = sub2(pl, sub2(qh, ph));
+// Q for the centre digits (d0, d1) of two adjacent outputs (packed FP32x2), returned as
+// Q = qa 2^20 + qb (the split ixi_combine takes).  u = uh + ul with uh = d0 2^(G-24) and
+// ul = d1 2^(G-48) (both exact floats); P = u^3 - u in double-float with error-free products and
+// sums, carried negated where that saves a negation (a packed FMA has no free operand sign):
+// m2 = -uh^2 rounded, u^2 = -m2 + e2; m3 = m2 uh = -(p2 uh) rounded, u^3 = -m3 + e3; then
+// -P = (m3 + uh) + (ul - e3), summed with TwoSum into s + lo.  R = -P (1/c) 2^(44-G) =
+// (s + lo)(ih + il) is formed as -nph + pl and renormalised with Fast2Sum to qh + ql
+// (|ql| <= half an ulp of qh).  round(qh + ql) comes from two FP32 rounding shifts:
+// 1.5 * 2^44 takes qh to a multiple of 2^21 (|qh| < 2^43), whose count k sits in the low mantissa
+// bits, and 1.5 * 2^23 rounds the rest (|rest| < 2^22) to k2; Q = -(k 2^21 + k2), so
+// qa = -2k and qb = -k2 (ties to even is symmetric).  The only conversions are the four exact
+// int -> float conversions of the digits.
+__device__ __forceinline__ void ixf_q2(int2 a, int2 b, const IxfConsts& k, int2& qa, int2& qb) {
+  const float2 D0 = make_float2(__int2float_rn(a.x), __int2float_rn(b.x));
+  const float2 D1 = make_float2(__int2float_rn(a.y), __int2float_rn(b.y));
+  const float2 uh = __fmul2_rn(D0, f2(k.p1));
+  const float2 nuh = __fmul2_rn(D0, f2(-k.p1));
+  const float2 ul = __fmul2_rn(D1, f2(k.p2));
+  const float2 nul = __fmul2_rn(D1, f2(-k.p2));
+  const float2 m2 = __fmul2_rn(nuh, uh);
+  float2 e2 = __ffma2_rn(uh, uh, m2);
+  e2 = __ffma2_rn(__fmul2_rn(D0, f2(2.0f * k.p1)), ul, e2);
+  const float2 m3 = __fmul2_rn(m2, uh);
+  float2 e3 = __ffma2_rn(m2, nuh, m3);
+  e3 = __ffma2_rn(m2, nul, e3);
+  e3 = __ffma2_rn(e2, uh, e3);
+  const float2 s = __fadd2_rn(m3, uh);  // TwoSum(m3, uh)
+  const float2 bb = sub2(s, m3);
+  const float2 err = __fadd2_rn(sub2(m3, sub2(s, bb)), sub2(uh, bb));
+  const float2 lo = __fadd2_rn(sub2(err, e3), ul);
+  const float2 nph = __fmul2_rn(s, f2(-k.ih));
+  float2 pl = __ffma2_rn(s, f2(k.ih), nph);
+  pl = __ffma2_rn(lo, f2(k.ih), pl);
+  pl = __ffma2_rn(s, f2(k.il), pl);
+  const float2 qh = sub2(pl, nph);  // Fast2Sum(-nph, pl)
+  const float2 ql = sub2(pl, __fadd2_rn(qh, nph));
   constexpr float M1 = 26388279066624.0f, M2 = 12582912.0f;  // 1.5 * 2^44, 1.5 * 2^23
   const float2 t = __fadd2_rn(qh, f2(M1));
   const float2 rest = __fadd2_rn(sub2(qh, sub2(t, f2(M1))), ql);
   const float2 t2 = __fadd2_rn(rest, f2(M2));
-  const int ka = static_cast<int>(__float_as_uint(t.x) - __float_as_uint(M1));
-  const int kb = static_cast<int>(__float_as_uint(t.y) - __float_as_uint(M1));
-  qa = static_cast<long long>(ka) * (1ll << 21) + static_cast<int>(__float_as_uint(t2.x) - __float_as_uint(M2));
-  qb = static_cast<long long>(kb) * (1ll << 21) + static_cast<int>(__float_as_uint(t2.y) - __float_as_uint(M2));
+  qa = make_int2(2 * static_cast<int>(__float_as_uint(M1) - __float_as_uint(t.x)),
+                 2 * static_cast<int>(__float_as_uint(M1) - __float_as_uint(t.y)));
+  qb = make_int2(static_cast<int>(__float_as_uint(M2) - __float_as_uint(t2.x)),
+                 static_cast<int>(__float_as_uint(M2) - __float_as_uint(t2.y)));
 }
 
 using ixd::ixi_combine;
@@ -598,12 +617,12 @@ __device__ __forceinline__ void ix_compute(const int2* sd2, double* __restrict__
     }
     const int done = i - (H - 1);  // output row complete after its last input row
     if (done >= 0) {
-      long long q0 = 0, q1 = 0;
+      int2 qa = make_int2(0, 0), qb = make_int2(0, 0);
       if constexpr (sd.epi) {
-        if (tile_e != 0) ixf_q2(ctr[done % H][0], ctr[done % H][1], kf, q0, q1);
+        if (tile_e != 0) ixf_q2(ctr[done % H][0], ctr[done % H][1], kf, qa, qb);
       }
-      const double val0 = ixi_combine(acc0[done % H][0], acc1[done % H][0], w, q0);
-      const double val1 = ixi_combine(acc0[done % H][1], acc1[done % H][1], w, q1);
+      const double val0 = ixi_combine(acc0[done % H][0], acc1[done % H][0], w, qa.x, qb.x);
+      const double val1 = ixi_combine(acc0[done % H][1], acc1[done % H][1], w, qa.y, qb.y);
       acc0[done % H][0] = acc0[done % H][1] = acc1[done % H][0] = acc1[done % H][1] = 0;
       if (done >= klo && done < khi) {
         if (both) {
