@@ -198,7 +198,7 @@ int cs_swap(cs_plan_t plan);
 /* Arithmetic used for CS_F64 stencils (GB300 issues FP64 at 1/64 of the FP32 rate).
  * CS_FP64_AUTO (default), for the specialised stencils:
  *   - weights w_k = c * n_k with integers n_k, sum |n_k| <= 64 (every stencil of the paper):
- *     exact digit evaluation -- each value cut into two signed 24-bit integer digits on a grid
+ *     exact digit evaluation -- each value cut into two 24-bit integer digits on a grid
  *     set by the largest value of its tile (tile = 64 x TY outputs plus halo; bits below 2^-48
  *     of the grid's top dropped), digit sums exact in int32, their combination rounded to 2^-44
  *     of the grid's top and scaled with one FP64 FMA; error at most (2^-47 + 2^-44 / sum|n_k|)

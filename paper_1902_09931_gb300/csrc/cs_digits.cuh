@@ -1,8 +1,9 @@
 // Exact digit evaluation of integer-weight sums of FP64 values on the integer pipe (GB300 issues
 // FP64 at 1/64 of the FP32 rate).  For weights w_k = c * n_k with integers n_k, sum |n_k| <= 64:
-// every staged value of a tile is cut into two signed 24-bit integer digits on a grid fixed by
-// the tile's largest exponent, x = (d0 2^24 + d1) 2^(G-48) + r with 0 <= |r| < 2^(G-48) (each digit
-// carries the sign of x), so each digit sum S_i = sum_k n_k d_{k,i} is exact in int32.
+// every staged value of a tile is cut into two 24-bit integer digits on a grid fixed by the
+// tile's largest exponent, x = (d0 2^24 + d1) 2^(G-48) + r with 0 <= |r| < 2^(G-48), r of the sign
+// of x (|x| is truncated on the grid), d0 signed and 0 <= d1 < 2^24, so each digit sum
+// S_i = sum_k n_k d_{k,i} is exact in int32.
 // T = S0 2^24 + S1 is then rounded to a multiple of 2^4 (ties to even) and scaled by c * 2^(G-48)
 // with one FP64 FMA: the result is within (2^-47 + 2^-44 / sum|n|) of sum|w| * (largest value of
 // the tile).  With sum |n_k| <= 8, 28-bit digits keep 56 bits and round to 2^(G-49).  The per-tile constants come from c's bits by integer exponent arithmetic, and
@@ -21,31 +22,45 @@ constexpr int kMaxExp = 1023 + 900;  // largest one
 constexpr int kIDigitBits = 24;
 constexpr int kIFracBits = 2 * kIDigitBits;  // bits kept below the tile's top 2^G
 
-// Largest high word (sign cleared) of the n staged FP64 values (n even, 16-byte aligned): its top
+// Largest high word (sign cleared) of the N staged FP64 values (N even, 16-byte aligned): its top
 // bits are the largest biased exponent, and it is >= 0x7ff00000 exactly when the tile holds an
-// inf or a nan.  Every thread of the block (NT threads) gets the result; s_red holds NT / 32 words.
-template <int NT>
-__device__ __forceinline__ uint32_t ix_tile_max_hi(const double* s, int n, unsigned* s_red) {
+// inf or a nan.  Every thread of the block (NT threads) gets the result; s_red holds NT / 32 words
+// (16-byte aligned).  The trip count is fixed at compile time: every thread takes the same number
+// of full rounds, and one guarded round covers the remainder.
+template <int NT, int N>
+__device__ __forceinline__ uint32_t ix_tile_max_hi(const double* s, unsigned* s_red) {
+  static_assert(N % 2 == 0 && NT % 128 == 0, "pairs of values; whole uint4 reads of s_red");
+  constexpr int P = N / 2, FULL = P / NT, REM = P % NT;
   const uint4* q = reinterpret_cast<const uint4*>(s);
   uint32_t m = 0u;
-#pragma unroll 4
-  for (int k = threadIdx.x; k < n / 2; k += NT) {
-    const uint4 v = q[k];
+#pragma unroll
+  for (int it = 0; it < FULL; ++it) {
+    const uint4 v = q[threadIdx.x + it * NT];
+    m = __vimax3_u32(m, v.y & 0x7fffffffu, v.w & 0x7fffffffu);
+  }
+  if (REM != 0 && static_cast<int>(threadIdx.x) < REM) {
+    const uint4 v = q[threadIdx.x + FULL * NT];
     m = __vimax3_u32(m, v.y & 0x7fffffffu, v.w & 0x7fffffffu);
   }
   m = __reduce_max_sync(0xffffffffu, m);
   if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = m;
   __syncthreads();
+  const uint4* r4 = reinterpret_cast<const uint4*>(s_red);
   uint32_t r = 0u;
 #pragma unroll
-  for (int w = 0; w < NT / 32; ++w) r = max(r, s_red[w]);
+  for (int w = 0; w < NT / 128; ++w) {
+    const uint4 v = r4[w];
+    r = __vimax3_u32(r, v.x, v.y);
+    r = __vimax3_u32(r, v.z, v.w);
+  }
   return r;
 }
 
 // Digit widths: DB = 24 (the default) keeps 48 bits below 2^G and serves sum |n_k| <= 64;
 // DB = 28 keeps 56 bits (every bit of a value within a factor 8 of the tile's largest) and serves
-// sum |n_k| <= 8, e.g. the 5-point Laplacian.  RS is the rounding shift of the combination, chosen
-// so that |T'| <= 2^52: T < (sum |n_k|) 2^(2 DB).
+// sum |n_k| <= 8 with the positive n_k summing to at most 7 (S1 <= 7 (2^28 - 1) leaves room for the
+// rounding's carry in int32), e.g. the 5-point Laplacian.  RS is the rounding shift of the
+// combination, chosen so that |T'| < 2^51: |T| < (sum |n_k|) 2^(2 DB).
 template <int DB> struct Digits;
 template <> struct Digits<24> { static constexpr int kFrac = 48, kRound = 4, kMaxSum = 64; };
 template <> struct Digits<28> { static constexpr int kFrac = 56, kRound = 8, kMaxSum = 8; };
@@ -60,11 +75,20 @@ __host__ __device__ inline double ixi_round51(double c) {
   return c;
 }
 
-// Digits of x on the grid whose top is 2^G, G = tile_e - 1022: A = floor(|x| / 2^(G-F)), F = 2 DB,
-// = (M << 3) >> (tile_e - e + 56 - F) for the 53-bit significand M of x (biased exponent e),
-// d0 = A >> DB, d1 = A mod 2^DB, branch-free (the shift is capped at 63, where A is 0).  Zeros
-// and subnormals: a digit tile has tile_e >= kMinExp, so the shift is >= 56 and both digits are
-// 0; an all-zero tile (tile_e 0) is scaled by 0.
+// Logical right shift of a 64-bit value; PTX clamps shift amounts above 64 to 64 (result 0), so
+// no range test is needed.
+__device__ __forceinline__ unsigned long long ixi_shr64(unsigned long long v, int sh) {
+  unsigned long long r;
+  asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(v), "r"(sh));
+  return r;
+}
+
+// Digits of x on the grid whose top is 2^G, G = tile_e - 1022, F = 2 DB: A = floor(|x| / 2^(G-F))
+// = M >> (tile_e - e + 53 - F) for the 53-bit significand M of x (biased exponent e <= tile_e;
+// for F > 53, M << (F - 53) >> (tile_e - e)), then As = sgn(x) A in two's complement and
+// d0 = As >> DB (arithmetic), d1 = As mod 2^DB, so d0 2^DB + d1 = As exactly.  Branch-free.
+// Zeros and subnormals: a digit tile has tile_e >= kMinExp, so the shift is >= 64 and A is 0; an
+// all-zero tile (tile_e 0) is scaled by 0.
 template <int DB = 24>
 __device__ __forceinline__ int2 ixi_split(double x, int tile_e) {
   constexpr int F = Digits<DB>::kFrac;
@@ -72,11 +96,14 @@ __device__ __forceinline__ int2 ixi_split(double x, int tile_e) {
   const uint32_t lo = static_cast<uint32_t>(__double2loint(x));
   const int e = static_cast<int>((hi >> 20) & 0x7ffu);
   const unsigned long long M = (static_cast<unsigned long long>((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
-  const unsigned long long A = (M << 3) >> min(tile_e - e + 56 - F, 63);
-  const int sgn = static_cast<int>(hi) >> 31;  // 0 or -1
-  const int d0 = static_cast<int>(A >> DB);
-  const int d1 = static_cast<int>(A & ((1u << DB) - 1u));
-  return make_int2((d0 ^ sgn) - sgn, (d1 ^ sgn) - sgn);
+  unsigned long long A;
+  if constexpr (F <= 53)
+    A = ixi_shr64(M, tile_e - e + 53 - F);
+  else
+    A = ixi_shr64(M << (F - 53), tile_e - e);
+  const long long sgn = static_cast<long long>(static_cast<int>(hi) >> 31);  // 0 or -1
+  const long long As = (static_cast<long long>(A) ^ sgn) - sgn;
+  return make_int2(static_cast<int>(As >> DB), static_cast<int>(As & ((1ll << DB) - 1)));
 }
 
 // T * 2^-RS * (2^RS scale) for T = S0 2^DB + S1, with one FP64 instruction:
@@ -125,19 +152,24 @@ __device__ __forceinline__ bool ixi_consts(double c, double c15, int tile_e, uin
   return true;
 }
 
-// Replaces the n staged FP64 values (n even, 16-byte aligned) by their integer digits (d0, d1)
-// in the values' own 8-byte slots.  Each of the NT threads converts two values at a time.
-template <int NT, int DB = 24>
-__device__ __forceinline__ void ixi_split_tile(double* s, int n, int tile_e) {
+// Replaces the N staged FP64 values (N even, 16-byte aligned) by their integer digits (d0, d1)
+// in the values' own 8-byte slots.  Each of the NT threads converts two values at a time, in a
+// compile-time number of rounds (one guarded round for the remainder).
+template <int NT, int N, int DB = 24>
+__device__ __forceinline__ void ixi_split_tile(double* s, int tile_e) {
+  static_assert(N % 2 == 0, "values in pairs");
+  constexpr int P = N / 2, FULL = P / NT, REM = P % NT;
   const double2* q = reinterpret_cast<const double2*>(s);
   int4* qi = reinterpret_cast<int4*>(s);
-#pragma unroll 4
-  for (int k = threadIdx.x; k < n / 2; k += NT) {
+  auto pair = [&](int k) {
     const double2 v = q[k];
     const int2 a = ixi_split<DB>(v.x, tile_e);
     const int2 b = ixi_split<DB>(v.y, tile_e);
     qi[k] = make_int4(a.x, a.y, b.x, b.y);
-  }
+  };
+#pragma unroll 4
+  for (int it = 0; it < FULL; ++it) pair(threadIdx.x + it * NT);
+  if (REM != 0 && static_cast<int>(threadIdx.x) < REM) pair(threadIdx.x + FULL * NT);
 }
 
 }  // namespace ixd

@@ -434,7 +434,7 @@ __device__ __forceinline__ void dd_add_cubic_minus2(float2& sh, float2& sl, floa
 // ---- exact digit evaluation of FP64-storage stencils with integer weight ratios ------------
 // When every weight is w_k = c * n_k with small integers (sum |n_k| <= 64; the paper's stencils
 // are of this kind), a tile is evaluated with integer-exact sums: every staged value is cut into
-// two signed 24-bit integer digits on a grid fixed by the tile's largest exponent,
+// two 24-bit integer digits (d0 signed, 0 <= d1 < 2^24) on a grid fixed by the tile's largest exponent,
 // x = (d0 2^24 + d1) 2^(G-48) + r with |r| < 2^(G-48), so each digit sum S_i = sum_k n_k d_{k,i}
 // is exact in int32 (per tap two integer multiply-adds).  The sums form T = S0 2^24 + S1, which is
 // rounded to a multiple of 2^4 and scaled by c * 2^(G-48) with one FP64 FMA (ixi_combine).  The
@@ -619,7 +619,7 @@ __device__ __forceinline__ void ix_compute(const int2* sd2, double* __restrict__
     if (done >= 0) {
       int2 qa = make_int2(0, 0), qb = make_int2(0, 0);
       if constexpr (sd.epi) {
-        if (tile_e != 0) ixf_q2(ctr[done % H][0], ctr[done % H][1], kf, qa, qb);
+        ixf_q2(ctr[done % H][0], ctr[done % H][1], kf, qa, qb);  // kf is all zero for a zero tile: Q = 0
       }
       const double val0 = ixi_combine(acc0[done % H][0], acc1[done % H][0], w, qa.x, qb.x);
       const double val1 = ixi_combine(acc0[done % H][1], acc1[done % H][1], w, qa.y, qb.y);
@@ -650,14 +650,14 @@ __global__ void __launch_bounds__(kThreads, 3)
   static_assert(!sd.xform, "digit kernel covers weighted stencils and the cubic user function");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* s = reinterpret_cast<double*>(smem_raw);
-  __shared__ unsigned s_red[kThreads / 32];
+  __shared__ __align__(16) unsigned s_red[kThreads / 32];
   static_assert(COLS % 2 == 0, "digit passes take values in pairs");
   const int64_t x0 = static_cast<int64_t>(blockIdx.x) * TX;
   const int64_t y0 = (static_cast<int64_t>(blockIdx.y) + ty0) * TY;
   load_tile_ct<double, ROWS, COLS>(s, in, nx, ny, periodic != 0, vec_ok != 0, x0, y0, sd.T, LA);
   // pass 1: the tile's largest exponent; inf / nan (and tiles outside the exponent window) take
   // native FP64
-  const uint32_t mhi = ixd::ix_tile_max_hi<kThreads>(s, ROWS * COLS, s_red);
+  const uint32_t mhi = ixd::ix_tile_max_hi<kThreads, ROWS * COLS>(s, s_red);
   const int tile_e = static_cast<int>(mhi >> 20);
   uint32_t w[4];
   if (!ixi_consts(itaps.c, itaps.c15, tile_e, w) || (sd.epi && !ixf_tile_ok(tile_e, itaps.c))) {
@@ -665,7 +665,7 @@ __global__ void __launch_bounds__(kThreads, 3)
     return;
   }
   // pass 2: integer digits over the values' own slots
-  ixd::ixi_split_tile<kThreads>(s, ROWS * COLS, tile_e);
+  ixd::ixi_split_tile<kThreads, ROWS * COLS>(s, tile_e);
   __syncthreads();
   ix_compute<TY, SPEC>(reinterpret_cast<const int2*>(s), out, nx, ny, periodic, x0, y0, itaps, w, tile_e);
 }
@@ -754,7 +754,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil2d_group(const __grid_const
   constexpr int LA = (sd.L + V - 1) / V * V, RA = (sd.R + V - 1) / V * V;
   constexpr int COLS = LA + TX + RA, ROWS = TY + sd.T + sd.B;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ unsigned s_red[kThreads / 32];
+  __shared__ __align__(16) unsigned s_red[kThreads / 32];
   T* s = reinterpret_cast<T*>(smem_raw);
   int j = 0;
   for (int b = static_cast<int>(blockIdx.x); b < tab.total_tiles; b += static_cast<int>(gridDim.x)) {
@@ -766,13 +766,13 @@ __global__ void __launch_bounds__(kThreads) k_stencil2d_group(const __grid_const
     __syncthreads();  // the previous tile's reads of s are done
     load_tile_ct<T, ROWS, COLS>(s, g.in, g.nx, g.ny, g.periodic != 0, g.vec_ok != 0, x0, y0, sd.T, LA);
     if constexpr (MODE == 1 && !sd.xform && sizeof(T) == 8) {
-      const uint32_t mhi = ixd::ix_tile_max_hi<kThreads>(s, ROWS * COLS, s_red);
+      const uint32_t mhi = ixd::ix_tile_max_hi<kThreads, ROWS * COLS>(s, s_red);
       const int tile_e = static_cast<int>(mhi >> 20);
       uint32_t w[4];
       if (!ixi_consts(g.itaps.c, g.itaps.c15, tile_e, w) || (sd.epi && !ixf_tile_ok(tile_e, g.itaps.c))) {
         spec_compute<double, TY, SPEC>(s, g.out, g.nx, g.ny, g.periodic, x0, y0, g.taps);
       } else {
-        ixd::ixi_split_tile<kThreads>(s, ROWS * COLS, tile_e);
+        ixd::ixi_split_tile<kThreads, ROWS * COLS>(s, tile_e);
         __syncthreads();
         ix_compute<TY, SPEC>(reinterpret_cast<const int2*>(s), g.out, g.nx, g.ny, g.periodic, x0, y0, g.itaps,
                              w, tile_e);
@@ -1222,7 +1222,7 @@ __global__ void __launch_bounds__(kThreads)
   constexpr int TY = G::TY, TX = G::TX, COLS = G::COLS, ROWS = G::ROWS, SE = G::SE;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar[kStages];
-  __shared__ int s_wmax[kThreads / 32];
+  __shared__ __align__(16) int s_wmax[kThreads / 32];
   const int tid = threadIdx.x;
   if (blockIdx.x >= tiles) return;
   const int my_tiles = (tiles - 1 - static_cast<int>(blockIdx.x)) / static_cast<int>(gridDim.x) + 1;
@@ -1268,13 +1268,13 @@ __global__ void __launch_bounds__(kThreads)
       spec_compute<T, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
     } else if constexpr (MODE == 1) {
       static_assert(COLS % 2 == 0, "digit passes take values in pairs");
-      const uint32_t mhi = ixd::ix_tile_max_hi<kThreads>(s, SE, reinterpret_cast<unsigned*>(s_wmax));
+      const uint32_t mhi = ixd::ix_tile_max_hi<kThreads, SE>(reinterpret_cast<const double*>(s), reinterpret_cast<unsigned*>(s_wmax));
       const int tile_e = static_cast<int>(mhi >> 20);
       uint32_t w[4];
       if (!ixi_consts(itaps.c, itaps.c15, tile_e, w) || (sd.epi && !ixf_tile_ok(tile_e, itaps.c))) {
         spec_compute<double, TY, SPEC>(s, out, nx, ny, periodic, x0, y0, taps);
       } else {
-        ixd::ixi_split_tile<kThreads>(s, SE, tile_e);
+        ixd::ixi_split_tile<kThreads, SE>(s, tile_e);
         __syncthreads();
         ix_compute<TY, SPEC>(reinterpret_cast<const int2*>(s), out, nx, ny, periodic, x0, y0, itaps, w, tile_e);
       }

@@ -388,12 +388,34 @@ __device__ __forceinline__ float2 upwind2(const float2 (&d)[6], bool posx, bool 
   return make_float2(weno5(v1.x, v2.x, v3.x, v4.x, v5.x, 0.0f), weno5(v1.y, v2.y, v3.y, v4.y, v5.y, 0.0f));
 }
 
+// Dynamic shared memory of k_weno_adv_f32x2: the C tile with its halo, then the u and v tiles.
+constexpr size_t kW2Smem = sizeof(float) * (static_cast<size_t>(kWTileRows) * kW2Cols + 2 * kWTY * kW2TX);
+
 __global__ void __launch_bounds__(kWThreads)
     k_weno_adv_f32x2(const float* __restrict__ c, const float* __restrict__ u, const float* __restrict__ v,
-                     float* __restrict__ out, int64_t nx, int64_t ny, int vec_ok, float inv_hx, float inv_hy) {
-  __shared__ __align__(16) float s[kWTileRows * kW2Cols];
+                     float* __restrict__ out, int64_t nx, int64_t ny, int vec_ok, int uv_ok, float inv_hx,
+                     float inv_hy) {
+  extern __shared__ __align__(16) float w2_smem[];
+  float* s = w2_smem;                        // C, rows y0 - 3 .. y0 + 34, columns x0 - 4 .. x0 + 131
+  float* su = s + kWTileRows * kW2Cols;      // u, rows y0 .. y0 + 31, columns x0 .. x0 + 127
+  float* sv = su + kWTY * kW2TX;             // v, likewise
   const int64_t x0 = static_cast<int64_t>(blockIdx.x) * kW2TX;
   const int64_t y0 = static_cast<int64_t>(blockIdx.y) * kWTY;
+  // u and v of a whole tile are staged with asynchronous 16-byte copies issued before the C tile's,
+  // so no row waits on a global load of its own; load_tile's wait covers all of them.  Edge tiles
+  // (and unaligned u, v) read u and v per row from global memory.
+  const bool staged = uv_ok && x0 + kW2TX <= nx && y0 + kWTY <= ny;
+  if (staged) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    static_assert(kW2TX == 4 * 32, "one 16-byte chunk per lane and row");
+#pragma unroll
+    for (int r = warp; r < kWTY; r += kWThreads / 32) {
+      const int64_t g = (y0 + r) * nx + x0 + 4 * lane;
+      const unsigned o = static_cast<unsigned>(r * kW2TX + 4 * lane) * static_cast<unsigned>(sizeof(float));
+      s2d::cp_async16_s(static_cast<unsigned>(__cvta_generic_to_shared(su)) + o, u + g);
+      s2d::cp_async16_s(static_cast<unsigned>(__cvta_generic_to_shared(sv)) + o, v + g);
+    }
+  }
   s2d::load_tile<float>(s, c, nx, ny, true, vec_ok != 0, x0, y0, kWHalo, kWLA, kW2Cols, kWTileRows);
   const int cx = 2 * (threadIdx.x % (kW2TX / 2));
   const int r0 = (threadIdx.x / (kW2TX / 2)) * kW2Rows;
@@ -427,7 +449,10 @@ __global__ void __launch_bounds__(kWThreads)
     }
     const int64_t o = gy * nx + gx;
     float2 uu, vv;
-    if (pair_store) {
+    if (staged) {
+      uu = *reinterpret_cast<const float2*>(su + (r0 + r) * kW2TX + cx);
+      vv = *reinterpret_cast<const float2*>(sv + (r0 + r) * kW2TX + cx);
+    } else if (pair_store) {
       uu = *reinterpret_cast<const float2*>(u + o);
       vv = *reinterpret_cast<const float2*>(v + o);
     } else {
@@ -464,10 +489,19 @@ int weno_launch(const WenoConfig* cfg, const void* c, const void* u, const void*
   const dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy));
   const double fx = 1e-99 * cfg->hx * cfg->hx, fy = 1e-99 * cfg->hy * cfg->hy;
   if (cfg->dtype == CS_F32) {
-    k_weno_adv_f32x2<<<grid, kWThreads, 0, st>>>(static_cast<const float*>(c), static_cast<const float*>(u),
-                                                 static_cast<const float*>(v), static_cast<float*>(out), cfg->nx,
-                                                 cfg->ny, vec_ok, static_cast<float>(1.0 / cfg->hx),
-                                                 static_cast<float>(1.0 / cfg->hy));
+    static bool attr_set = false;
+    if (!attr_set) {
+      CS_CUDA_TRY(cudaFuncSetAttribute(k_weno_adv_f32x2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kW2Smem)));
+      attr_set = true;
+    }
+    const int uv_ok = reinterpret_cast<uintptr_t>(u) % 16 == 0 && reinterpret_cast<uintptr_t>(v) % 16 == 0 &&
+                      (cfg->nx * eb) % 16 == 0;
+    k_weno_adv_f32x2<<<grid, kWThreads, kW2Smem, st>>>(static_cast<const float*>(c), static_cast<const float*>(u),
+                                                       static_cast<const float*>(v), static_cast<float*>(out),
+                                                       cfg->nx, cfg->ny, vec_ok, uv_ok,
+                                                       static_cast<float>(1.0 / cfg->hx),
+                                                       static_cast<float>(1.0 / cfg->hy));
   } else {
     k_weno_adv<double><<<grid, kWThreads, 0, st>>>(static_cast<const double*>(c), static_cast<const double*>(u),
                                                    static_cast<const double*>(v), static_cast<double*>(out), cfg->nx,
