@@ -52,25 +52,28 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s; probe: 1.9 DFMA/clk)
+# FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # FP64 instructions (DFMA, DADD, DMUL each one): 152 SMs x 2 per clock x 2.07 GHz
 FP64_PEAK_GOPS = 152 * 2 * 2.07
-# FP32/INT lanes: 152 SMs x 128 lanes x 2.07 GHz, one operation per lane per clock
+# Instruction issue in lane operations: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz (also the
+# FP32 FMA lane rate)
 FP32_LANE_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 
 
 def dd_ops_per_point(taps: int, name: str) -> int:
-    """FP32/INT lane operations per output point of the FP64-storage formulations.  Exact digit
-    path (weights c * small integers: the 9-point, 13-point and first-derivative stencils): 3
-    FFMA per tap, 24 to cut the one new input value per point into three digits, 20 to
-    recombine the digit sums into an int64 and round it to FP64.  Double-float path (the cubic
-    user function): 12 per tap (product, its FMA error, two cross terms, TwoSum, error
-    accumulation), 20 for u^3 - u, 12 to split the new value into a float pair, 8 to widen the
-    result.  The single FP64 multiply or add per point runs on the FP64 pipe."""
+    """Integer / FP32 lane operations per output point of the FP64-storage formulation (exact
+    integer digits; weights c * small integers): two integer multiply-adds per tap for the two
+    digit sums, 13 to cut one input value into its two digits (exponent, significand, one
+    shift, the sign as a two's complement, the two digits), 9 to round and assemble the 64-bit
+    integer the one FP64 FMA scales.  The cubic user function adds 20: its u^3 - u in
+    double-float on packed FP32x2 instructions (32 per pair of outputs), two exact int -> float
+    conversions and two integer adds to join Q.  Loads, address arithmetic and control are not
+    counted (the executed count is in the ncu summary)."""
+    ops = 2 * taps + 13 + 9
     if name == "cubic_minus_lap":
-        return 12 * taps + 20 + 12 + 8
-    return 3 * taps + 24 + 20
+        ops += 20
+    return ops
 
 
 def stencil_suite(h):
@@ -318,14 +321,14 @@ def run_ours(args):
             "bytes_per_launch": dom["bytes"], "launch_ms": round(dom_ms, 4),
             "traffic": traffic_for(dom_key)}
     if dom["eb"] == 8:
-        # FP64 storage is evaluated on the FP32 / integer pipes (exact digits or double-float):
-        # the formulation's own lane-operation count, against the derived FP32/INT lane peak
+        # FP64 storage is evaluated on the integer / FP32 pipes (exact digits): the formulation's
+        # own lane-operation count, against the instruction-issue peak in lane operations
         ops = dd_ops_per_point(dom["taps"], dom["name"]) * dom["points"]
         lane = ops / (dom_ms * 1e-3) / 1e12
         roof["formulation"] = {"ops_per_point": dd_ops_per_point(dom["taps"], dom["name"]),
                                "achieved_tops": round(lane, 3), "peak_tops": round(FP32_LANE_PEAK_TOPS, 3),
                                "frac": round(lane / FP32_LANE_PEAK_TOPS, 4),
-                               "peak_kind": "derived: 152 SM x 128 lanes x 2.07 GHz"}
+                               "peak_kind": "derived: instruction issue, 152 SM x 4 schedulers x 32 lanes x 2.07 GHz"}
 
     # every sweep against the HBM roofline
     f32 = {}

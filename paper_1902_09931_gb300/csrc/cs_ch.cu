@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kThreads)
                                   : static_cast<int64_t>(wrapn(gy, n)) * n + wrapn(gx, n);
     const double cv = widen(cur[off]);
     sc[idx] = cv;
-    sb[idx] = 2.0 * cv - widen(prev[off]);
+    sb[idx] = fma(2.0, cv, -widen(prev[off]));  // one FP64 instruction (2 cv - p as two adds is two)
   }
   __syncthreads();
   if (rhs) {
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kThreads)
     // one FP64 FMA; the first one's scaling carries -a, so the FP64 pipe keeps only Cbar, u u,
     // N, Z, the two scalings, C^n - C^{n-1} and the final combination (8.6 FP64 operations per
     // point).  A tile whose values leave the digit range takes the FP64 formula for that Laplacian.
-    __shared__ unsigned s_red[kThreads / 32];
+    __shared__ __align__(16) unsigned s_red[kThreads / 32];
     auto lap5 = [&](const double* t, int i, int pitch) {
       return (t[i - pitch] + t[i + pitch]) + (t[i - 1] + t[i + 1]) - 4.0 * t[i];
     };
@@ -195,11 +195,11 @@ __global__ void __launch_bounds__(kThreads)
     double* zt = sz;
     const double* cn = sc;
     {
-      const int te = static_cast<int>(ixd::ix_tile_max_hi<kThreads>(cb, HR * HC, s_red) >> 20);
+      const int te = static_cast<int>(ixd::ix_tile_max_hi<kThreads, HR * HC>(cb, s_red) >> 20);
       uint32_t w[4];
       const bool dig = ixd::ixi_consts<28>(am51, -1.5 * am51, te, w);  // uniform over the block
       if (dig) {
-        ixd::ixi_split_tile<kThreads, 28>(cb, HR * HC, te);
+        ixd::ixi_split_tile<kThreads, HR * HC, 28>(cb, te);
         __syncthreads();
       }
       for (int idx = threadIdx.x; idx < ZR * ZC; idx += kThreads) {
@@ -219,11 +219,11 @@ __global__ void __launch_bounds__(kThreads)
       __syncthreads();
     }
     {
-      const int te = static_cast<int>(ixd::ix_tile_max_hi<kThreads>(zt, ZR * ZC, s_red) >> 20);
+      const int te = static_cast<int>(ixd::ix_tile_max_hi<kThreads, ZR * ZC>(zt, s_red) >> 20);
       uint32_t w[4];
       const bool dig = ixd::ixi_consts<28>(1.0, -1.5, te, w);
       if (dig) {
-        ixd::ixi_split_tile<kThreads, 28>(zt, ZR * ZC, te);
+        ixd::ixi_split_tile<kThreads, ZR * ZC, 28>(zt, te);
         __syncthreads();
       }
       for (int idx = threadIdx.x; idx < kTY * kTX; idx += kThreads) {

@@ -347,7 +347,13 @@ constexpr int kW2Rows = kWTY / kW2Groups;
 __device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
 
 // weno_scaled<float> on two lanes (w* already scaled by each lane's own 2^(127 - e))
-__device__ __forceinline__ float2 weno_scaled2(float2 w1, float2 w2, float2 w3, float2 w4, float2 w5, float2 mw) {
+// The WENO value of two lanes from their differences w1..w5 (unscaled) and max |w| (mw, with
+// 2^-40 <= mw < 2^41), eps = 1e-6 mw^2.  Only the indicator sums t_k = s_k + eps are scaled, by
+// sc2 = 2^(2 (127 - e)) (e the biased exponent of mw), so that the fourth powers in the weights
+// stay in range; phi and the result need no scaling.  Powers of two commute with the roundings,
+// so this gives the bits of scaling the differences themselves by 2^(127 - e).
+__device__ __forceinline__ float2 weno_scaled2(float2 w1, float2 w2, float2 w3, float2 w4, float2 w5, float2 mw,
+                                               float2 sc2) {
   const float2 phi1 = __ffma2_rn(f2s(1.0f / 3.0f), w1, __ffma2_rn(f2s(-7.0f / 6.0f), w2, __fmul2_rn(f2s(11.0f / 6.0f), w3)));
   const float2 phi2 = __ffma2_rn(f2s(-1.0f / 6.0f), w2, __ffma2_rn(f2s(5.0f / 6.0f), w3, __fmul2_rn(f2s(1.0f / 3.0f), w4)));
   const float2 phi3 = __ffma2_rn(f2s(1.0f / 3.0f), w3, __ffma2_rn(f2s(5.0f / 6.0f), w4, __fmul2_rn(f2s(-1.0f / 6.0f), w5)));
@@ -358,13 +364,20 @@ __device__ __forceinline__ float2 weno_scaled2(float2 w1, float2 w2, float2 w3, 
   const float2 s2 = __ffma2_rn(__fmul2_rn(f2s(13.0f / 12.0f), a2), a2, __fmul2_rn(__fmul2_rn(f2s(0.25f), b2), b2));
   const float2 s3 = __ffma2_rn(__fmul2_rn(f2s(13.0f / 12.0f), a3), a3, __fmul2_rn(__fmul2_rn(f2s(0.25f), b3), b3));
   const float2 eps = __fmul2_rn(f2s(1e-6f), __fmul2_rn(mw, mw));
-  const float2 t1 = __fadd2_rn(s1, eps), t2 = __fadd2_rn(s2, eps), t3 = __fadd2_rn(s3, eps);
+  const float2 t1 = __fmul2_rn(__fadd2_rn(s1, eps), sc2), t2 = __fmul2_rn(__fadd2_rn(s2, eps), sc2);
+  const float2 t3 = __fmul2_rn(__fadd2_rn(s3, eps), sc2);
   const float2 q1 = __fmul2_rn(t1, t1), q2 = __fmul2_rn(t2, t2), q3 = __fmul2_rn(t3, t3);
   const float2 p1 = __fmul2_rn(f2s(0.1f), __fmul2_rn(q2, q3)), p2 = __fmul2_rn(f2s(0.6f), __fmul2_rn(q1, q3));
   const float2 p3 = __fmul2_rn(f2s(0.3f), __fmul2_rn(q1, q2));
   const float2 num = __ffma2_rn(p1, phi1, __ffma2_rn(p2, phi2, __fmul2_rn(p3, phi3)));
   const float2 den = __fadd2_rn(__fadd2_rn(p1, p2), p3);
   return make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
+}
+
+// Lanes whose max |w| is zero, denormal or outside [2^-40, 2^41): the scalar form, out of line so
+// the unrolled rows of the kernel stay small.
+__device__ __noinline__ float2 weno5_pair_slow(float2 v1, float2 v2, float2 v3, float2 v4, float2 v5) {
+  return make_float2(weno5(v1.x, v2.x, v3.x, v4.x, v5.x, 0.0f), weno5(v1.y, v2.y, v3.y, v4.y, v5.y, 0.0f));
 }
 
 // upwinded WENO derivative (unscaled: the caller divides by h) of two lanes; d[k] the differences
@@ -377,15 +390,12 @@ __device__ __forceinline__ float2 upwind2(const float2 (&d)[6], bool posx, bool 
   };
   const float mx = lane_max(v1.x, v2.x, v3.x, v4.x, v5.x), my = lane_max(v1.y, v2.y, v3.y, v4.y, v5.y);
   const int ex = static_cast<int>(__float_as_uint(mx) >> 23), ey = static_cast<int>(__float_as_uint(my) >> 23);
-  if (ex >= 1 && ex <= 253 && ey >= 1 && ey <= 253) {
-    const float2 sc = make_float2(__uint_as_float(static_cast<unsigned>(254 - ex) << 23),
-                                  __uint_as_float(static_cast<unsigned>(254 - ey) << 23));
-    const float2 r = weno_scaled2(__fmul2_rn(v1, sc), __fmul2_rn(v2, sc), __fmul2_rn(v3, sc), __fmul2_rn(v4, sc),
-                                  __fmul2_rn(v5, sc), __fmul2_rn(make_float2(mx, my), sc));
-    return __fmul2_rn(r, make_float2(__uint_as_float(static_cast<unsigned>(ex) << 23),
-                                     __uint_as_float(static_cast<unsigned>(ey) << 23)));
+  if (ex >= 127 - 40 && ex <= 127 + 40 && ey >= 127 - 40 && ey <= 127 + 40) {
+    const float2 sc2 = make_float2(__uint_as_float(static_cast<unsigned>(381 - 2 * ex) << 23),
+                                   __uint_as_float(static_cast<unsigned>(381 - 2 * ey) << 23));
+    return weno_scaled2(v1, v2, v3, v4, v5, make_float2(mx, my), sc2);
   }
-  return make_float2(weno5(v1.x, v2.x, v3.x, v4.x, v5.x, 0.0f), weno5(v1.y, v2.y, v3.y, v4.y, v5.y, 0.0f));
+  return weno5_pair_slow(v1, v2, v3, v4, v5);
 }
 
 // Dynamic shared memory of k_weno_adv_f32x2: the C tile with its halo, then the u and v tiles.
