@@ -217,7 +217,10 @@ int cs_plan_set_fp64_mode(cs_plan_t plan, int32_t mode);
  *   1  tiles of 64 rows staged with cp.async, one tile per CTA
  *   2  TMA-pipelined persistent sweep: tiles of 64 rows, each CTA walks its tiles through a
  *      two-stage shared-memory ring filled by tensor-memory-access copies (default; used when
- *      nx is a multiple of 16 bytes / element size and d_in is 16-byte aligned, else 1). */
+ *      nx is a multiple of 16 bytes / element size and d_in is 16-byte aligned, else 1).
+ * Choices 1 and 2 give the same results bit for bit (the same tiles).  Choice 0 does too for
+ * FP32 storage; on the FP64 integer-digit path its digit grid is set by 32-row tiles, so results
+ * can differ from choices 1 and 2 within that path's error bound.  CS_EINVAL for another value. */
 int cs_plan_set_tile_choice(cs_plan_t plan, int32_t choice);
 int cs_plan_get_tile_choice(cs_plan_t plan, int32_t* choice);
 
@@ -388,7 +391,7 @@ int cs_ch_solver_check(int64_t n, int32_t chunks, double a, int32_t boundary, do
  *   library holds it (4 MiB + 256 B) until the process exits.  total_len is limited to
  *   2^26 = 67,108,864 elements; larger requests return CS_EINVAL (use a plan instead).
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *   that device current; make that first call before any stream capture.
+ *   that device current.
  *   Every call shares the array and overwrites it: calls that overlap on the GPU (different
  *   streams, or host threads) race and must be serialised by the caller.
  *   The offsets are validated on the device first: every call synchronises the stream once,
