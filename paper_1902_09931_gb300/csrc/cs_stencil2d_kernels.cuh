@@ -637,9 +637,18 @@ __device__ __forceinline__ void ix_compute(const int2* sd2, double* __restrict__
   }
 }
 
-// At least 3 resident CTAs: a register budget of 85 per thread.
+// Resident CTAs of the digit kernel: at least 6 (40 registers per thread, 48 warps per SM; the
+// tile's shared memory allows 6) for footprints of at most 13 taps over at most 5 rows, whose
+// rolling digit sums fit that budget; at least 3 (85 registers) for the larger footprints.  More
+// resident CTAs let one CTA's load and reduction phases overlap the others' digit sums.
+constexpr int ix_min_blocks(int spec) {
+  int taps = 0;
+  for (unsigned m = kSpecs[spec].mask; m != 0u; m &= m - 1u) ++taps;
+  return kSpecs[spec].T + kSpecs[spec].B + 1 <= 5 && taps <= 13 ? 6 : 3;
+}
+
 template <int TY, int SPEC>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, ix_min_blocks(SPEC))
     k_stencil2d_ix(const double* __restrict__ in, double* __restrict__ out, int64_t nx, int64_t ny,
                    int periodic, int vec_ok, Taps<double> taps, IxTaps itaps, int ty0) {
   constexpr SpecDesc sd = kSpecs[SPEC];
