@@ -154,8 +154,7 @@ __global__ void __launch_bounds__(kThreads)
   constexpr int ZR = kTY + 2, ZC = kTX + 2;  // halo-1 tile
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* sc = reinterpret_cast<double*>(smem_raw);  // C^n
-  double* sb = sc + HR * HC;                         // Cbar
-  double* sz = sb + HR * HC;                         // Z
+  double* sb = sc + HR * HC;                         // Cbar, then Z (halo-1 tile) once Cbar is used up
   const int64_t x0 = static_cast<int64_t>(blockIdx.x) * kTX;
   const int64_t y0 = static_cast<int64_t>(blockIdx.y) * kTY;
   // band != 0: cur and prev are row bands padded with the 2 rows above and the 2 rows below (the
@@ -192,7 +191,7 @@ __global__ void __launch_bounds__(kThreads)
     };
     // the one-FMA scaling of a digit sum by m 2^(G - 56) (ixi_consts); false: the FP64 formula
     double* cb = sb;
-    double* zt = sz;
+    double* zt = sb;  // Z takes Cbar's place (held in registers until every thread has read Cbar)
     const double* cn = sc;
     {
       const int te = static_cast<int>(ixd::ix_tile_max_hi<kThreads, HR * HC>(cb, s_red) >> 20);
@@ -202,19 +201,31 @@ __global__ void __launch_bounds__(kThreads)
         ixd::ixi_split_tile<kThreads, HR * HC, 28>(cb, te);
         __syncthreads();
       }
-      for (int idx = threadIdx.x; idx < ZR * ZC; idx += kThreads) {
-        const int r = idx / ZC, c = idx - r * ZC;
-        const int hidx = (r + 1) * HC + (c + 1);
-        double lap_a;  // -a * Laplacian(Cbar)
-        if (dig) {
-          int q0, q1;
-          lap5_digits(cb, hidx, HC, q0, q1);
-          lap_a = ixd::ixi_combine<28>(q0, q1, w);
-        } else {
-          lap_a = -a * lap5(cb, hidx, HC);
+      constexpr int NZ = (ZR * ZC + kThreads - 1) / kThreads;
+      double zv[NZ];
+#pragma unroll
+      for (int k = 0; k < NZ; ++k) {
+        const int idx = threadIdx.x + k * kThreads;
+        if (k + 1 < NZ || idx < ZR * ZC) {
+          const int r = idx / ZC, c = idx - r * ZC;
+          const int hidx = (r + 1) * HC + (c + 1);
+          double lap_a;  // -a * Laplacian(Cbar)
+          if (dig) {
+            int q0, q1;
+            lap5_digits(cb, hidx, HC, q0, q1);
+            lap_a = ixd::ixi_combine<28>(q0, q1, w);
+          } else {
+            lap_a = -a * lap5(cb, hidx, HC);
+          }
+          const double u = cn[hidx];
+          zv[k] = fma(alpha, fma(u * u, u, -u), lap_a);
         }
-        const double u = cn[hidx];
-        zt[idx] = fma(alpha, fma(u * u, u, -u), lap_a);
+      }
+      __syncthreads();  // every thread is done with Cbar
+#pragma unroll
+      for (int k = 0; k < NZ; ++k) {
+        const int idx = threadIdx.x + k * kThreads;
+        if (k + 1 < NZ || idx < ZR * ZC) zt[idx] = zv[k];
       }
       __syncthreads();
     }
@@ -714,7 +725,7 @@ int default_chunks(int64_t n) {
 
 // FP64 tiles (C^n, Cbar: halo 2; Z: halo 1), for either storage type.
 size_t rhs_smem_bytes() {
-  return 8 * (2 * (kTY + 4) * (kTX + 4) + (kTY + 2) * (kTX + 2));
+  return 8 * (2 * (kTY + 4) * (kTX + 4));  // C^n and Cbar (Z reuses Cbar's space)
 }
 
 template <typename T> int set_rhs_attr() {
