@@ -201,8 +201,9 @@ int cs_swap(cs_plan_t plan);
  *     exact digit evaluation -- each value cut into two 24-bit integer digits on a grid
  *     set by the largest value of its tile (tile = 64 x TY outputs plus halo; bits below 2^-48
  *     of the grid's top dropped), digit sums exact in int32, their combination rounded to 2^-44
- *     of the grid's top and scaled with one FP64 FMA; error at most (2^-47 + 2^-44 / sum|n_k|)
- *     of sum|w| * (largest |value| in the tile and its halo);
+ *     of the grid's top and scaled with one FP64 FMA (c rounded to 51 bits, so that its
+ *     constants are exact); error at most (2^-47 + 2^-44 / sum|n_k| + 2^-50) of
+ *     sum|w| * (largest |value| in the tile and its halo);
  *   - other weights: double-float arithmetic (values as unevaluated float pairs, error-free
  *     products and sums on the FP32 pipes); error below ~2^-46 of sum|w| * max|in|;
  *   tiles holding inf / nan or values outside the methods' exponent ranges, and weights

@@ -5,9 +5,10 @@
 // of x (|x| is truncated on the grid), d0 signed and 0 <= d1 < 2^24, so each digit sum
 // S_i = sum_k n_k d_{k,i} is exact in int32.
 // T = S0 2^24 + S1 is then rounded to a multiple of 2^4 (ties to even) and scaled by c * 2^(G-48)
-// with one FP64 FMA: the result is within (2^-47 + 2^-44 / sum|n|) of sum|w| * (largest value of
-// the tile).  With sum |n_k| <= 8, 28-bit digits keep 56 bits and round to 2^(G-49).  The per-tile constants come from c's bits by integer exponent arithmetic, and
-// nothing converts between integers and floating point (on GB300 those conversions share the FP64
+// with one FP64 FMA: the result is within (2^-47 + 2^-44 / sum|n| + 2^-50) of sum|w| * (largest
+// value of the tile), the last term for c's rounding to 51 bits and the FMA's own rounding.  With
+// sum |n_k| <= 8, 28-bit digits keep 56 bits and round to 2^(G-49).  The per-tile constants come
+// from c's bits by integer exponent arithmetic, and nothing converts between integers and floating point (on GB300 those conversions share the FP64
 // pipe).  Used by the 2D stencil sweep and by the Laplacians of the Cahn-Hilliard right-hand side.
 #pragma once
 
@@ -65,8 +66,9 @@ template <int DB> struct Digits;
 template <> struct Digits<24> { static constexpr int kFrac = 48, kRound = 4, kMaxSum = 64; };
 template <> struct Digits<28> { static constexpr int kFrac = 56, kRound = 8, kMaxSum = 8; };
 
-// The common weight scale c as the combination uses it: rounded to 51 significant bits (a relative
-// change below 2^-52, the size of the weights' own FP64 rounding), so that 1.5 c is exact too.
+// The common weight scale c as the combination uses it: rounded to 51 significant bits (at most two
+// units in c's last place, 2^-51 relative; the weights' own FP64 rounding is 2^-53), so that
+// 1.5 c is exact too.
 __host__ __device__ inline double ixi_round51(double c) {
   unsigned long long b;
   memcpy(&b, &c, sizeof b);

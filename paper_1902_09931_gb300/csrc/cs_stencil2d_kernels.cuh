@@ -438,7 +438,7 @@ __device__ __forceinline__ void dd_add_cubic_minus2(float2& sh, float2& sl, floa
 // x = (d0 2^24 + d1) 2^(G-48) + r with |r| < 2^(G-48), so each digit sum S_i = sum_k n_k d_{k,i}
 // is exact in int32 (per tap two integer multiply-adds).  The sums form T = S0 2^24 + S1, which is
 // rounded to a multiple of 2^4 and scaled by c * 2^(G-48) with one FP64 FMA (ixi_combine).  The
-// error is at most (2^-47 + 2^-44 / sum|n|) of sum|w| * max|in| (native FP64 accumulation: about
+// error is at most (2^-47 + 2^-44 / sum|n| + 2^-50) of sum|w| * max|in| (native FP64 accumulation: about
 // taps * 2^-53 of sum|w| |in|).  Tiles holding inf / nan, or whose largest value is outside
 // [2^-900, 2^900], are evaluated in native FP64.
 
