@@ -333,12 +333,13 @@ int cs_ch_set_fields(cs_plan_t plan, void* d_c_prev, void* d_c_cur, void* d_c_ne
  * *chunks pieces of *chunk_len points (see cs_ch_create); either output may be NULL. */
 int cs_ch_config(cs_plan_t plan, int32_t* chunks, int32_t* chunk_len);
 
-/* ---- a periodic Cahn-Hilliard grid decomposed into row bands (one process per GPU) ----------
+/* ---- a Cahn-Hilliard grid decomposed into row bands (one process per GPU) -------------------
  * The paper's route to several GPUs (Sec. 6.2) splits the grid into bands of rows with halo
  * exchanges between neighbours.  For the ADI step (Sec. 5.1) a rank holding rows [r0, r0 + rows)
- * of the n x n periodic field runs, per step:
+ * of the n x n field runs, per step:
  *   1. exchange 2 halo rows of C^n and C^{n-1} with its neighbours (periodic: the last band's
- *      neighbour below is the first band);
+ *      neighbour below is the first band; no-flux: the first band's rows above and the last
+ *      band's rows below are its own rows mirrored, ghost row -1 = row 0, -2 = row 1);
  *   2. cs_ch_band_rhs: the right-hand side of its rows (and, optionally, its mass and energy sums);
  *   3. cs_ch_band_solve: the x line solves, one per row;
  *   4. a transpose among the ranks (all-to-all), so each rank holds a band of columns as rows;
@@ -349,16 +350,18 @@ int cs_ch_config(cs_plan_t plan, int32_t* chunks, int32_t* chunk_len);
  * with torch.distributed); the arithmetic is the full-grid step's own kernels, so the decomposed
  * step gives the values cs_ch_step gives.
  *
- * cs_ch_band_create: desc as for cs_ch_create (boundary must be CS_CH_PERIODIC: CS_EUNSUPPORTED
- *   otherwise); rows = the band's row count, a multiple of 32 in [32, n].  The plan owns the line
- *   solver's tables and an FP64 scratch of rows x n, plus 4 * chunks * rows values.
+ * cs_ch_band_create: desc as for cs_ch_create (boundary CS_CH_PERIODIC or CS_CH_NOFLUX; the
+ *   partition is the one cs_ch_create picks for the same description); rows = the band's row
+ *   count, a multiple of 32 in [32, n].  The plan owns the line solver's tables and an FP64
+ *   scratch of rows x n, plus 4 * chunks * rows values.
  * Padded fields: (rows + 4) x n values of the storage type, row-major; rows 0-1 hold the two rows
  *   above the band, rows 2 .. rows+1 the band, rows rows+2 .. rows+3 the two rows below.
  * cs_ch_band_rhs(d_prev, d_cur): padded C^{n-1}, C^n (halos filled) -> d_rhs (rows x n FP64; may be
  *   NULL when only sums are wanted); d_sums (device, 2 FP64, nullable): h^2 sum C and h^2 sum of
  *   the free-energy density over the band's rows (Eq. 1, forward differences), for an allreduce.
  * cs_ch_band_solve(d_in, d_out): (I + a D4) x = b along each of the rows rows of n values (FP64,
- *   row-major, periodic lines); d_out may equal d_in.
+ *   row-major; periodic lines, or with no-flux the reflected fourth difference); d_out may equal
+ *   d_in.
  * cs_ch_band_update(d_prev, d_cur, d_v, d_next): the band rows of the padded d_next get
  *   2 C^n - C^{n-1} + v (v: rows x n FP64), rounded to the storage type; its halo rows are not
  *   written.  The three padded fields must not overlap.

@@ -158,11 +158,12 @@ __global__ void __launch_bounds__(kThreads)
   const int64_t x0 = static_cast<int64_t>(blockIdx.x) * kTX;
   const int64_t y0 = static_cast<int64_t>(blockIdx.y) * kTY;
   // band != 0: cur and prev are row bands padded with the 2 rows above and the 2 rows below (the
-  // neighbours' rows, exchanged by the caller); output row r of the band is padded row r + 2
+  // neighbours' rows, exchanged by the caller, or at a no-flux edge of the grid the band's own rows
+  // mirrored); output row r of the band is padded row r + 2
   for (int idx = threadIdx.x; idx < HR * HC; idx += kThreads) {
     const int r = idx / HC, c = idx - r * HC;
     const int64_t gy = y0 - 2 + r, gx = x0 - 2 + c;
-    const int64_t off = band      ? (gy + 2) * n + wrapn(gx, n)
+    const int64_t off = band      ? (gy + 2) * n + (noflux ? mirrorn(gx, n) : wrapn(gx, n))
                         : noflux  ? static_cast<int64_t>(mirrorn(gy, n)) * n + mirrorn(gx, n)
                                   : static_cast<int64_t>(wrapn(gy, n)) * n + wrapn(gx, n);
     const double cv = widen(cur[off]);
@@ -1308,8 +1309,9 @@ int ch_config(CHPlan* p, int32_t* chunks, int32_t* chunk_len) {
 
 void ch_destroy(CHPlan* p) { free_plan(p); }
 
-// ---- a row band of a periodic grid decomposed over several GPUs -----------------------------------
-// The pieces of the ADI step that a caller runs on its own band of rows (Sec. 6.2's decomposition):
+// ---- a row band of a grid decomposed over several GPUs ----------------------------------------------
+// The pieces of the ADI step that a caller runs on its own band of rows (Sec. 6.2's decomposition),
+// periodic or with no-flux boundaries:
 // the right-hand side and invariant sums of the band from padded C^n, C^{n-1} (2 halo rows each
 // side, exchanged by the caller), line solves along the rows of a buffer (the x lines of the band,
 // or after a transpose the y lines of a band of columns), and the update C^{n+1} = Cbar + v on the
@@ -1317,6 +1319,7 @@ void ch_destroy(CHPlan* p) { free_plan(p); }
 struct CHBand {
   int64_t n, rows;
   int storage;
+  int noflux;  // CS_CH_NOFLUX: mirrored columns, non-cyclic line solves
   double D, gamma, dt, h, a, alpha;
   int P, m;
   double* coef;
@@ -1353,7 +1356,8 @@ void free_band(CHBand* b) {
 int ch_band_create(CHBand** out, const cs_ch_desc* d, int64_t rows) {
   *out = nullptr;
   if (!d) return set_error(CS_EINVAL, "null Cahn-Hilliard description");
-  if (d->boundary != CS_CH_PERIODIC) return set_error(CS_EUNSUPPORTED, "row bands are for the periodic domain");
+  if (d->boundary != CS_CH_PERIODIC && d->boundary != CS_CH_NOFLUX)
+    return set_error(CS_EINVAL, "boundary must be CS_CH_PERIODIC or CS_CH_NOFLUX");
   if (d->n < 64 || d->n % 64 != 0 || d->n > 65536) return set_error(CS_EINVAL, "n must be a multiple of 64 in [64, 65536]");
   if (rows < kTY || rows % kTY != 0 || rows > d->n) return set_error(CS_EINVAL, "band rows must be a multiple of %d in [%d, n]", kTY, kTY);
   if (d->storage != CS_F64 && d->storage != CS_F32) return set_error(CS_EINVAL, "storage must be CS_F64 or CS_F32");
@@ -1363,6 +1367,7 @@ int ch_band_create(CHBand** out, const cs_ch_desc* d, int64_t rows) {
   if (!b) return set_error(CS_ENOMEM, "out of host memory");
   memset(b, 0, sizeof *b);
   b->n = d->n; b->rows = rows; b->storage = d->storage;
+  b->noflux = d->boundary == CS_CH_NOFLUX;
   b->D = d->D; b->gamma = d->gamma; b->dt = d->dt;
   b->h = 2.0 * M_PI / static_cast<double>(d->n);
   const double h2 = b->h * b->h;
@@ -1370,13 +1375,14 @@ int ch_band_create(CHBand** out, const cs_ch_desc* d, int64_t rows) {
   b->alpha = (2.0 / 3.0) * d->D * d->dt / h2;
   int P = default_chunks(d->n), choice;
   char key[96];
-  snprintf(key, sizeof key, "ch|%s|n%lld|sm%d", d->storage == CS_F32 ? "f32" : "f64", (long long)d->n, num_sms());
+  snprintf(key, sizeof key, "ch|%s%s|n%lld|sm%d", d->storage == CS_F32 ? "f32" : "f64",
+           b->noflux ? "|noflux" : "", (long long)d->n, num_sms());  // the full-grid plan's partition
   if (tune_lookup(key, &choice) && valid_chunks(d->n, choice)) P = choice;
   b->P = P;
   b->m = static_cast<int>(d->n / P);
   b->rhs_blocks = static_cast<int>((d->n / kTX) * (rows / kTY));
   std::vector<double> coef, K;
-  int rc = build_tables(d->n, P, b->a, false, coef, K);
+  int rc = build_tables(d->n, P, b->a, b->noflux != 0, coef, K);
   if (rc != CS_OK) { free_band(b); return rc; }
   cudaError_t e = cudaMalloc(&b->coef, coef.size() * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&b->K, K.size() * sizeof(double));
@@ -1403,11 +1409,11 @@ int ch_band_rhs(CHBand* b, const void* prev, const void* cur, double* rhs, doubl
   double* part = sums ? b->partials : nullptr;
   if (b->storage == CS_F32)
     k_ch_rhs<float><<<grid, kThreads, rhs_smem_bytes(), s>>>(static_cast<const float*>(cur), static_cast<const float*>(prev),
-                                                              rhs, b->n, b->alpha, b->a, hg, part, 0,
+                                                              rhs, b->n, b->alpha, b->a, hg, part, b->noflux,
                                                               ixd::ixi_round51(-b->a), 1);
   else
     k_ch_rhs<double><<<grid, kThreads, rhs_smem_bytes(), s>>>(static_cast<const double*>(cur), static_cast<const double*>(prev),
-                                                               rhs, b->n, b->alpha, b->a, hg, part, 0,
+                                                               rhs, b->n, b->alpha, b->a, hg, part, b->noflux,
                                                                ixd::ixi_round51(-b->a), 1);
   CS_CUDA_TRY(cudaGetLastError());
   count_launches(1);
@@ -1422,12 +1428,19 @@ int ch_band_rhs(CHBand* b, const void* prev, const void* cur, double* rhs, doubl
 int ch_band_solve(CHBand* b, const double* in, double* out, cudaStream_t s) {
   if (!in || !out) return set_error(CS_EINVAL, "null buffer");
   const unsigned sgrid = static_cast<unsigned>((b->rows * b->P + kSolveThreads - 1) / kSolveThreads);
-  const size_t ksmem = static_cast<size_t>(16) * b->P * sizeof(double);
   // rows lines of n points, line stride n, element stride 1 (the kernels' line count is `rows`)
-  k_solve_local<double, true, false><<<sgrid, kSolveThreads, 0, s>>>(in, b->B, b->bnd, b->coef, b->rows, b->P, b->m,
-                                                                    b->n, 1);
-  k_solve_correct<0, double, true, false><<<sgrid, kSolveThreads, ksmem, s>>>(
-      b->B, b->bnd, b->coef, b->K, b->rows, b->P, b->m, b->n, 1, out, nullptr, nullptr, nullptr);
+  if (b->noflux) {
+    k_solve_local<double, true, true><<<sgrid, kSolveThreads, 0, s>>>(in, b->B, b->bnd, b->coef, b->rows, b->P,
+                                                                     b->m, b->n, 1);
+    k_solve_correct<0, double, true, true><<<sgrid, kSolveThreads, 0, s>>>(
+        b->B, b->bnd, b->coef, b->K, b->rows, b->P, b->m, b->n, 1, out, nullptr, nullptr, nullptr);
+  } else {
+    const size_t ksmem = static_cast<size_t>(16) * b->P * sizeof(double);
+    k_solve_local<double, true, false><<<sgrid, kSolveThreads, 0, s>>>(in, b->B, b->bnd, b->coef, b->rows, b->P,
+                                                                      b->m, b->n, 1);
+    k_solve_correct<0, double, true, false><<<sgrid, kSolveThreads, ksmem, s>>>(
+        b->B, b->bnd, b->coef, b->K, b->rows, b->P, b->m, b->n, 1, out, nullptr, nullptr, nullptr);
+  }
   CS_CUDA_TRY(cudaGetLastError());
   count_launches(2);
   return CS_OK;

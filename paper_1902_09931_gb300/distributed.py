@@ -175,30 +175,43 @@ def _stage(t: torch.Tensor, group) -> torch.Tensor:
     return t.cpu() if t.is_cuda and dist.get_backend(group) == "gloo" else t
 
 
-def exchange_halo_inplace(padded: torch.Tensor, halo: int, group=None) -> None:
-    """Fills the `halo` rows above and below the band held in padded[halo:-halo] (periodic rows:
-    the first band's neighbour above is the last band) with the neighbours' rows, in place, so the
-    band never moves."""
+def exchange_halo_inplace(padded: torch.Tensor, halo: int, group=None, periodic: bool = True) -> None:
+    """Fills the `halo` rows above and below the band held in padded[halo:-halo] with the
+    neighbours' rows, in place, so the band never moves.  Periodic rows: the first band's
+    neighbour above is the last band.  Otherwise (no-flux boundaries) the first band's rows above
+    and the last band's rows below are its own rows mirrored about the grid's edge (ghost row -1
+    holds row 0, -2 holds row 1, and likewise below), the reflection the full-grid step uses."""
     world = dist.get_world_size(group)
     rank = dist.get_rank(group)
     rows = padded.shape[0] - 2 * halo
     if rows < halo:
         raise ValueError(f"band of {rows} rows is thinner than the halo ({halo})")
+    up = rank - 1 if rank > 0 else (world - 1 if periodic else None)
+    down = rank + 1 if rank < world - 1 else (0 if periodic else None)
+    if up is None:
+        padded[:halo] = padded[halo:2 * halo].flip(0)
+    if down is None:
+        padded[rows + halo:] = padded[rows:rows + halo].flip(0)
     if world == 1:
-        padded[:halo] = padded[rows:rows + halo]
-        padded[rows + halo:] = padded[halo:2 * halo]
+        if periodic:
+            padded[:halo] = padded[rows:rows + halo]
+            padded[rows + halo:] = padded[halo:2 * halo]
         return
-    up, down = (rank - 1) % world, (rank + 1) % world
     top = _stage(torch.empty_like(padded[:halo]), group)
     bottom = _stage(torch.empty_like(padded[:halo]), group)
-    reqs = [dist.irecv(top, src=up, group=group, tag=_TAG_TOP),
-            dist.irecv(bottom, src=down, group=group, tag=_TAG_BOTTOM),
-            dist.isend(_stage(padded[rows:rows + halo].contiguous(), group), dst=down, group=group, tag=_TAG_TOP),
-            dist.isend(_stage(padded[halo:2 * halo].contiguous(), group), dst=up, group=group, tag=_TAG_BOTTOM)]
+    reqs = []
+    if up is not None:
+        reqs.append(dist.irecv(top, src=up, group=group, tag=_TAG_TOP))
+        reqs.append(dist.isend(_stage(padded[halo:2 * halo].contiguous(), group), dst=up, group=group, tag=_TAG_BOTTOM))
+    if down is not None:
+        reqs.append(dist.irecv(bottom, src=down, group=group, tag=_TAG_BOTTOM))
+        reqs.append(dist.isend(_stage(padded[rows:rows + halo].contiguous(), group), dst=down, group=group, tag=_TAG_TOP))
     for r in reqs:
         r.wait()
-    padded[:halo].copy_(top)
-    padded[rows + halo:].copy_(bottom)
+    if up is not None:
+        padded[:halo].copy_(top)
+    if down is not None:
+        padded[rows + halo:].copy_(bottom)
 
 
 def transpose_bands_device(local: torch.Tensor, n: int, group=None) -> torch.Tensor:
@@ -212,18 +225,22 @@ def transpose_bands_device(local: torch.Tensor, n: int, group=None) -> torch.Ten
 
 
 class DeviceCHBand:
-    """The periodic Cahn-Hilliard ADI step (Sec. 5.1) of an n x n grid split into row bands over
-    the ranks of `group`, one band per rank, computed by this library's band entry points
-    (cs_ch_band_*): halo exchange of C^n and C^{n-1} (2 rows, in place in padded buffers), the
-    band's right-hand side, the x line solves, an all-to-all transpose, the y line solves, the
-    transpose back and the update.  `c0` is this rank's band of the initial field (rows x n, on
-    the GPU; C^{-1} = C^0).  The three padded fields rotate as in cs_ch_step."""
+    """The Cahn-Hilliard ADI step (Sec. 5.1) of an n x n grid split into row bands over the ranks
+    of `group`, one band per rank, computed by this library's band entry points (cs_ch_band_*):
+    halo exchange of C^n and C^{n-1} (2 rows, in place in padded buffers), the band's right-hand
+    side, the x line solves, an all-to-all transpose, the y line solves, the transpose back and
+    the update.  `c0` is this rank's band of the initial field (rows x n, on the GPU;
+    C^{-1} = C^0).  `boundary` is CS_CH_PERIODIC or CS_CH_NOFLUX (mirrored halos at the grid's
+    first and last rows, non-cyclic line solves).  The three padded fields rotate as in
+    cs_ch_step."""
 
     HALO = 2
 
-    def __init__(self, n: int, storage: int, D: float, gamma: float, dt: float, c0: torch.Tensor, group=None):
-        from . import CHDesc, CS_F64, cs_ch_band_create
+    def __init__(self, n: int, storage: int, D: float, gamma: float, dt: float, c0: torch.Tensor, group=None,
+                 boundary: int = 0):
+        from . import CHDesc, CS_F64, CS_CH_PERIODIC, cs_ch_band_create
         self.group = group
+        self.periodic = boundary == CS_CH_PERIODIC
         self.n = n
         world = dist.get_world_size(group)
         rank = dist.get_rank(group)
@@ -238,12 +255,13 @@ class DeviceCHBand:
         self.ip, self.ic, self.inext = 0, 1, 2
         self.rhs = torch.empty(self.rows, n, dtype=torch.float64, device=c0.device)
         self.sums = torch.zeros(2, dtype=torch.float64, device=c0.device)
-        self.plan = cs_ch_band_create(CHDesc(n=n, storage=storage, D=D, gamma=gamma, dt=dt), self.rows)
+        self.plan = cs_ch_band_create(CHDesc(n=n, storage=storage, D=D, gamma=gamma, dt=dt, boundary=boundary),
+                                      self.rows)
         self.steps = 0
 
     def _halos(self):
-        exchange_halo_inplace(self.f[self.ip], self.HALO, self.group)
-        exchange_halo_inplace(self.f[self.ic], self.HALO, self.group)
+        exchange_halo_inplace(self.f[self.ip], self.HALO, self.group, self.periodic)
+        exchange_halo_inplace(self.f[self.ic], self.HALO, self.group, self.periodic)
 
     def invariants(self):
         """(mass, energy) of the current field: the bands' FP64 sums, allreduced."""

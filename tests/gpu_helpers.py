@@ -127,7 +127,8 @@ def check_ch_step(orc, prev, cur, got, n, dt, storage, what, noflux=False):
     tol, B = ch_step_bound(orc, prev, cur, ref, n, dt, storage, noflux)
     err = np.abs(got - ref).max()
     print(f"[ch step{' noflux' if noflux else ''}] {what} n={n} storage={'f32' if storage else 'f64'}: "
-          f"err {err:.3e} = {err / B:.3f} B (B = {B:.3e}), {err / np.abs(ref).max():.3e} of max|C|")
+          f"err {err:.3e} = {err / tol:.3f} of the tolerance {tol:.3e} (the FP64 rounding bound B = {B:.3e}"
+          f"{'; FP32 storage adds the roundings to FP32' if storage else ''}), {err / np.abs(ref).max():.3e} of max|C|")
     assert err <= tol, (what, err, tol, err / B)
     if storage == 1:
         assert err <= 1e-5 * np.abs(ref).max(), (what, err / np.abs(ref).max())

@@ -190,3 +190,37 @@ def _errors_worker(rank, world, port, q):
 def test_single_rank_halo_and_errors():
     (rank, out), = _run(_errors_worker, 1)
     assert out == {"thin": True, "shape": True, "wrap": True, "nowrap": True}
+
+
+def _halo_worker(rank, world, port, q):
+    dist = _init(rank, world, port)
+    import torch
+    from paper_1902_09931_gb300 import distributed as D
+    n, halo = 29, 2
+    A = np.arange(n * 5, dtype=np.float64).reshape(n, 5)
+    r0, r1 = D.band(n, world, rank)
+    ok = {}
+    for periodic in (True, False):
+        padded = torch.full((r1 - r0 + 2 * halo, 5), -1.0, dtype=torch.float64)
+        padded[halo:-halo] = torch.from_numpy(A[r0:r1])
+        D.exchange_halo_inplace(padded, halo, periodic=periodic)
+        rows = []
+        for j in range(-halo, r1 - r0 + halo):
+            g = r0 + j
+            if periodic:
+                g %= n
+            else:  # even reflection about the grid's edges: -1 -> 0, -2 -> 1, n -> n-1, n+1 -> n-2
+                g = -1 - g if g < 0 else (2 * n - 1 - g if g >= n else g)
+            rows.append(A[g])
+        ok[periodic] = bool(np.array_equal(padded.numpy(), np.array(rows)))
+    q.put((rank, ok))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [1, 2, 3])
+def test_halo_exchange_in_place_periodic_and_mirrored(world):
+    """exchange_halo_inplace fills the 2 rows above and below each rank's band with the global
+    rows the full-grid step reads there: wrapped rows (periodic) or the even reflection about the
+    grid's first and last rows (no-flux), with neighbours' rows between bands."""
+    for rank, ok in _run(_halo_worker, world):
+        assert ok == {True: True, False: True}, (rank, ok)

@@ -46,11 +46,11 @@ def test_device_band_sweep_matches_oracle(env, bc):
         assert np.abs(got - ref).max() <= 1e-12 * np.abs(w).sum() * np.abs(u).max(), name
 
 
-def _full_grid_run(cs, torch, c0, storage, dt, steps):
+def _full_grid_run(cs, torch, c0, storage, dt, steps, boundary=0):
     tdt = torch.float64 if storage == 0 else torch.float32
     f = [torch.from_numpy(c0).to("cuda", tdt), torch.from_numpy(c0).to("cuda", tdt),
          torch.zeros(c0.shape, dtype=tdt, device="cuda")]
-    plan = cs.cs_ch_create(cs.CHDesc(n=c0.shape[0], storage=storage, D=1.0, gamma=0.01, dt=dt), *f)
+    plan = cs.cs_ch_create(cs.CHDesc(n=c0.shape[0], storage=storage, D=1.0, gamma=0.01, dt=dt, boundary=boundary), *f)
     mass, energy = cs.cs_ch_step(plan, steps, invariants=True)
     _, cur, _ = cs.cs_ch_fields(plan)
     out = [t for t in f if t.data_ptr() == cur][0].clone()
@@ -58,20 +58,22 @@ def _full_grid_run(cs, torch, c0, storage, dt, steps):
     return out, mass[-1], energy[-1]
 
 
+@pytest.mark.parametrize("boundary", [0, 1])
 @pytest.mark.parametrize("storage", [0, 1])
-def test_device_band_ch_step_equals_full_grid_step(env, storage):
+def test_device_band_ch_step_equals_full_grid_step(env, storage, boundary):
     """The decomposed Cahn-Hilliard step (cs_ch_band_* with the halo exchange and the transposes of
     the distributed module) on one rank gives the full-grid cs_ch_step's fields bit for bit (the
-    same kernels on the same values) and the same invariants."""
+    same kernels on the same values) and the same invariants, periodic and with no-flux boundaries
+    (mirrored halos, non-cyclic line solves)."""
     cs, torch, orc, D = env
     n = 320  # a size no other test autotunes: every process uses the default partition
     dt = 0.1 * 2 * np.pi / n
     c0 = W.ch_initial(n, seed=44)
     if storage == 1:
         c0 = c0.astype(np.float32).astype(np.float64)
-    ref, m_ref, e_ref = _full_grid_run(cs, torch, c0, storage, dt, 3)
+    ref, m_ref, e_ref = _full_grid_run(cs, torch, c0, storage, dt, 3, boundary)
     tdt = torch.float64 if storage == 0 else torch.float32
-    b = D.DeviceCHBand(n, storage, 1.0, 0.01, dt, torch.from_numpy(c0).to("cuda", tdt))
+    b = D.DeviceCHBand(n, storage, 1.0, 0.01, dt, torch.from_numpy(c0).to("cuda", tdt), boundary=boundary)
     b.step(3)
     mass, energy = b.invariants()
     got = b.field().clone()
@@ -81,7 +83,7 @@ def test_device_band_ch_step_equals_full_grid_step(env, storage):
     assert mass == m_ref and energy == e_ref
 
 
-def _band_worker(rank, world, port, storage, q):
+def _band_worker(rank, world, port, storage, boundary, q):
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     sys.path.insert(0, root)
@@ -99,7 +101,8 @@ def _band_worker(rank, world, port, storage, q):
     c0 = W.ch_initial(n, seed=45)
     tdt = torch.float64 if storage == 0 else torch.float32
     r0, r1 = D.band(n, world, rank)
-    b = D.DeviceCHBand(n, storage, 1.0, 0.01, dt, torch.from_numpy(c0[r0:r1].copy()).to("cuda", tdt))
+    b = D.DeviceCHBand(n, storage, 1.0, 0.01, dt, torch.from_numpy(c0[r0:r1].copy()).to("cuda", tdt),
+                       boundary=boundary)
     b.step(3)
     mass, energy = b.invariants()
     q.put((rank, b.field().cpu().numpy().astype(np.float64), mass, energy))
@@ -107,8 +110,9 @@ def _band_worker(rank, world, port, storage, q):
     dist.destroy_process_group()
 
 
+@pytest.mark.parametrize("boundary", [0, 1])
 @pytest.mark.parametrize("storage", [0, 1])
-def test_device_band_ch_step_two_ranks(env, storage):
+def test_device_band_ch_step_two_ranks(env, storage, boundary):
     """Two ranks (two processes sharing this GPU, gloo through host memory; nothing on the device
     waits for the other rank) each step their 160-row band three times; the bands put together
     equal the full-grid step bit for bit, and the allreduced invariants agree to rounding."""
@@ -119,13 +123,13 @@ def test_device_band_ch_step_two_ranks(env, storage):
     c0 = W.ch_initial(n, seed=45)
     if storage == 1:
         c0 = c0.astype(np.float32).astype(np.float64)
-    ref, m_ref, e_ref = _full_grid_run(cs, torch, c0, storage, dt, 3)
+    ref, m_ref, e_ref = _full_grid_run(cs, torch, c0, storage, dt, 3, boundary)
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
         port = s.getsockname()[1]
-    procs = [ctx.Process(target=_band_worker, args=(r, 2, port, storage, q)) for r in range(2)]
+    procs = [ctx.Process(target=_band_worker, args=(r, 2, port, storage, boundary, q)) for r in range(2)]
     for p in procs:
         p.start()
     res = sorted([q.get(timeout=300) for _ in procs], key=lambda t: t[0])
