@@ -144,7 +144,11 @@ __device__ __forceinline__ void block_reduce2(double m, double e, double* out2) 
 // free-energy density of C^n.  rhs == nullptr computes the sums only.  The tile is staged in FP64
 // whatever the storage type T (FP32 values widen exactly): the right-hand side carries terms of
 // size ~64 a |Cbar| (a = 1.8e5 at n = 4096) that the solves cancel back down to |C|, so it needs
-// FP64 precision; evaluated in FP32 it loses all of C's digits at the large grids.
+// FP64 precision; evaluated in FP32 it loses all of C's digits at the large grids.  The one
+// exception: with FP32 storage Cbar = 2 C^n - C^{n-1} is formed in FP32 (one rounding) exactly as
+// the update forms it, then widened.  Both uses of Cbar then agree, so the step is the scheme
+// applied to that Cbar, whose rounding reaches C^{n+1} at most undamped (it is of the size of the
+// stored result's own rounding); everything after it is FP64.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_ch_rhs(const T* __restrict__ cur, const T* __restrict__ prev, double* __restrict__ rhs, int64_t n,
@@ -168,7 +172,10 @@ __global__ void __launch_bounds__(kThreads)
                                   : static_cast<int64_t>(wrapn(gy, n)) * n + wrapn(gx, n);
     const double cv = widen(cur[off]);
     sc[idx] = cv;
-    sb[idx] = fma(2.0, cv, -widen(prev[off]));  // one FP64 instruction (2 cv - p as two adds is two)
+    if constexpr (sizeof(T) == 4)
+      sb[idx] = widen(fmaf(2.0f, cur[off], -prev[off]));  // as the FP32 update forms Cbar
+    else
+      sb[idx] = fma(2.0, cv, -prev[off]);  // one FP64 instruction (2 cv - p as two adds is two)
   }
   __syncthreads();
   if (rhs) {
@@ -467,13 +474,14 @@ __global__ void __launch_bounds__(kSolveThreads)
     } else {
       if constexpr (sizeof(T) == 4) {
         // FP32 storage: Cbar = 2 C^n - C^{n-1} in FP32 arithmetic (one rounding, of the size of
-        // the result's own), widened exactly; the FP64 add of x and the round-to-nearest narrowing
-        // (F2F, the same rounding as an integer-pipe narrowing) keep this kernel's integer work small
+        // the result's own), widened exactly; one FP64 add of x, then the round-to-nearest-even
+        // narrowing on the integer pipe (this kernel is FP64-bound, and a conversion instruction
+        // would take an FP64 issue slot)
         float cb[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) cb[u] = fmaf(2.0f, cur[base + (k0 + u) * es], -prev[base + (k0 + u) * es]);
 #pragma unroll
-        for (int u = 0; u < kU; ++u) next[base + (k0 + u) * es] = __double2float_rn(widen(cb[u]) + x[u]);
+        for (int u = 0; u < kU; ++u) next[base + (k0 + u) * es] = narrow_rn(widen(cb[u]) + x[u]);
       } else {
         double c[kU], pv[kU];
 #pragma unroll
@@ -1340,7 +1348,7 @@ __global__ void __launch_bounds__(256)
   const int64_t o = i + 2 * n;  // padded row r + 2
   if constexpr (sizeof(T) == 4) {
     const float cb = fmaf(2.0f, cur[o], -prev[o]);  // as the full-grid update forms it
-    next[o] = __double2float_rn(widen(cb) + v[i]);
+    next[o] = narrow_rn(widen(cb) + v[i]);
   } else {
     next[o] = fma(2.0, cur[o], -prev[o]) + v[i];
   }
