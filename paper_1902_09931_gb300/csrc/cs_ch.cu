@@ -178,6 +178,17 @@ __global__ void __launch_bounds__(kThreads)
       sb[idx] = fma(2.0, cv, -prev[off]);  // one FP64 instruction (2 cv - p as two adds is two)
   }
   __syncthreads();
+  __shared__ __align__(16) unsigned s_red[kThreads / 32];
+  auto lap5 = [&](const double* t, int i, int pitch) {
+    return (t[i - pitch] + t[i + pitch]) + (t[i - 1] + t[i + 1]) - 4.0 * t[i];
+  };
+  // digit sums of the 5-point Laplacian at i of a split tile (int2 digits over t's slots)
+  auto lap5_digits = [&](const double* t, int i, int pitch, int& q0, int& q1) {
+    const int2* d = reinterpret_cast<const int2*>(t);
+    const int2 u = d[i - pitch], v = d[i + pitch], w = d[i - 1], x = d[i + 1], c = d[i];
+    q0 = (u.x + v.x) + (w.x + x.x) - 4 * c.x;
+    q1 = (u.y + v.y) + (w.y + x.y) - 4 * c.y;
+  };
   if (rhs) {
     // Both 5-point Laplacians as exact integer-digit sums (weights 1, 1, 1, 1, -4; 28-bit digits, which
     // hold every bit of a value within a factor 8 of its tile's largest, so neighbouring tiles,
@@ -186,17 +197,6 @@ __global__ void __launch_bounds__(kThreads)
     // one FP64 FMA; the first one's scaling carries -a, so the FP64 pipe keeps only Cbar, u u,
     // N, Z, the two scalings, C^n - C^{n-1} and the final combination (8.6 FP64 operations per
     // point).  A tile whose values leave the digit range takes the FP64 formula for that Laplacian.
-    __shared__ __align__(16) unsigned s_red[kThreads / 32];
-    auto lap5 = [&](const double* t, int i, int pitch) {
-      return (t[i - pitch] + t[i + pitch]) + (t[i - 1] + t[i + 1]) - 4.0 * t[i];
-    };
-    // digit sums of the 5-point Laplacian at i of a split tile (int2 digits over t's slots)
-    auto lap5_digits = [&](const double* t, int i, int pitch, int& q0, int& q1) {
-      const int2* d = reinterpret_cast<const int2*>(t);
-      const int2 u = d[i - pitch], v = d[i + pitch], w = d[i - 1], x = d[i + 1], c = d[i];
-      q0 = (u.x + v.x) + (w.x + x.x) - 4 * c.x;
-      q1 = (u.y + v.y) + (w.y + x.y) - 4 * c.y;
-    };
     // the one-FMA scaling of a digit sum by m 2^(G - 56) (ixi_consts); false: the FP64 formula
     double* cb = sb;
     double* zt = sb;  // Z takes Cbar's place (held in registers until every thread has read Cbar)
@@ -264,17 +264,47 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   if (partials) {
-    double m = 0.0, e = 0.0;
+    // Mass sum C and free-energy density sum (1/4)(C^2 - 1)^2 + (gamma / 2h^2)(|D+x C|^2 + |D+y C|^2)
+    // (Eq. 1 with forward differences).  The gradient part is summed by parts: over the periodic
+    // grid, and with the even reflection of the no-flux boundary, the sum of the squared forward
+    // differences equals -sum C Lap5(C) (Lap5 the unscaled 5-point Laplacian, reading the staged
+    // halo).  Lap5(C) is an exact digit sum scaled by one FP64 FMA, so a point costs 5 FP64
+    // operations instead of 9; only the grid total (the sum over all blocks, or over all bands
+    // with their halos) equals the forward-difference sum, not each block's share.
+    __syncthreads();  // sb (Cbar, then Z) is no longer read: it takes C's digits
+    const int te = static_cast<int>(ixd::ix_tile_max_hi<kThreads, HR * HC>(sc, s_red) >> 20);
+    uint32_t w4[4];
+    const bool dig = ixd::ixi_consts<28>(1.0, -1.5, te, w4);  // uniform over the block
+    if (dig) {
+      constexpr int NP = HR * HC / 2;
+      const double2* q = reinterpret_cast<const double2*>(sc);
+      int4* qi = reinterpret_cast<int4*>(sb);
+      for (int k = threadIdx.x; k < NP; k += kThreads) {
+        const double2 v = q[k];
+        const int2 a0 = ixd::ixi_split<28>(v.x, te), a1 = ixd::ixi_split<28>(v.y, te);
+        qi[k] = make_int4(a0.x, a0.y, a1.x, a1.y);
+      }
+      __syncthreads();
+    }
+    double m = 0.0, ew = 0.0, eg = 0.0;
     for (int idx = threadIdx.x; idx < kTY * kTX; idx += kThreads) {
       const int r = idx / kTX, c = idx - r * kTX;
       const int hidx = (r + 2) * HC + (c + 2);
       const double u = sc[hidx];
-      const double gx = sc[hidx + 1] - u;
-      const double gy = sc[hidx + HC] - u;
-      const double w = u * u - 1.0;
+      double lap;
+      if (dig) {
+        int q0, q1;
+        lap5_digits(sb, hidx, HC, q0, q1);
+        lap = ixd::ixi_combine<28>(q0, q1, w4);
+      } else {
+        lap = lap5(sc, hidx, HC);
+      }
+      const double w = fma(u, u, -1.0);
       m += u;
-      e += 0.25 * w * w + half_gamma_over_h2 * (gx * gx + gy * gy);
+      ew = fma(w, w, ew);
+      eg = fma(u, lap, eg);
     }
+    const double e = fma(0.25, ew, -half_gamma_over_h2 * eg);
     block_reduce2<T>(m, e, partials + 2 * (static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x));
   }
 }
