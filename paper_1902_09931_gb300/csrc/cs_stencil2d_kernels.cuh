@@ -532,7 +532,10 @@ using ixd::ixi_consts;
 // are read as 16-byte (d0, d1, d0', d1') pairs of columns, W + 1 columns (+1 when L is odd)
 // serving both outputs, and the two results leave as one 16-byte store where both columns are
 // written.
-template <int TY, int SPEC>
+// FULL: every output of the tile is written and 16-byte stores apply (the launch checked that the
+// grid is periodic, nx a multiple of 64, ny of TY, and out 16-byte aligned); the per-row range and
+// alignment tests are left out.
+template <int TY, int SPEC, bool FULL = false>
 __device__ __forceinline__ void ix_compute(const int2* sd2, double* __restrict__ out, int64_t nx,
                                            int64_t ny, int periodic, int64_t x0, int64_t y0,
                                            const IxTaps& taps, const uint32_t (&w)[4], int tile_e) {
@@ -624,7 +627,9 @@ __device__ __forceinline__ void ix_compute(const int2* sd2, double* __restrict__
       const double val0 = ixi_combine(acc0[done % H][0], acc1[done % H][0], w, qa.x, qb.x);
       const double val1 = ixi_combine(acc0[done % H][1], acc1[done % H][1], w, qa.y, qb.y);
       acc0[done % H][0] = acc0[done % H][1] = acc1[done % H][0] = acc1[done % H][1] = 0;
-      if (done >= klo && done < khi) {
+      if constexpr (FULL) {
+        *reinterpret_cast<double2*>(op) = make_double2(val0, val1);
+      } else if (done >= klo && done < khi) {
         if (both) {
           *reinterpret_cast<double2*>(op) = make_double2(val0, val1);
         } else {
@@ -647,7 +652,7 @@ constexpr int ix_min_blocks(int spec) {
   return kSpecs[spec].T + kSpecs[spec].B + 1 <= 5 && taps <= 13 ? 6 : 3;
 }
 
-template <int TY, int SPEC>
+template <int TY, int SPEC, bool FULL>
 __global__ void __launch_bounds__(kThreads, ix_min_blocks(SPEC))
     k_stencil2d_ix(const double* __restrict__ in, double* __restrict__ out, int64_t nx, int64_t ny,
                    int periodic, int vec_ok, Taps<double> taps, IxTaps itaps, int ty0) {
@@ -676,7 +681,7 @@ __global__ void __launch_bounds__(kThreads, ix_min_blocks(SPEC))
   // pass 2: integer digits over the values' own slots
   ixd::ixi_split_tile<kThreads, ROWS * COLS>(s, tile_e);
   __syncthreads();
-  ix_compute<TY, SPEC>(reinterpret_cast<const int2*>(s), out, nx, ny, periodic, x0, y0, itaps, w, tile_e);
+  ix_compute<TY, SPEC, FULL>(reinterpret_cast<const int2*>(s), out, nx, ny, periodic, x0, y0, itaps, w, tile_e);
 }
 
 // Output rows [row0, row1) of the next launches on this host thread (row0 a multiple of 64, so
@@ -701,11 +706,14 @@ int launch_ix(const double* in, double* out, int64_t nx, int64_t ny, int periodi
               const Taps<double>& taps, const IxTaps& itaps, cudaStream_t st) {
   constexpr SpecDesc sd = kSpecs[SPEC];
   const size_t smem = tile_smem_bytes<double>(sd.L, sd.R, sd.T, sd.B, TY, false);
-  auto kern = k_stencil2d_ix<TY, SPEC>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  // the FULL form when every tile's outputs are all written with 16-byte stores
+  const bool full = periodic && nx % tile_x<double>() == 0 && ny % TY == 0 &&
+                    (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
+  auto kern = full ? k_stencil2d_ix<TY, SPEC, true> : k_stencil2d_ix<TY, SPEC, false>;
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[full]) {
     CS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-    attr_set = true;
+    attr_set[full] = true;
   }
   int ty0, nty;
   window_tiles(TY, ny, &ty0, &nty);
