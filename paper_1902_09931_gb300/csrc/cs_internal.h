@@ -54,6 +54,10 @@ struct Stencil2DConfig {
   mutable int status_seen;  // counter value at the last cs_plan_check
   int stall_from;     // test hook (cs_plan_debug_stall): CTA-local tile from which the TMA sweep
                       // issues no copies, so its wait runs out; -1 = off
+  // non-periodic FP64 digit sweeps: the border tiles run on this stream beside the interior
+  // tiles' launch (fork and join by the two events); created with the plan
+  cudaStream_t aux;
+  cudaEvent_t ev_fork, ev_join;
 };
 int stencil2d_prepare(Stencil2DConfig* cfg);  // picks variant, allocates generic weights
 void stencil2d_release(Stencil2DConfig* cfg);

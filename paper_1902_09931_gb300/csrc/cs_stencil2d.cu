@@ -53,6 +53,8 @@ int stencil2d_prepare(Stencil2DConfig* cfg) {
   cfg->d_weights = nullptr;
   cfg->d_weights_f = nullptr;
   cfg->d_status = nullptr;
+  cfg->aux = nullptr;
+  cfg->ev_fork = cfg->ev_join = nullptr;
   cfg->status_seen = 0;
   cfg->stall_from = -1;
   cfg->variant = -1;
@@ -154,6 +156,15 @@ int stencil2d_prepare(Stencil2DConfig* cfg) {
     stencil2d_release(cfg);
     return cuda_error(e, "cudaMalloc(status)");
   }
+  if (cfg->dtype == CS_F64 && cfg->bc != CS_BC_PERIODIC && cfg->ix_ok) {
+    cudaError_t e2 = cudaStreamCreateWithFlags(&cfg->aux, cudaStreamNonBlocking);
+    if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&cfg->ev_fork, cudaEventDisableTiming);
+    if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&cfg->ev_join, cudaEventDisableTiming);
+    if (e2 != cudaSuccess) {
+      stencil2d_release(cfg);
+      return cuda_error(e2, "border stream");
+    }
+  }
   int choice;
   if (tune_lookup(stencil2d_shape_key(cfg), &choice)) stencil2d_set_tile_choice(cfg, choice);
   return CS_OK;
@@ -163,9 +174,14 @@ void stencil2d_release(Stencil2DConfig* cfg) {
   if (cfg->d_weights) cudaFree(cfg->d_weights);
   if (cfg->d_weights_f) cudaFree(cfg->d_weights_f);
   if (cfg->d_status) cudaFree(cfg->d_status);
+  if (cfg->ev_fork) cudaEventDestroy(cfg->ev_fork);
+  if (cfg->ev_join) cudaEventDestroy(cfg->ev_join);
+  if (cfg->aux) cudaStreamDestroy(cfg->aux);
   cfg->d_weights = nullptr;
   cfg->d_weights_f = nullptr;
   cfg->d_status = nullptr;
+  cfg->aux = nullptr;
+  cfg->ev_fork = cfg->ev_join = nullptr;
 }
 
 // Waits for the stream, then reads the plan's timeout counter: a TMA sweep whose bounded

@@ -655,7 +655,8 @@ constexpr int ix_min_blocks(int spec) {
 template <int TY, int SPEC, bool FULL>
 __global__ void __launch_bounds__(kThreads, ix_min_blocks(SPEC))
     k_stencil2d_ix(const double* __restrict__ in, double* __restrict__ out, int64_t nx, int64_t ny,
-                   int periodic, int vec_ok, Taps<double> taps, IxTaps itaps, int ty0) {
+                   int periodic, int vec_ok, Taps<double> taps, IxTaps itaps, int tx0, int ty0, int ring_nbx,
+                   int ring_nby) {
   constexpr SpecDesc sd = kSpecs[SPEC];
   constexpr int V = Vec<double>::n;
   constexpr int TX = tile_x<double>();
@@ -666,8 +667,26 @@ __global__ void __launch_bounds__(kThreads, ix_min_blocks(SPEC))
   double* s = reinterpret_cast<double*>(smem_raw);
   __shared__ __align__(16) unsigned s_red[kThreads / 32];
   static_assert(COLS % 2 == 0, "digit passes take values in pairs");
-  const int64_t x0 = static_cast<int64_t>(blockIdx.x) * TX;
-  const int64_t y0 = (static_cast<int64_t>(blockIdx.y) + ty0) * TY;
+  // the tile: (blockIdx.x + tx0, blockIdx.y + ty0), or with ring_nbx > 0 the CTA's tile of the
+  // border ring of an nbx x nby tile grid (the top row, the bottom row, then the first and last
+  // columns of the rows between)
+  int64_t bx = static_cast<int64_t>(blockIdx.x) + tx0, by = static_cast<int64_t>(blockIdx.y) + ty0;
+  if (ring_nbx > 0) {
+    const int b = static_cast<int>(blockIdx.x), mid = ring_nby - 2;
+    if (b < ring_nbx) {
+      bx = b;
+      by = 0;
+    } else if (b < 2 * ring_nbx) {
+      bx = b - ring_nbx;
+      by = ring_nby - 1;
+    } else {
+      const int c = b - 2 * ring_nbx, side = c / mid;
+      bx = side ? ring_nbx - 1 : 0;
+      by = 1 + (c - side * mid);
+    }
+  }
+  const int64_t x0 = bx * TX;
+  const int64_t y0 = by * TY;
   load_tile_ct<double, ROWS, COLS>(s, in, nx, ny, periodic != 0, vec_ok != 0, x0, y0, sd.T, LA);
   // pass 1: the tile's largest exponent; inf / nan (and tiles outside the exponent window) take
   // native FP64
@@ -703,34 +722,57 @@ inline void window_tiles(int ty, int64_t ny, int* ty0, int* nty) {
 
 template <int TY, int SPEC>
 int launch_ix(const double* in, double* out, int64_t nx, int64_t ny, int periodic, int vec_ok,
-              const Taps<double>& taps, const IxTaps& itaps, cudaStream_t st) {
+              const Taps<double>& taps, const IxTaps& itaps, const Stencil2DConfig* cfg, cudaStream_t st) {
   constexpr SpecDesc sd = kSpecs[SPEC];
+  constexpr int TX = tile_x<double>();
   const size_t smem = tile_smem_bytes<double>(sd.L, sd.R, sd.T, sd.B, TY, false);
-  // the FULL form when every tile's outputs are all written with 16-byte stores
-  const bool full = periodic && nx % tile_x<double>() == 0 && ny % TY == 0 &&
-                    (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
-  auto kern = full ? k_stencil2d_ix<TY, SPEC, true> : k_stencil2d_ix<TY, SPEC, false>;
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[full]) {
-    CS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-    attr_set[full] = true;
+  auto kfull = k_stencil2d_ix<TY, SPEC, true>;
+  auto kedge = k_stencil2d_ix<TY, SPEC, false>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    CS_CUDA_TRY(cudaFuncSetAttribute(kfull, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    CS_CUDA_TRY(cudaFuncSetAttribute(kedge, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    attr_set = true;
   }
   int ty0, nty;
   window_tiles(TY, ny, &ty0, &nty);
   if (nty == 0) return CS_OK;
-  dim3 grid(static_cast<unsigned>((nx + tile_x<double>() - 1) / tile_x<double>()), static_cast<unsigned>(nty));
-  kern<<<grid, kThreads, smem, st>>>(in, out, nx, ny, periodic, vec_ok, taps, itaps, ty0);
+  const int64_t nbx = (nx + TX - 1) / TX, nby = (ny + TY - 1) / TY;
+  // the FULL form (every output of a tile written, 16-byte stores) applies to every tile of a
+  // periodic grid of whole tiles, and to the inner tiles of a non-periodic one
+  const bool whole = nx % TX == 0 && ny % TY == 0 && (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
+  if (periodic || !whole || !cfg || !cfg->aux || ty0 != 0 || nty != nby || nbx < 3 || nby < 3) {
+    auto kern = periodic && whole ? kfull : kedge;
+    dim3 grid(static_cast<unsigned>(nbx), static_cast<unsigned>(nty));
+    kern<<<grid, kThreads, smem, st>>>(in, out, nx, ny, periodic, vec_ok, taps, itaps, 0, ty0, 0, 0);
+    CS_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return CS_OK;
+  }
+  // non-periodic: the border ring of tiles (the general form) on the plan's second stream, beside
+  // the inner tiles (FULL) on st; st then waits for both
+  CS_CUDA_TRY(cudaEventRecord(cfg->ev_fork, st));
+  CS_CUDA_TRY(cudaStreamWaitEvent(cfg->aux, cfg->ev_fork, 0));
+  const unsigned nring = static_cast<unsigned>(2 * nbx + 2 * (nby - 2));
+  kedge<<<nring, kThreads, smem, cfg->aux>>>(in, out, nx, ny, periodic, vec_ok, taps, itaps, 0, 0,
+                                             static_cast<int>(nbx), static_cast<int>(nby));
   CS_CUDA_TRY(cudaGetLastError());
-  count_launches(1);
+  CS_CUDA_TRY(cudaEventRecord(cfg->ev_join, cfg->aux));
+  dim3 grid(static_cast<unsigned>(nbx - 2), static_cast<unsigned>(nby - 2));
+  kfull<<<grid, kThreads, smem, st>>>(in, out, nx, ny, periodic, vec_ok, taps, itaps, 1, 1, 0, 0);
+  CS_CUDA_TRY(cudaGetLastError());
+  CS_CUDA_TRY(cudaStreamWaitEvent(st, cfg->ev_join, 0));
+  count_launches(2);
   return CS_OK;
 }
 
 template <int TY>
 int dispatch_ix(int variant, const double* in, double* out, int64_t nx, int64_t ny, int periodic,
-                int vec_ok, const Taps<double>& taps, const IxTaps& itaps, cudaStream_t st) {
+                int vec_ok, const Taps<double>& taps, const IxTaps& itaps, const Stencil2DConfig* cfg,
+                cudaStream_t st) {
   switch (variant) {
 #define CS_IX_CASE(I) \
-  case I: return launch_ix<TY, I>(in, out, nx, ny, periodic, vec_ok, taps, itaps, st);
+  case I: return launch_ix<TY, I>(in, out, nx, ny, periodic, vec_ok, taps, itaps, cfg, st);
     CS_IX_CASE(0) CS_IX_CASE(1) CS_IX_CASE(2) CS_IX_CASE(3) CS_IX_CASE(4)
     CS_IX_CASE(5) CS_IX_CASE(6) CS_IX_CASE(7) CS_IX_CASE(8) CS_IX_CASE(9)
     CS_IX_CASE(10) CS_IX_CASE(11) CS_IX_CASE(13)
@@ -1521,8 +1563,8 @@ int launch_stencil2d_t(const Stencil2DConfig* cfg, const void* vin, void* vout, 
         it.inv_hi = static_cast<float>(1.0 / cfg->ix_c);
         it.inv_lo = static_cast<float>(1.0 / cfg->ix_c - static_cast<double>(it.inv_hi));
         if (cfg->tile_rows == 32)
-          return dispatch_ix<32>(cfg->variant, in, out, cfg->nx, cfg->ny, periodic, vec_ok, taps, it, st);
-        return dispatch_ix<64>(cfg->variant, in, out, cfg->nx, cfg->ny, periodic, vec_ok, taps, it, st);
+          return dispatch_ix<32>(cfg->variant, in, out, cfg->nx, cfg->ny, periodic, vec_ok, taps, it, cfg, st);
+        return dispatch_ix<64>(cfg->variant, in, out, cfg->nx, cfg->ny, periodic, vec_ok, taps, it, cfg, st);
       }
       if (cfg->dd_ok && cfg->fp64_mode == CS_FP64_AUTO) {
         DDTaps dt;
