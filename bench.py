@@ -269,13 +269,18 @@ def run_ours(args):
     hbm_peak, peak_kind = peaks()
     stream = torch.cuda.current_stream()
     only = tuple(args.only.split(",")) if args.only else None
+    cached = bool(args.tune_file) and os.path.exists(args.tune_file)
+    if cached:  # the tile choices of an earlier run (plans look the cache up when created)
+        cs.cs_tune_load(args.tune_file)
     sweeps, keep = build_suite(cs, torch, rank, only)
     if args.tile_choice >= 0:
         for sw in sweeps:
             cs.cs_plan_set_tile_choice(sw["plan"], args.tile_choice)
-    elif not args.no_autotune:
+    elif not args.no_autotune and not cached:
         for sw in sweeps:  # pick tile shapes with the project's autotuner
             cs.cs_autotune(sw["plan"], stream)
+        if args.tune_file and rank == 0:
+            cs.cs_tune_save(args.tune_file)
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
     for _ in range(args.warmup):
         timed_sweeps(cs, torch, sweeps, flush, stream, None)
@@ -1063,6 +1068,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile-choice", type=int, default=-1, help="force a tile choice (0, 1, 2) instead of autotuning")
     ap.add_argument("--only", default="", help="profile one sweep: name,n,f64|f32,p|np")
+    ap.add_argument("--tune-file", default="", help="stencil suite: load the tile choices from this autotuner "
+                    "cache if it exists (no autotuning), else autotune and save them there")
     ap.add_argument("--sharded", action="store_true", help="one CH grid split into row bands over the ranks")
     ap.add_argument("--sharded-n", type=int, default=4096)
     ap.add_argument("--part", default="", help="run one part alone: ch:<n>:<f64|f32>:<steps>[:noflux], ch_runs, single_call, group, batch1d, serve, coarsening, streamed or weno")
