@@ -120,7 +120,10 @@ int cs_plan_create_1d_batch(cs_plan_t* plan, const cs_stencil_desc* desc, int64_
                             const int64_t* d_offsets, int64_t total_len, const void* d_in,
                             void* d_out);
 
-/* Compute (Sec. 3): applies the stencil, d_in -> d_out, stream-ordered and asynchronous. */
+/* Compute (Sec. 3): applies the stencil, d_in -> d_out, stream-ordered and asynchronous.  A
+ * non-periodic FP64 2D plan on the digit path runs the border ring of its tiles on a stream the
+ * plan owns, forked from cuda_stream and joined back into it by two events, so work issued on
+ * cuda_stream afterwards still follows the whole sweep. */
 int cs_compute(cs_plan_t plan, void* cuda_stream);
 
 /* Grouped Compute: applies `count` 2D stencil plans -- independent grids of any sizes -- in one

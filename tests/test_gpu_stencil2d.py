@@ -193,11 +193,14 @@ def test_swap_applies_stencil_again(env):
     assert np.abs(got - ref).max() <= 1e-12 * 8 ** 3
 
 
+@pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("dtype", [0, 1])
-def test_graph_replay_matches_direct(env, dtype):
+def test_graph_replay_matches_direct(env, dtype, bc):
+    """Graph replay equals direct compute; for the non-periodic FP64 grid (4 x 4 whole tiles) the
+    captured sweep includes the fork to the plan's second stream (border ring) and the join."""
     cs, torch, orc = env
     u = W.sines_field(256, seed=8)
-    kw = dict(dir=2, bc=1, left=2, right=2, top=2, bottom=2, weights=biharm13())
+    kw = dict(dir=2, bc=bc, left=2, right=2, top=2, bottom=2, weights=biharm13())
     a = run2d(cs, torch, u, kw, dtype, reps=4)
     b = run2d(cs, torch, u, kw, dtype, reps=4, graph=True)
     assert np.array_equal(a, b)
