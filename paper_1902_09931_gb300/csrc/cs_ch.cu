@@ -74,7 +74,7 @@ void drop_graphs(CHPlan* p);
 
 namespace {
 
-constexpr int kTX = 64, kTY = 32, kThreads = 256, kSolveThreads = 128;
+constexpr int kTX = 64, kTY = 32, kThreads = 256, kSolveThreads = 32;
 constexpr int kU = 8;  // line elements per register batch in the solves
 
 // ---- exact conversions on the integer pipe (f32 <-> f64 conversion runs on the FP64 pipe) ----
