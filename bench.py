@@ -744,11 +744,12 @@ def ch_fp64_ops_per_point(chunks: int, m: int) -> float:
     """FP64-pipe operations per grid point of one ADI step as the kernels perform them, for either
     storage: the right-hand side 8.6 (Cbar on the halo-2 tile: 1.2; on the halo-1 tile u u, N,
     the first digit Laplacian's scaling (carrying -a) and Z: 4 x 1.1; the second scaling,
-    C^n - C^{n-1} and the final combination: 3), two sweeps of local LU (5) + spike correction (4)
-    + chunk-end system (16 chunks / m), and the update (2: FP64 storage Cbar and the add; FP32
-    storage the add and the narrowing conversion, which runs on the FP64 pipe)."""
+    C^n - C^{n-1} and the final combination: 3; FP32 storage forms Cbar in FP32), two sweeps of
+    local LU (5) + spike correction (4) + chunk-end system (16 chunks / m), and the update's one
+    add (Cbar comes from the right-hand side kernel through the C^{n+1} buffer; FP32 storage
+    narrows on the integer pipe)."""
     per_sweep = 5 + 4 + 16.0 * chunks / m
-    return 8.6 + 2 * per_sweep + 2
+    return 8.6 + 2 * per_sweep + 1
 
 
 def _median_event_ms(torch, stream, launch, flush, reps=12, skip=2):

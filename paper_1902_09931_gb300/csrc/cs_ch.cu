@@ -153,7 +153,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_ch_rhs(const T* __restrict__ cur, const T* __restrict__ prev, double* __restrict__ rhs, int64_t n,
              double alpha, double a, double half_gamma_over_h2, double* __restrict__ partials, int noflux,
-             double am51, int band) {
+             double am51, int band, T* __restrict__ cbar_out) {
   constexpr int HR = kTY + 4, HC = kTX + 4;  // halo-2 tiles
   constexpr int ZR = kTY + 2, ZC = kTX + 2;  // halo-1 tile
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -172,10 +172,18 @@ __global__ void __launch_bounds__(kThreads)
                                   : static_cast<int64_t>(wrapn(gy, n)) * n + wrapn(gx, n);
     const double cv = widen(cur[off]);
     sc[idx] = cv;
-    if constexpr (sizeof(T) == 4)
-      sb[idx] = widen(fmaf(2.0f, cur[off], -prev[off]));  // as the FP32 update forms Cbar
-    else
-      sb[idx] = fma(2.0, cv, -prev[off]);  // one FP64 instruction (2 cv - p as two adds is two)
+    // cbar_out (the step's C^{n+1} buffer, non-null for the full-grid step): the tile's own Cbar,
+    // which the fused update then reads instead of forming it again from C^n and C^{n-1}
+    const bool own = cbar_out && r >= 2 && r < kTY + 2 && c >= 2 && c < kTX + 2;
+    if constexpr (sizeof(T) == 4) {
+      const float cb = fmaf(2.0f, cur[off], -prev[off]);  // as the FP32 update forms Cbar
+      sb[idx] = widen(cb);
+      if (own) cbar_out[gy * n + gx] = cb;
+    } else {
+      const double cb = fma(2.0, cv, -prev[off]);  // one FP64 instruction (2 cv - p as two adds is two)
+      sb[idx] = cb;
+      if (own) cbar_out[gy * n + gx] = cb;
+    }
   }
   __syncthreads();
   __shared__ __align__(16) unsigned s_red[kThreads / 32];
@@ -502,25 +510,23 @@ __global__ void __launch_bounds__(kSolveThreads)
     if constexpr (MODE == 0) {
       store_batch<CONTIG>(w_out, base + k0 * es, es, x);
     } else {
+      // next holds Cbar = 2 C^n - C^{n-1}, written there by this step's right-hand side kernel
+      // (FP32 storage: formed in FP32, one rounding of the size of the result's own); C^{n+1} =
+      // Cbar + v replaces it element by element
       if constexpr (sizeof(T) == 4) {
-        // FP32 storage: Cbar = 2 C^n - C^{n-1} in FP32 arithmetic (one rounding, of the size of
-        // the result's own), widened exactly; one FP64 add of x, then the round-to-nearest-even
-        // narrowing on the integer pipe (this kernel is FP64-bound, and a conversion instruction
-        // would take an FP64 issue slot)
+        // one FP64 add of x, then the round-to-nearest-even narrowing on the integer pipe (this
+        // kernel is FP64-bound, and a conversion instruction would take an FP64 issue slot)
         float cb[kU];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) cb[u] = fmaf(2.0f, cur[base + (k0 + u) * es], -prev[base + (k0 + u) * es]);
+        for (int u = 0; u < kU; ++u) cb[u] = next[base + (k0 + u) * es];
 #pragma unroll
         for (int u = 0; u < kU; ++u) next[base + (k0 + u) * es] = narrow_rn(widen(cb[u]) + x[u]);
       } else {
-        double c[kU], pv[kU];
+        double cb[kU];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-          c[u] = cur[base + (k0 + u) * es];
-          pv[u] = prev[base + (k0 + u) * es];
-        }
+        for (int u = 0; u < kU; ++u) cb[u] = next[base + (k0 + u) * es];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) store_as<T>(next + base + (k0 + u) * es, fma(2.0, c[u], -pv[u]) + x[u]);
+        for (int u = 0; u < kU; ++u) store_as<T>(next + base + (k0 + u) * es, cb[u] + x[u]);
       }
     }
   }
@@ -785,9 +791,10 @@ int launch_rhs(CHPlan* p, bool with_rhs, double* partials, cudaStream_t s) {
   const T* cur = static_cast<const T*>(p->field[p->icur]);
   const T* prev = static_cast<const T*>(p->field[p->iprev]);
   double* rhs = with_rhs ? p->A : nullptr;
+  T* cbar = with_rhs ? static_cast<T*>(p->field[p->inext]) : nullptr;
   k_ch_rhs<T><<<grid, kThreads, rhs_smem_bytes(), s>>>(cur, prev, rhs, p->n, p->alpha, p->a,
                                                         0.5 * p->gamma / (p->h * p->h), partials, p->noflux,
-                                                        ixd::ixi_round51(-p->a), 0);
+                                                        ixd::ixi_round51(-p->a), 0, cbar);
   CS_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return CS_OK;
@@ -1448,11 +1455,13 @@ int ch_band_rhs(CHBand* b, const void* prev, const void* cur, double* rhs, doubl
   if (b->storage == CS_F32)
     k_ch_rhs<float><<<grid, kThreads, rhs_smem_bytes(), s>>>(static_cast<const float*>(cur), static_cast<const float*>(prev),
                                                               rhs, b->n, b->alpha, b->a, hg, part, b->noflux,
-                                                              ixd::ixi_round51(-b->a), 1);
+                                                              ixd::ixi_round51(-b->a), 1,
+                                                              nullptr);
   else
     k_ch_rhs<double><<<grid, kThreads, rhs_smem_bytes(), s>>>(static_cast<const double*>(cur), static_cast<const double*>(prev),
                                                                rhs, b->n, b->alpha, b->a, hg, part, b->noflux,
-                                                               ixd::ixi_round51(-b->a), 1);
+                                                               ixd::ixi_round51(-b->a), 1,
+                                                              nullptr);
   CS_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   if (sums) {
