@@ -108,6 +108,104 @@ __device__ __forceinline__ float narrow_rn(double x) {
   return __uint_as_float(r);
 }
 
+// ---- the cubic term of Z on the Laplacian's digit grid ----------------------------------------
+// Z = alpha N - a Lap(Cbar), N = u^3 - u (u = C^n).  Lap(Cbar) is an exact digit sum T on the grid
+// 2^(G-56) of Cbar's tile, combined as (T' + Q) c 2^(G-48) with T' = round(T / 2^8) and c = -a
+// rounded to 51 bits (ixi_combine<28>).  N joins it as the integer Q = round(alpha N / (c 2^(G-48))),
+// formed in double-float arithmetic on the FP32 pipe, two points per packed instruction; Z then
+// costs the one FP64 FMA of the combination instead of four FP64 operations.  Q is rounded to the
+// grid unit c 2^(G-48) that T' already has, so Z's error stays of the size of the Laplacian's own
+// rounding.  Used where alpha / |c| <= 2^-6 (the host passes a zero inverse otherwise), which keeps
+// the double-float error of Q (<= 2^-46 |alpha N| plus 2^-47 |u| |3u^2 - 1| alpha / |c| in grid
+// units) below a tenth of a unit; points outside the ranges below take the FP64 formula.
+struct CubicInv { float hi, lo; };  // alpha / c as a float pair, or zero: the FP64 formula
+
+inline CubicInv cubic_inv(double alpha, double c) {
+  const double r = alpha / c;
+  if (!(std::fabs(r) <= 0.015625) || r == 0.0) return {0.0f, 0.0f};
+  const float hi = static_cast<float>(r);
+  return {hi, static_cast<float>(r - static_cast<double>(hi))};
+}
+
+// (alpha / c) 2^(48 - G) as a float pair, by exponent arithmetic on the host's pair; false when
+// the inverse is zero or the scaled pair would leave the normal float range.
+__device__ __forceinline__ bool cubic_scaled(CubicInv inv, int tile_e, float& ih, float& il) {
+  const int sh = 1070 - tile_e;  // 48 - G, G = tile_e - 1022
+  const int eh = static_cast<int>((__float_as_uint(inv.hi) >> 23) & 0xffu) + sh;
+  if (inv.hi == 0.0f || eh < 25 || eh > 254) return false;
+  ih = __uint_as_float(__float_as_uint(inv.hi) + (static_cast<uint32_t>(sh) << 23));
+  const int el = static_cast<int>((__float_as_uint(inv.lo) >> 23) & 0xffu) + sh;
+  il = (inv.lo == 0.0f || el < 1) ? 0.0f : __uint_as_float(__float_as_uint(inv.lo) + (static_cast<uint32_t>(sh) << 23));
+  return true;
+}
+
+// u as the float pair h + l with |u - h - l| < 2^-47 |u|, by integer operations alone: h holds u's
+// sign, exponent and leading 24 significand bits, l the next 24 bits.  Valid for biased exponents
+// e in [944, 1150]; e = 0 (zero or subnormal) gives h = l = 0.
+__device__ __forceinline__ void split_hl(double u, float& h, float& l) {
+  const uint32_t hw = static_cast<uint32_t>(__double2hiint(u)), lw = static_cast<uint32_t>(__double2loint(u));
+  // hw << 3 | lw >> 29 puts the exponent's low 8 bits over the top 23 significand bits; with the
+  // exponent's bit 7 flipped first those 8 bits read e - 896, the float exponent (e in [897, 1150])
+  const uint32_t top = __funnelshift_l(lw, hw ^ 0x08000000u, 3);
+  const uint32_t hb = (top & 0x7fffffffu) | (hw & 0x80000000u);
+  // the next 24 bits as an exact integer times 2^(e - 1070), with u's sign: float exponent e - 943
+  const float x = __uint2float_rn((lw >> 5) & 0xffffffu);
+  const float sc = __uint_as_float((hb & 0xff800000u) - (47u << 23));
+  const bool zero = (hw & 0x7ff00000u) == 0u;
+  h = zero ? 0.0f : __uint_as_float(hb);
+  l = zero ? 0.0f : __fmul_rn(x, sc);
+}
+
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2s(-1.0f), a); }
+
+// Q for two points u = h + l (packed lanes), returned as qa 2^20 + qb, the split ixi_combine<28>
+// takes, with qh (|qh| < 2^43 is required; the caller checks it).  Steps, all error-free apart from
+// the dropped l^2 and a l terms (2^-48 relative) and the roundings of the small parts:
+//   u^2 = A + a2:   nA = -h h rounded, a2 = (h h + nA) + 2 h l
+//   u^3 = s3 + b:   ns3 = nA h rounded (= -s3), b = (A h - s3) + A l + a2 h
+//   -N = u - u^3 = (ns3 + h) + (l - b) = S + lo (TwoSum of ns3 and h)
+//   R = -N (alpha / c) 2^(48 - G) = qh + ql (the product's error by FMA, renormalised by Fast2Sum)
+// and Q = -round(R) in two FP32 rounding shifts: 1.5 2^44 takes qh to k 2^21 (k in the low
+// mantissa bits), 1.5 2^23 rounds the rest (qh - k 2^21 + ql, |rest| < 2^21) to k2; Q = -(k 2^21 + k2).
+__device__ __forceinline__ void cubic_q2(float2 h, float2 l, float ih, float il, int2& qa, int2& qb, float2& qh) {
+  const float2 nh = __fmul2_rn(h, f2s(-1.0f)), nl = __fmul2_rn(l, f2s(-1.0f));
+  const float2 nA = __fmul2_rn(nh, h);
+  const float2 a2 = __ffma2_rn(__fadd2_rn(h, h), l, __ffma2_rn(h, h, nA));
+  const float2 ns3 = __fmul2_rn(nA, h);
+  float2 b = __ffma2_rn(nA, nh, ns3);
+  b = __ffma2_rn(nA, nl, b);
+  b = __ffma2_rn(a2, h, b);
+  const float2 S = __fadd2_rn(ns3, h);
+  const float2 bb = sub2(S, ns3);
+  const float2 t = __fadd2_rn(sub2(ns3, sub2(S, bb)), sub2(h, bb));
+  const float2 lo = __fadd2_rn(sub2(t, b), l);
+  const float2 np = __fmul2_rn(S, f2s(-ih));
+  float2 pl = __ffma2_rn(S, f2s(ih), np);
+  pl = __ffma2_rn(lo, f2s(ih), pl);
+  pl = __ffma2_rn(S, f2s(il), pl);
+  qh = sub2(pl, np);
+  const float2 ql = sub2(pl, __fadd2_rn(qh, np));
+  constexpr float M1 = 26388279066624.0f, M2 = 12582912.0f;  // 1.5 2^44, 1.5 2^23
+  const float2 t1 = __fadd2_rn(qh, f2s(M1));
+  const float2 rest = __fadd2_rn(sub2(qh, sub2(t1, f2s(M1))), ql);
+  const float2 t2 = __fadd2_rn(rest, f2s(M2));
+  qa = make_int2(2 * static_cast<int>(__float_as_uint(M1) - __float_as_uint(t1.x)),
+                 2 * static_cast<int>(__float_as_uint(M1) - __float_as_uint(t1.y)));
+  qb = make_int2(static_cast<int>(__float_as_uint(M2) - __float_as_uint(t2.x)),
+                 static_cast<int>(__float_as_uint(M2) - __float_as_uint(t2.y)));
+}
+
+// Whether a point may take the digit form: u zero or with biased exponent in [944, tile_e + 1]
+// (|u| < 2^(G+1), which bounds the double-float error of Q), |qh| < 2^43 (the rounding shifts'
+// range; false for inf and nan), and the Laplacian's high digit sum |S0| <= 2^31 - 2^24, so that
+// |T' + Q| < 2^51 as the combination requires.
+__device__ __forceinline__ bool cubic_ok(double u, int tile_e, float qh, int s0) {
+  const int e = static_cast<int>((static_cast<uint32_t>(__double2hiint(u)) >> 20) & 0x7ffu);
+  return (e == 0 || (e >= 944 && e <= tile_e + 1)) && fabsf(qh) < 8796093022208.0f &&
+         abs(s0) <= 2147483647 - 16777215;
+}
+
 template <typename T> __device__ __forceinline__ void store_as(T* p, double v);
 template <> __device__ __forceinline__ void store_as<double>(double* p, double v) { *p = v; }
 template <> __device__ __forceinline__ void store_as<float>(float* p, double v) { *p = narrow_rn(v); }
@@ -153,7 +251,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_ch_rhs(const T* __restrict__ cur, const T* __restrict__ prev, double* __restrict__ rhs, int64_t n,
              double alpha, double a, double half_gamma_over_h2, double* __restrict__ partials, int noflux,
-             double am51, int band, T* __restrict__ cbar_out) {
+             double am51, CubicInv cinv, int band, T* __restrict__ cbar_out) {
   constexpr int HR = kTY + 4, HC = kTX + 4;  // halo-2 tiles
   constexpr int ZR = kTY + 2, ZC = kTX + 2;  // halo-1 tile
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -202,9 +300,11 @@ __global__ void __launch_bounds__(kThreads)
     // hold every bit of a value within a factor 8 of its tile's largest, so neighbouring tiles,
     // which evaluate Z on each other's border, agree on it to 2^-56 of the tile's scale and the sum
     // of the Laplacian over the grid stays zero to that level: mass is conserved), each scaled with
-    // one FP64 FMA; the first one's scaling carries -a, so the FP64 pipe keeps only Cbar, u u,
-    // N, Z, the two scalings, C^n - C^{n-1} and the final combination (8.6 FP64 operations per
-    // point).  A tile whose values leave the digit range takes the FP64 formula for that Laplacian.
+    // one FP64 FMA; the first one's scaling carries -a, and the cubic term N joins its digit sum
+    // as an integer (cubic_q2), so the FP64 pipe keeps only Cbar, Z, the second scaling,
+    // C^n - C^{n-1} and the final combination (5.3 FP64 operations per point).  A tile whose values
+    // leave the digit range takes the FP64 formula for that Laplacian; a warp with a point outside
+    // cubic_ok's ranges forms N in FP64.
     // the one-FMA scaling of a digit sum by m 2^(G - 56) (ixi_consts); false: the FP64 formula
     double* cb = sb;
     double* zt = sb;  // Z takes Cbar's place (held in registers until every thread has read Cbar)
@@ -213,28 +313,68 @@ __global__ void __launch_bounds__(kThreads)
       const int te = static_cast<int>(ixd::ix_tile_max_hi<kThreads, HR * HC>(cb, s_red) >> 20);
       uint32_t w[4];
       const bool dig = ixd::ixi_consts<28>(am51, -1.5 * am51, te, w);  // uniform over the block
+      float ih = 0.0f, il = 0.0f;
+      const bool cub = dig && te != 0 && cubic_scaled(cinv, te, ih, il);  // uniform too
       if (dig) {
         ixd::ixi_split_tile<kThreads, HR * HC, 28>(cb, te);
         __syncthreads();
       }
       constexpr int NZ = (ZR * ZC + kThreads - 1) / kThreads;
       double zv[NZ];
+      // Z point k of this thread: the Laplacian's digit sums and u (a point past the tile reads
+      // the first one; its result is not stored)
+      auto zpoint = [&](int k, int& q0, int& q1, double& u) {
+        int idx = threadIdx.x + k * kThreads;
+        if (idx >= ZR * ZC) idx = 0;
+        const int r = idx / ZC, c = idx - r * ZC;
+        const int hidx = (r + 1) * HC + (c + 1);
+        lap5_digits(cb, hidx, HC, q0, q1);
+        u = cn[hidx];
+      };
+      if (cub) {
 #pragma unroll
-      for (int k = 0; k < NZ; ++k) {
-        const int idx = threadIdx.x + k * kThreads;
-        if (k + 1 < NZ || idx < ZR * ZC) {
-          const int r = idx / ZC, c = idx - r * ZC;
-          const int hidx = (r + 1) * HC + (c + 1);
-          double lap_a;  // -a * Laplacian(Cbar)
-          if (dig) {
-            int q0, q1;
-            lap5_digits(cb, hidx, HC, q0, q1);
-            lap_a = ixd::ixi_combine<28>(q0, q1, w);
+        for (int k = 0; k < NZ; k += 2) {  // two points per packed cubic term
+          const int k1 = k + 1 < NZ ? k + 1 : k;
+          int a0, a1, b0, b1;
+          double u0, u1;
+          zpoint(k, a0, a1, u0);
+          zpoint(k1, b0, b1, u1);
+          float h0, l0, h1, l1;
+          split_hl(u0, h0, l0);
+          split_hl(u1, h1, l1);
+          int2 qa, qb;
+          float2 qh;
+          cubic_q2(make_float2(h0, h1), make_float2(l0, l1), ih, il, qa, qb, qh);
+          const bool ok = cubic_ok(u0, te, qh.x, a0) && cubic_ok(u1, te, qh.y, b0);
+          double z0, z1;
+          if (__all_sync(0xffffffffu, ok)) {
+            z0 = ixd::ixi_combine<28>(a0, a1, w, qa.x, qb.x);
+            z1 = ixd::ixi_combine<28>(b0, b1, w, qa.y, qb.y);
           } else {
-            lap_a = -a * lap5(cb, hidx, HC);
+            z0 = fma(alpha, fma(u0 * u0, u0, -u0), ixd::ixi_combine<28>(a0, a1, w));
+            z1 = fma(alpha, fma(u1 * u1, u1, -u1), ixd::ixi_combine<28>(b0, b1, w));
           }
-          const double u = cn[hidx];
-          zv[k] = fma(alpha, fma(u * u, u, -u), lap_a);
+          zv[k] = z0;
+          if (k + 1 < NZ) zv[k + 1] = z1;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < NZ; ++k) {
+          const int idx = threadIdx.x + k * kThreads;
+          if (k + 1 < NZ || idx < ZR * ZC) {
+            const int r = idx / ZC, c = idx - r * ZC;
+            const int hidx = (r + 1) * HC + (c + 1);
+            double lap_a;  // -a * Laplacian(Cbar)
+            if (dig) {
+              int q0, q1;
+              lap5_digits(cb, hidx, HC, q0, q1);
+              lap_a = ixd::ixi_combine<28>(q0, q1, w);
+            } else {
+              lap_a = -a * lap5(cb, hidx, HC);
+            }
+            const double u = cn[hidx];
+            zv[k] = fma(alpha, fma(u * u, u, -u), lap_a);
+          }
         }
       }
       __syncthreads();  // every thread is done with Cbar
@@ -794,7 +934,8 @@ int launch_rhs(CHPlan* p, bool with_rhs, double* partials, cudaStream_t s) {
   T* cbar = with_rhs ? static_cast<T*>(p->field[p->inext]) : nullptr;
   k_ch_rhs<T><<<grid, kThreads, rhs_smem_bytes(), s>>>(cur, prev, rhs, p->n, p->alpha, p->a,
                                                         0.5 * p->gamma / (p->h * p->h), partials, p->noflux,
-                                                        ixd::ixi_round51(-p->a), 0, cbar);
+                                                        ixd::ixi_round51(-p->a),
+                                                        cubic_inv(p->alpha, ixd::ixi_round51(-p->a)), 0, cbar);
   CS_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return CS_OK;
@@ -1455,13 +1596,13 @@ int ch_band_rhs(CHBand* b, const void* prev, const void* cur, double* rhs, doubl
   if (b->storage == CS_F32)
     k_ch_rhs<float><<<grid, kThreads, rhs_smem_bytes(), s>>>(static_cast<const float*>(cur), static_cast<const float*>(prev),
                                                               rhs, b->n, b->alpha, b->a, hg, part, b->noflux,
-                                                              ixd::ixi_round51(-b->a), 1,
-                                                              nullptr);
+                                                              ixd::ixi_round51(-b->a),
+                                                              cubic_inv(b->alpha, ixd::ixi_round51(-b->a)), 1, nullptr);
   else
     k_ch_rhs<double><<<grid, kThreads, rhs_smem_bytes(), s>>>(static_cast<const double*>(cur), static_cast<const double*>(prev),
                                                                rhs, b->n, b->alpha, b->a, hg, part, b->noflux,
-                                                               ixd::ixi_round51(-b->a), 1,
-                                                              nullptr);
+                                                               ixd::ixi_round51(-b->a),
+                                                               cubic_inv(b->alpha, ixd::ixi_round51(-b->a)), 1, nullptr);
   CS_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   if (sums) {

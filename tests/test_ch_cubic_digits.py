@@ -1,0 +1,200 @@
+"""The Cahn-Hilliard right-hand side's Z = alpha (u^3 - u) - a Lap(Cbar) with the cubic term joined
+to the Laplacian's digit sum (Sec. 5.1, the factored RHS), emulated bit by bit on the CPU: the split
+of a double u into the float pair h + l by integer operations, the packed double-float steps that
+give the integer Q = round(alpha (u^3 - u) / (c 2^(G-48))), and the one-FMA combination of the
+28-bit digit sum with Q.  Each step is written from its definition (IEEE round-to-nearest-even,
+one rounding per FMA, integer shifts) and checked against exact rational arithmetic:
+
+* h + l is u truncated to 48 significant bits (|u - h - l| < 2^-47 |u|), zero for zero;
+* Q is within 0.6 of a unit U = |c| 2^(G-48) of the exact quotient (0.5 for the rounding, the rest
+  the double-float error) wherever the kernel takes the digit form (alpha / |c| <= 2^-6, u in the
+  exponent window, |qh| < 2^43);
+* Z is within 2.2 U + 2^-52 |Z| of alpha (u^3 - u) - a Lap(Cbar) with the unrounded a: the digits'
+  truncation (U / 32), the sum's rounding (U / 2), Q (0.6 U), a rounded to 51 bits (U) and the
+  FMA's own rounding; the FP64 formula's own bound differs only by Q's 0.6 U."""
+import math
+from fractions import Fraction as Fr
+
+import numpy as np
+import pytest
+
+from test_digit_arithmetic import (dbits, fbits, ffrom, f32, fmul, fadd, ffma, fsub, round51, split,
+                                   consts, combine, tile_exp)
+
+M1, M2 = f32(1.5 * 2 ** 44), f32(1.5 * 2 ** 23)
+
+
+def ch_params(n: int, gamma: float = 0.01, D: float = 1.0):
+    """alpha and a of the scheme on [0, 2 pi)^2 with dt = 0.1 h (the paper's setup)."""
+    h = 2 * math.pi / n
+    dt = 0.1 * h
+    return (2.0 / 3.0) * D * dt / (h * h), (2.0 / 3.0) * D * gamma * dt / h ** 4
+
+
+def cubic_inv(alpha: float, c: float):
+    r = alpha / c
+    if not abs(r) <= 2.0 ** -6 or r == 0.0:
+        return None
+    hi = f32(r)
+    return hi, f32(r - float(hi))
+
+
+def split_hl(u: float):
+    b = dbits(u)
+    hw, lw = b >> 32, b & 0xFFFFFFFF
+    top = ((((hw ^ 0x08000000) << 3) | (lw >> 29)) & 0xFFFFFFFF)
+    hb = (top & 0x7FFFFFFF) | (hw & 0x80000000)
+    x = f32((lw >> 5) & 0xFFFFFF)
+    sc = ffrom(((hb & 0xFF800000) - (47 << 23)) & 0xFFFFFFFF)
+    if hw & 0x7FF00000 == 0:
+        return f32(0.0), f32(0.0)
+    return ffrom(hb), fmul(x, sc)
+
+
+def scaled_inv(inv, tile_e: int):
+    hi, lo = inv
+    sh = 1070 - tile_e
+    eh = ((fbits(hi) >> 23) & 0xFF) + sh
+    if eh < 25 or eh > 254:
+        return None
+    ih = ffrom(fbits(hi) + (sh << 23))
+    el = ((fbits(lo) >> 23) & 0xFF) + sh
+    il = f32(0.0) if lo == 0 or el < 1 else ffrom(fbits(lo) + (sh << 23))
+    return ih, il
+
+
+def cubic_q(h, l, ih, il):
+    """One lane of the packed steps, in the kernel's order."""
+    nh, nl = fmul(h, f32(-1.0)), fmul(l, f32(-1.0))
+    nA = fmul(nh, h)
+    a2 = ffma(fadd(h, h), l, ffma(h, h, nA))
+    ns3 = fmul(nA, h)
+    b = ffma(nA, nh, ns3)
+    b = ffma(nA, nl, b)
+    b = ffma(a2, h, b)
+    S = fadd(ns3, h)
+    bb = fsub(S, ns3)
+    t = fadd(fsub(ns3, fsub(S, bb)), fsub(h, bb))
+    lo = fadd(fsub(t, b), l)
+    np_ = fmul(S, -ih)
+    pl = ffma(S, ih, np_)
+    pl = ffma(lo, ih, pl)
+    pl = ffma(S, il, pl)
+    qh = fsub(pl, np_)
+    ql = fsub(pl, fadd(qh, np_))
+    t1 = fadd(qh, M1)
+    rest = fadd(fsub(qh, fsub(t1, M1)), ql)
+    t2 = fadd(rest, M2)
+    return 2 * (fbits(M1) - fbits(t1)), fbits(M2) - fbits(t2), qh
+
+
+def cubic_ok(u: float, tile_e: int, qh, s0: int) -> bool:
+    e = (dbits(u) >> 52) & 0x7FF
+    return (e == 0 or 944 <= e <= tile_e + 1) and abs(float(qh)) < 2.0 ** 43 and abs(s0) <= 2 ** 31 - 1 - (2 ** 24 - 1)
+
+
+def test_split_is_u_truncated_to_48_bits():
+    rng = np.random.default_rng(5)
+    for k in range(2000):
+        e = int(rng.integers(944 - 1023, 1150 - 1023))
+        u = float(rng.uniform(1, 2) * 2.0 ** e * (1 if k % 2 else -1))
+        h, l = split_hl(u)
+        b = dbits(u)
+        trunc = dfrom_trunc(b)
+        assert Fr(float(h)) + Fr(float(l)) == trunc, (u, h, l)
+        assert abs(Fr(u) - trunc) < Fr(2) ** -47 * abs(Fr(u))
+        assert abs(Fr(float(h))) <= abs(Fr(u)) and (float(h) == 0 or np.sign(float(h)) == np.sign(u))
+    for z in (0.0, -0.0, 5e-324):
+        assert split_hl(z) == (0.0, 0.0)
+
+
+def dfrom_trunc(b: int) -> Fr:
+    """The double with bits b, its lowest 5 significand bits cleared (48 significant bits)."""
+    import struct
+    return Fr(struct.unpack("<d", struct.pack("<Q", b & ~0x1F))[0])
+
+
+@pytest.mark.parametrize("n", [512, 1024, 4096, 8192])
+def test_cubic_q_within_0p6_unit(n):
+    alpha, a = ch_params(n)
+    c = round51(-a)
+    inv = cubic_inv(alpha, c)
+    assert inv is not None
+    rng = np.random.default_rng(n)
+    worst, cases = Fr(0), 0
+    while cases < 300:
+        mag = float(rng.uniform(0.02, 1.6))  # the tile's largest |Cbar|
+        te = tile_exp([mag])
+        G = te - 1022
+        k = scaled_inv(inv, te)
+        assert k is not None
+        ih, il = k
+        mode = cases % 4
+        if mode == 0:
+            u = rng.uniform(-1.2, 1.2) * min(mag, 1.0)
+        elif mode == 1:  # near the wells and the extremum of u^3 - u, where the terms cancel
+            u = (1.0, math.sqrt(1 / 3))[int(rng.integers(0, 2))] * (1 + rng.uniform(-1e-6, 1e-6)) * (1 if rng.random() < 0.5 else -1)
+        elif mode == 2:  # small values
+            u = rng.uniform(-1, 1) * 2.0 ** -int(rng.integers(5, 70))
+        else:
+            u = 0.0
+        u = float(u)
+        h, l = split_hl(u)
+        qa, qb, qh = cubic_q(h, l, ih, il)
+        if not cubic_ok(u, te, qh, 0):
+            continue
+        U = Fr(c) * Fr(2) ** (G - 48)
+        exact = Fr(alpha) * (Fr(u) ** 3 - Fr(u)) / U
+        err = abs(Fr(qa * 2 ** 20 + qb) - exact)
+        worst = max(worst, err)
+        assert err <= Fr(6, 10), (n, u, float(err))
+        cases += 1
+    print(f"[ch cubic] n={n}: worst |Q - alpha N / U| = {float(worst):.4f} units")
+
+
+def test_inverse_is_zero_above_2_pow_minus_6():
+    # alpha / a = h^2 / gamma: the digit form serves n >= 512 at gamma = 0.01, and not n = 256
+    for n, ok in ((256, False), (512, True), (4096, True)):
+        alpha, a = ch_params(n)
+        assert (cubic_inv(alpha, round51(-a)) is not None) == ok
+
+
+@pytest.mark.parametrize("n", [512, 1024, 4096])
+def test_z_within_bound(n):
+    """Z at the centre of a 5-point Laplacian of random Cbar values: digits of Cbar on its tile's
+    grid, the 28-bit digit sum, Q joined as (qa, qb), one FMA; against exact arithmetic."""
+    alpha, a = ch_params(n)
+    c = round51(-a)
+    inv = cubic_inv(alpha, c)
+    w = [1, 1, -4, 1, 1]
+    rng = np.random.default_rng(7 + n)
+    worst, cases = 0.0, 0
+    while cases < 150:
+        mag = float(rng.uniform(0.05, 1.2))
+        cb = [float(v) for v in rng.uniform(-1, 1, 5) * mag]
+        if cases % 3 == 0:  # a smooth patch: the Laplacian is small against its terms
+            base, slope = float(rng.uniform(-1, 1) * mag), float(rng.uniform(-1e-3, 1e-3))
+            cb = [base + slope * d for d in (-1.0, 0.0, 0.0, 0.0, 1.0)]
+            cb[2] = base + float(rng.uniform(-1e-6, 1e-6))
+        u = float(cb[2] * (1 + rng.uniform(-0.1, 0.1)))  # C^n, close to Cbar
+        te = tile_exp(cb)
+        G = te - 1022
+        sc, cs = consts(c, te, 28)
+        d = [split(v, te, 28) for v in cb]
+        S0 = sum(k * x for k, (x, _) in zip(w, d))
+        S1 = sum(k * y for k, (_, y) in zip(w, d))
+        ih, il = scaled_inv(inv, te)
+        h, l = split_hl(u)
+        qa, qb, qh = cubic_q(h, l, ih, il)
+        if not cubic_ok(u, te, qh, S0):
+            continue
+        z = combine(S0, S1, sc, cs, 28, qa, qb)
+        lap = sum(k * Fr(v) for k, v in zip(w, cb))
+        exact = Fr(alpha) * (Fr(u) ** 3 - Fr(u)) - Fr(a) * lap
+        U = abs(Fr(c)) * Fr(2) ** (G - 48)
+        err = abs(Fr(z) - exact)
+        bound = Fr(22, 10) * U + Fr(2) ** -52 * abs(Fr(z))
+        worst = max(worst, float(err / U))
+        assert err <= bound, (n, float(err / U))
+        cases += 1
+    print(f"[ch cubic] n={n}: worst |Z - exact| = {worst:.3f} units")
