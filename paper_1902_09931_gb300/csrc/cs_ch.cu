@@ -206,6 +206,18 @@ __device__ __forceinline__ bool cubic_ok(double u, int tile_e, float qh, int s0)
          abs(s0) <= 2147483647 - 16777215;
 }
 
+// 2^k as a double (k in the normal range), by its bit pattern
+__device__ __forceinline__ double pow2d(int k) { return __longlong_as_double(static_cast<long long>(k + 1023) << 52); }
+
+// a 128-bit integer as a double, within 2^-52 of its value: magnitude in two 64-bit halves
+__device__ __forceinline__ double i128_to_double(__int128 v) {
+  const bool neg = v < 0;
+  const unsigned __int128 a = neg ? static_cast<unsigned __int128>(-v) : static_cast<unsigned __int128>(v);
+  const double r = fma(__ull2double_rn(static_cast<unsigned long long>(a >> 64)), 18446744073709551616.0,
+                       __ull2double_rn(static_cast<unsigned long long>(a)));
+  return neg ? -r : r;
+}
+
 template <typename T> __device__ __forceinline__ void store_as(T* p, double v);
 template <> __device__ __forceinline__ void store_as<double>(double* p, double v) { *p = v; }
 template <> __device__ __forceinline__ void store_as<float>(float* p, double v) { *p = narrow_rn(v); }
@@ -434,25 +446,58 @@ __global__ void __launch_bounds__(kThreads)
       }
       __syncthreads();
     }
-    double m = 0.0, ew = 0.0, eg = 0.0;
-    for (int idx = threadIdx.x; idx < kTY * kTX; idx += kThreads) {
-      const int r = idx / kTX, c = idx - r * kTX;
-      const int hidx = (r + 2) * HC + (c + 2);
-      const double u = sc[hidx];
-      double lap;
-      if (dig) {
+    double m = 0.0, e;
+    const int G = te - 1022;  // the tile's values lie below 2^G
+    if (dig && G >= -3 && G <= 3) {
+      // Each thread's share in exact integer arithmetic on the digit grid, u = U 2^(G-56) with
+      // U = d0 2^28 + d1 (every bit of a value within a factor 8 of the tile's largest) and
+      // Lap5(u) = L 2^(G-56), L the exact digit sum: sum U (< 2^59), sum U L (< 2^118) and
+      // sum W^2 with W = (U^2 - 2^(112-2G)) 2^-58 rounded (u^2 - 1 in units of 2^(2G-54), |W| < 2^61;
+      // sum < 2^125), then one conversion each to FP64 for the block's FP64 reduction.  No FP64
+      // operation per point (the formula below takes 5).
+      long long sm = 0;
+      __int128 sg = 0, sw = 0;
+      const __int128 K = static_cast<__int128>(1) << (112 - 2 * G);
+      const __int128 half = static_cast<__int128>(1) << 57;
+      const int2* dg = reinterpret_cast<const int2*>(sb);
+      for (int idx = threadIdx.x; idx < kTY * kTX; idx += kThreads) {
+        const int r = idx / kTX, c = idx - r * kTX;
+        const int hidx = (r + 2) * HC + (c + 2);
+        const int2 d = dg[hidx];
+        const long long U = static_cast<long long>(d.x) * (1ll << 28) + d.y;
         int q0, q1;
         lap5_digits(sb, hidx, HC, q0, q1);
-        lap = ixd::ixi_combine<28>(q0, q1, w4);
-      } else {
-        lap = lap5(sc, hidx, HC);
+        const long long L = static_cast<long long>(q0) * (1ll << 28) + q1;
+        sm += U;
+        sg += static_cast<__int128>(U) * L;
+        const long long W = static_cast<long long>((static_cast<__int128>(U) * U - K + half) >> 58);
+        sw += static_cast<__int128>(W) * W;
       }
-      const double w = fma(u, u, -1.0);
-      m += u;
-      ew = fma(w, w, ew);
-      eg = fma(u, lap, eg);
+      m = static_cast<double>(sm) * pow2d(G - 56);
+      const double ew = i128_to_double(sw) * pow2d(4 * G - 108);
+      const double eg = i128_to_double(sg) * pow2d(2 * G - 112);
+      e = fma(0.25, ew, -half_gamma_over_h2 * eg);
+    } else {
+      double ew = 0.0, eg = 0.0;
+      for (int idx = threadIdx.x; idx < kTY * kTX; idx += kThreads) {
+        const int r = idx / kTX, c = idx - r * kTX;
+        const int hidx = (r + 2) * HC + (c + 2);
+        const double u = sc[hidx];
+        double lap;
+        if (dig) {
+          int q0, q1;
+          lap5_digits(sb, hidx, HC, q0, q1);
+          lap = ixd::ixi_combine<28>(q0, q1, w4);
+        } else {
+          lap = lap5(sc, hidx, HC);
+        }
+        const double w = fma(u, u, -1.0);
+        m += u;
+        ew = fma(w, w, ew);
+        eg = fma(u, lap, eg);
+      }
+      e = fma(0.25, ew, -half_gamma_over_h2 * eg);
     }
-    const double e = fma(0.25, ew, -half_gamma_over_h2 * eg);
     block_reduce2<T>(m, e, partials + 2 * (static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x));
   }
 }
@@ -1118,9 +1163,14 @@ int ch_step(CHPlan* p, int64_t nsteps, double* h_mass, double* h_energy, cudaStr
       rotate(p); rotate(p); rotate(p);
       nsteps -= 3;
     }
-    if (nsteps == 0) return CS_OK;
+    for (; nsteps > 0; --nsteps) {
+      int rc = p->storage == CS_F32 ? launch_step<float>(p, nullptr, s) : launch_step<double>(p, nullptr, s);
+      if (rc != CS_OK) return rc;
+      rotate(p);
+    }
+    return CS_OK;
   }
-  if (want && p->inv_cap < nsteps) {
+  if (p->inv_cap < nsteps) {
     if (p->inv) cudaFree(p->inv);
     p->inv = nullptr;
     p->inv_cap = 0;
@@ -1130,7 +1180,7 @@ int ch_step(CHPlan* p, int64_t nsteps, double* h_mass, double* h_energy, cudaStr
   }
   for (int64_t st = 0; st < nsteps; ++st) {
     // the RHS kernel of step st reads C^n = the field after step st-1: reduce it on the way
-    double* part = (want && st > 0) ? p->partials : nullptr;
+    double* part = st > 0 ? p->partials : nullptr;
     int rc = p->storage == CS_F32 ? launch_step<float>(p, part, s) : launch_step<double>(p, part, s);
     if (rc != CS_OK) return rc;
     if (part) {
@@ -1141,7 +1191,6 @@ int ch_step(CHPlan* p, int64_t nsteps, double* h_mass, double* h_energy, cudaStr
     }
     rotate(p);
   }
-  if (!want) return CS_OK;
   int rc = reduce_current(p, p->inv + 2 * (nsteps - 1), s);
   if (rc != CS_OK) return rc;
   std::vector<double> h(static_cast<size_t>(2) * nsteps);

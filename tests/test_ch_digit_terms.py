@@ -11,7 +11,14 @@ one rounding per FMA, integer shifts) and checked against exact rational arithme
   exponent window, |qh| < 2^43);
 * Z is within 2.2 U + 2^-52 |Z| of alpha (u^3 - u) - a Lap(Cbar) with the unrounded a: the digits'
   truncation (U / 32), the sum's rounding (U / 2), Q (0.6 U), a rounded to 51 bits (U) and the
-  FMA's own rounding; the FP64 formula's own bound differs only by Q's 0.6 U."""
+  FMA's own rounding; the FP64 formula's own bound differs only by Q's 0.6 U.
+
+And the invariants' per-thread sums (Eq. 1's mass and free energy, the gradient part summed by
+parts) in exact integer arithmetic on the 28-bit digit grid of C's tile: sum U, sum U L and
+sum W^2 with W = round((U^2 - 2^(112-2G)) / 2^58), each converted once to FP64 with the scale
+2^(G-56), 2^(2G-112), 2^(4G-108): within 2^-50 of the exact sums of the digit values (the
+truncation of values below an eighth of the tile's largest is the digits' own), and the integers
+stay inside 64 and 128 bits for every G in [-3, 3]."""
 import math
 from fractions import Fraction as Fr
 
@@ -198,3 +205,54 @@ def test_z_within_bound(n):
         assert err <= bound, (n, float(err / U))
         cases += 1
     print(f"[ch cubic] n={n}: worst |Z - exact| = {worst:.3f} units")
+
+
+def i128_to_double(v: int) -> float:
+    """The kernel's conversion: the magnitude's two 64-bit halves, each rounded to a double, joined
+    by one FMA (exact product 2^64 hi, then one rounding)."""
+    a = abs(v)
+    hi, lo = a >> 64, a & (2 ** 64 - 1)
+    r = float(Fr(float(hi)) * 2 ** 64 + Fr(float(lo)))
+    return -r if v < 0 else r
+
+
+@pytest.mark.parametrize("G", [-3, -1, 0, 1, 3])
+def test_invariant_sums_in_integers(G):
+    """Eight points of a thread: u, its four neighbours, on a tile whose largest value lies in
+    [2^(G-1), 2^G); the integer sums against exact rational sums of the digit values."""
+    rng = np.random.default_rng(100 + G)
+    te = G + 1022
+    for trial in range(40):
+        mag = float(rng.uniform(0.5, 1.0)) * 2.0 ** G
+        vals = rng.uniform(-1, 1, (8, 5)) * mag
+        if trial % 4 == 0:  # the wells: u near +-1 where u^2 - 1 cancels (where the tile allows)
+            vals = np.sign(vals) * np.minimum(1.0 + rng.uniform(-1e-7, 1e-7, vals.shape), 0.999 * 2.0 ** G)
+        vals = [[float(v) for v in row] for row in vals]
+        K = 1 << (112 - 2 * G)
+        sm = sg = sw = 0
+        ex_m = ex_g = ex_w = Fr(0)
+        for row in vals:  # centre, north, south, west, east
+            d = [split(v, te, 28) for v in row]
+            U = [hi * 2 ** 28 + lo for hi, lo in d]
+            assert all(abs(x) < 2 ** 56 for x in U)
+            L = U[1] + U[2] + U[3] + U[4] - 4 * U[0]
+            sm += U[0]
+            sg += U[0] * L
+            W = (U[0] * U[0] - K + 2 ** 57) >> 58
+            assert abs(W) < 2 ** 61
+            sw += W * W
+            # exact sums of the digit values (u as its digits represent it)
+            s = Fr(2) ** (G - 56)
+            u = [Fr(x) * s for x in U]
+            ex_m += u[0]
+            ex_g += u[0] * (u[1] + u[2] + u[3] + u[4] - 4 * u[0])
+            ex_w += (u[0] ** 2 - 1) ** 2
+        assert abs(sm) < 2 ** 59 and abs(sg) < 2 ** 118 and abs(sw) < 2 ** 125
+        m = float(Fr(float(sm)) * Fr(2) ** (G - 56))
+        eg = float(Fr(i128_to_double(sg)) * Fr(2) ** (2 * G - 112))
+        ew = float(Fr(i128_to_double(sw)) * Fr(2) ** (4 * G - 108))
+        assert abs(Fr(m) - ex_m) <= Fr(2) ** -53 * abs(ex_m)
+        assert abs(Fr(eg) - ex_g) <= Fr(2) ** -51 * abs(ex_g) + Fr(2) ** -200
+        # W's rounding: |delta W| <= 1/2 unit of 2^(2G-54), so |delta W^2| <= (|w| + 2^(2G-55)) 2^(2G-54)
+        tol = sum(abs(Fr(r[0]) ** 2 - 1) for r in vals) * Fr(2) ** (2 * G - 54) + 8 * Fr(2) ** (4 * G - 108)
+        assert abs(Fr(ew) - ex_w) <= tol + Fr(2) ** -51 * ex_w, (G, trial)
