@@ -232,6 +232,40 @@ __device__ __forceinline__ int mirrorn(int64_t k, int64_t n) {
 // line-solve chunk type: bit 0 the line's first chunk, bit 1 its last (no-flux tables)
 __host__ __device__ __forceinline__ int chunk_type(int p, int P) { return (p == 0 ? 1 : 0) | (p == P - 1 ? 2 : 0); }
 
+// 128-bit shuffle (two 64-bit halves)
+__device__ __forceinline__ __int128 shfl_down_i128(__int128 v, int off) {
+  const unsigned long long lo = __shfl_down_sync(0xffffffffu, static_cast<unsigned long long>(v), off);
+  const long long hi = __shfl_down_sync(0xffffffffu, static_cast<long long>(v >> 64), off);
+  return static_cast<__int128>(hi) * (static_cast<__int128>(1) << 64) + static_cast<__int128>(lo);
+}
+
+// The block's exact integer invariant sums (mass digits S0, S1; sum U L; sum W^2, see k_ch_rhs),
+// reduced in integers over the block (every total stays below 2^127), then converted once to
+// FP64 by thread 0: out2 = (sum C, sum energy density) of the block.
+__device__ __forceinline__ void block_reduce_int(long long s0, long long s1, __int128 sg, __int128 sw, int G,
+                                                 double half_gamma_over_h2, double* out2) {
+  __shared__ long long rs[2][kThreads / 32];
+  __shared__ __int128 rq[2][kThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, off);
+    s1 += __shfl_down_sync(0xffffffffu, s1, off);
+    sg += shfl_down_i128(sg, off);
+    sw += shfl_down_i128(sw, off);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { rs[0][warp] = s0; rs[1][warp] = s1; rq[0][warp] = sg; rq[1][warp] = sw; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long a = 0, b = 0;
+    __int128 g = 0, w = 0;
+    for (int k = 0; k < kThreads / 32; ++k) { a += rs[0][k]; b += rs[1][k]; g += rq[0][k]; w += rq[1][k]; }
+    out2[0] = fma(static_cast<double>(a), 268435456.0, static_cast<double>(b)) * pow2d(G - 56);
+    const double ew = i128_to_double(w) * pow2d(4 * G - 102);
+    const double eg = i128_to_double(g) * pow2d(2 * G - 112);
+    out2[1] = fma(0.25, ew, -half_gamma_over_h2 * eg);
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void block_reduce2(double m, double e, double* out2) {
   __shared__ double red[2][kThreads / 32];
@@ -258,9 +292,10 @@ __device__ __forceinline__ void block_reduce2(double m, double e, double* out2) 
 // exception: with FP32 storage Cbar = 2 C^n - C^{n-1} is formed in FP32 (one rounding) exactly as
 // the update forms it, then widened.  Both uses of Cbar then agree, so the step is the scheme
 // applied to that Cbar, whose rounding reaches C^{n+1} at most undamped (it is of the size of the
-// stored result's own rounding); everything after it is FP64.
+// stored result's own rounding); everything after it is FP64.  At least 5 CTAs per SM (the two
+// staged tiles' 39 KB of shared memory allow 5): 48 registers, no spills.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 5)
     k_ch_rhs(const T* __restrict__ cur, const T* __restrict__ prev, double* __restrict__ rhs, int64_t n,
              double alpha, double a, double half_gamma_over_h2, double* __restrict__ partials, int noflux,
              double am51, CubicInv cinv, int band, T* __restrict__ cbar_out) {
@@ -446,39 +481,53 @@ __global__ void __launch_bounds__(kThreads)
       }
       __syncthreads();
     }
-    double m = 0.0, e;
+    double* out2 = partials + 2 * (static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x);
     const int G = te - 1022;  // the tile's values lie below 2^G
     if (dig && G >= -3 && G <= 3) {
-      // Each thread's share in exact integer arithmetic on the digit grid, u = U 2^(G-56) with
-      // U = d0 2^28 + d1 (every bit of a value within a factor 8 of the tile's largest) and
-      // Lap5(u) = L 2^(G-56), L the exact digit sum: sum U (< 2^59), sum U L (< 2^118) and
-      // sum W^2 with W = (U^2 - 2^(112-2G)) 2^-58 rounded (u^2 - 1 in units of 2^(2G-54), |W| < 2^61;
-      // sum < 2^125), then one conversion each to FP64 for the block's FP64 reduction.  No FP64
-      // operation per point (the formula below takes 5).
-      long long sm = 0;
-      __int128 sg = 0, sw = 0;
-      const __int128 K = static_cast<__int128>(1) << (112 - 2 * G);
-      const __int128 half = static_cast<__int128>(1) << 57;
+      // Each thread's share in exact integer arithmetic on the digit grid: u = U 2^(G-56) with
+      // U = d0 2^28 + d1 (every bit of a value within a factor 8 of the tile's largest), and
+      // Lap5(u) = L 2^(G-56) with L = q0 2^28 + q1 the exact digit sums.  Per point, only 32 x 32
+      // -> 64-bit multiply-adds into 64-bit sums:
+      //   mass      sum d0, sum d1;
+      //   U L       sum d0 q0, sum (d0 q1 + d1 q0), sum d1 q1;
+      //   u^2 - 1   W = round((U^2 - 2^(112-2G)) / 2^61) (units 2^(2G-51), |W| <= 2^57 + 1), from
+      //             A = d0^2 - 2^(56-2G) and B = 2 d0 d1 + floor(d1^2 / 2^28) as
+      //             (A >> 5) + ((A mod 32) 2^28 + B + 2^32) >> 33 (d1^2's dropped bits are below
+      //             2^-33 of W's unit);
+      //   W^2       with W = Wh 2^29 + Wl: sum Wh^2, sum Wh Wl, sum Wl^2.
+      // Every sum of the thread's 8 points stays below 2^63; each is joined once in 128 bits, the
+      // block reduces them in integers, and thread 0 converts the block's totals to FP64.  No FP64
+      // operation per point or per thread (the formula below takes 5 per point, and its FP64
+      // shuffle reduction 10 per thread).
+      int s0 = 0, s1 = 0;
+      long long g2 = 0, g1 = 0, g0 = 0, w2 = 0, w1 = 0, w0 = 0;
+      const long long K56 = 1ll << (56 - 2 * G);
       const int2* dg = reinterpret_cast<const int2*>(sb);
       for (int idx = threadIdx.x; idx < kTY * kTX; idx += kThreads) {
         const int r = idx / kTX, c = idx - r * kTX;
         const int hidx = (r + 2) * HC + (c + 2);
         const int2 d = dg[hidx];
-        const long long U = static_cast<long long>(d.x) * (1ll << 28) + d.y;
         int q0, q1;
         lap5_digits(sb, hidx, HC, q0, q1);
-        const long long L = static_cast<long long>(q0) * (1ll << 28) + q1;
-        sm += U;
-        sg += static_cast<__int128>(U) * L;
-        const long long W = static_cast<long long>((static_cast<__int128>(U) * U - K + half) >> 58);
-        sw += static_cast<__int128>(W) * W;
+        s0 += d.x;
+        s1 += d.y;
+        g2 += static_cast<long long>(d.x) * q0;
+        g1 += static_cast<long long>(d.x) * q1 + static_cast<long long>(d.y) * q0;
+        g0 += static_cast<long long>(d.y) * q1;
+        const long long A = static_cast<long long>(d.x) * d.x - K56;
+        const long long B = static_cast<long long>(d.x) * (2 * d.y) +
+                            static_cast<long long>(static_cast<unsigned long long>(static_cast<unsigned>(d.y)) * static_cast<unsigned>(d.y) >> 28);
+        const long long W = (A >> 5) + ((((A & 31) << 28) + B + (1ll << 32)) >> 33);
+        const int wh = static_cast<int>(W >> 29), wl = static_cast<int>(W & ((1ll << 29) - 1));
+        w2 += static_cast<long long>(wh) * wh;
+        w1 += static_cast<long long>(wh) * wl;
+        w0 += static_cast<long long>(wl) * wl;
       }
-      m = static_cast<double>(sm) * pow2d(G - 56);
-      const double ew = i128_to_double(sw) * pow2d(4 * G - 108);
-      const double eg = i128_to_double(sg) * pow2d(2 * G - 112);
-      e = fma(0.25, ew, -half_gamma_over_h2 * eg);
+      const __int128 sg = (static_cast<__int128>(g2) << 56) + (static_cast<__int128>(g1) << 28) + g0;
+      const __int128 sw = (static_cast<__int128>(w2) << 58) + (static_cast<__int128>(w1) << 30) + w0;
+      block_reduce_int(s0, s1, sg, sw, G, half_gamma_over_h2, out2);
     } else {
-      double ew = 0.0, eg = 0.0;
+      double m = 0.0, ew = 0.0, eg = 0.0;
       for (int idx = threadIdx.x; idx < kTY * kTX; idx += kThreads) {
         const int r = idx / kTX, c = idx - r * kTX;
         const int hidx = (r + 2) * HC + (c + 2);
@@ -496,9 +545,8 @@ __global__ void __launch_bounds__(kThreads)
         ew = fma(w, w, ew);
         eg = fma(u, lap, eg);
       }
-      e = fma(0.25, ew, -half_gamma_over_h2 * eg);
+      block_reduce2<T>(m, fma(0.25, ew, -half_gamma_over_h2 * eg), out2);
     }
-    block_reduce2<T>(m, e, partials + 2 * (static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x));
   }
 }
 

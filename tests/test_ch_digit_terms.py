@@ -14,11 +14,12 @@ one rounding per FMA, integer shifts) and checked against exact rational arithme
   FMA's own rounding; the FP64 formula's own bound differs only by Q's 0.6 U.
 
 And the invariants' per-thread sums (Eq. 1's mass and free energy, the gradient part summed by
-parts) in exact integer arithmetic on the 28-bit digit grid of C's tile: sum U, sum U L and
-sum W^2 with W = round((U^2 - 2^(112-2G)) / 2^58), each converted once to FP64 with the scale
-2^(G-56), 2^(2G-112), 2^(4G-108): within 2^-50 of the exact sums of the digit values (the
-truncation of values below an eighth of the tile's largest is the digits' own), and the integers
-stay inside 64 and 128 bits for every G in [-3, 3]."""
+parts) in exact integer arithmetic on the 28-bit digit grid of C's tile, from 32 x 32 -> 64-bit
+products of the digits only: sum d0, sum d1; sum U L as three digit-product sums; u^2 - 1 as
+W = round((U^2 - 2^(112-2G)) / 2^61) formed from d0^2 and 2 d0 d1 + floor(d1^2 / 2^28); W^2 from W's
+two 29-bit digits.  Each sum of a thread's 8 points stays below 2^63, the joined sums within 2^-50
+of the exact sums of the digit values (the truncation of values below an eighth of the tile's
+largest is the digits' own), W within 2^-33 of a unit of its rounding, for every G in [-3, 3]."""
 import math
 from fractions import Fraction as Fr
 
@@ -218,41 +219,74 @@ def i128_to_double(v: int) -> float:
 
 @pytest.mark.parametrize("G", [-3, -1, 0, 1, 3])
 def test_invariant_sums_in_integers(G):
-    """Eight points of a thread: u, its four neighbours, on a tile whose largest value lies in
-    [2^(G-1), 2^G); the integer sums against exact rational sums of the digit values."""
+    """Eight points of a thread: u and its four neighbours, on a tile whose largest value lies in
+    [2^(G-1), 2^G); the kernel's integer sums against exact rational sums of the digit values."""
     rng = np.random.default_rng(100 + G)
     te = G + 1022
-    for trial in range(40):
+    I63 = 2 ** 63
+    for trial in range(60):
         mag = float(rng.uniform(0.5, 1.0)) * 2.0 ** G
         vals = rng.uniform(-1, 1, (8, 5)) * mag
         if trial % 4 == 0:  # the wells: u near +-1 where u^2 - 1 cancels (where the tile allows)
             vals = np.sign(vals) * np.minimum(1.0 + rng.uniform(-1e-7, 1e-7, vals.shape), 0.999 * 2.0 ** G)
+        if trial % 4 == 1:  # the extremes of the digit ranges: values at the tile's top
+            vals = np.sign(vals) * (2.0 ** G) * (1 - 2.0 ** -50)
         vals = [[float(v) for v in row] for row in vals]
-        K = 1 << (112 - 2 * G)
-        sm = sg = sw = 0
+        K56 = 1 << (56 - 2 * G)
+        s0 = s1 = g2 = g1 = g0 = w2 = w1 = w0 = 0
         ex_m = ex_g = ex_w = Fr(0)
+        worst_w = Fr(0)
         for row in vals:  # centre, north, south, west, east
             d = [split(v, te, 28) for v in row]
-            U = [hi * 2 ** 28 + lo for hi, lo in d]
-            assert all(abs(x) < 2 ** 56 for x in U)
-            L = U[1] + U[2] + U[3] + U[4] - 4 * U[0]
-            sm += U[0]
-            sg += U[0] * L
-            W = (U[0] * U[0] - K + 2 ** 57) >> 58
-            assert abs(W) < 2 ** 61
-            sw += W * W
-            # exact sums of the digit values (u as its digits represent it)
-            s = Fr(2) ** (G - 56)
-            u = [Fr(x) * s for x in U]
+            d0, d1 = d[0]
+            q0 = d[1][0] + d[2][0] + d[3][0] + d[4][0] - 4 * d0
+            q1 = d[1][1] + d[2][1] + d[3][1] + d[4][1] - 4 * d1
+            assert -2 ** 31 <= q0 < 2 ** 31 and -2 ** 31 <= q1 < 2 ** 31
+            s0 += d0
+            s1 += d1
+            g2 += d0 * q0
+            g1 += d0 * q1 + d1 * q0
+            g0 += d1 * q1
+            A = d0 * d0 - K56
+            B = d0 * (2 * d1) + ((d1 * d1) >> 28)
+            assert abs(A) < I63 and abs(B) < I63
+            W = (A >> 5) + ((((A & 31) << 28) + B + (1 << 32)) >> 33)
+            U = d0 * 2 ** 28 + d1
+            exact_W = Fr(U * U - (1 << (112 - 2 * G)), 2 ** 61)
+            worst_w = max(worst_w, abs(W - exact_W))
+            assert abs(W) <= 2 ** 57 + 1
+            wh, wl = W >> 29, W & (2 ** 29 - 1)
+            assert -2 ** 31 <= wh < 2 ** 31
+            w2 += wh * wh
+            w1 += wh * wl
+            w0 += wl * wl
+            for acc in (g2, g1, g0, w2, w1, w0):
+                assert abs(acc) < I63
+            sc = Fr(2) ** (G - 56)
+            u = [Fr(x * 2 ** 28 + y) * sc for x, y in d]
             ex_m += u[0]
             ex_g += u[0] * (u[1] + u[2] + u[3] + u[4] - 4 * u[0])
             ex_w += (u[0] ** 2 - 1) ** 2
-        assert abs(sm) < 2 ** 59 and abs(sg) < 2 ** 118 and abs(sw) < 2 ** 125
-        m = float(Fr(float(sm)) * Fr(2) ** (G - 56))
+        assert abs(s0) < 2 ** 31 and s1 < 2 ** 31
+        assert worst_w <= Fr(1, 2) + Fr(1, 2 ** 33)  # round half up, d1^2's dropped bits
+        sg = (g2 << 56) + (g1 << 28) + g0
+        sw = (w2 << 58) + (w1 << 30) + w0
+        m = float(Fr(float(Fr(s0) * 2 ** 28 + s1)) * Fr(2) ** (G - 56))
         eg = float(Fr(i128_to_double(sg)) * Fr(2) ** (2 * G - 112))
-        ew = float(Fr(i128_to_double(sw)) * Fr(2) ** (4 * G - 108))
-        assert abs(Fr(m) - ex_m) <= Fr(2) ** -53 * abs(ex_m)
-        assert abs(Fr(eg) - ex_g) <= Fr(2) ** -51 * abs(ex_g) + Fr(2) ** -200
-        # W's rounding: |delta W| <= 1/2 unit of 2^(2G-54), so |delta W^2| <= (|w| + 2^(2G-55)) 2^(2G-54)
-        tol = sum(abs(Fr(r[0]) ** 2 - 1) for r in vals) * Fr(2) ** (2 * G - 54) + 8 * Fr(2) ** (4 * G - 108)
+        ew = float(Fr(i128_to_double(sw)) * Fr(2) ** (4 * G - 102))
+        assert abs(Fr(m) - ex_m) <= Fr(2) ** -53 * abs(ex_m) + Fr(2) ** -300
+        assert abs(Fr(eg) - ex_g) <= Fr(2) ** -51 * abs(ex_g) + Fr(2) ** -300
+        # W within (1/2 + 2^-33) of its unit 2^(2G-51): |delta W^2| <= (2 |w| + unit) unit per point
+        unit = Fr(2) ** (2 * G - 51)
+        tol = sum(2 * abs(Fr(r[0]) ** 2 - 1) + unit for r in vals) * unit
         assert abs(Fr(ew) - ex_w) <= tol + Fr(2) ** -51 * ex_w, (G, trial)
+
+
+def test_block_totals_fit_in_128_bits():
+    """The block (256 threads of 8 points) reduces the thread sums in integers: the per-thread
+    bounds (|sum d0|, sum d1 < 2^31; |sum U L| < 2^118; sum W^2 <= 8 (2^57 + 1)^2) times 256 stay below the
+    64-bit (mass digits) and 128-bit (energy) limits."""
+    threads, pts = 256, 8
+    assert threads * pts * 2 ** 28 < 2 ** 63  # sum d0, sum d1 over the block
+    assert threads * pts * 2 ** 56 * 2 ** 59 < 2 ** 127  # sum U L: |U| < 2^56, |L| < 8 2^56
+    assert threads * pts * (2 ** 57 + 1) ** 2 < 2 ** 127  # sum W^2: |U^2 - K| <= 2^118, |W| <= 2^57 + 1
