@@ -123,6 +123,29 @@ def test_integer_data_bit_exact(env, dtype, bc, n, ext):
     assert np.array_equal(got, ref)
 
 
+BIHARM_N = np.array([0, 0, 1, 0, 0, 0, 2, -8, 2, 0, 1, -8, 20, -8, 1, 0, 2, -8, 2, 0, 0, 0, 1, 0, 0], float)
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("tile_choice", [0, 1])
+@pytest.mark.parametrize("shape", [(1, 1), (3, 5), (17, 64), (67, 130), (130, 67), (256, 384)])
+def test_biharmonic_digits_bit_exact(env, sign, bc, tile_choice, shape):
+    """FP64 weights c (1, 2, -8, 20) and their negatives on the 13-point footprint (the digit
+    path's integer ratios n_k); on integer data every sum is exact, so the output equals the
+    oracle's bit for bit in both tile heights: edge tiles, periodic wrap of grids smaller than the
+    footprint, and the cells a non-periodic sweep leaves untouched."""
+    cs, torch, orc = env
+    ny, nx = shape
+    field = W.integer_field(ny, nx, seed=ny * 1000 + nx)
+    w = sign * 0.25 * BIHARM_N
+    sentinel = np.full(shape, 12345.0)
+    kw = dict(dir=2, bc=bc, left=2, right=2, top=2, bottom=2, weights=w)
+    got = run2d(cs, torch, field, kw, 0, out_init=sentinel, tile_choice=tile_choice)
+    ref = orc.stencil2d(field, w, 2, bc, 2, 2, 2, 2, out=sentinel)
+    assert np.array_equal(got, ref)
+
+
 @pytest.mark.parametrize("dtype", [0, 1])
 def test_impulse_gives_flipped_stencil(env, dtype):
     cs, torch, orc = env
