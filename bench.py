@@ -466,7 +466,7 @@ def bench_ch(cs, torch, stream, cases=None, autotune=True):
         chunks, m = cs.cs_ch_config(plan)
         cs.cs_destroy(plan)
         key = f"n{n}_{'f64' if storage == cs.CS_F64 else 'f32'}" + ("_noflux" if boundary == cs.CS_CH_NOFLUX else "")
-        fp64_ops = ch_fp64_ops_per_point(chunks, m) * n * n
+        fp64_ops = ch_fp64_ops_per_point(chunks, m, storage == cs.CS_F32) * n * n
         out[key] = {"ms_per_step": round(ms, 4), "steps_per_s": round(1e3 / ms, 1),
                     "fp64_gops": round(fp64_ops / (ms * 1e-3) / 1e9, 1),
                     "fp64_frac": round(fp64_ops / (ms * 1e-3) / 1e9 / FP64_PEAK_GOPS, 3),
@@ -740,16 +740,20 @@ def bench_serve(cs, torch, factors=(0.5, 0.9, 1.5), count=120, seed=2026):
     return out
 
 
-def ch_fp64_ops_per_point(chunks: int, m: int) -> float:
-    """FP64-pipe operations per grid point of one ADI step as the kernels perform them, for either
-    storage: the right-hand side 8.6 (Cbar on the halo-2 tile: 1.2; on the halo-1 tile u u, N,
-    the first digit Laplacian's scaling (carrying -a) and Z: 4 x 1.1; the second scaling,
-    C^n - C^{n-1} and the final combination: 3; FP32 storage forms Cbar in FP32), two sweeps of
-    local LU (5) + spike correction (4) + chunk-end system (16 chunks / m), and the update's one
-    add (Cbar comes from the right-hand side kernel through the C^{n+1} buffer; FP32 storage
-    narrows on the integer pipe)."""
+def ch_fp64_ops_per_point(chunks: int, m: int, fp32_storage: bool = False) -> float:
+    """FP64-pipe operations per grid point of one ADI step as the kernels perform them (ncu's
+    DFMA + DADD + DMUL counts of the 4096^2 FP64 step: 5.45 + 5 + 5 + 5 + 6 = 26.4 at 16 chunks
+    of 256).  The right-hand side, per CTA of 64 x 32 points: Cbar = 2 C^n - C^{n-1} on the 68 x 36
+    halo-2 tile (one FMA; FP32 storage forms it in FP32), Z's one digit-combination FMA on the
+    66 x 34 halo-1 tile (the cubic term joins the integer digit sum), then per point the second
+    combination, C^n - C^{n-1} and the final FMA, and one multiply per thread for the combination's
+    constant.  Each sweep: local LU 4 FMAs and 1 multiply, the spike correction 4 FMAs and the
+    chunk-end system 16 chunks / m.  The update: one add (Cbar comes from the right-hand side kernel
+    through the C^{n+1} buffer; FP32 storage narrows on the integer pipe)."""
+    tile = 64 * 32
+    rhs = (0 if fp32_storage else 68 * 36 / tile) + 66 * 34 / tile + 3 + 256 / tile
     per_sweep = 5 + 4 + 16.0 * chunks / m
-    return 8.6 + 2 * per_sweep + 1
+    return rhs + 2 * per_sweep + 1
 
 
 def _median_event_ms(torch, stream, launch, flush, reps=12, skip=2):

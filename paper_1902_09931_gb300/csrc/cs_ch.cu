@@ -309,7 +309,43 @@ __global__ void __launch_bounds__(kThreads, 5)
   // band != 0: cur and prev are row bands padded with the 2 rows above and the 2 rows below (the
   // neighbours' rows, exchanged by the caller, or at a no-flux edge of the grid the band's own rows
   // mirrored); output row r of the band is padded row r + 2
-  for (int idx = threadIdx.x; idx < HR * HC; idx += kThreads) {
+  const uintptr_t addr_bits = reinterpret_cast<uintptr_t>(cur) | reinterpret_cast<uintptr_t>(prev) |
+                              reinterpret_cast<uintptr_t>(cbar_out);
+  const bool inner = x0 >= 2 && x0 + kTX + 2 <= n && (band || (y0 >= 2 && y0 + kTY + 2 <= n)) &&
+                     (addr_bits & (2 * sizeof(T) - 1)) == 0;
+  if (inner) {
+    // a tile whose halo lies inside the grid (or inside the padded band): no wrap or mirror, two
+    // adjacent values per load and store (x0 - 2 and n are even; 16 bytes for FP64 storage, 8 for
+    // FP32), a fixed trip count so that the loads of several pairs are in flight together
+    constexpr int HP = HC / 2, NPAIR = HR * HP, IT = (NPAIR + kThreads - 1) / kThreads;
+#pragma unroll
+    for (int k = 0; k < IT; ++k) {
+      const int idx = threadIdx.x + k * kThreads;
+      if (k + 1 < IT || idx < NPAIR) {
+        const int r = idx / HP, cp = idx - r * HP;
+        const int64_t gy = y0 - 2 + r, gx = x0 - 2 + 2 * cp;
+        const int64_t off = (band ? gy + 2 : gy) * n + gx;
+        const bool own = cbar_out && r >= 2 && r < kTY + 2 && cp >= 1 && cp < HP - 1;
+        const int i0 = r * HC + 2 * cp;
+        if constexpr (sizeof(T) == 4) {
+          const float2 cf = *reinterpret_cast<const float2*>(cur + off);
+          const float2 pf = *reinterpret_cast<const float2*>(prev + off);
+          const float2 cb = make_float2(fmaf(2.0f, cf.x, -pf.x), fmaf(2.0f, cf.y, -pf.y));
+          *reinterpret_cast<double2*>(sc + i0) = make_double2(widen(cf.x), widen(cf.y));
+          *reinterpret_cast<double2*>(sb + i0) = make_double2(widen(cb.x), widen(cb.y));
+          if (own) *reinterpret_cast<float2*>(cbar_out + gy * n + gx) = cb;
+        } else {
+          const double2 cd = *reinterpret_cast<const double2*>(cur + off);
+          const double2 pd = *reinterpret_cast<const double2*>(prev + off);
+          const double2 cb = make_double2(fma(2.0, cd.x, -pd.x), fma(2.0, cd.y, -pd.y));
+          *reinterpret_cast<double2*>(sc + i0) = cd;
+          *reinterpret_cast<double2*>(sb + i0) = cb;
+          if (own) *reinterpret_cast<double2*>(cbar_out + gy * n + gx) = cb;
+        }
+      }
+    }
+  }
+  for (int idx = inner ? HR * HC : threadIdx.x; idx < HR * HC; idx += kThreads) {
     const int r = idx / HC, c = idx - r * HC;
     const int64_t gy = y0 - 2 + r, gx = x0 - 2 + c;
     const int64_t off = band      ? (gy + 2) * n + (noflux ? mirrorn(gx, n) : wrapn(gx, n))
@@ -577,24 +613,28 @@ __global__ void k_reduce_final(const double* __restrict__ partials, int nblocks,
 
 // A batch of kU line elements starting at `at` (element stride es): 16-byte vector accesses
 // when the line is contiguous (rows; `at` is then a multiple of kU), strided scalars otherwise.
-template <typename IT, bool CONTIG>
+// STREAM: loads marked evict-first (ld.global.cs) for data read once, so that they do not push
+// the solve's own intermediate out of L2 before it is read back.
+template <typename IT, bool CONTIG, bool STREAM = false>
 __device__ __forceinline__ void load_batch(const IT* __restrict__ p, int64_t at, int64_t es, double (&v)[8]) {
   if constexpr (CONTIG && sizeof(IT) == 8) {
 #pragma unroll
     for (int u = 0; u < 8; u += 2) {
-      const double2 d = *reinterpret_cast<const double2*>(p + at + u);
+      const double2* q = reinterpret_cast<const double2*>(p + at + u);
+      const double2 d = STREAM ? __ldcs(q) : *q;
       v[u] = d.x;
       v[u + 1] = d.y;
     }
   } else if constexpr (CONTIG) {
 #pragma unroll
     for (int u = 0; u < 8; u += 4) {
-      const float4 f = *reinterpret_cast<const float4*>(p + at + u);
+      const float4* q = reinterpret_cast<const float4*>(p + at + u);
+      const float4 f = STREAM ? __ldcs(q) : *q;
       v[u] = widen(f.x); v[u + 1] = widen(f.y); v[u + 2] = widen(f.z); v[u + 3] = widen(f.w);
     }
   } else {
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = widen(p[at + u * es]);
+    for (int u = 0; u < 8; ++u) v[u] = widen(STREAM ? __ldcs(p + at + u * es) : p[at + u * es]);
   }
 }
 template <bool CONTIG>
@@ -630,9 +670,12 @@ __global__ void __launch_bounds__(kSolveThreads)
   const double* nu2 = coef + 4 * m;
   const int64_t base = line * line_stride + static_cast<int64_t>(p) * m * es;
   double y1 = 0.0, y2 = 0.0;
+  // the forward pass streams the right-hand side in (read once) and writes the line's
+  // intermediate, which the backward pass reads back right after: the input's loads are marked
+  // evict-first so that the intermediate stays in L2 (at 4096^2 it is 134 MB)
   for (int k0 = 0; k0 < m; k0 += kU) {
     double v[kU];
-    load_batch<IT, CONTIG>(in, base + k0 * es, es, v);
+    load_batch<IT, CONTIG, true>(in, base + k0 * es, es, v);
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const double y = fma(__ldg(nl1 + k0 + u), y1, fma(__ldg(nl2 + k0 + u), y2, v[u]));
