@@ -613,28 +613,24 @@ __global__ void k_reduce_final(const double* __restrict__ partials, int nblocks,
 
 // A batch of kU line elements starting at `at` (element stride es): 16-byte vector accesses
 // when the line is contiguous (rows; `at` is then a multiple of kU), strided scalars otherwise.
-// STREAM: loads marked evict-first (ld.global.cs) for data read once, so that they do not push
-// the solve's own intermediate out of L2 before it is read back.
-template <typename IT, bool CONTIG, bool STREAM = false>
+template <typename IT, bool CONTIG>
 __device__ __forceinline__ void load_batch(const IT* __restrict__ p, int64_t at, int64_t es, double (&v)[8]) {
   if constexpr (CONTIG && sizeof(IT) == 8) {
 #pragma unroll
     for (int u = 0; u < 8; u += 2) {
-      const double2* q = reinterpret_cast<const double2*>(p + at + u);
-      const double2 d = STREAM ? __ldcs(q) : *q;
+      const double2 d = *reinterpret_cast<const double2*>(p + at + u);
       v[u] = d.x;
       v[u + 1] = d.y;
     }
   } else if constexpr (CONTIG) {
 #pragma unroll
     for (int u = 0; u < 8; u += 4) {
-      const float4* q = reinterpret_cast<const float4*>(p + at + u);
-      const float4 f = STREAM ? __ldcs(q) : *q;
+      const float4 f = *reinterpret_cast<const float4*>(p + at + u);
       v[u] = widen(f.x); v[u + 1] = widen(f.y); v[u + 2] = widen(f.z); v[u + 3] = widen(f.w);
     }
   } else {
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = widen(STREAM ? __ldcs(p + at + u * es) : p[at + u * es]);
+    for (int u = 0; u < 8; ++u) v[u] = widen(p[at + u * es]);
   }
 }
 template <bool CONTIG>
@@ -670,12 +666,9 @@ __global__ void __launch_bounds__(kSolveThreads)
   const double* nu2 = coef + 4 * m;
   const int64_t base = line * line_stride + static_cast<int64_t>(p) * m * es;
   double y1 = 0.0, y2 = 0.0;
-  // the forward pass streams the right-hand side in (read once) and writes the line's
-  // intermediate, which the backward pass reads back right after: the input's loads are marked
-  // evict-first so that the intermediate stays in L2 (at 4096^2 it is 134 MB)
   for (int k0 = 0; k0 < m; k0 += kU) {
     double v[kU];
-    load_batch<IT, CONTIG, true>(in, base + k0 * es, es, v);
+    load_batch<IT, CONTIG>(in, base + k0 * es, es, v);
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const double y = fma(__ldg(nl1 + k0 + u), y1, fma(__ldg(nl2 + k0 + u), y2, v[u]));
