@@ -5,9 +5,14 @@ in-flight slot is free and their fields fit the device-memory budget, keeps ever
 resident on the device, launches every admitted 2D sweep of the same stencil shape in one
 grouped kernel launch (cs_compute_group), runs each Cahn-Hilliard advance on its own stream so
 independent jobs overlap on the GPU, and retires jobs as their completion events fire, which
-frees their slot and memory for the next arrivals.  The sequential baseline runs the same
-jobs one at a time with plain calls.  All GPU work goes through the C ABI; this module only
-schedules.
+frees their slot and memory for the next arrivals.  Heavy jobs (those of at least
+HEAVY_WORK point-steps: the Cahn-Hilliard advances of 2048^2 and 4096^2, each of which fills the
+GPU alone) run at most `max_heavy` at a time in arrival order, and lighter jobs may pass a heavy
+job that waits for that limit; two heavy advances sharing the GPU would each take about twice as
+long, which is what sets the tail latency at light load.  The backend runs light jobs on
+higher-priority streams, so a heavy advance in flight does not hold their kernels back.  The
+sequential baseline runs the same jobs one at a time with plain calls.  All GPU work goes
+through the C ABI; this module only schedules.
 
 The scheduler talks to a backend (prepare / launch_sweeps / launch_ch / query / release) so
 that its admission and slot logic can be exercised without a GPU.
@@ -25,6 +30,7 @@ import numpy as np
 
 SWEEP_STENCILS = ("lap9", "biharm13", "ddx4", "ddy4")
 SIZES = (128, 256, 512, 1024, 2048, 4096)
+HEAVY_WORK = 2048 * 2048 * 10  # point-steps from which a job counts as heavy
 
 
 @dataclass
@@ -40,10 +46,16 @@ class Job:
     done: float = math.nan  # completion time
     output: object = None  # device tensor holding the result
     res: dict = field(default_factory=dict)
+    heavy: bool = False  # set by the server: runs under the heavy-job limit, lower stream priority
 
     @property
     def latency(self) -> float:
         return self.done - self.arrival
+
+    @property
+    def work(self) -> int:
+        """Point-steps: n^2 for a sweep, n^2 times the steps for a Cahn-Hilliard advance."""
+        return self.n * self.n * (self.steps if self.kind == "ch" else 1)
 
 
 def footprint(job: Job, elem_bytes: int = 4) -> int:
@@ -77,12 +89,15 @@ class Server:
     overlap independent jobs on streams, retire on completion."""
 
     def __init__(self, backend, max_inflight: int = 8, hbm_budget: Optional[int] = None,
-                 group: bool = True, clock: Callable[[], float] = time.perf_counter):
+                 group: bool = True, clock: Callable[[], float] = time.perf_counter,
+                 max_heavy: Optional[int] = 1, heavy_work: int = HEAVY_WORK):
         self.backend = backend
         self.max_inflight = max_inflight
         self.budget = hbm_budget if hbm_budget is not None else backend.default_budget()
         self.group = group
         self.clock = clock
+        self.max_heavy = max_heavy  # None: no limit
+        self.heavy_work = heavy_work
         self.launches = 0
 
     def run(self, jobs: List[Job]) -> Dict:
@@ -90,10 +105,12 @@ class Server:
         for j in jobs:
             if footprint(j) > self.budget:
                 raise ValueError(f"job {j.jid} needs {footprint(j)} bytes, above the budget {self.budget}")
+            j.heavy = self.max_heavy is not None and j.work >= self.heavy_work
         waiting = collections.deque()
         inflight = []  # (handle, [jobs])
         used = 0
         busy = 0
+        heavy = 0  # heavy jobs in flight
         nxt = 0
         finished = 0
         peak_inflight = 0
@@ -103,13 +120,22 @@ class Server:
             while nxt < len(jobs) and jobs[nxt].arrival <= now:
                 waiting.append(jobs[nxt])
                 nxt += 1
-            # admission in arrival order (a job that does not fit waits: no overtaking)
+            # admission in arrival order (a job that does not fit the memory budget waits, and no
+            # job passes it); a heavy job that waits for the heavy-job limit lets lighter ones pass
             admitted = []
-            while waiting and busy + len(admitted) < self.max_inflight and used + footprint(waiting[0]) <= self.budget:
-                j = waiting.popleft()
+            i = 0
+            while i < len(waiting) and busy + len(admitted) < self.max_inflight:
+                j = waiting[i]
+                if used + footprint(j) > self.budget:
+                    break
+                if j.heavy and heavy >= self.max_heavy:
+                    i += 1
+                    continue
+                del waiting[i]
                 self.backend.prepare(j)
                 j.start = self.clock() - t0
                 used += footprint(j)
+                heavy += j.heavy
                 admitted.append(j)
             # dispatch: sweeps of one stencil shape share a launch; each CH job has its stream
             if admitted:
@@ -134,6 +160,7 @@ class Server:
                     for j in js:
                         j.done = t
                         used -= footprint(j)
+                        heavy -= j.heavy
                         self.backend.release(j)
                         finished += 1
                     busy -= len(js)
@@ -182,8 +209,10 @@ class GpuBackend:
         self.cs, self.torch = cs, torch
         self.keep_outputs = keep_outputs
         self.dev = torch.device("cuda", torch.cuda.current_device())
-        self.pool_streams = [torch.cuda.Stream() for _ in range(streams)]
-        self.free_streams = list(self.pool_streams)
+        # light jobs on streams of the highest priority, heavy ones on default-priority streams
+        self.pool_streams = {False: [torch.cuda.Stream(priority=-1) for _ in range(streams)],
+                             True: [torch.cuda.Stream() for _ in range(max(1, streams // 4))]}
+        self.free_streams = {k: list(v) for k, v in self.pool_streams.items()}
         self.ch_plans: Dict[int, list] = collections.defaultdict(list)
         # sweep plans are reused (rebound to each job's buffers): creating and destroying a plan
         # per job allocates and frees device memory, and a free synchronises the device
@@ -249,14 +278,15 @@ class GpuBackend:
             cs.cs_ch_set_fields(plan, *f)
             job.res = {"plan": plan, "fields": f}
 
-    def _stream(self):
-        s = self.free_streams.pop() if self.free_streams else self.pool_streams[0]
+    def _stream(self, heavy: bool):
+        free = self.free_streams[heavy]
+        s = free.pop() if free else self.pool_streams[heavy][0]
         # the job's inputs were produced on the current stream at admission
         s.wait_stream(self.torch.cuda.current_stream())
         return s
 
     def launch_sweeps(self, jobs: List[Job]):
-        s = self._stream()
+        s = self._stream(any(j.heavy for j in jobs))
         plans = [j.res["plan"] for j in jobs]
         with self.torch.cuda.stream(s):
             if len(plans) == 1:
@@ -272,7 +302,7 @@ class GpuBackend:
         return (ev, s)
 
     def launch_ch(self, job: Job):
-        s = self._stream()
+        s = self._stream(job.heavy)
         with self.torch.cuda.stream(s):
             self.cs.cs_ch_step(job.res["plan"], job.steps, stream=s)
             ev = self.torch.cuda.Event()
@@ -287,8 +317,9 @@ class GpuBackend:
 
     def release_handle(self, handle):
         s = handle[1]
-        if s not in self.free_streams:
-            self.free_streams.append(s)
+        for heavy, pool in self.pool_streams.items():
+            if any(s is q for q in pool) and not any(s is q for q in self.free_streams[heavy]):
+                self.free_streams[heavy].append(s)
 
     def release(self, job: Job):
         if job.kind == "sweep":

@@ -145,3 +145,39 @@ def test_sequential_runs_one_at_a_time():
     for a, b in zip(order, order[1:]):
         assert b.start >= a.done
     assert be.peak_inflight == 1
+
+
+def test_heavy_jobs_run_one_at_a_time_and_light_jobs_pass():
+    """Heavy jobs (Cahn-Hilliard advances of 2048^2 and up) run one at a time in arrival order;
+    lighter jobs that arrive behind a waiting heavy job go ahead of it."""
+    clock = FakeClock()
+    jobs = [S.Job(0, "ch", 4096, 0.0, seed=1), S.Job(1, "ch", 2048, 0.0, seed=2),
+            S.Job(2, "sweep", 256, 0.0, seed=3), S.Job(3, "ch", 128, 0.0, seed=4),
+            S.Job(4, "sweep", 4096, 0.0, seed=5)]
+    be = FakeBackend(clock, 1 << 40)
+    S.Server(be, max_inflight=8, clock=clock).run(jobs)
+    h0, h1, l2, l3, l4 = jobs
+    assert h0.heavy and h1.heavy and not (l2.heavy or l3.heavy or l4.heavy)
+    assert h1.start >= h0.done
+    assert max(l2.start, l3.start, l4.start) < h0.done
+    # without the limit both heavy jobs are in flight together
+    jobs2 = [S.Job(0, "ch", 4096, 0.0), S.Job(1, "ch", 2048, 0.0)]
+    be2 = FakeBackend(FakeClock(), 1 << 40)
+    S.Server(be2, max_inflight=8, clock=be2.clock, max_heavy=None).run(jobs2)
+    assert jobs2[1].start < jobs2[0].done and be2.peak_inflight == 2
+
+
+def test_heavy_limit_keeps_memory_order():
+    """A job that does not fit the memory budget still blocks the jobs behind it (no job passes
+    it), whether or not a heavy job waits ahead of it."""
+    clock = FakeClock()
+    big = S.Job(0, "ch", 4096, 0.0)
+    budget = S.footprint(big) + S.footprint(S.Job(0, "sweep", 256, 0.0))
+    jobs = [big, S.Job(1, "ch", 2048, 0.0), S.Job(2, "sweep", 256, 0.0), S.Job(3, "sweep", 2048, 0.0),
+            S.Job(4, "sweep", 128, 0.0)]
+    be = FakeBackend(clock, budget)
+    S.Server(be, max_inflight=8, clock=clock).run(jobs)
+    assert all(not math.isnan(j.done) for j in jobs)
+    assert be.peak_resident <= budget
+    # job 3 (2048^2 sweep) does not fit beside job 0: job 4 waits behind it
+    assert jobs[4].start >= jobs[3].start
