@@ -611,11 +611,28 @@ __global__ void k_reduce_final(const double* __restrict__ partials, int nblocks,
   }
 }
 
-// A batch of kU line elements starting at `at` (element stride es): 16-byte vector accesses
-// when the line is contiguous (rows; `at` is then a multiple of kU), strided scalars otherwise.
+// 32-byte global accesses (one whole sector per thread and instruction)
+__device__ __forceinline__ void ld_v4(const double* p, double& a, double& b, double& c, double& d) {
+  asm volatile("ld.global.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(a), "=d"(b), "=d"(c), "=d"(d) : "l"(p) : "memory");
+}
+__device__ __forceinline__ void st_v4(double* p, double a, double b, double c, double d) {
+  asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(a), "d"(b), "d"(c), "d"(d) : "memory");
+}
+
+// A batch of kU line elements starting at `at` (element stride es): when the line is contiguous
+// (rows; `at` is then a multiple of kU) 32-byte accesses where both buffers of the kernel are
+// 32-byte aligned (wide), else 16-byte ones; strided scalars for the other direction.  A thread of
+// the row solves walks its own row, so a warp's access touches 32 rows: the 32-byte form fetches a
+// whole sector per thread and instruction.
 template <typename IT, bool CONTIG>
-__device__ __forceinline__ void load_batch(const IT* __restrict__ p, int64_t at, int64_t es, double (&v)[8]) {
+__device__ __forceinline__ void load_batch(const IT* __restrict__ p, int64_t at, int64_t es, double (&v)[8],
+                                           bool wide = false) {
   if constexpr (CONTIG && sizeof(IT) == 8) {
+    if (wide) {
+      ld_v4(p + at, v[0], v[1], v[2], v[3]);
+      ld_v4(p + at + 4, v[4], v[5], v[6], v[7]);
+      return;
+    }
 #pragma unroll
     for (int u = 0; u < 8; u += 2) {
       const double2 d = *reinterpret_cast<const double2*>(p + at + u);
@@ -634,8 +651,14 @@ __device__ __forceinline__ void load_batch(const IT* __restrict__ p, int64_t at,
   }
 }
 template <bool CONTIG>
-__device__ __forceinline__ void store_batch(double* __restrict__ p, int64_t at, int64_t es, const double (&v)[8]) {
+__device__ __forceinline__ void store_batch(double* __restrict__ p, int64_t at, int64_t es, const double (&v)[8],
+                                            bool wide = false) {
   if constexpr (CONTIG) {
+    if (wide) {
+      st_v4(p + at, v[0], v[1], v[2], v[3]);
+      st_v4(p + at + 4, v[4], v[5], v[6], v[7]);
+      return;
+    }
 #pragma unroll
     for (int u = 0; u < 8; u += 2) *reinterpret_cast<double2*>(p + at + u) = make_double2(v[u], v[u + 1]);
   } else {
@@ -665,10 +688,13 @@ __global__ void __launch_bounds__(kSolveThreads)
   const double* nu1 = coef + 3 * m;
   const double* nu2 = coef + 4 * m;
   const int64_t base = line * line_stride + static_cast<int64_t>(p) * m * es;
+  // rows: base is a multiple of kU elements (m and the line stride are multiples of 64)
+  const bool wide = CONTIG && sizeof(IT) == 8 &&
+                    ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(G)) & 31u) == 0;
   double y1 = 0.0, y2 = 0.0;
   for (int k0 = 0; k0 < m; k0 += kU) {
     double v[kU];
-    load_batch<IT, CONTIG>(in, base + k0 * es, es, v);
+    load_batch<IT, CONTIG>(in, base + k0 * es, es, v, wide);
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const double y = fma(__ldg(nl1 + k0 + u), y1, fma(__ldg(nl2 + k0 + u), y2, v[u]));
@@ -676,12 +702,12 @@ __global__ void __launch_bounds__(kSolveThreads)
       y2 = y1;
       y1 = y;
     }
-    store_batch<CONTIG>(G, base + k0 * es, es, v);
+    store_batch<CONTIG>(G, base + k0 * es, es, v, wide);
   }
   double g1 = 0.0, g2 = 0.0, g_last = 0.0, g_last2 = 0.0;
   for (int k0 = m - kU; k0 >= 0; k0 -= kU) {
     double v[kU];
-    load_batch<double, CONTIG>(G, base + k0 * es, es, v);
+    load_batch<double, CONTIG>(G, base + k0 * es, es, v, wide);
 #pragma unroll
     for (int u = kU - 1; u >= 0; --u) {
       const int k = k0 + u;
@@ -694,7 +720,7 @@ __global__ void __launch_bounds__(kSolveThreads)
       g_last2 = v[kU - 2];
       g_last = v[kU - 1];
     }
-    store_batch<CONTIG>(G, base + k0 * es, es, v);
+    store_batch<CONTIG>(G, base + k0 * es, es, v, wide);
   }
   // chunk-end values: k = 0, 1 are g1, g2 after the loop; k = m-2, m-1 kept from the first batch
   double* b = bnd + static_cast<int64_t>(p) * 4 * n + line;
@@ -767,9 +793,11 @@ __global__ void __launch_bounds__(kSolveThreads)
   const double* sr0 = coef + 7 * m;
   const double* sr1 = coef + 8 * m;
   const int64_t base = line * line_stride + static_cast<int64_t>(p) * m * es;
+  const bool wide = CONTIG && MODE == 0 &&
+                    ((reinterpret_cast<uintptr_t>(G) | reinterpret_cast<uintptr_t>(w_out)) & 31u) == 0;
   for (int k0 = 0; k0 < m; k0 += kU) {
     double x[kU];
-    load_batch<double, CONTIG>(G, base + k0 * es, es, x);
+    load_batch<double, CONTIG>(G, base + k0 * es, es, x, wide);
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int k = k0 + u;
@@ -777,7 +805,7 @@ __global__ void __launch_bounds__(kSolveThreads)
              fma(-__ldg(sr0 + k), h0, fma(-__ldg(sr1 + k), h1, x[u]))));
     }
     if constexpr (MODE == 0) {
-      store_batch<CONTIG>(w_out, base + k0 * es, es, x);
+      store_batch<CONTIG>(w_out, base + k0 * es, es, x, wide);
     } else {
       // next holds Cbar = 2 C^n - C^{n-1}, written there by this step's right-hand side kernel
       // (FP32 storage: formed in FP32, one rounding of the size of the result's own); C^{n+1} =
