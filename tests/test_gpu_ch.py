@@ -208,3 +208,54 @@ def test_autotune_restores_state_and_keeps_parity(env, storage):
     _, got, _ = r.state()
     r.close()
     check_ch_step(orc, prev, cur, got, n, dt, storage, "after autotune")
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+@pytest.mark.parametrize("boundary", [0, 1])
+@pytest.mark.parametrize("via", ["create", "set_fields"])
+def test_resume_from_checkpoint_is_bit_identical(env, storage, boundary, via):
+    """Checkpoint and resume: a run stopped after 7 steps (C^{n-1} and C^n copied to the host, the
+    plan destroyed or rebound) and resumed from those two fields, on a new plan or on another
+    plan through cs_ch_set_fields, ends bit for bit where the run straight through ends after 20
+    steps, with the same per-step mass and energy; the step count restarts at 0."""
+    cs, torch, orc = env
+    n = 128
+    tdt = torch.float64 if storage == 0 else torch.float32
+    c0 = W.ch_initial(n, seed=31 + boundary)
+    desc = cs.CHDesc(n=n, storage=storage, D=D, gamma=GAMMA, dt=0.1 * 2 * np.pi / n, boundary=boundary)
+
+    def fields(prev, cur):
+        return [torch.from_numpy(np.ascontiguousarray(prev)).to("cuda", tdt),
+                torch.from_numpy(np.ascontiguousarray(cur)).to("cuda", tdt), torch.zeros(n, n, dtype=tdt, device="cuda")]
+
+    def current(plan, f):
+        p, c, s = cs.cs_ch_fields(plan)
+        pick = lambda ptr: [t for t in f if t.data_ptr() == ptr][0].cpu()
+        return pick(p), pick(c), s
+
+    f = fields(c0, c0)
+    straight = cs.cs_ch_create(desc, *f)
+    m_all, e_all = cs.cs_ch_step(straight, 20, invariants=True)
+    _, end_straight, steps = current(straight, f)
+    cs.cs_destroy(straight)
+    assert steps == 20
+
+    g = fields(c0, c0)
+    first = cs.cs_ch_create(desc, *g)
+    m1, e1 = cs.cs_ch_step(first, 7, invariants=True)
+    ck_prev, ck_cur, steps = current(first, g)
+    assert steps == 7
+    h = fields(ck_prev.numpy(), ck_cur.numpy())
+    if via == "create":
+        cs.cs_destroy(first)
+        second = cs.cs_ch_create(desc, *h)
+    else:
+        second = first
+        cs.cs_ch_set_fields(second, *h)
+    assert cs.cs_ch_fields(second)[2] == 0
+    m2, e2 = cs.cs_ch_step(second, 13, invariants=True)
+    _, end_resumed, steps = current(second, h)
+    cs.cs_destroy(second)
+    assert steps == 13
+    assert torch.equal(end_straight, end_resumed)
+    assert np.array_equal(np.concatenate([m1, m2]), m_all) and np.array_equal(np.concatenate([e1, e2]), e_all)
