@@ -345,33 +345,43 @@ constexpr int kW2TX = 128, kW2Cols = kWLA + kW2TX + kWLA, kW2Groups = kWThreads 
 constexpr int kW2Rows = kWTY / kW2Groups;
 
 __device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+// a - b on two lanes as one packed FMA (a packed FMA has no free operand sign)
+__device__ __forceinline__ float2 sub2w(float2 a, float2 b) { return __ffma2_rn(b, f2s(-1.0f), a); }
 
-// weno_scaled<float> on two lanes (w* already scaled by each lane's own 2^(127 - e))
 // The WENO value of two lanes from their differences w1..w5 (unscaled) and max |w| (mw, with
-// 2^-40 <= mw < 2^41), eps = 1e-6 mw^2.  Only the indicator sums t_k = s_k + eps are scaled, by
-// sc2 = 2^(2 (127 - e)) (e the biased exponent of mw), so that the fourth powers in the weights
-// stay in range; phi and the result need no scaling.  Powers of two commute with the roundings,
-// so this gives the bits of scaling the differences themselves by 2^(127 - e).
+// 2^-40 <= mw < 2^41), eps = 1e-6 mw^2, in a form with fewer operations than the textbook one
+// (the same quantities up to rounding):
+//   * with d_k = w_k - w_{k+1}: a_k = d_k - d_{k+1} (the indicators' second differences),
+//     b1 = d1 - 3 d2, b2 = d2 + d3, b3 = 3 d3 - d4;
+//   * the indicators s_k = (13/12) a_k^2 + (1/4) b_k^2 and eps enter only through their ratios,
+//     so S_k = a_k^2 + (3/13) b_k^2 = (12/13) s_k and eps' = (12/13) eps are used;
+//   * only the indicator sums are scaled, by sc2 = 2^(2 (127 - e)) (e the biased exponent of mw),
+//     so that the fourth powers stay in range: t_k = fma(S_k, sc2, eps' sc2) (a power of two
+//     commutes with the roundings);
+//   * with q_k = t_k^2 and the weights g = (0.1, 0.6, 0.3) taken as (1, 6, 3), the value is
+//     phi_2 + (g1 q2 q3 (phi_1 - phi_2) + g3 q1 q2 (phi_3 - phi_2)) / (g1 q2 q3 + g2 q1 q3 + g3 q1 q2),
+//     where phi_1 - phi_2 = (a1 - a2) / 3 and phi_3 - phi_2 = (a2 - a3) / 6 are third differences:
+//     phi_2 + (m1 (a1 - a2) + 1.5 m3 (a2 - a3)) / (3 m1 + 18 m2 + 9 m3), m1 = q2 q3, m2 = q1 q3,
+//     m3 = q1 q2.
 __device__ __forceinline__ float2 weno_scaled2(float2 w1, float2 w2, float2 w3, float2 w4, float2 w5, float2 mw,
                                                float2 sc2) {
-  const float2 phi1 = __ffma2_rn(f2s(1.0f / 3.0f), w1, __ffma2_rn(f2s(-7.0f / 6.0f), w2, __fmul2_rn(f2s(11.0f / 6.0f), w3)));
-  const float2 phi2 = __ffma2_rn(f2s(-1.0f / 6.0f), w2, __ffma2_rn(f2s(5.0f / 6.0f), w3, __fmul2_rn(f2s(1.0f / 3.0f), w4)));
-  const float2 phi3 = __ffma2_rn(f2s(1.0f / 3.0f), w3, __ffma2_rn(f2s(5.0f / 6.0f), w4, __fmul2_rn(f2s(-1.0f / 6.0f), w5)));
-  const float2 a1 = __fadd2_rn(__ffma2_rn(f2s(-2.0f), w2, w1), w3), b1 = __fadd2_rn(__ffma2_rn(f2s(-4.0f), w2, w1), __fmul2_rn(f2s(3.0f), w3));
-  const float2 a2 = __fadd2_rn(__ffma2_rn(f2s(-2.0f), w3, w2), w4), b2 = __ffma2_rn(w4, f2s(-1.0f), w2);
-  const float2 a3 = __fadd2_rn(__ffma2_rn(f2s(-2.0f), w4, w3), w5), b3 = __ffma2_rn(f2s(3.0f), w3, __ffma2_rn(f2s(-4.0f), w4, w5));
-  const float2 s1 = __ffma2_rn(__fmul2_rn(f2s(13.0f / 12.0f), a1), a1, __fmul2_rn(__fmul2_rn(f2s(0.25f), b1), b1));
-  const float2 s2 = __ffma2_rn(__fmul2_rn(f2s(13.0f / 12.0f), a2), a2, __fmul2_rn(__fmul2_rn(f2s(0.25f), b2), b2));
-  const float2 s3 = __ffma2_rn(__fmul2_rn(f2s(13.0f / 12.0f), a3), a3, __fmul2_rn(__fmul2_rn(f2s(0.25f), b3), b3));
-  const float2 eps = __fmul2_rn(f2s(1e-6f), __fmul2_rn(mw, mw));
-  const float2 t1 = __fmul2_rn(__fadd2_rn(s1, eps), sc2), t2 = __fmul2_rn(__fadd2_rn(s2, eps), sc2);
-  const float2 t3 = __fmul2_rn(__fadd2_rn(s3, eps), sc2);
+  const float2 d1 = sub2w(w1, w2), d2 = sub2w(w2, w3), d3 = sub2w(w3, w4), d4n = sub2w(w5, w4);
+  const float2 a1 = sub2w(d1, d2), a2 = sub2w(d2, d3), a3 = __fadd2_rn(d3, d4n);
+  const float2 b1 = __ffma2_rn(f2s(-3.0f), d2, d1), b2 = __fadd2_rn(d2, d3), b3 = __ffma2_rn(f2s(3.0f), d3, d4n);
+  constexpr float k313 = 3.0f / 13.0f;
+  const float2 S1 = __ffma2_rn(a1, a1, __fmul2_rn(__fmul2_rn(f2s(k313), b1), b1));
+  const float2 S2 = __ffma2_rn(a2, a2, __fmul2_rn(__fmul2_rn(f2s(k313), b2), b2));
+  const float2 S3 = __ffma2_rn(a3, a3, __fmul2_rn(__fmul2_rn(f2s(k313), b3), b3));
+  const float2 es = __fmul2_rn(__fmul2_rn(mw, mw), __fmul2_rn(f2s(1e-6f * 12.0f / 13.0f), sc2));
+  const float2 t1 = __ffma2_rn(S1, sc2, es), t2 = __ffma2_rn(S2, sc2, es), t3 = __ffma2_rn(S3, sc2, es);
   const float2 q1 = __fmul2_rn(t1, t1), q2 = __fmul2_rn(t2, t2), q3 = __fmul2_rn(t3, t3);
-  const float2 p1 = __fmul2_rn(f2s(0.1f), __fmul2_rn(q2, q3)), p2 = __fmul2_rn(f2s(0.6f), __fmul2_rn(q1, q3));
-  const float2 p3 = __fmul2_rn(f2s(0.3f), __fmul2_rn(q1, q2));
-  const float2 num = __ffma2_rn(p1, phi1, __ffma2_rn(p2, phi2, __fmul2_rn(p3, phi3)));
-  const float2 den = __fadd2_rn(__fadd2_rn(p1, p2), p3);
-  return make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
+  const float2 m1 = __fmul2_rn(q2, q3), m2 = __fmul2_rn(q1, q3), m3 = __fmul2_rn(q1, q2);
+  const float2 den = __ffma2_rn(f2s(18.0f), m2, __ffma2_rn(f2s(9.0f), m3, __fmul2_rn(f2s(3.0f), m1)));
+  const float2 num = __ffma2_rn(m1, sub2w(a1, a2), __fmul2_rn(m3, __fmul2_rn(f2s(1.5f), sub2w(a2, a3))));
+  const float2 phi2 = __ffma2_rn(f2s(-1.0f / 6.0f), w2, __ffma2_rn(f2s(5.0f / 6.0f), w3, __fmul2_rn(f2s(1.0f / 3.0f), w4)));
+  // the fast division's reciprocal (2 ulp; den lies in [1e-24, 2e9], well inside its range) --
+  // FP32 storage is held to 1e-5
+  return __ffma2_rn(num, make_float2(__fdividef(1.0f, den.x), __fdividef(1.0f, den.y)), phi2);
 }
 
 // Lanes whose max |w| is zero, denormal or outside [2^-40, 2^41): the scalar form, out of line so
