@@ -526,6 +526,19 @@ __device__ __forceinline__ void ixf_q2(int2 a, int2 b, const IxfConsts& k, int2&
 using ixd::ixi_combine;
 using ixd::ixi_consts;
 
+// Compile-time weight ratios of the digit sums (CW = 2): the 5-point pattern of the user function
+// c^3 - c - Lap c, whose ratios the plan always sets to (0, -1, 0, -1, 4, -1, 0, -1, 0); the
+// compiler then forms the sum from adds and one shift instead of an integer multiply-add per tap.
+// Every other stencil takes the plan's ratios (CW = 0).
+template <int CW>
+__device__ __forceinline__ int ix_weight(const IxTaps& taps, int k) {
+  if constexpr (CW == 2) {  // 3 x 3 footprint, k = row * 3 + column
+    return k == 4 ? 4 : (k == 1 || k == 3 || k == 5 || k == 7) ? -1 : 0;
+  } else {
+    return static_cast<int>(taps.n[k]);
+  }
+}
+
 // Digit sums of two adjacent tile columns per thread, "push" form: every staged row adds its
 // contributions to the (up to H) output rows it feeds, held in H rolling accumulators per column
 // and digit; an output row is complete once its last input row has been added.  A row's digits
@@ -535,7 +548,7 @@ using ixd::ixi_consts;
 // FULL: every output of the tile is written and 16-byte stores apply (the launch checked that the
 // grid is periodic, nx a multiple of 64, ny of TY, and out 16-byte aligned); the per-row range and
 // alignment tests are left out.
-template <int TY, int SPEC, bool FULL = false>
+template <int TY, int SPEC, bool FULL = false, int CW = 0>
 __device__ __forceinline__ void ix_compute(const int2* sd2, double* __restrict__ out, int64_t nx,
                                            int64_t ny, int periodic, int64_t x0, int64_t y0,
                                            const IxTaps& taps, const uint32_t (&w)[4], int tile_e) {
@@ -606,7 +619,7 @@ __device__ __forceinline__ void ix_compute(const int2* sd2, double* __restrict__
 #pragma unroll
         for (int p = 0; p < W; ++p)
           if ((sd.mask >> (q * W + p)) & 1u) {
-            const int n = static_cast<int>(taps.n[q * W + p]);
+            const int n = ix_weight<CW>(taps, q * W + p);
             acc0[o % H][j] += n * v[X + j + p].x;
             acc1[o % H][j] += n * v[X + j + p].y;
           }
@@ -652,7 +665,7 @@ constexpr int ix_min_blocks(int spec) {
   return kSpecs[spec].T + kSpecs[spec].B + 1 <= 5 && taps <= 13 ? 6 : 3;
 }
 
-template <int TY, int SPEC, bool FULL>
+template <int TY, int SPEC, bool FULL, int CW = 0>
 __global__ void __launch_bounds__(kThreads, ix_min_blocks(SPEC))
     k_stencil2d_ix(const double* __restrict__ in, double* __restrict__ out, int64_t nx, int64_t ny,
                    int periodic, int vec_ok, Taps<double> taps, IxTaps itaps, int tx0, int ty0, int ring_nbx,
@@ -700,7 +713,7 @@ __global__ void __launch_bounds__(kThreads, ix_min_blocks(SPEC))
   // pass 2: integer digits over the values' own slots
   ixd::ixi_split_tile<kThreads, ROWS * COLS>(s, tile_e);
   __syncthreads();
-  ix_compute<TY, SPEC, FULL>(reinterpret_cast<const int2*>(s), out, nx, ny, periodic, x0, y0, itaps, w, tile_e);
+  ix_compute<TY, SPEC, FULL, CW>(reinterpret_cast<const int2*>(s), out, nx, ny, periodic, x0, y0, itaps, w, tile_e);
 }
 
 // Output rows [row0, row1) of the next launches on this host thread (row0 a multiple of 64, so
@@ -726,8 +739,10 @@ int launch_ix(const double* in, double* out, int64_t nx, int64_t ny, int periodi
   constexpr SpecDesc sd = kSpecs[SPEC];
   constexpr int TX = tile_x<double>();
   const size_t smem = tile_smem_bytes<double>(sd.L, sd.R, sd.T, sd.B, TY, false);
-  auto kfull = k_stencil2d_ix<TY, SPEC, true>;
-  auto kedge = k_stencil2d_ix<TY, SPEC, false>;
+  // the cubic user function's fixed ratios are compiled in (ix_weight)
+  constexpr int CWS = SPEC == 13 ? 2 : 0;
+  auto kfull = k_stencil2d_ix<TY, SPEC, true, CWS>;
+  auto kedge = k_stencil2d_ix<TY, SPEC, false, CWS>;
   static bool attr_set = false;
   if (!attr_set) {
     CS_CUDA_TRY(cudaFuncSetAttribute(kfull, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
