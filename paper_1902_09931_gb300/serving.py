@@ -96,6 +96,10 @@ class Server:
         self.budget = hbm_budget if hbm_budget is not None else backend.default_budget()
         self.group = group
         self.clock = clock
+        if max_inflight < 1:
+            raise ValueError("max_inflight must be at least 1")
+        if max_heavy is not None and max_heavy < 1:
+            raise ValueError("max_heavy must be at least 1, or None for no limit")
         self.max_heavy = max_heavy  # None: no limit
         self.heavy_work = heavy_work
         self.launches = 0

@@ -181,3 +181,9 @@ def test_heavy_limit_keeps_memory_order():
     assert be.peak_resident <= budget
     # job 3 (2048^2 sweep) does not fit beside job 0: job 4 waits behind it
     assert jobs[4].start >= jobs[3].start
+
+
+@pytest.mark.parametrize("kw", [dict(max_heavy=0), dict(max_inflight=0)])
+def test_limits_that_would_stall_the_loop_are_refused(kw):
+    with pytest.raises(ValueError):
+        S.Server(FakeBackend(FakeClock(), 1 << 40), **kw)
