@@ -14,7 +14,9 @@ ranks (Sec. 6.2, MPI).  Here:
 
 Everything here is communication and index bookkeeping: the arithmetic of a band is a callable
 the caller supplies (a device plan of this library on the GPU path).  Point-to-point exchanges use
-``isend`` / ``irecv``, so any backend works (gloo for CPU tensors, NCCL for CUDA tensors).
+``isend`` / ``irecv``, so any backend works (gloo for CPU tensors, NCCL for CUDA tensors).  On the
+device the bands stay in place: DeviceBandStencil and DeviceCHBand keep each band inside a
+persistent padded buffer and receive the neighbours' rows into its halo rows.
 """
 from __future__ import annotations
 
@@ -212,6 +214,101 @@ def exchange_halo_inplace(padded: torch.Tensor, halo: int, group=None, periodic:
         padded[:halo].copy_(top)
     if down is not None:
         padded[rows + halo:].copy_(bottom)
+
+
+def exchange_rows_inplace(padded: torch.Tensor, top: int, bottom: int, group=None, periodic: bool = True) -> None:
+    """The stencil sweep's halo exchange, in place: `padded` holds this rank's band with room for
+    the `top` rows of the band above and the `bottom` rows of the band below (a stencil's reach
+    upwards and downwards).  A non-periodic grid's first band has no room above and its last band
+    none below (its sweep leaves those rows untouched, as the full grid's does); with periodic
+    rows the first band's neighbour above is the last band.  The received rows land in the
+    padded buffer's halo rows, so the band never moves."""
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    has_top = top > 0 and (periodic or rank > 0)
+    has_bottom = bottom > 0 and (periodic or rank < world - 1)
+    t = top if has_top else 0
+    b = bottom if has_bottom else 0
+    rows = padded.shape[0] - t - b
+    if rows < max(top, bottom):
+        raise ValueError(f"band of {rows} rows is thinner than the stencil's reach ({top}, {bottom})")
+    if world == 1:
+        if has_top:
+            padded[:t] = padded[rows:rows + t]
+        if has_bottom:
+            padded[t + rows:] = padded[t:t + b]
+        return
+    up, down = (rank - 1) % world, (rank + 1) % world
+    recv_top = _stage(torch.empty_like(padded[:t]), group) if has_top else None
+    recv_bottom = _stage(torch.empty_like(padded[t + rows:]), group) if has_bottom else None
+    reqs = []
+    if has_top:
+        reqs.append(dist.irecv(recv_top, src=up, group=group, tag=_TAG_TOP))
+    if has_bottom:
+        reqs.append(dist.irecv(recv_bottom, src=down, group=group, tag=_TAG_BOTTOM))
+    # my last `top` rows are the top halo of the band below; my first `bottom` rows the bottom
+    # halo of the band above
+    if top > 0 and (periodic or rank < world - 1):
+        reqs.append(dist.isend(_stage(padded[t + rows - top:t + rows].contiguous(), group), dst=down, group=group,
+                               tag=_TAG_TOP))
+    if bottom > 0 and (periodic or rank > 0):
+        reqs.append(dist.isend(_stage(padded[t:t + bottom].contiguous(), group), dst=up, group=group,
+                               tag=_TAG_BOTTOM))
+    for r in reqs:
+        r.wait()
+    if has_top:
+        padded[:t].copy_(recv_top)
+    if has_bottom:
+        padded[t + rows:].copy_(recv_bottom)
+
+
+class DeviceBandStencil:
+    """A stencil sweep of this rank's row band of an nx-wide grid with no copy of the band: the
+    band lives in the middle of a persistent padded input buffer (`band()` is a view of it: write
+    the band there), the neighbours' rows are received in place into its halo rows
+    (exchange_rows_inplace), one plan of this library is bound to the padded input and output
+    buffers for the object's life, and `__call__` returns the band's rows of the output as a view.
+    `swap()` makes the output the next sweep's input (cs_swap), for repeated sweeps.  `desc_kw` are
+    the StencilDesc fields other than nx and ny (the grid's boundary condition, extents, weights or
+    function, dtype).  The output buffer starts at zero, so cells a non-periodic sweep leaves
+    untouched read 0 until written."""
+
+    def __init__(self, rows: int, nx: int, desc_kw: dict, group=None):
+        from . import StencilDesc, cs_plan_create_2d, CS_BC_PERIODIC, CS_F64
+        self.group = group
+        self._kw = dict(desc_kw)
+        self.T, self.B = int(self._kw.get("top", 0)), int(self._kw.get("bottom", 0))
+        self.periodic = self._kw.get("bc", CS_BC_PERIODIC) == CS_BC_PERIODIC
+        world = dist.get_world_size(group)
+        rank = dist.get_rank(group)
+        self.t = self.T if self.T > 0 and (self.periodic or rank > 0) else 0
+        self.b = self.B if self.B > 0 and (self.periodic or rank < world - 1) else 0
+        self.rows = rows
+        tdt = torch.float64 if self._kw.get("dtype", CS_F64) == CS_F64 else torch.float32
+        self._in = torch.zeros(rows + self.t + self.b, nx, dtype=tdt, device="cuda")
+        self._out = torch.zeros_like(self._in)
+        self.plan = cs_plan_create_2d(StencilDesc(nx=nx, ny=rows + self.t + self.b, **self._kw), self._in, self._out)
+
+    def band(self) -> torch.Tensor:
+        """This rank's band of the input (a view of the padded input buffer)."""
+        return self._in[self.t:self.t + self.rows]
+
+    def __call__(self) -> torch.Tensor:
+        from . import cs_compute
+        exchange_rows_inplace(self._in, self.T, self.B, self.group, self.periodic)
+        cs_compute(self.plan)
+        return self._out[self.t:self.t + self.rows]
+
+    def swap(self) -> None:
+        from . import cs_swap
+        cs_swap(self.plan)
+        self._in, self._out = self._out, self._in
+
+    def close(self) -> None:
+        from . import cs_destroy
+        if self.plan is not None:
+            cs_destroy(self.plan)
+        self.plan = None
 
 
 def transpose_bands_device(local: torch.Tensor, n: int, group=None) -> torch.Tensor:

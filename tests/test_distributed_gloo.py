@@ -224,3 +224,41 @@ def test_halo_exchange_in_place_periodic_and_mirrored(world):
     grid's first and last rows (no-flux), with neighbours' rows between bands."""
     for rank, ok in _run(_halo_worker, world):
         assert ok == {True: True, False: True}, (rank, ok)
+
+
+def _rows_worker(rank, world, port, q):
+    dist = _init(rank, world, port)
+    import torch
+    import oracle
+    from paper_1902_09931_gb300 import distributed as D
+    n, nx = 31, 6
+    A = np.arange(n * nx, dtype=np.float64).reshape(n, nx)
+    r0, r1 = D.band(n, world, rank)
+    ok = []
+    for top, bottom in [(1, 1), (2, 2), (0, 2), (3, 1), (4, 0)]:
+        for periodic in (True, False):
+            t = top if top > 0 and (periodic or rank > 0) else 0
+            b = bottom if bottom > 0 and (periodic or rank < world - 1) else 0
+            padded = torch.full((r1 - r0 + t + b, nx), -1.0, dtype=torch.float64)
+            padded[t:t + r1 - r0] = torch.from_numpy(A[r0:r1])
+            D.exchange_rows_inplace(padded, top, bottom, periodic=periodic)
+            want = A[[(g % n) for g in range(r0 - t, r1 + b)]]
+            good = bool(np.array_equal(padded.numpy(), want))
+            # the sweep of the padded band, restricted to the band, is the full grid's sweep
+            w = np.arange(1, 4 * (top + bottom + 1) + 1, dtype=np.float64)
+            full = oracle.stencil2d(A, w, 2, int(periodic), 1, 2, top, bottom)
+            part = oracle.stencil2d(padded.numpy(), w, 2, int(periodic), 1, 2, top, bottom)
+            good = good and bool(np.array_equal(part[t:t + r1 - r0], full[r0:r1]))
+            ok.append(((top, bottom, periodic), good))
+    q.put((rank, ok))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [1, 2, 3])
+def test_row_exchange_in_place_for_stencil_bands(world):
+    """exchange_rows_inplace fills the `top` rows above and `bottom` rows below each rank's band
+    (asymmetric reaches, none at a non-periodic grid's first and last rows) with the global rows,
+    and the stencil of the padded band restricted to the band equals the full grid's, periodic and
+    non-periodic (whose untouched edge rows then match too)."""
+    for rank, ok in _run(_rows_worker, world):
+        assert all(g for _, g in ok), (rank, [k for k, g in ok if not g])

@@ -141,3 +141,98 @@ def test_device_band_ch_step_two_ranks(env, storage, boundary):
     scale = (2 * np.pi / n) ** 2 * np.abs(c0).sum()
     for r in res:
         assert abs(r[2] - m_ref) <= 1e-14 * scale and abs(r[3] - e_ref) <= 1e-13 * abs(e_ref)
+
+
+BAND_STENCILS = [("lap9", 1, 1, 1, 1, 2), ("biharm13", 2, 2, 2, 2, 2), ("ddy4", 0, 0, 2, 2, 1),
+                 ("asym", 3, 1, 0, 2, 2)]
+
+
+def _band_stencil_run(cs, torch, D, u, rows_of, dtype, bc, name, L, R, T, B, d, sweeps):
+    """This rank's band after `sweeps` sweeps of DeviceBandStencil (swapping between sweeps)."""
+    w = W.integer_weights((L + R + 1) * (T + B + 1), seed=len(name) + 7 * T + L, bound=3)
+    r0, r1 = rows_of
+    s = D.DeviceBandStencil(r1 - r0, u.shape[1], dict(dir=d, bc=bc, left=L, right=R, top=T, bottom=B,
+                                                       weights=w, dtype=dtype))
+    tdt = torch.float64 if dtype == 0 else torch.float32
+    s.band().copy_(torch.from_numpy(u[r0:r1].copy()).to(tdt))
+    for k in range(sweeps):
+        out = s()
+        if k + 1 < sweeps:
+            s.swap()
+    got = out.cpu().numpy().astype(np.float64)
+    s.close()
+    return got, w
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_device_band_stencil_one_rank_bit_exact(env, dtype, bc):
+    """DeviceBandStencil on one rank (the band is the grid, its halo the periodic wrap or nothing):
+    on integer data every sum is exact, so one sweep and two sweeps with swap equal the oracle's bit
+    for bit (non-periodic: cells the sweep leaves untouched read 0 in a first sweep and keep the
+    first sweep's values in the second, as the band's own buffers do)."""
+    cs, torch, orc, D = env
+    ny, nx = 75, 130
+    u = W.integer_field(ny, nx, seed=13, bound=64)
+    for name, L, R, T, B, d in BAND_STENCILS:
+        got1, w = _band_stencil_run(cs, torch, D, u, (0, ny), dtype, bc, name, L, R, T, B, d, 1)
+        ref1 = orc.stencil2d(u, w, d, bc, L, R, T, B)
+        assert np.array_equal(got1, ref1), name
+        got2, _ = _band_stencil_run(cs, torch, D, u, (0, ny), dtype, bc, name, L, R, T, B, d, 2)
+        ref2 = orc.stencil2d(ref1, w, d, bc, L, R, T, B, out=np.zeros_like(u) if bc == 1 else u.copy())
+        assert np.array_equal(got2, ref2), name
+
+
+def _band_stencil_worker(rank, world, port, q):
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    sys.path.insert(0, os.path.join(root, "tests"))
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch
+    import torch.distributed as dist
+    import workloads as W
+    import paper_1902_09931_gb300 as cs
+    from paper_1902_09931_gb300 import distributed as D
+    torch.cuda.set_device(0)
+    cs.load()
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ny, nx = 75, 130
+    u = W.integer_field(ny, nx, seed=13, bound=64)
+    res = {}
+    for dtype in (0, 1):
+        for bc in (0, 1):
+            for name, L, R, T, B, d in BAND_STENCILS:
+                got, _ = _band_stencil_run(cs, torch, D, u, D.band(ny, world, rank), dtype, bc, name, L, R, T, B, d, 1)
+                res[(dtype, bc, name)] = got
+    q.put((rank, res))
+    dist.destroy_process_group()
+
+
+def test_device_band_stencil_two_ranks_bit_exact(env):
+    """Two ranks (two processes sharing this GPU, gloo through host memory) each sweep their band
+    with DeviceBandStencil; on integer data the bands put together equal the oracle's full-grid
+    sweep bit for bit, for every stencil, both boundary conditions and both storage types."""
+    cs, torch, orc, D = env
+    import multiprocessing as mp
+    ny, nx = 75, 130
+    u = W.integer_field(ny, nx, seed=13, bound=64)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    procs = [ctx.Process(target=_band_stencil_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted([q.get(timeout=300) for _ in procs], key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for key in res[0][1]:
+        dtype, bc, name = key
+        L, R, T, B, d = [c for c in BAND_STENCILS if c[0] == name][0][1:]
+        w = W.integer_weights((L + R + 1) * (T + B + 1), seed=len(name) + 7 * T + L, bound=3)
+        ref = orc.stencil2d(u, w, d, bc, L, R, T, B)
+        got = np.concatenate([res[0][1][key], res[1][1][key]])
+        assert np.array_equal(got, ref), key
