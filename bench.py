@@ -986,8 +986,10 @@ def run_reference(args):
 def run_sharded(args):
     """--sharded: one periodic CH grid (n = 4096 by default, FP64) split into row bands over the
     ranks (one GPU each; NCCL, or a single gloo rank on one GPU), stepped with the library's band
-    entry points: halo exchange, band right-hand side, x solves, all-to-all transpose, y solves,
-    transpose back, update (strong scaling: the grid is fixed).  Prints one JSON line."""
+    entry points: halo exchange, band right-hand side, x solves, the y solves by chunks with the
+    chunks' end values all-gathered (or, when the chunks do not split evenly over the ranks,
+    through all-to-all transposes), update (strong scaling: the grid is fixed).  Prints one JSON
+    line."""
     import torch
     import torch.distributed as dist
     import paper_1902_09931_gb300 as cs
@@ -1026,7 +1028,7 @@ def run_sharded(args):
                           "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "strong",
                           "dtype": "f64", "data": "synthetic",
                           "config": {"workload": f"CH-ADI periodic {n}^2, FP64, row bands of {r1 - r0} rows",
-                                     "parallelism": f"row bands x{world}"},
+                                     "parallelism": f"row bands x{world}", "y_lines": b.mode},
                           "mass": mass, "energy": energy}), flush=True)
     dist.destroy_process_group()
 

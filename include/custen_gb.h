@@ -352,6 +352,13 @@ int cs_ch_config(cs_plan_t plan, int32_t* chunks, int32_t* chunk_len);
  * Steps 1, 4 and 6 are the caller's communication (paper_1902_09931_gb300.distributed does them
  * with torch.distributed); the arithmetic is the full-grid step's own kernels, so the decomposed
  * step gives the values cs_ch_step gives.
+ * Without transposes, when every band is a whole number of the y lines' chunks (the spike
+ * method's partition, cs_ch_partition): steps 4-6 become
+ *   4'. cs_ch_band_ycols_local: the chunk-local solves of the band's chunks of every column, and
+ *       their end values (4 per column and chunk);
+ *   5'. an all-gather of the end values of every band, in chunk order (4 * chunks * n values, the
+ *       only data the ranks exchange for the y lines);
+ *   6'. cs_ch_band_ycols_correct: the spike correction of the band's chunks, giving v.
  *
  * cs_ch_band_create: desc as for cs_ch_create (boundary CS_CH_PERIODIC or CS_CH_NOFLUX; the
  *   partition is the one cs_ch_create picks for the same description); rows = the band's row
@@ -375,6 +382,26 @@ int cs_ch_band_rhs(cs_plan_t plan, const void* d_prev, const void* d_cur, double
 int cs_ch_band_solve(cs_plan_t plan, const double* d_in, double* d_out, void* cuda_stream);
 int cs_ch_band_update(cs_plan_t plan, const void* d_prev, const void* d_cur, const double* d_v, void* d_next,
                       void* cuda_stream);
+
+/* The line partition of the ADI step (Sec. 5.1: the line solves, each line cut into *chunks chunks
+ * of *chunk_len points for the partitioned solve) that cs_ch_create and cs_ch_band_create pick for
+ * desc (the autotuner's recorded choice for it, else the default); either output may be NULL.
+ * CS_EINVAL for an invalid description.  Host only. */
+int cs_ch_partition(const cs_ch_desc* desc, int32_t* chunks, int32_t* chunk_len);
+
+/* The y line solves of a band holding chunks chunk0 .. chunk0 + rows / chunk_len - 1 of every
+ * column (rows a whole number of chunks; CS_EINVAL otherwise), in two phases:
+ * cs_ch_band_ycols_local(d_in, d_ends): d_in the band's rows x n FP64 values of w (the x solves'
+ *   result); solves each chunk of each column locally into the plan's scratch and writes the
+ *   chunks' end values to d_ends (device, 4 * (rows / chunk_len) * n FP64, chunk-major).
+ * cs_ch_band_ycols_correct(d_ends_all, d_v): d_ends_all the end values of all chunks of the line,
+ *   in chunk order (every band's d_ends, gathered); writes v (rows x n FP64) for the band's rows,
+ *   which cs_ch_band_update turns into C^{n+1}.  Uses the scratch phase 1 filled: no
+ *   cs_ch_band_solve between the two.
+ * Stream-ordered and asynchronous. */
+int cs_ch_band_ycols_local(cs_plan_t plan, int64_t chunk0, const double* d_in, double* d_ends, void* cuda_stream);
+int cs_ch_band_ycols_correct(cs_plan_t plan, int64_t chunk0, const double* d_ends_all, double* d_v,
+                             void* cuda_stream);
 
 /* Self-check of the line solver (no counterpart in the paper; host code only, no GPU needed):
  * builds the partitioned-solve tables cs_ch_create would build for lines of n points split into

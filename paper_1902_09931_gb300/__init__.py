@@ -124,6 +124,9 @@ _SYMBOLS = {
     "cs_ch_band_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_ch_band_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_ch_band_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "cs_ch_partition": (ctypes.c_int, [ctypes.POINTER(_CCHDesc), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "cs_ch_band_ycols_local": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "cs_ch_band_ycols_correct": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_ch_solver_check": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "cs_batch1d_compute_noalloc": (ctypes.c_int, [ctypes.POINTER(_CStencilDesc), ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cs_last_error": (ctypes.c_char_p, []),
@@ -377,6 +380,24 @@ def cs_ch_band_solve(plan, d_in, d_out, stream=None) -> None:
 
 def cs_ch_band_update(plan, d_prev, d_cur, d_v, d_next, stream=None) -> None:
     _check(load().cs_ch_band_update(plan, _ptr(d_prev), _ptr(d_cur), _ptr(d_v), _ptr(d_next), _stream(stream)))
+
+
+def cs_ch_partition(desc: CHDesc):
+    """(chunks per line, chunk length) that cs_ch_create / cs_ch_band_create pick for desc."""
+    c = _CCHDesc()
+    c.n, c.storage, c.D, c.gamma, c.dt = desc.n, desc.storage, desc.D, desc.gamma, desc.dt
+    c.boundary = desc.boundary
+    k, m = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().cs_ch_partition(ctypes.byref(c), ctypes.byref(k), ctypes.byref(m)))
+    return k.value, m.value
+
+
+def cs_ch_band_ycols_local(plan, chunk0: int, d_in, d_ends, stream=None) -> None:
+    _check(load().cs_ch_band_ycols_local(plan, int(chunk0), _ptr(d_in), _ptr(d_ends), _stream(stream)))
+
+
+def cs_ch_band_ycols_correct(plan, chunk0: int, d_ends_all, d_v, stream=None) -> None:
+    _check(load().cs_ch_band_ycols_correct(plan, int(chunk0), _ptr(d_ends_all), _ptr(d_v), _stream(stream)))
 
 
 def cs_ch_solver_check(n: int, chunks: int, a: float, boundary: int) -> float:

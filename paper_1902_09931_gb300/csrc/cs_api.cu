@@ -833,6 +833,20 @@ int cs_ch_band_update(cs_plan_t p, const void* d_prev, const void* d_cur, const 
   return ch_band_update(p->chb, d_prev, d_cur, d_v, d_next, static_cast<cudaStream_t>(stream));
 }
 
+int cs_ch_partition(const cs_ch_desc* d, int32_t* chunks, int32_t* chunk_len) {
+  return ch_partition(d, chunks, chunk_len);
+}
+
+int cs_ch_band_ycols_local(cs_plan_t p, int64_t chunk0, const double* d_in, double* d_ends, void* stream) {
+  if (!p || p->kind != kCHBand) return set_error(CS_EINVAL, "not a Cahn-Hilliard band plan");
+  return ch_band_ycols_local(p->chb, chunk0, d_in, d_ends, static_cast<cudaStream_t>(stream));
+}
+
+int cs_ch_band_ycols_correct(cs_plan_t p, int64_t chunk0, const double* d_ends_all, double* d_v, void* stream) {
+  if (!p || p->kind != kCHBand) return set_error(CS_EINVAL, "not a Cahn-Hilliard band plan");
+  return ch_band_ycols_correct(p->chb, chunk0, d_ends_all, d_v, static_cast<cudaStream_t>(stream));
+}
+
 int cs_ch_step(cs_plan_t p, int64_t nsteps, double* h_mass, double* h_energy, void* stream) {
   if (!p || p->kind != kCahnHilliard) return set_error(CS_EINVAL, "not a Cahn-Hilliard plan");
   return ch_step(p->ch, nsteps, h_mass, h_energy, static_cast<cudaStream_t>(stream));

@@ -675,11 +675,15 @@ template <typename IT, bool CONTIG, bool NF>
 __global__ void __launch_bounds__(kSolveThreads)
     k_solve_local(const IT* __restrict__ in, double* __restrict__ G, double* __restrict__ bnd,
                   const double* __restrict__ coef, int64_t n, int P, int m, int64_t line_stride,
-                  int64_t elem_stride) {
+                  int64_t elem_stride, int p0 = 0, int Pl = -1) {
+  // chunks p0 .. p0 + Pl - 1 of every line (all P of them by default); the data, G and bnd hold
+  // only those, indexed from the first
+  if (Pl < 0) Pl = P;
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= n * P) return;
+  if (t >= n * Pl) return;
   const int64_t line = t % n;
-  const int p = static_cast<int>(t / n);
+  const int pl = static_cast<int>(t / n);
+  const int p = p0 + pl;
   const int64_t es = CONTIG ? 1 : elem_stride;
   if constexpr (NF) coef += static_cast<int64_t>(chunk_type(p, P)) * 9 * m;
   const double* nl1 = coef;
@@ -687,7 +691,7 @@ __global__ void __launch_bounds__(kSolveThreads)
   const double* dinv = coef + 2 * m;
   const double* nu1 = coef + 3 * m;
   const double* nu2 = coef + 4 * m;
-  const int64_t base = line * line_stride + static_cast<int64_t>(p) * m * es;
+  const int64_t base = line * line_stride + static_cast<int64_t>(pl) * m * es;
   // rows: base is a multiple of kU elements (m and the line stride are multiples of 64)
   const bool wide = CONTIG && sizeof(IT) == 8 &&
                     ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(G)) & 31u) == 0;
@@ -723,7 +727,7 @@ __global__ void __launch_bounds__(kSolveThreads)
     store_batch<CONTIG>(G, base + k0 * es, es, v, wide);
   }
   // chunk-end values: k = 0, 1 are g1, g2 after the loop; k = m-2, m-1 kept from the first batch
-  double* b = bnd + static_cast<int64_t>(p) * 4 * n + line;
+  double* b = bnd + static_cast<int64_t>(pl) * 4 * n + line;
   b[0] = g1;
   b[n] = g2;
   b[2 * n] = g_last2;
@@ -741,16 +745,21 @@ __global__ void __launch_bounds__(kSolveThreads)
     k_solve_correct(const double* __restrict__ G, const double* __restrict__ bnd,
                     const double* __restrict__ coef, const double* __restrict__ K, int64_t n, int P,
                     int m, int64_t line_stride, int64_t elem_stride, double* __restrict__ w_out,
-                    const T* __restrict__ cur, const T* __restrict__ prev, T* __restrict__ next) {
+                    const T* __restrict__ cur, const T* __restrict__ prev, T* __restrict__ next, int p0 = 0,
+                    int Pl = -1) {
+  // chunks p0 .. p0 + Pl - 1 of every line (all P by default): G, w_out and the fields hold only
+  // those, indexed from the first; bnd holds the end values of all P chunks
   extern __shared__ double sK[];
+  if (Pl < 0) Pl = P;
   if constexpr (!NF) {
     for (int i = threadIdx.x; i < 16 * P; i += blockDim.x) sK[i] = K[i];
     __syncthreads();
   }
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= n * P) return;
+  if (t >= n * Pl) return;
   const int64_t line = t % n;
-  const int p = static_cast<int>(t / n);
+  const int pl = static_cast<int>(t / n);
+  const int p = p0 + pl;
   const int64_t es = CONTIG ? 1 : elem_stride;
   double t0 = 0.0, t1 = 0.0, h0 = 0.0, h1 = 0.0;
   if constexpr (NF) {
@@ -792,7 +801,7 @@ __global__ void __launch_bounds__(kSolveThreads)
   const double* sl1 = coef + 6 * m;
   const double* sr0 = coef + 7 * m;
   const double* sr1 = coef + 8 * m;
-  const int64_t base = line * line_stride + static_cast<int64_t>(p) * m * es;
+  const int64_t base = line * line_stride + static_cast<int64_t>(pl) * m * es;
   const bool wide = CONTIG && MODE == 0 &&
                     ((reinterpret_cast<uintptr_t>(G) | reinterpret_cast<uintptr_t>(w_out)) & 31u) == 0;
   for (int k0 = 0; k0 < m; k0 += kU) {
@@ -1700,6 +1709,17 @@ void free_band(CHBand* b) {
 }
 }  // namespace
 
+// The partition (chunks per line) cs_ch_create picks for a description: the autotuner's choice
+// for it when one is recorded, else the default.
+static int band_partition(const cs_ch_desc* d) {
+  int P = default_chunks(d->n), choice;
+  char key[96];
+  snprintf(key, sizeof key, "ch|%s%s|n%lld|sm%d", d->storage == CS_F32 ? "f32" : "f64",
+           d->boundary == CS_CH_NOFLUX ? "|noflux" : "", (long long)d->n, num_sms());
+  if (tune_lookup(key, &choice) && valid_chunks(d->n, choice)) P = choice;
+  return P;
+}
+
 int ch_band_create(CHBand** out, const cs_ch_desc* d, int64_t rows) {
   *out = nullptr;
   if (!d) return set_error(CS_EINVAL, "null Cahn-Hilliard description");
@@ -1720,11 +1740,7 @@ int ch_band_create(CHBand** out, const cs_ch_desc* d, int64_t rows) {
   const double h2 = b->h * b->h;
   b->a = (2.0 / 3.0) * d->D * d->gamma * d->dt / (h2 * h2);
   b->alpha = (2.0 / 3.0) * d->D * d->dt / h2;
-  int P = default_chunks(d->n), choice;
-  char key[96];
-  snprintf(key, sizeof key, "ch|%s%s|n%lld|sm%d", d->storage == CS_F32 ? "f32" : "f64",
-           b->noflux ? "|noflux" : "", (long long)d->n, num_sms());  // the full-grid plan's partition
-  if (tune_lookup(key, &choice) && valid_chunks(d->n, choice)) P = choice;
+  const int P = band_partition(d);  // the full-grid plan's partition
   b->P = P;
   b->m = static_cast<int>(d->n / P);
   b->rhs_blocks = static_cast<int>((d->n / kTX) * (rows / kTY));
@@ -1792,6 +1808,69 @@ int ch_band_solve(CHBand* b, const double* in, double* out, cudaStream_t s) {
   }
   CS_CUDA_TRY(cudaGetLastError());
   count_launches(2);
+  return CS_OK;
+}
+
+int ch_partition(const cs_ch_desc* d, int32_t* chunks, int32_t* chunk_len) {
+  if (!d) return set_error(CS_EINVAL, "null Cahn-Hilliard description");
+  if (d->n < 64 || d->n % 64 != 0 || d->n > 65536) return set_error(CS_EINVAL, "n must be a multiple of 64 in [64, 65536]");
+  if (d->boundary != CS_CH_PERIODIC && d->boundary != CS_CH_NOFLUX)
+    return set_error(CS_EINVAL, "boundary must be CS_CH_PERIODIC or CS_CH_NOFLUX");
+  const int P = band_partition(d);
+  if (chunks) *chunks = P;
+  if (chunk_len) *chunk_len = static_cast<int32_t>(d->n / P);
+  return CS_OK;
+}
+
+// The y lines of a band whose rows are whole chunks of those lines: chunks chunk0 .. chunk0 +
+// rows / m - 1 of every column.  Phase 1 solves each of them locally (the x pass's own kernel with
+// lines = the n columns, line stride 1, element stride n) into the plan's scratch and writes their
+// end values to ends; phase 2, once the caller has gathered every band's end values in chunk order,
+// applies the spike correction and writes v.
+static int band_ycols_check(const CHBand* b, int64_t chunk0) {
+  if (b->rows % b->m != 0)
+    return set_error(CS_EINVAL, "band of %lld rows is not a whole number of %d-row chunks", (long long)b->rows, b->m);
+  if (chunk0 < 0 || chunk0 + b->rows / b->m > b->P)
+    return set_error(CS_EINVAL, "chunks %lld .. %lld outside the %d chunks of a line", (long long)chunk0,
+                     (long long)(chunk0 + b->rows / b->m - 1), b->P);
+  return CS_OK;
+}
+
+int ch_band_ycols_local(CHBand* b, int64_t chunk0, const double* in, double* ends, cudaStream_t s) {
+  if (!in || !ends) return set_error(CS_EINVAL, "null buffer");
+  int rc = band_ycols_check(b, chunk0);
+  if (rc != CS_OK) return rc;
+  const int Pl = static_cast<int>(b->rows / b->m);
+  const unsigned sgrid = static_cast<unsigned>((b->n * Pl + kSolveThreads - 1) / kSolveThreads);
+  if (b->noflux)
+    k_solve_local<double, false, true><<<sgrid, kSolveThreads, 0, s>>>(in, b->B, ends, b->coef, b->n, b->P, b->m, 1,
+                                                                       b->n, static_cast<int>(chunk0), Pl);
+  else
+    k_solve_local<double, false, false><<<sgrid, kSolveThreads, 0, s>>>(in, b->B, ends, b->coef, b->n, b->P, b->m, 1,
+                                                                        b->n, static_cast<int>(chunk0), Pl);
+  CS_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return CS_OK;
+}
+
+int ch_band_ycols_correct(CHBand* b, int64_t chunk0, const double* ends_all, double* v, cudaStream_t s) {
+  if (!ends_all || !v) return set_error(CS_EINVAL, "null buffer");
+  int rc = band_ycols_check(b, chunk0);
+  if (rc != CS_OK) return rc;
+  const int Pl = static_cast<int>(b->rows / b->m);
+  const unsigned sgrid = static_cast<unsigned>((b->n * Pl + kSolveThreads - 1) / kSolveThreads);
+  if (b->noflux) {
+    k_solve_correct<0, double, false, true><<<sgrid, kSolveThreads, 0, s>>>(
+        b->B, ends_all, b->coef, b->K, b->n, b->P, b->m, 1, b->n, v, nullptr, nullptr, nullptr,
+        static_cast<int>(chunk0), Pl);
+  } else {
+    const size_t ksmem = static_cast<size_t>(16) * b->P * sizeof(double);
+    k_solve_correct<0, double, false, false><<<sgrid, kSolveThreads, ksmem, s>>>(
+        b->B, ends_all, b->coef, b->K, b->n, b->P, b->m, 1, b->n, v, nullptr, nullptr, nullptr,
+        static_cast<int>(chunk0), Pl);
+  }
+  CS_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
   return CS_OK;
 }
 

@@ -116,6 +116,9 @@ int ch_band_create(CHBand** out, const cs_ch_desc* d, int64_t rows);
 int ch_band_rhs(CHBand* b, const void* prev, const void* cur, double* rhs, double* sums, cudaStream_t s);
 int ch_band_solve(CHBand* b, const double* in, double* out, cudaStream_t s);
 int ch_band_update(CHBand* b, const void* prev, const void* cur, const double* v, void* next, cudaStream_t s);
+int ch_partition(const cs_ch_desc* d, int32_t* chunks, int32_t* chunk_len);
+int ch_band_ycols_local(CHBand* b, int64_t chunk0, const double* in, double* ends, cudaStream_t s);
+int ch_band_ycols_correct(CHBand* b, int64_t chunk0, const double* ends_all, double* v, cudaStream_t s);
 void ch_band_destroy(CHBand* b);
 
 }  // namespace cs

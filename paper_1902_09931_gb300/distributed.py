@@ -8,9 +8,12 @@ ranks (Sec. 6.2, MPI).  Here:
   ``bottom`` rows below it from its neighbours; with periodic rows the last and first ranks are
   neighbours.  The sweep then runs on the padded band; the halo rows' own outputs are dropped.
 * Cahn-Hilliard ADI (Sec. 5.1): the right-hand side needs a 2-row halo of C^n and C^{n-1}; the
-  x-line solves are local to a row band; the y-line solves run after an all-to-all transpose that
-  gives every rank a band of columns, and a second transpose brings the result back.  Mass and
-  energy are sums of per-rank FP64 partials (an allreduce).
+  x-line solves are local to a row band.  The y lines are cut into the partitioned solver's
+  chunks; when the bands are whole numbers of chunks each rank solves its own chunks and the ranks
+  all-gather only the chunks' end values (4 per column and chunk) for the spike correction;
+  otherwise the y-line solves run after an all-to-all transpose that gives every rank a band of
+  columns, and a second transpose brings the result back.  Mass and energy are sums of per-rank
+  FP64 partials (an allreduce).
 
 Everything here is communication and index bookkeeping: the arithmetic of a band is a callable
 the caller supplies (a device plan of this library on the GPU path).  Point-to-point exchanges use
@@ -321,21 +324,39 @@ def transpose_bands_device(local: torch.Tensor, n: int, group=None) -> torch.Ten
     return transpose_bands(local, n, group)
 
 
+def _all_gather_rows(t: torch.Tensor, group=None) -> torch.Tensor:
+    """The ranks' equal-sized tensors `t` concatenated in rank order (through host memory on gloo)."""
+    world = dist.get_world_size(group)
+    if world == 1:
+        return t
+    src = _stage(t.contiguous(), group)
+    parts = [torch.empty_like(src) for _ in range(world)]
+    dist.all_gather(parts, src, group=group)
+    return torch.cat(parts).to(t.device)
+
+
 class DeviceCHBand:
     """The Cahn-Hilliard ADI step (Sec. 5.1) of an n x n grid split into row bands over the ranks
     of `group`, one band per rank, computed by this library's band entry points (cs_ch_band_*):
     halo exchange of C^n and C^{n-1} (2 rows, in place in padded buffers), the band's right-hand
-    side, the x line solves, an all-to-all transpose, the y line solves, the transpose back and
-    the update.  `c0` is this rank's band of the initial field (rows x n, on the GPU;
-    C^{-1} = C^0).  `boundary` is CS_CH_PERIODIC or CS_CH_NOFLUX (mirrored halos at the grid's
-    first and last rows, non-cyclic line solves).  The three padded fields rotate as in
-    cs_ch_step."""
+    side, the x line solves, the y line solves and the update.  The y lines run in one of two ways:
+      * "chunks" (whenever the spike method's chunks of a line, cs_ch_partition, split evenly over
+        the ranks: then every band is a whole number of chunks of every column): each rank solves
+        its chunks locally (cs_ch_band_ycols_local), the ranks all-gather the chunks' end values (4
+        per column and chunk: 4 * chunks * n values in all), and each applies the spike correction
+        to its own chunks (cs_ch_band_ycols_correct); the field never moves between ranks;
+      * "transposes" (otherwise): an all-to-all transpose gives each rank a band of columns, solved
+        as rows, and a second transpose brings the result back.
+    Both give the full-grid step's values bit for bit.  `c0` is this rank's band of the initial
+    field (rows band(n, world, rank), on the GPU; C^{-1} = C^0).  `boundary` is CS_CH_PERIODIC or
+    CS_CH_NOFLUX (mirrored halos at the grid's first and last rows, non-cyclic line solves).  The
+    three padded fields rotate as in cs_ch_step."""
 
     HALO = 2
 
     def __init__(self, n: int, storage: int, D: float, gamma: float, dt: float, c0: torch.Tensor, group=None,
-                 boundary: int = 0):
-        from . import CHDesc, CS_F64, CS_CH_PERIODIC, cs_ch_band_create
+                 boundary: int = 0, mode: str = "auto"):
+        from . import CHDesc, CS_F64, CS_CH_PERIODIC, cs_ch_band_create, cs_ch_partition
         self.group = group
         self.periodic = boundary == CS_CH_PERIODIC
         self.n = n
@@ -343,6 +364,16 @@ class DeviceCHBand:
         rank = dist.get_rank(group)
         r0, r1 = band(n, world, rank)
         self.rows = r1 - r0
+        desc = CHDesc(n=n, storage=storage, D=D, gamma=gamma, dt=dt, boundary=boundary)
+        chunks, chunk_len = cs_ch_partition(desc)
+        even = chunks % world == 0  # then band(n, world, rank) is a whole number of chunks
+        if mode == "auto":
+            mode = "chunks" if even else "transposes"
+        if mode not in ("chunks", "transposes") or (mode == "chunks" and not even):
+            raise ValueError(f"mode {mode!r}: the {chunks} chunks of a line do not split over {world} ranks"
+                             if mode == "chunks" else f"unknown mode {mode!r}")
+        self.mode = mode
+        self.chunk0 = r0 // chunk_len
         if tuple(c0.shape) != (self.rows, n):
             raise ValueError(f"band of shape {tuple(c0.shape)}, expected {(self.rows, n)}")
         tdt = torch.float64 if storage == CS_F64 else torch.float32
@@ -352,8 +383,9 @@ class DeviceCHBand:
         self.ip, self.ic, self.inext = 0, 1, 2
         self.rhs = torch.empty(self.rows, n, dtype=torch.float64, device=c0.device)
         self.sums = torch.zeros(2, dtype=torch.float64, device=c0.device)
-        self.plan = cs_ch_band_create(CHDesc(n=n, storage=storage, D=D, gamma=gamma, dt=dt, boundary=boundary),
-                                      self.rows)
+        self.ends = torch.empty(4 * (self.rows // chunk_len) * n, dtype=torch.float64, device=c0.device) \
+            if mode == "chunks" else None
+        self.plan = cs_ch_band_create(desc, self.rows)
         self.steps = 0
 
     def _halos(self):
@@ -368,14 +400,22 @@ class DeviceCHBand:
         return tuple(float(v) for v in allreduce_sum(_stage(self.sums, self.group), self.group))
 
     def step(self, nsteps: int = 1) -> None:
-        from . import cs_ch_band_rhs, cs_ch_band_solve, cs_ch_band_update
+        from . import (cs_ch_band_rhs, cs_ch_band_solve, cs_ch_band_update, cs_ch_band_ycols_correct,
+                       cs_ch_band_ycols_local)
         for _ in range(nsteps):
             self._halos()
             cs_ch_band_rhs(self.plan, self.f[self.ip], self.f[self.ic], self.rhs)
             cs_ch_band_solve(self.plan, self.rhs, self.rhs)                   # x lines: the band's rows
-            wt = transpose_bands_device(self.rhs, self.n, self.group)         # a band of columns, as rows
-            cs_ch_band_solve(self.plan, wt, wt)                               # y lines
-            v = transpose_bands_device(wt, self.n, self.group)
+            if self.mode == "chunks":
+                # y lines: the band's chunks of every column, then their end values from all bands
+                cs_ch_band_ycols_local(self.plan, self.chunk0, self.rhs, self.ends)
+                ends_all = _all_gather_rows(self.ends, self.group)
+                cs_ch_band_ycols_correct(self.plan, self.chunk0, ends_all, self.rhs)
+                v = self.rhs
+            else:
+                wt = transpose_bands_device(self.rhs, self.n, self.group)     # a band of columns, as rows
+                cs_ch_band_solve(self.plan, wt, wt)                           # y lines
+                v = transpose_bands_device(wt, self.n, self.group)
             cs_ch_band_update(self.plan, self.f[self.ip], self.f[self.ic], v, self.f[self.inext])
             self.ip, self.ic, self.inext = self.ic, self.inext, self.ip
             self.steps += 1

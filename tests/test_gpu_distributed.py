@@ -58,13 +58,15 @@ def _full_grid_run(cs, torch, c0, storage, dt, steps, boundary=0):
     return out, mass[-1], energy[-1]
 
 
+@pytest.mark.parametrize("mode", ["chunks", "transposes"])
 @pytest.mark.parametrize("boundary", [0, 1])
 @pytest.mark.parametrize("storage", [0, 1])
-def test_device_band_ch_step_equals_full_grid_step(env, storage, boundary):
-    """The decomposed Cahn-Hilliard step (cs_ch_band_* with the halo exchange and the transposes of
-    the distributed module) on one rank gives the full-grid cs_ch_step's fields bit for bit (the
-    same kernels on the same values) and the same invariants, periodic and with no-flux boundaries
-    (mirrored halos, non-cyclic line solves)."""
+def test_device_band_ch_step_equals_full_grid_step(env, storage, boundary, mode):
+    """The decomposed Cahn-Hilliard step (cs_ch_band_* with the halo exchange of the distributed
+    module; the y lines by chunks with their end values gathered, or through transposes) on one
+    rank gives the full-grid cs_ch_step's fields bit for bit (the same kernels on the same values)
+    and the same invariants, periodic and with no-flux boundaries (mirrored halos, non-cyclic line
+    solves)."""
     cs, torch, orc, D = env
     n = 320  # a size no other test autotunes: every process uses the default partition
     dt = 0.1 * 2 * np.pi / n
@@ -73,7 +75,9 @@ def test_device_band_ch_step_equals_full_grid_step(env, storage, boundary):
         c0 = c0.astype(np.float32).astype(np.float64)
     ref, m_ref, e_ref = _full_grid_run(cs, torch, c0, storage, dt, 3, boundary)
     tdt = torch.float64 if storage == 0 else torch.float32
-    b = D.DeviceCHBand(n, storage, 1.0, 0.01, dt, torch.from_numpy(c0).to("cuda", tdt), boundary=boundary)
+    b = D.DeviceCHBand(n, storage, 1.0, 0.01, dt, torch.from_numpy(c0).to("cuda", tdt), boundary=boundary,
+                       mode=mode)
+    assert b.mode == mode
     b.step(3)
     mass, energy = b.invariants()
     got = b.field().clone()
@@ -83,7 +87,7 @@ def test_device_band_ch_step_equals_full_grid_step(env, storage, boundary):
     assert mass == m_ref and energy == e_ref
 
 
-def _band_worker(rank, world, port, storage, boundary, q):
+def _band_worker(rank, world, port, storage, boundary, mode, q):
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     sys.path.insert(0, root)
@@ -102,7 +106,8 @@ def _band_worker(rank, world, port, storage, boundary, q):
     tdt = torch.float64 if storage == 0 else torch.float32
     r0, r1 = D.band(n, world, rank)
     b = D.DeviceCHBand(n, storage, 1.0, 0.01, dt, torch.from_numpy(c0[r0:r1].copy()).to("cuda", tdt),
-                       boundary=boundary)
+                       boundary=boundary, mode=mode)
+    assert b.mode == mode
     b.step(3)
     mass, energy = b.invariants()
     q.put((rank, b.field().cpu().numpy().astype(np.float64), mass, energy))
@@ -110,12 +115,15 @@ def _band_worker(rank, world, port, storage, boundary, q):
     dist.destroy_process_group()
 
 
+@pytest.mark.parametrize("mode", ["chunks", "transposes"])
 @pytest.mark.parametrize("boundary", [0, 1])
 @pytest.mark.parametrize("storage", [0, 1])
-def test_device_band_ch_step_two_ranks(env, storage, boundary):
+def test_device_band_ch_step_two_ranks(env, storage, boundary, mode):
     """Two ranks (two processes sharing this GPU, gloo through host memory; nothing on the device
-    waits for the other rank) each step their 160-row band three times; the bands put together
-    equal the full-grid step bit for bit, and the allreduced invariants agree to rounding."""
+    waits for the other rank) each step their 160-row band (4 of the 8 chunks of every column)
+    three times, the y lines by chunks with the end values all-gathered, or through transposes;
+    the bands put together equal the full-grid step bit for bit, and the allreduced invariants
+    agree to rounding."""
     cs, torch, orc, D = env
     import multiprocessing as mp
     n = 320  # a size no other test autotunes: every process uses the default partition
@@ -129,7 +137,7 @@ def test_device_band_ch_step_two_ranks(env, storage, boundary):
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
         port = s.getsockname()[1]
-    procs = [ctx.Process(target=_band_worker, args=(r, 2, port, storage, boundary, q)) for r in range(2)]
+    procs = [ctx.Process(target=_band_worker, args=(r, 2, port, storage, boundary, mode, q)) for r in range(2)]
     for p in procs:
         p.start()
     res = sorted([q.get(timeout=300) for _ in procs], key=lambda t: t[0])
