@@ -132,3 +132,17 @@ def test_ch_boundary_rejected_on_host(cs):
 def test_wrong_plan_kind_rejected(cs):
     assert rc_of(cs.cs_ch_step, None, 1, False, 0) == cs.CS_EINVAL
     assert rc_of(cs.cs_ch_coarsening, None, 0) == cs.CS_EINVAL
+
+
+def test_ch_partition_on_host(cs):
+    """cs_ch_partition (host only): the line solver's partition for a description covers the line
+    exactly with valid chunks (at least 16 points, whole batches of 8, at most 64 chunks); invalid
+    descriptions are refused."""
+    for n in (64, 320, 1024, 4096, 8192):
+        for boundary in (0, 1):
+            k, m = cs.cs_ch_partition(cs.CHDesc(n=n, storage=0, D=1.0, gamma=0.01, dt=0.01, boundary=boundary))
+            assert k * m == n and 1 <= k <= 64 and m >= 16 and m % 8 == 0, (n, k, m)
+    for bad in (dict(n=100), dict(n=32), dict(n=128, boundary=5)):
+        kw = dict(n=128, storage=0, D=1.0, gamma=0.01, dt=0.01) | bad
+        with pytest.raises(cs.CSError):
+            cs.cs_ch_partition(cs.CHDesc(**kw))
