@@ -66,3 +66,25 @@ def test_served_results_match_oracle(env):
     assert abs(orc.ch_energy(got, 0.01) - ref_e[-1]) <= 1e-5 * abs(ref_e[-1])
     s_ref = orc.ch_coarsening_s(ref_c)
     assert abs(orc.ch_coarsening_s(got) - s_ref) <= 1e-5 * s_ref
+
+
+def test_heavy_jobs_in_the_mix_match_alone(env):
+    """Two heavy jobs (10-step CH advances of 2048^2, run one at a time on default-priority streams)
+    among light ones (on high-priority streams, passing the waiting heavy job): every result is the
+    same as the job's run alone, bit for bit, and the heavy jobs did not overlap."""
+    cs, torch, orc, S = env
+    jobs = [S.Job(0, "ch", 2048, 0.0, seed=501), S.Job(1, "ch", 2048, 0.0, seed=502),
+            S.Job(2, "sweep", 512, 0.0, stencil="lap9", seed=503), S.Job(3, "ch", 256, 0.0, seed=504),
+            S.Job(4, "sweep", 1024, 0.0, stencil="biharm13", seed=505)]
+    be = S.GpuBackend(cs, torch, streams=8)
+    mix = copy.deepcopy(jobs)
+    S.Server(be, max_inflight=8).run(mix)
+    torch.cuda.synchronize()
+    h0, h1 = [m for m in mix if m.jid in (0, 1)]
+    assert h0.heavy and h1.heavy and h1.start >= h0.done
+    for j in jobs:
+        alone = copy.deepcopy(j)
+        S.run_sequential(be, [alone])
+        torch.cuda.synchronize()
+        got = [m for m in mix if m.jid == j.jid][0]
+        assert torch.equal(got.output, alone.output), (j.jid, j.kind, j.n)
