@@ -430,7 +430,8 @@ int cs_ch_solver_check(int64_t n, int32_t chunks, double a, int32_t boundary, do
  *   streams, or host threads) race and must be serialised by the caller.
  *   The offsets are validated on the device first: every call synchronises the stream once,
  *   to read the result of that check back to the host; invalid offsets return CS_EINVAL and
- *   leave d_out untouched. */
+ *   leave d_out untouched.  Because of that read-back no call can be captured into a CUDA
+ *   graph: under stream capture the call returns CS_ECUDA and the capture is invalidated. */
 int cs_batch1d_compute_noalloc(const cs_stencil_desc* desc, int64_t num_lines,
                                const int64_t* d_offsets, int64_t total_len, const void* d_in,
                                void* d_out, void* cuda_stream);
