@@ -262,3 +262,29 @@ def test_row_exchange_in_place_for_stencil_bands(world):
     non-periodic (whose untouched edge rows then match too)."""
     for rank, ok in _run(_rows_worker, world):
         assert all(g for _, g in ok), (rank, [k for k, g in ok if not g])
+
+
+def _gather_worker(rank, world, port, q):
+    dist = _init(rank, world, port)
+    import torch
+    from paper_1902_09931_gb300 import distributed as D
+    chunks, chunk_len, n = 8, 16, 5
+    rows = D.band(chunks * chunk_len, world, rank)
+    c0, c1 = rows[0] // chunk_len, rows[1] // chunk_len
+    # each value names its place in the whole line's chunk-major array: (chunk, end value k, column)
+    mine = torch.tensor([[[c * 100 + k * 10 + j for j in range(n)] for k in range(4)] for c in range(c0, c1)],
+                        dtype=torch.float64).reshape(-1)
+    got = D._all_gather_rows(mine, None)
+    want = torch.tensor([[[c * 100 + k * 10 + j for j in range(n)] for k in range(4)] for c in range(chunks)],
+                        dtype=torch.float64).reshape(-1)
+    q.put((rank, [(rows, bool(torch.equal(got, want)))]))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [1, 2, 4])
+def test_chunk_ends_gather_in_chunk_order(world):
+    """The band CH step's y-line exchange: when the chunks of a line split evenly over the ranks,
+    each rank's band starts at a chunk boundary, and the ranks' chunk-major end values gathered in
+    rank order are the whole line's end values in chunk order."""
+    for rank, ok in _run(_gather_worker, world):
+        assert all(g for _, g in ok), (rank, ok)
