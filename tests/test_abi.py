@@ -146,3 +146,22 @@ def test_ch_partition_on_host(cs):
         kw = dict(n=128, storage=0, D=1.0, gamma=0.01, dt=0.01) | bad
         with pytest.raises(cs.CSError):
             cs.cs_ch_partition(cs.CHDesc(**kw))
+
+
+def test_bands_cover_whole_chunks_when_the_chunks_split_evenly(cs):
+    """The row-band CH step solves its y lines by chunks when a line's chunk count is a multiple of
+    the rank count: then every rank's band (distributed.band) starts and ends on a chunk boundary,
+    which is what cs_ch_band_ycols_local / _correct require of their band."""
+    from paper_1902_09931_gb300.distributed import band
+    seen = 0
+    for n in (64, 256, 320, 1024, 4096, 8192):
+        for boundary in (0, 1):
+            k, m = cs.cs_ch_partition(cs.CHDesc(n=n, storage=0, D=1.0, gamma=0.01, dt=0.01, boundary=boundary))
+            for world in (1, 2, 3, 4, 8):
+                if k % world:
+                    continue
+                seen += 1
+                bands = [band(n, world, r) for r in range(world)]
+                assert all(r0 % m == 0 and (r1 - r0) % m == 0 for r0, r1 in bands), (n, world, k, m)
+                assert bands[0][0] == 0 and bands[-1][1] == n
+    assert seen > 10
